@@ -1,0 +1,571 @@
+/*
+ * FP64 CPU oracle for the Dynamic Cutoff Method's per-timestep path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code with the CUDA implementation.
+ *
+ * Everything is plain, sequential, double precision and written for checking
+ * by eye against the paper (Springer, Ismail, Bientinesi, "A Scalable,
+ * Linear-Time Dynamic Cutoff Algorithm for Molecular Dynamics"):
+ *   - binning into linked cells (Sections 2.1 and 2.3),
+ *   - gray-scale density volume, two-phase segmentation and interface boxes
+ *     (Section 2.1, Eq. 4),
+ *   - cutoff-based fast sweeping (Section 2.2, Algorithm 2.1) plus Jacobi and
+ *     Gauss-Seidel sweeps used as independent checks,
+ *   - trilinear particle-interface distance and cutoff rule (Section 2.2),
+ *   - i-centric Lennard-Jones forces without Newton's third law (Section 2.4,
+ *     Algorithms 2.2 and 2.3), both O(N^2) and over cells,
+ *   - velocity Verlet (Section 2),
+ *   - the adjoint of a loss on forces and energy (extension; see below).
+ * Inputs are FP32 values widened exactly to double by the caller.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Binning (Section 2.1: particles binned into boxes; Section 2.3: linked    */
+/* cells).  Cell of coordinate x is the exact floor(x / l), clamped to       */
+/* [0, n-1].  l has a short mantissa (checked by the caller), so k*l is      */
+/* exact in double and the correction loop makes the floor exact.            */
+/* ------------------------------------------------------------------------ */
+int64_t orc_cell_coord(double x, double l, int64_t n) {
+  double q = floor(x / l);
+  while (q * l > x) q -= 1.0;
+  while ((q + 1.0) * l <= x) q += 1.0;
+  int64_t k = (int64_t)q;
+  if (k < 0) k = 0;
+  if (k > n - 1) k = n - 1;
+  return k;
+}
+
+int64_t orc_cell_of(const double* p, const double* l, const int64_t* nc) {
+  int64_t cx = orc_cell_coord(p[0], l[0], nc[0]);
+  int64_t cy = orc_cell_coord(p[1], l[1], nc[1]);
+  int64_t cz = orc_cell_coord(p[2], l[2], nc[2]);
+  return cx + nc[0] * (cy + nc[1] * cz);
+}
+
+/* Stable counting sort of particles by cell.  cell[i]: cell of input particle
+ * i; count[c]; start[c] = exclusive prefix sum (start[ncell] = n); perm[k]:
+ * input index of the particle in sorted slot k (ties kept in input order). */
+void orc_bin(int64_t n, const double* pos, const double* l, const int64_t* nc, int32_t* cell,
+             int32_t* count, int32_t* start, int32_t* perm) {
+  int64_t ncell = nc[0] * nc[1] * nc[2];
+  for (int64_t c = 0; c < ncell; ++c) count[c] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    cell[i] = (int32_t)orc_cell_of(pos + 3 * i, l, nc);
+    count[cell[i]]++;
+  }
+  int64_t run = 0;
+  for (int64_t c = 0; c < ncell; ++c) {
+    start[c] = (int32_t)run;
+    run += count[c];
+  }
+  start[ncell] = (int32_t)run;
+  int32_t* fill = (int32_t*)calloc((size_t)ncell, sizeof(int32_t));
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cell[i];
+    perm[start[c] + fill[c]] = (int32_t)i;
+    fill[c]++;
+  }
+  free(fill);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interface detection (Section 2.1, Eq. 4).                                 */
+/* ------------------------------------------------------------------------ */
+static int64_t wrap(int64_t k, int64_t n) {
+  k %= n;
+  return k < 0 ? k + n : k;
+}
+
+/* Gray-scale volume: box sum of particle counts over the (2w+1)^3 periodic
+ * neighbourhood of every box (plain definition, one box at a time). */
+void orc_smooth(const int32_t* count, const int64_t* nh, int w, int32_t* g) {
+  for (int64_t z = 0; z < nh[2]; ++z)
+    for (int64_t y = 0; y < nh[1]; ++y)
+      for (int64_t x = 0; x < nh[0]; ++x) {
+        int64_t s = 0;
+        for (int c = -w; c <= w; ++c)
+          for (int b = -w; b <= w; ++b)
+            for (int a = -w; a <= w; ++a)
+              s += count[wrap(x + a, nh[0]) + nh[0] * (wrap(y + b, nh[1]) + nh[1] * wrap(z + c, nh[2]))];
+        g[x + nh[0] * (y + nh[1] * z)] = (int32_t)s;
+      }
+}
+
+/* Two-phase segmentation without the length term: with phase means c0 < c1
+ * fixed, the minimiser of the piecewise-constant two-phase functional is the
+ * threshold at (c0 + c1) / 2; alternating means and threshold is 2-means.
+ * Integer form: s = (g >= T), T = floor(midpoint) + 1.  Returns T; if one
+ * phase is empty the volume has no interface and T = g_max + 1. */
+int64_t orc_two_means(const int32_t* g, int64_t nbox, int max_iter) {
+  int64_t gmin = g[0], gmax = g[0];
+  for (int64_t b = 1; b < nbox; ++b) {
+    if (g[b] < gmin) gmin = g[b];
+    if (g[b] > gmax) gmax = g[b];
+  }
+  int64_t T = (gmin + gmax) / 2;
+  for (int it = 0; it < max_iter; ++it) {
+    int64_t n0 = 0, n1 = 0, s0 = 0, s1 = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+      if (g[b] < T) {
+        n0++;
+        s0 += g[b];
+      } else {
+        n1++;
+        s1 += g[b];
+      }
+    }
+    if (n0 == 0 || n1 == 0) return gmax + 1;
+    int64_t Tn = (s0 * n1 + s1 * n0) / (2 * n0 * n1) + 1;
+    if (Tn == T) break;
+    T = Tn;
+  }
+  return T;
+}
+
+/* Segmented volume S (Eq. 4) and interface boxes: a box is at the interface if
+ * it is in the high-density phase and one of its six face neighbours is not. */
+void orc_segment(const int32_t* g, const int64_t* nh, int64_t T, uint8_t* s, uint8_t* iface) {
+  int64_t nbox = nh[0] * nh[1] * nh[2];
+  for (int64_t b = 0; b < nbox; ++b) s[b] = g[b] >= T ? 1 : 0;
+  for (int64_t z = 0; z < nh[2]; ++z)
+    for (int64_t y = 0; y < nh[1]; ++y)
+      for (int64_t x = 0; x < nh[0]; ++x) {
+        int64_t b = x + nh[0] * (y + nh[1] * z);
+        int f = 0;
+        if (s[b]) {
+          f |= !s[wrap(x - 1, nh[0]) + nh[0] * (y + nh[1] * z)];
+          f |= !s[wrap(x + 1, nh[0]) + nh[0] * (y + nh[1] * z)];
+          f |= !s[x + nh[0] * (wrap(y - 1, nh[1]) + nh[1] * z)];
+          f |= !s[x + nh[0] * (wrap(y + 1, nh[1]) + nh[1] * z)];
+          f |= !s[x + nh[0] * (y + nh[1] * wrap(z - 1, nh[2]))];
+          f |= !s[x + nh[0] * (y + nh[1] * wrap(z + 1, nh[2]))];
+        }
+        iface[b] = (uint8_t)f;
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Box-interface distances (Section 2.2).                                    */
+/* ------------------------------------------------------------------------ */
+/* Local fast-sweeping update of one box (Zhao's Godunov upwind discretisation
+ * of |grad d| = 1 on spacing h): a_k = smaller of the two axis-k neighbours,
+ * sorted a1 <= a2 <= a3; the candidate is the 1-, 2- or 3-neighbour solution,
+ * and the box keeps the smaller of its value and the candidate. */
+static double godunov(const double* D, const int64_t* nh, int64_t x, int64_t y, int64_t z, double h) {
+  double a[3];
+  a[0] = fmin(D[wrap(x - 1, nh[0]) + nh[0] * (y + nh[1] * z)], D[wrap(x + 1, nh[0]) + nh[0] * (y + nh[1] * z)]);
+  a[1] = fmin(D[x + nh[0] * (wrap(y - 1, nh[1]) + nh[1] * z)], D[x + nh[0] * (wrap(y + 1, nh[1]) + nh[1] * z)]);
+  a[2] = fmin(D[x + nh[0] * (y + nh[1] * wrap(z - 1, nh[2]))], D[x + nh[0] * (y + nh[1] * wrap(z + 1, nh[2]))]);
+  /* sort ascending */
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2 - i; ++j)
+      if (a[j] > a[j + 1]) {
+        double t = a[j];
+        a[j] = a[j + 1];
+        a[j + 1] = t;
+      }
+  double d = a[0] + h;
+  if (d > a[1]) {
+    d = 0.5 * (a[0] + a[1] + sqrt(2.0 * h * h - (a[0] - a[1]) * (a[0] - a[1])));
+    if (d > a[2]) {
+      double sa = a[0] + a[1] + a[2];
+      double sq = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+      d = (sa + sqrt(sa * sa - 3.0 * (sq - h * h))) / 3.0;
+    }
+  }
+  double cur = D[x + nh[0] * (y + nh[1] * z)];
+  return d < cur ? d : cur;
+}
+
+/* Initial distances (Algorithm 2.1, initialize): 0 at interface boxes and in
+ * the low-density phase, +inf in the high-density phase. */
+void orc_distance_init(const uint8_t* s, const uint8_t* iface, int64_t nbox, double* D) {
+  for (int64_t b = 0; b < nbox; ++b) D[b] = (!s[b] || iface[b]) ? 0.0 : INFINITY;
+}
+
+/* Cutoff-based fast sweeping, Algorithm 2.1, on one process (no ghost
+ * exchange; periodic neighbours are local).  Q starts with the boxes adjacent
+ * to the interface that have non-zero distance; each pass processes Q
+ * breadth-first, accepts an updated distance only if it is <= r_grid, records
+ * the largest change and queues the six neighbours of every accepted box.
+ * Readings: the local FSM update keeps min(current, candidate); the change
+ * tolerance epsilon tends to 0, i.e. the loop stops after the first pass that
+ * changes no box.  Returns the number of passes, or -1 if iter_max passes did
+ * not converge. */
+int orc_cfsm(const uint8_t* s, const uint8_t* iface, const int64_t* nh, double h, double r_grid,
+             int iter_max, double* D) {
+  int64_t nbox = nh[0] * nh[1] * nh[2];
+  orc_distance_init(s, iface, nbox, D);
+  int64_t* Q = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbox);
+  int64_t* Qn = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbox);
+  uint8_t* inq = (uint8_t*)calloc((size_t)nbox, 1);
+  int64_t nq = 0, nqn = 0;
+  /* initialize(D, Q): boxes with non-zero distance next to a zero-distance box */
+  for (int64_t z = 0; z < nh[2]; ++z)
+    for (int64_t y = 0; y < nh[1]; ++y)
+      for (int64_t x = 0; x < nh[0]; ++x) {
+        int64_t b = x + nh[0] * (y + nh[1] * z);
+        if (D[b] == 0.0) continue;
+        int64_t nb[6] = {wrap(x - 1, nh[0]) + nh[0] * (y + nh[1] * z), wrap(x + 1, nh[0]) + nh[0] * (y + nh[1] * z),
+                         x + nh[0] * (wrap(y - 1, nh[1]) + nh[1] * z), x + nh[0] * (wrap(y + 1, nh[1]) + nh[1] * z),
+                         x + nh[0] * (y + nh[1] * wrap(z - 1, nh[2])), x + nh[0] * (y + nh[1] * wrap(z + 1, nh[2]))};
+        for (int k = 0; k < 6; ++k)
+          if (D[nb[k]] == 0.0 && iface[nb[k]]) {
+            Q[nq++] = b;
+            inq[b] = 1;
+            break;
+          }
+      }
+  int iter = 0, converged = 0;
+  for (iter = 0; iter < iter_max; ++iter) {
+    double de = 0.0;
+    memset(inq, 0, (size_t)nbox);
+    nqn = 0;
+    for (int64_t qi = 0; qi < nq; ++qi) {
+      int64_t b = Q[qi];
+      int64_t x = b % nh[0], y = (b / nh[0]) % nh[1], z = b / (nh[0] * nh[1]);
+      double dn = godunov(D, nh, x, y, z, h);
+      if (dn <= r_grid) {
+        double ch = fabs(D[b] - dn);
+        if (ch > de) de = ch;
+        D[b] = dn;
+        int64_t nb[6] = {wrap(x - 1, nh[0]) + nh[0] * (y + nh[1] * z), wrap(x + 1, nh[0]) + nh[0] * (y + nh[1] * z),
+                         x + nh[0] * (wrap(y - 1, nh[1]) + nh[1] * z), x + nh[0] * (wrap(y + 1, nh[1]) + nh[1] * z),
+                         x + nh[0] * (y + nh[1] * wrap(z - 1, nh[2])), x + nh[0] * (y + nh[1] * wrap(z + 1, nh[2]))};
+        for (int k = 0; k < 6; ++k)
+          if (D[nb[k]] != 0.0 && !inq[nb[k]]) {
+            inq[nb[k]] = 1;
+            Qn[nqn++] = nb[k];
+          }
+      }
+    }
+    /* swapQueues, emptyQueue */
+    int64_t* t = Q;
+    Q = Qn;
+    Qn = t;
+    nq = nqn;
+    if (!(de > 0.0)) {
+      converged = 1;
+      ++iter;
+      break;
+    }
+  }
+  free(Q);
+  free(Qn);
+  free(inq);
+  return converged ? iter : -1;
+}
+
+/* Independent check 1: Jacobi iteration of the same local update over every
+ * box (all boxes read the previous iterate), accepting values <= r_grid,
+ * until no box changes.  Returns the number of sweeps or -1. */
+int orc_distance_jacobi(const uint8_t* s, const uint8_t* iface, const int64_t* nh, double h,
+                        double r_grid, int iter_max, double* D) {
+  int64_t nbox = nh[0] * nh[1] * nh[2];
+  orc_distance_init(s, iface, nbox, D);
+  double* Dn = (double*)malloc(sizeof(double) * (size_t)nbox);
+  int it;
+  for (it = 0; it < iter_max; ++it) {
+    int changed = 0;
+    for (int64_t z = 0; z < nh[2]; ++z)
+      for (int64_t y = 0; y < nh[1]; ++y)
+        for (int64_t x = 0; x < nh[0]; ++x) {
+          int64_t b = x + nh[0] * (y + nh[1] * z);
+          double dn = godunov(D, nh, x, y, z, h);
+          Dn[b] = (dn <= r_grid) ? dn : D[b];
+          if (Dn[b] != D[b]) changed = 1;
+        }
+    memcpy(D, Dn, sizeof(double) * (size_t)nbox);
+    if (!changed) break;
+  }
+  free(Dn);
+  return it < iter_max ? it + 1 : -1;
+}
+
+/* Independent check 2: Gauss-Seidel sweeps in Zhao's eight alternating
+ * orderings (x, y, z each ascending or descending), updated in place. */
+int orc_distance_sweep8(const uint8_t* s, const uint8_t* iface, const int64_t* nh, double h,
+                        double r_grid, int iter_max, double* D) {
+  int64_t nbox = nh[0] * nh[1] * nh[2];
+  orc_distance_init(s, iface, nbox, D);
+  int it;
+  for (it = 0; it < iter_max; ++it) {
+    int changed = 0;
+    for (int o = 0; o < 8; ++o) {
+      int sx = (o & 1) ? -1 : 1, sy = (o & 2) ? -1 : 1, sz = (o & 4) ? -1 : 1;
+      for (int64_t kz = 0; kz < nh[2]; ++kz) {
+        int64_t z = sz > 0 ? kz : nh[2] - 1 - kz;
+        for (int64_t ky = 0; ky < nh[1]; ++ky) {
+          int64_t y = sy > 0 ? ky : nh[1] - 1 - ky;
+          for (int64_t kx = 0; kx < nh[0]; ++kx) {
+            int64_t x = sx > 0 ? kx : nh[0] - 1 - kx;
+            int64_t b = x + nh[0] * (y + nh[1] * z);
+            double dn = godunov(D, nh, x, y, z, h);
+            if (dn <= r_grid && dn != D[b]) {
+              D[b] = dn;
+              changed = 1;
+            }
+          }
+        }
+      }
+    }
+    if (!changed) break;
+  }
+  return it < iter_max ? it + 1 : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cutoff assignment (Section 2.2): particle-interface distance delta_i by   */
+/* trilinear interpolation of min(D, r_grid) between box centres (k + 1/2)h  */
+/* (periodic), then rc = clamp(rc_max - (rc_max - rc_min) delta/ramp).       */
+/* ------------------------------------------------------------------------ */
+double orc_interp_distance(const double* p, const double* D, const int64_t* nh, double h, double r_grid) {
+  int64_t k[3];
+  double t[3];
+  for (int d = 0; d < 3; ++d) {
+    double u = p[d] / h - 0.5;
+    double f = floor(u);
+    /* exact floor of (x - h/2) / h: (f + 1/2) h is exact for short-mantissa h */
+    while ((f + 0.5) * h > p[d]) f -= 1.0;
+    while ((f + 1.5) * h <= p[d]) f += 1.0;
+    k[d] = (int64_t)f;
+    t[d] = (p[d] - (f + 0.5) * h) / h;
+  }
+  double acc = 0.0;
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        int64_t bx = wrap(k[0] + a, nh[0]), by = wrap(k[1] + b, nh[1]), bz = wrap(k[2] + c, nh[2]);
+        double v = D[bx + nh[0] * (by + nh[1] * bz)];
+        if (v > r_grid) v = r_grid;
+        double w = (a ? t[0] : 1.0 - t[0]) * (b ? t[1] : 1.0 - t[1]) * (c ? t[2] : 1.0 - t[2]);
+        acc += w * v;
+      }
+  return acc;
+}
+
+double orc_cutoff_rule(double delta, double rc_min, double rc_max, double ramp) {
+  if (!(ramp > 0.0)) return delta > 0.0 ? rc_min : rc_max; /* step: no ramp */
+  double rc = rc_max - (rc_max - rc_min) * delta / ramp;
+  if (rc < rc_min) rc = rc_min;
+  if (rc > rc_max) rc = rc_max;
+  return rc;
+}
+
+void orc_cutoffs(int64_t n, const double* pos, const double* D, const int64_t* nh, double h,
+                 double r_grid, double rc_min, double rc_max, double ramp, double* delta, double* rc) {
+  for (int64_t i = 0; i < n; ++i) {
+    double di = orc_interp_distance(pos + 3 * i, D, nh, h, r_grid);
+    if (delta) delta[i] = di;
+    rc[i] = orc_cutoff_rule(di, rc_min, rc_max, ramp);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forces (Section 2.4, Algorithms 2.2/2.3).                                 */
+/* Pair rule: j contributes to i iff j != i and |r_ij| < rc[i] (strict), with */
+/* r_ij = r_i - r_j the minimum image.  No Newton's third law: f_j is never  */
+/* updated from i's loop.  Lennard-Jones 12-6 with Lorentz-Berthelot mixing: */
+/* U(r) = 4 eps [(s/r)^12 - (s/r)^6], F_i += 24 eps [2(s/r)^12 - (s/r)^6]/r^2 */
+/* r_ij.  Energy e_i = 1/2 sum_j U (minus U(rc_i) per pair if shifted),     */
+/* virial W = 1/2 sum_i sum_j r_ij . F_ij.                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int ntypes;
+  double eps[16];   /* per type pair a*ntypes+b */
+  double sig2[16];
+} ljtab_t;
+
+static void lj_table(int ntypes, const double* eps, const double* sigma, ljtab_t* t) {
+  t->ntypes = ntypes;
+  for (int a = 0; a < ntypes; ++a)
+    for (int b = 0; b < ntypes; ++b) {
+      double e = sqrt(eps[a] * eps[b]);
+      double s = 0.5 * (sigma[a] + sigma[b]);
+      t->eps[a * ntypes + b] = e;
+      t->sig2[a * ntypes + b] = s * s;
+    }
+}
+
+static double min_image(double d, double L) {
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
+
+static void lj_pair(double r2, double eps, double sig2, double* fscal, double* u) {
+  double s2 = sig2 / r2;
+  double s6 = s2 * s2 * s2;
+  *fscal = 24.0 * eps * (2.0 * s6 * s6 - s6) / r2;
+  *u = 4.0 * eps * (s6 * s6 - s6);
+}
+
+static void accumulate_pair(const double* pi, const double* pj, int ti, int tj, double rci,
+                            const double* L, const ljtab_t* tab, int shift, double* f, double* e,
+                            double* w, int64_t* np) {
+  double dx = min_image(pi[0] - pj[0], L[0]);
+  double dy = min_image(pi[1] - pj[1], L[1]);
+  double dz = min_image(pi[2] - pj[2], L[2]);
+  double r2 = dx * dx + dy * dy + dz * dz;
+  if (!(r2 < rci * rci)) return;
+  int pt = ti * tab->ntypes + tj;
+  double fs, u;
+  lj_pair(r2, tab->eps[pt], tab->sig2[pt], &fs, &u);
+  if (shift) {
+    double fc, uc;
+    lj_pair(rci * rci, tab->eps[pt], tab->sig2[pt], &fc, &uc);
+    u -= uc;
+  }
+  f[0] += fs * dx;
+  f[1] += fs * dy;
+  f[2] += fs * dz;
+  *e += 0.5 * u;
+  *w += 0.5 * fs * r2;
+  *np += 1;
+}
+
+/* O(N^2) reference: every ordered pair (i, j != i).  out[0] = E, out[1] = W;
+ * npairs = number of accepted ordered pairs. */
+void orc_forces_brute(int64_t n, const double* pos, const int32_t* type, const double* rc,
+                      const double* L, int ntypes, const double* eps, const double* sigma, int shift,
+                      double* F, double* e, double* out, int64_t* npairs) {
+  ljtab_t tab;
+  lj_table(ntypes, eps, sigma, &tab);
+  double E = 0.0, W = 0.0;
+  int64_t np = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double f[3] = {0, 0, 0}, ei = 0.0, wi = 0.0;
+    int ti = type ? type[i] : 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      accumulate_pair(pos + 3 * i, pos + 3 * j, ti, type ? type[j] : 0, rc[i], L, &tab, shift, f, &ei, &wi, &np);
+    }
+    F[3 * i] = f[0];
+    F[3 * i + 1] = f[1];
+    F[3 * i + 2] = f[2];
+    if (e) e[i] = ei;
+    E += ei;
+    W += wi;
+  }
+  out[0] = E;
+  out[1] = W;
+  if (npairs) *npairs = np;
+}
+
+/* Cell-list form (Algorithm 2.2's bins and Algorithm 2.3's loop fused): bin
+ * with edge l, then for every i visit all bins within ceil(rc_i / l) bins in
+ * each direction (each bin once, even if the stencil wraps past the box) and
+ * apply the same pair rule.  The i-loop is shared among threads with the
+ * paper's dynamic schedule of 20 particles per task (Section 2.4). */
+void orc_forces_cells(int64_t n, const double* pos, const int32_t* type, const double* rc,
+                      const double* L, const double* l, const int64_t* nc, int ntypes,
+                      const double* eps, const double* sigma, int shift, int nthreads, double* F,
+                      double* e, double* out, int64_t* npairs) {
+  ljtab_t tab;
+  lj_table(ntypes, eps, sigma, &tab);
+  int64_t ncell = nc[0] * nc[1] * nc[2];
+  int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* count = (int32_t*)malloc(sizeof(int32_t) * (size_t)ncell);
+  int32_t* start = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ncell + 1));
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  double* wl = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* el = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  int64_t* pl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  orc_bin(n, pos, l, nc, cell, count, start, perm);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 20)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double f[3] = {0, 0, 0}, ei = 0.0, wi = 0.0;
+    int64_t np = 0;
+    int ti = type ? type[i] : 0;
+    int64_t c = cell[i];
+    int64_t cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+    int64_t H[3], lo[3], cnt[3];
+    int64_t cc[3] = {cx, cy, cz};
+    for (int d = 0; d < 3; ++d) {
+      H[d] = (int64_t)ceil(rc[i] / l[d]);
+      if (2 * H[d] + 1 >= nc[d]) {
+        lo[d] = 0;
+        cnt[d] = nc[d];
+      } else {
+        lo[d] = cc[d] - H[d];
+        cnt[d] = 2 * H[d] + 1;
+      }
+    }
+    for (int64_t a = 0; a < cnt[2]; ++a) {
+      int64_t jz = wrap(lo[2] + a, nc[2]);
+      for (int64_t b = 0; b < cnt[1]; ++b) {
+        int64_t jy = wrap(lo[1] + b, nc[1]);
+        for (int64_t k = 0; k < cnt[0]; ++k) {
+          int64_t jx = wrap(lo[0] + k, nc[0]);
+          int64_t jc = jx + nc[0] * (jy + nc[1] * jz);
+          for (int32_t s = start[jc]; s < start[jc + 1]; ++s) {
+            int64_t j = perm[s];
+            if (j == i) continue;
+            accumulate_pair(pos + 3 * i, pos + 3 * j, ti, type ? type[j] : 0, rc[i], L, &tab, shift, f, &ei, &wi, &np);
+          }
+        }
+      }
+    }
+    F[3 * i] = f[0];
+    F[3 * i + 1] = f[1];
+    F[3 * i + 2] = f[2];
+    el[i] = ei;
+    wl[i] = wi;
+    pl[i] = np;
+  }
+  double E = 0.0, W = 0.0;
+  int64_t np = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (e) e[i] = el[i];
+    E += el[i];
+    W += wl[i];
+    np += pl[i];
+  }
+  out[0] = E;
+  out[1] = W;
+  if (npairs) *npairs = np;
+  free(cell);
+  free(count);
+  free(start);
+  free(perm);
+  free(wl);
+  free(el);
+  free(pl);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Velocity Verlet (Section 2, box 5 of Fig. 3), unit masses.                */
+/* ------------------------------------------------------------------------ */
+void orc_kick(int64_t n, double* vel, const double* F, double half_dt) {
+  for (int64_t k = 0; k < 3 * n; ++k) vel[k] += half_dt * F[k];
+}
+
+/* Drift and wrap into [0, L). */
+void orc_drift(int64_t n, double* pos, const double* vel, double dt, const double* L) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      double x = pos[3 * i + d] + dt * vel[3 * i + d];
+      if (x >= L[d]) x -= L[d];
+      if (x < 0.0) x += L[d];
+      if (x >= L[d]) x = 0.0;
+      pos[3 * i + d] = x;
+    }
+}
+
+double orc_kinetic(int64_t n, const double* vel) {
+  double k = 0.0;
+  for (int64_t i = 0; i < 3 * n; ++i) k += 0.5 * vel[i] * vel[i];
+  return k;
+}
