@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""DCM timestep throughput on GB300: particle-steps/s on the 15.5M-particle slab.
+
+One benchmark "step" is one full recomputation period of the dynamic cutoff
+method: K = 10 velocity-Verlet timesteps, each with binning, forces and both
+half kicks, plus interface detection, fast-sweeping distances and cutoff
+assignment once.  So every stage of the hot path runs in every step, and the
+reported throughput counts N x 10 particle-timesteps per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank steps its own
+independent replica (seed = rank): weak scaling, no data-path collective.
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a column of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DCM step particle-steps/s at N=16M"
+UNIT = "particle-steps/s"
+K_RECOMPUTE = 10
+DT = 0.005
+FLOP_PER_PAIR = 18          # FP32-pipe instructions per accepted pair
+FP32_LANES_PER_SM = 128
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="slab_16m")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ ranks
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, local, backend):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def aggregate(dist, units: float, seconds: float):
+    """Whole-job throughput: units summed over ranks, time = max over ranks."""
+    if dist is None:
+        return units, seconds
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------------- profiles
+def recorded_traffic(workload):
+    """DRAM bytes per force launch from the committed ncu summary, if it was
+    taken on the current force kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1701_05242_gb300", "csrc", "forces.cu")
+    path = os.path.join(ROOT, "profiles", f"forces_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"forces_cu_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------- CPU baseline
+def cpu_sample_spec(workload: str, width: float = 30.0):
+    """The same slab recipe (densities, z-profile, surface-wave amplitude,
+    seed) on a width x width cross-section: a bounded sample the oracle
+    steps in seconds."""
+    from paper_1701_05242_gb300 import synth
+    spec = synth.named(workload)
+    spec.box = (float(width), float(width), float(spec.box[2]))
+    spec.name = f"{workload}_cross_section_{width:g}"
+    return spec
+
+
+def oracle_rate(workload, width, nsteps, warmup, nthreads):
+    """Particle-steps/s of the FP64 oracle on the cross-section sample, with
+    cutoffs recomputed every K_RECOMPUTE steps as in the GPU run."""
+    import oracle as O
+    from paper_1701_05242_gb300 import synth
+    spec = cpu_sample_spec(workload, width)
+    slab = synth.make_slab(spec)
+    p = O.Params(box=slab.box, recompute_every=K_RECOMPUTE)
+    st = O.init_state(slab.pos, slab.vel, p, nthreads=nthreads)
+    for _ in range(warmup):
+        st = O.step(st, DT, p, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        st = O.step(st, DT, p, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return slab.n * nsteps / dt, slab.n, dt, slab.box
+
+
+# ------------------------------------------------------------------ main
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    nthreads = os.cpu_count() or 1
+    width = 30.0
+    # each step is one oracle timestep (the cadence-10 recomputation included)
+    rate, n_s, secs, box = oracle_rate(args.workload, width, args.steps, args.warmup, nthreads)
+    sample = (f"{n_s} particles: the {args.workload} recipe on a {box[0]:g}x{box[1]:g}x{box[2]:g} cross-section, "
+              f"{args.steps} oracle timesteps (cutoffs every {K_RECOMPUTE})")
+    out = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "sample_particles": n_s, "timesteps_per_step": 1},
+           "cpu_baseline": {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, local, "nccl")
+    import paper_1701_05242_gb300.dcm as D
+    from paper_1701_05242_gb300 import synth
+
+    spec = synth.named(args.workload)
+    spec.seed = rank
+    slab = synth.make_slab(spec)
+    n = slab.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    def new_state(prec):
+        p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE)
+        ctx = D.Context(p)
+        real = ctx.real
+        st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real, dev),
+                      D.to_real4(torch.from_numpy(slab.vel), None, real, dev))
+        D.dcm_step_init(ctx, st)
+        return ctx, st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- mixed form: the timed path
+    ctx, st = new_state(D.DCM_PREC_MIXED)
+    for _ in range(args.warmup):
+        D.dcm_step(ctx, st, DT, K_RECOMPUTE)
+    barrier()
+    D.dcm_set_timing(ctx, args.steps * K_RECOMPUTE + 8)
+    D.dcm_launch_count(ctx, reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        D.dcm_step(ctx, st, DT, K_RECOMPUTE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = D.dcm_launch_count(ctx)
+    stages = D.dcm_stage_times(ctx)
+    thermo = st.thermo.cpu().numpy()
+    status = D.dcm_status(ctx)
+    barrier()
+    units = float(n) * args.steps * K_RECOMPUTE
+    tot_units, secs = aggregate(dist, units, ms / 1000.0)
+    value = tot_units / secs
+
+    # roofline of the dominant kernel (forces): FP32-pipe instructions
+    f_ms, f_cnt = stages["forces"]
+    pairs = float(thermo[3])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    fmax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tinstr = sms * FP32_LANES_PER_SM * fmax * 1e6 / 1e12
+    f_avg_s = (f_ms / max(f_cnt, 1)) / 1000.0
+    achieved = pairs * FLOP_PER_PAIR / f_avg_s / 1e12 if f_avg_s > 0 else None
+    roof = {"bound": "alu", "kernel": "k_forces", "achieved": achieved, "peak": peak_tinstr,
+            "unit": "T FP32-instr/s", "frac": (achieved / peak_tinstr) if achieved else None,
+            "traffic": recorded_traffic(args.workload), "avg_launch_ms": f_ms / max(f_cnt, 1),
+            "pairs_per_launch": pairs, "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
+    stage_ms = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
+
+    # ---------------- plain FP64 form on the same GPU (per-step launches)
+    fp64 = None
+    if not args.skip_fp64:
+        del st
+        ctx.close()
+        torch.cuda.empty_cache()
+        c64, s64 = new_state(D.DCM_PREC_FP64)
+        D.dcm_step(c64, s64, DT, K_RECOMPUTE)
+        k64 = max(1, min(2, args.steps))
+        barrier()
+        e0.record(stream)
+        for _ in range(k64):
+            D.dcm_step(c64, s64, DT, K_RECOMPUTE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        u64, t64 = aggregate(dist, float(n) * k64 * K_RECOMPUTE, ms64 / 1000.0)
+        fp64 = {"value": u64 / t64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                "speedup_mixed_over_fp64": value / (u64 / t64)}
+        del s64
+        c64.close()
+        torch.cuda.empty_cache()
+        ctx, st = new_state(D.DCM_PREC_MIXED)
+
+    # ---------------- end to end through the public API with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        pos_h = D.to_real4(torch.from_numpy(slab.pos), None, torch.float32, "cpu").pin_memory()
+        vel_h = D.to_real4(torch.from_numpy(slab.vel), None, torch.float32, "cpu").pin_memory()
+        pos_o = torch.empty_like(pos_h).pin_memory()
+        vel_o = torch.empty_like(vel_h).pin_memory()
+        th_o = torch.empty(4, dtype=torch.float64).pin_memory()
+        ke = max(1, min(5, args.steps))
+
+        def e2e_step():
+            k = st.c.cur
+            st.pos[k].copy_(pos_h, non_blocking=True)
+            st.vel[k].copy_(vel_h, non_blocking=True)
+            D.dcm_step_init(ctx, st)
+            D.dcm_step(ctx, st, DT, K_RECOMPUTE)
+            k = st.c.cur
+            pos_o.copy_(st.pos[k], non_blocking=True)
+            vel_o.copy_(st.vel[k], non_blocking=True)
+            th_o.copy_(st.thermo, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = e0.elapsed_time(e1)
+        ue, te = aggregate(dist, float(n) * ke * K_RECOMPUTE, mse / 1000.0)
+        e2e = {"value": ue / te, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 16,
+               "d2h_bytes_per_step": 2 * n * 16 + 32, "steps": ke,
+               "note": "pinned host state in, dcm_step_init + 10 timesteps, state and thermo out"}
+
+    # ---------------- CPU oracle on the host cores (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        nthreads = os.cpu_count() or 1
+        rate, n_s, secs, box = oracle_rate(args.workload, 30.0, 10, 1, nthreads)
+        cpu = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"{n_s} particles: the {args.workload} recipe on a {box[0]:g}x{box[1]:g}x{box[2]:g} "
+                         f"cross-section, 10 oracle timesteps incl. one cutoff recomputation (cell-list forces "
+                         f"threaded with dynamic(20), other stages single-threaded)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": secs * 1000.0 / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": args.workload, "particles_per_gpu": n, "box": list(slab.box),
+                          "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": 1.5, "dt": DT,
+                          "timesteps_per_step": K_RECOMPUTE, "recompute_every": K_RECOMPUTE,
+                          "precision": "fp32 pair math, fp64 totals", "l2": "inputs larger than L2 (positions 248 MB)",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+               "stage_ms_per_step": stage_ms, "fp64_form": fp64, "device_status": status,
+               "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
+                               "pairs": pairs}}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,266 @@
+/*
+ * dcm.h - C ABI of the GB300 (sm_103a) implementation of the per-timestep hot
+ * path of the Dynamic Cutoff Method (DCM) of Springer, Ismail and Bientinesi,
+ * "A Scalable, Linear-Time Dynamic Cutoff Algorithm for Molecular Dynamics".
+ *
+ * The path of one timestep (Fig. 3 of the paper, boxes 1-5):
+ *   dcm_bin               particles -> cells (Sections 2.1 and 2.3)
+ *   dcm_box_counts        particles -> particle count per density box (Sec. 2.1)
+ *   dcm_detect_interface  counts -> gray-scale volume -> segmented volume S
+ *                         (Eq. 4) -> interface boxes (Section 2.1)
+ *   dcm_distance          S, interface -> box-interface distances D by
+ *                         cutoff-based fast sweeping (Section 2.2, Alg. 2.1)
+ *   dcm_cutoffs           D -> particle-interface distance (trilinear) ->
+ *                         per-particle cutoff rc_i (Section 2.2)
+ *   dcm_forces            i-centric Lennard-Jones force and energy with
+ *                         per-particle cutoffs, no Newton's third law
+ *                         (Section 2.4, Algorithms 2.2 and 2.3)
+ *   dcm_step              velocity Verlet around all of the above (Section 2)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller, unless a
+ *   parameter says "host".  The library never frees them.  The library owns
+ *   only the scratch inside a dcm_ctx (allocated once by dcm_create).
+ * - Every call is asynchronous on the given stream unless documented
+ *   otherwise; a call returns after enqueuing its kernels.  Calls on one
+ *   context must not overlap in time on different streams (they share the
+ *   context's scratch).
+ * - Every call returns DCM_OK (0) or a DCM_ERR_* code; dcm_last_error() gives
+ *   a message for the last failing call on that context.  Kernels never trap:
+ *   device-side failures (capacity, non-convergence) are written to a device
+ *   status word that dcm_status() reads.
+ * - Precision forms (dcm_params.precision):
+ *     DCM_PREC_MIXED: positions/velocities/forces are float4, cutoffs and
+ *       distances float; pair arithmetic in FP32, per-particle sums in FP32,
+ *       energy/virial/kinetic totals reduced in FP64.
+ *     DCM_PREC_FP64:  the same arrays as double4 / double; all arithmetic FP64.
+ *   "real4" below means float4 or double4 accordingly, "real" float or double.
+ * - Positions are real4 {x, y, z, w}: w holds the particle type as a number
+ *   (0, 1, ...; 0 for one-type systems).  Coordinates must lie in [0, L);
+ *   values outside are clamped into the boundary cells by the binning.
+ * - Forces are real4 {fx, fy, fz, e_i}: e_i is the particle's energy (half of
+ *   every accepted pair's U).
+ * - Cell and box indices are linear: c = cx + nx * (cy + ny * cz).
+ */
+#ifndef DCM_H
+#define DCM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream (same object as cudaStream_t; NULL = legacy default stream). */
+typedef struct CUstream_st* dcm_stream_t;
+
+enum dcm_status_code {
+  DCM_OK = 0,
+  DCM_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad parameter */
+  DCM_ERR_BOX = 2,           /* box not a multiple of l or h, rc_max > L/2, bad edge */
+  DCM_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+  DCM_ERR_NOT_CONVERGED = 4, /* fast sweeping did not converge within iter_max */
+  DCM_ERR_CAPACITY = 5,      /* n > n_max, or a density value range beyond the histogram */
+  DCM_ERR_NOMEM = 6          /* scratch allocation failed in dcm_create */
+};
+
+enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };
+
+/* Parameters of one system.  dcm_params_default() fills the defaults used for
+ * the liquid/vapor slabs (reduced LJ units). */
+typedef struct dcm_params {
+  double box[3];          /* periodic box lengths Lx, Ly, Lz */
+  double h;               /* density-box edge (Section 2.1, footnote 2); L/h integer. Default 1.5 */
+  double l;               /* force-cell edge (Section 2.3: l <= rc_min); L/l integer. Default 1.5 */
+  double rc_min;          /* smallest cutoff (Section 2.2). Default 3.0 */
+  double rc_max;          /* largest cutoff, at the interface and in vapor. Default 6.0 */
+  double ramp;            /* distance over which rc falls from rc_max to rc_min; <= 0 -> rc_max - rc_min */
+  double r_grid;          /* CFSM threshold r_c^grid (Alg. 2.1); <= 0 -> ramp + 2 h */
+  int32_t smooth_w;       /* gray-scale box-sum half width (boxes). Default 2 */
+  int32_t threshold;      /* < 0: 2-means threshold; >= 0: fixed threshold T on the box sums */
+  int32_t iter_max;       /* CFSM iteration cap (Alg. 2.1). Default 1000 */
+  int32_t ntypes;         /* 1..4 particle types */
+  double eps[4];          /* per-type LJ epsilon (Lorentz-Berthelot: sqrt(eps_a eps_b)) */
+  double sigma[4];        /* per-type LJ sigma   (Lorentz-Berthelot: (sigma_a + sigma_b)/2) */
+  int32_t shift_energy;   /* 1: pair energy U(r) - U(rc_i); forces unchanged. Default 0 */
+  int32_t precision;      /* DCM_PREC_MIXED (default) or DCM_PREC_FP64 */
+  int32_t recompute_every;/* K: interface, distances and cutoffs every K steps. Default 10 */
+  int32_t reserved;
+  int64_t n_max;          /* largest particle count any call on this context will pass */
+} dcm_params;
+
+typedef struct dcm_ctx dcm_ctx;
+
+/* Particle state for dcm_step.  Each array has two buffers; the step reads
+ * buffer `cur`, writes the cell-sorted particles into buffer 1-cur and flips
+ * `cur`.  pos/vel/force are real4[n]; rc is real[n] (the particle's cutoff,
+ * which travels with it between recomputations); id is int32[n] (any payload
+ * that travels with the particle, e.g. its original index).  thermo is
+ * double[4] on the device: {E, W, KE, accepted pairs} after the last step.
+ * t counts timesteps since dcm_step_init (recomputation when t % K == 0). */
+typedef struct dcm_state {
+  void* pos[2];
+  void* vel[2];
+  void* rc[2];
+  int32_t* id[2];
+  void* force;
+  double* thermo;
+  int32_t cur;
+  int32_t reserved;
+  int64_t t;
+} dcm_state;
+
+/* ---- host-only helpers (no GPU needed) -------------------------------- */
+
+/* Fill *p with defaults (box left at 0). Returns DCM_OK or DCM_ERR_INVALID_ARG. */
+int dcm_params_default(dcm_params* p);
+
+/* Check *p without touching the GPU.  Rules: box > 0; h and l have at most 8
+ * significant bits (so k*l is exact in FP32) and divide every box length
+ * into fewer than 65536 cells; 0 < rc_min <= rc_max <= min(L)/2 (so at most
+ * one periodic image of a particle lies within any cutoff); 1 <= ntypes <= 4;
+ * eps, sigma > 0; smooth_w >= 0; 1 <= iter_max <= 100000; recompute_every
+ * >= 1; 0 <= n_max < 2^31.
+ * On failure writes a message to msg (if msg_len > 0) and returns
+ * DCM_ERR_BOX or DCM_ERR_INVALID_ARG. */
+int dcm_validate_params(const dcm_params* p, char* msg, int32_t msg_len);
+
+/* Grid shapes for a parameter set: cells3 = force cells per dimension (L/l),
+ * boxes3 = density boxes per dimension (L/h).  Host-only. */
+int dcm_grid_dims(const dcm_params* p, int64_t* cells3, int64_t* boxes3);
+
+/* Bytes of device scratch dcm_create allocates for *p (host-only). */
+int dcm_scratch_bytes(const dcm_params* p, int64_t* bytes);
+
+/* Library version string (host-only). */
+const char* dcm_version(void);
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Validate *p, then allocate the context and its device scratch on the
+ * current CUDA device (synchronous).  *out receives the context. */
+int dcm_create(const dcm_params* p, dcm_ctx** out);
+
+/* Free the context and its scratch (synchronous).  NULL is a no-op. */
+void dcm_destroy(dcm_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none). */
+const char* dcm_last_error(const dcm_ctx* ctx);
+
+/* Synchronise `stream`, read and clear the device status word of ctx.
+ * Returns DCM_OK or the first device-side error recorded since the last call
+ * (DCM_ERR_NOT_CONVERGED, DCM_ERR_CAPACITY). */
+int dcm_status(dcm_ctx* ctx, dcm_stream_t stream);
+
+/* ---- the hot path ------------------------------------------------------ */
+
+/* Binning, Sections 2.1 and 2.3.  Cell of particle i: cx = floor(x_i / l)
+ * computed exactly (clamped to [0, nx-1]), same for y and z.  Stable counting
+ * sort: particles of one cell keep their input order.
+ *   pos        real4[n]       input positions (any order)
+ *   cell       int32[n]       out: cell of input particle i
+ *   cell_start int32[ncell+1] out: first sorted slot of each cell; cell_start[ncell] = n
+ *   perm       int32[n]       out: input index of the particle in sorted slot k
+ *   pos_sorted real4[n]       out (nullable): pos[perm[k]]
+ * n <= n_max, else DCM_ERR_CAPACITY. */
+int dcm_bin(dcm_ctx* ctx, int64_t n, const void* pos, int32_t* cell, int32_t* cell_start,
+            int32_t* perm, void* pos_sorted, dcm_stream_t stream);
+
+/* Particle count per density box of edge h (the gray-scale volume's input,
+ * Section 2.1).  box_count int32[nboxes] is overwritten. */
+int dcm_box_counts(dcm_ctx* ctx, int64_t n, const void* pos, int32_t* box_count, dcm_stream_t stream);
+
+/* Interface detection, Section 2.1 and Eq. 4.  g = box sum of box_count over
+ * the (2w+1)^3 periodic neighbourhood; T = integer 2-means threshold of g (or
+ * the fixed params.threshold); s = (g >= T); iface = s AND some face
+ * neighbour has s = 0.  If one phase is empty, T = max(g) + 1 (no interface).
+ *   box_count int32[nboxes] in;  s, iface uint8[nboxes] out;
+ *   threshold int32[1] out (device);  g int32[nboxes] out (nullable). */
+int dcm_detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t* iface,
+                         int32_t* threshold, int32_t* g, dcm_stream_t stream);
+
+/* Box-interface distances, Section 2.2 and Algorithm 2.1.  D = 0 on boxes
+ * with s = 0 or iface = 1, +inf elsewhere; then Godunov fast-sweeping updates
+ * d = min(d, solve(neighbours)) accepted only if <= r_grid, iterated (Jacobi)
+ * until no box changes.  Boxes farther than r_grid stay +inf.
+ *   D real[nboxes] out;  iters int32[1] out (device, nullable): sweeps used.
+ * SYNCHRONOUS: returns DCM_ERR_NOT_CONVERGED if iter_max sweeps did not
+ * converge (D then holds the last iterate). */
+int dcm_distance(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,
+                 dcm_stream_t stream);
+
+/* Per-particle cutoffs, Section 2.2.  delta_i = trilinear interpolation of
+ * min(D, r_grid) between box centres (k + 1/2) h (periodic);
+ * rc_i = clamp(rc_max - (rc_max - rc_min) delta_i / ramp, rc_min, rc_max).
+ *   pos real4[n] in; D real[nboxes] in; rc real[n] out. */
+int dcm_cutoffs(dcm_ctx* ctx, int64_t n, const void* pos, const void* D, void* rc,
+                dcm_stream_t stream);
+
+/* Forces, Section 2.4 and Algorithms 2.2/2.3.  For every particle i:
+ *   F_i = sum over j != i with |r_ij| < rc_i (strict; minimum image) of
+ *         24 eps_ij [2 (s_ij/r)^12 - (s_ij/r)^6] / r^2 * r_ij,
+ *   e_i = 1/2 sum of the same pairs' U = 4 eps_ij [(s_ij/r)^12 - (s_ij/r)^6]
+ *         (minus U(rc_i) per pair if shift_energy);
+ * no Newton's third law (j's force is not touched from i's loop).
+ *   pos_sorted real4[n]     positions sorted by cell (dcm_bin's pos_sorted)
+ *   rc         real[n]      cutoff of sorted particle k (values outside
+ *                           [0, rc_max], and NaN, are clamped into it)
+ *   cell_start int32[ncell+1] from dcm_bin
+ *   force      real4[n] out {fx, fy, fz, e_i}
+ *   totals     double[3] out (device, nullable): {E, W, accepted pairs}, with
+ *              W = 1/2 sum_i sum_j r_ij . F_ij. */
+int dcm_forces(dcm_ctx* ctx, int64_t n, const void* pos_sorted, const void* rc,
+               const int32_t* cell_start, void* force, double* totals, dcm_stream_t stream);
+
+/* Initial evaluation before the first step: bin (state reordered into buffer
+ * 1-cur), interface, distances, cutoffs and forces for the current positions;
+ * sets t = 0 and thermo.  Synchronous only if distance sweeps need a host
+ * check (see dcm_step). */
+int dcm_step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, dcm_stream_t stream);
+
+/* nsteps velocity-Verlet timesteps (Section 2; Fig. 3 boxes 1-5):
+ *   v += dt/2 F;  x += dt v (wrapped);  bin;
+ *   if t % K == 0: box counts, interface, distances, cutoffs;
+ *   forces;  v += dt/2 F;  thermo = {E, W, KE, pairs}.
+ * Masses are 1.  The distance sweeps run a fixed budget of iterations with a
+ * device-side convergence flag, so the call never waits on the host;
+ * non-convergence is reported by dcm_status(). */
+int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, dcm_stream_t stream);
+
+/* ---- instrumentation -------------------------------------------------- */
+
+/* Stages of dcm_step whose GPU time can be measured. */
+enum dcm_stage {
+  DCM_STAGE_KICK_DRIFT = 0, /* half kick, drift, cell count */
+  DCM_STAGE_BIN = 1,        /* scan, scatter, per-cell sort, gather of the state */
+  DCM_STAGE_DETECT = 2,     /* dcm_detect_interface */
+  DCM_STAGE_DISTANCE = 3,   /* dcm_distance sweeps */
+  DCM_STAGE_CUTOFFS = 4,    /* dcm_cutoffs */
+  DCM_STAGE_FORCES = 5,     /* dcm_forces kernel (without the final reduction) */
+  DCM_STAGE_KICK = 6,       /* second half kick and kinetic energy */
+  DCM_NSTAGES = 7
+};
+
+/* capacity > 0: every later stage run on ctx records a CUDA event pair on the
+ * launching stream around the stage, for up to `capacity` runs per stage
+ * between two dcm_stage_times calls (events are created here, which
+ * synchronises the device when the table grows); capacity = 0 turns timing
+ * off (the default after dcm_create).  Clears the record. */
+int dcm_set_timing(dcm_ctx* ctx, int32_t capacity);
+
+/* SYNCHRONOUS (device-wide): ms[s] receives the summed GPU time of stage s
+ * over the event pairs recorded since the last call and count[s] how many
+ * stage runs there were (either pointer may be NULL); the record is then
+ * cleared.  Returns DCM_ERR_CAPACITY if more runs than the capacity happened
+ * (ms then covers the first `capacity` runs only). */
+int dcm_stage_times(dcm_ctx* ctx, double* ms, int64_t* count);
+
+/* Number of CUDA kernels this context has launched; reset if reset != 0. */
+int dcm_launch_count(dcm_ctx* ctx, int64_t* count, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DCM_H */

@@ -77,6 +77,8 @@ def _load():
                                             _f64p, _f64p, _f64p, _i64p]),
                 "orc_forces_cells": (None, [I64, _f64p, _i32p, _f64p, _f64p, _f64p, _i64p, I32, _f64p,
                                             _f64p, I32, I32, _f64p, _f64p, _f64p, _i64p]),
+                "orc_forces_subset": (None, [I64, _f64p, _i32p, _f64p, _f64p, _f64p, _i64p, I32, _f64p, _f64p,
+                                             I32, I64, _i64p, I32, _f64p, _f64p, _f64p, _i64p]),
                 "orc_kick": (None, [I64, _f64p, _f64p, D]),
                 "orc_drift": (None, [I64, _f64p, _f64p, D, _f64p]),
                 "orc_kinetic": (D, [I64, _f64p]),
@@ -276,6 +278,28 @@ def forces_cells(pos, rc, box, l, types=None, eps=(1.0,), sigma=(1.0,), shift=Fa
                              _p(eps, _f64p), _p(sigma, _f64p), int(shift), int(nthreads),
                              _p(F, _f64p), _p(e, _f64p), _p(out, _f64p), ctypes.byref(npairs))
     return ForceResult(F[:n], e[:n], float(out[0]), float(out[1]), int(npairs.value))
+
+
+def forces_subset(pos, rc, box, l, idx, types=None, eps=(1.0,), sigma=(1.0,), shift=False, nthreads: int = 1):
+    """Cell-list forces of the particles idx only: (F[m,3], e[m], w[m], npairs[m]),
+    with e and w each particle's half-pair energy and virial sums."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    rc = _f64(np.broadcast_to(rc, (n,)))
+    eps, sigma = _lj_arrays(eps, sigma)
+    nc = grid_dims(box, l)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    m = idx.size
+    t = None if types is None else np.ascontiguousarray(types, dtype=np.int32)
+    F = np.empty((max(m, 1), 3))
+    e = np.empty(max(m, 1))
+    w = np.empty(max(m, 1))
+    npairs = np.empty(max(m, 1), np.int64)
+    _load().orc_forces_subset(n, _p(pos, _f64p), None if t is None else _p(t, _i32p), _p(rc, _f64p),
+                              _p(_vec3(box), _f64p), _p(_vec3(l), _f64p), _p(nc, _i64p), eps.size, _p(eps, _f64p),
+                              _p(sigma, _f64p), int(shift), m, _p(idx, _i64p), int(nthreads), _p(F, _f64p),
+                              _p(e, _f64p), _p(w, _f64p), _p(npairs, _i64p))
+    return F[:m], e[:m], w[:m], npairs[:m]
 
 
 def lj_pair(r, eps=1.0, sigma=1.0):

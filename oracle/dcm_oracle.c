@@ -35,9 +35,11 @@
 /* exact in double and the correction loop makes the floor exact.            */
 /* ------------------------------------------------------------------------ */
 int64_t orc_cell_coord(double x, double l, int64_t n) {
+  if (!(x >= 0.0)) return 0;               /* negative or NaN: first cell */
+  if (!(x < (double)n * l)) return n - 1;  /* beyond the box or +inf: last cell */
   double q = floor(x / l);
-  while (q * l > x) q -= 1.0;
-  while ((q + 1.0) * l <= x) q += 1.0;
+  if (q * l > x) q -= 1.0;                 /* x / l is within one unit of the quotient */
+  else if ((q + 1.0) * l <= x) q += 1.0;
   int64_t k = (int64_t)q;
   if (k < 0) k = 0;
   if (k > n - 1) k = n - 1;
@@ -333,10 +335,10 @@ double orc_interp_distance(const double* p, const double* D, const int64_t* nh, 
   double t[3];
   for (int d = 0; d < 3; ++d) {
     double u = p[d] / h - 0.5;
-    double f = floor(u);
+    double f = isfinite(u) ? floor(u) : 0.0;
     /* exact floor of (x - h/2) / h: (f + 1/2) h is exact for short-mantissa h */
-    while ((f + 0.5) * h > p[d]) f -= 1.0;
-    while ((f + 1.5) * h <= p[d]) f += 1.0;
+    if ((f + 0.5) * h > p[d]) f -= 1.0;
+    else if ((f + 1.5) * h <= p[d]) f += 1.0;
     k[d] = (int64_t)f;
     t[d] = (p[d] - (f + 0.5) * h) / h;
   }
@@ -461,6 +463,78 @@ void orc_forces_brute(int64_t n, const double* pos, const int32_t* type, const d
   if (npairs) *npairs = np;
 }
 
+/* Forces of one particle i over the bins around it (shared by the two
+ * cell-list entry points below). */
+static void cells_one(int64_t i, const double* pos, const int32_t* type, const double* rc, const double* L,
+                      const double* l, const int64_t* nc, const ljtab_t* tab, int shift, const int32_t* cell,
+                      const int32_t* start, const int32_t* perm, double* f, double* ei, double* wi, int64_t* np) {
+  int ti = type ? type[i] : 0;
+  int64_t c = cell[i];
+  int64_t cc[3] = {c % nc[0], (c / nc[0]) % nc[1], c / (nc[0] * nc[1])};
+  int64_t lo[3], cnt[3];
+  for (int d = 0; d < 3; ++d) {
+    int64_t H = (int64_t)ceil(rc[i] / l[d]);
+    if (2 * H + 1 >= nc[d]) {
+      lo[d] = 0;
+      cnt[d] = nc[d];
+    } else {
+      lo[d] = cc[d] - H;
+      cnt[d] = 2 * H + 1;
+    }
+  }
+  for (int64_t a = 0; a < cnt[2]; ++a) {
+    int64_t jz = wrap(lo[2] + a, nc[2]);
+    for (int64_t b = 0; b < cnt[1]; ++b) {
+      int64_t jy = wrap(lo[1] + b, nc[1]);
+      for (int64_t k = 0; k < cnt[0]; ++k) {
+        int64_t jx = wrap(lo[0] + k, nc[0]);
+        int64_t jc = jx + nc[0] * (jy + nc[1] * jz);
+        for (int32_t s = start[jc]; s < start[jc + 1]; ++s) {
+          int64_t j = perm[s];
+          if (j == i) continue;
+          accumulate_pair(pos + 3 * i, pos + 3 * j, ti, type ? type[j] : 0, rc[i], L, tab, shift, f, ei, wi, np);
+        }
+      }
+    }
+  }
+}
+
+/* Forces, energies, virials and accepted-pair counts of the m particles
+ * idx[0..m) only (the full system is binned); used to check large systems on
+ * a sample of particles. */
+void orc_forces_subset(int64_t n, const double* pos, const int32_t* type, const double* rc, const double* L,
+                       const double* l, const int64_t* nc, int ntypes, const double* eps, const double* sigma,
+                       int shift, int64_t m, const int64_t* idx, int nthreads, double* F, double* e, double* w,
+                       int64_t* np) {
+  ljtab_t tab;
+  lj_table(ntypes, eps, sigma, &tab);
+  int64_t ncell = nc[0] * nc[1] * nc[2];
+  int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* count = (int32_t*)malloc(sizeof(int32_t) * (size_t)ncell);
+  int32_t* start = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ncell + 1));
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  orc_bin(n, pos, l, nc, cell, count, start, perm);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 20)
+#endif
+  for (int64_t k = 0; k < m; ++k) {
+    double f[3] = {0, 0, 0}, ei = 0.0, wi = 0.0;
+    int64_t p = 0;
+    cells_one(idx[k], pos, type, rc, L, l, nc, &tab, shift, cell, start, perm, f, &ei, &wi, &p);
+    F[3 * k] = f[0];
+    F[3 * k + 1] = f[1];
+    F[3 * k + 2] = f[2];
+    e[k] = ei;
+    w[k] = wi;
+    np[k] = p;
+  }
+  free(cell);
+  free(count);
+  free(start);
+  free(perm);
+}
+
 /* Cell-list form (Algorithm 2.2's bins and Algorithm 2.3's loop fused): bin
  * with edge l, then for every i visit all bins within ceil(rc_i / l) bins in
  * each direction (each bin once, even if the stencil wraps past the box) and
@@ -488,36 +562,7 @@ void orc_forces_cells(int64_t n, const double* pos, const int32_t* type, const d
   for (int64_t i = 0; i < n; ++i) {
     double f[3] = {0, 0, 0}, ei = 0.0, wi = 0.0;
     int64_t np = 0;
-    int ti = type ? type[i] : 0;
-    int64_t c = cell[i];
-    int64_t cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
-    int64_t H[3], lo[3], cnt[3];
-    int64_t cc[3] = {cx, cy, cz};
-    for (int d = 0; d < 3; ++d) {
-      H[d] = (int64_t)ceil(rc[i] / l[d]);
-      if (2 * H[d] + 1 >= nc[d]) {
-        lo[d] = 0;
-        cnt[d] = nc[d];
-      } else {
-        lo[d] = cc[d] - H[d];
-        cnt[d] = 2 * H[d] + 1;
-      }
-    }
-    for (int64_t a = 0; a < cnt[2]; ++a) {
-      int64_t jz = wrap(lo[2] + a, nc[2]);
-      for (int64_t b = 0; b < cnt[1]; ++b) {
-        int64_t jy = wrap(lo[1] + b, nc[1]);
-        for (int64_t k = 0; k < cnt[0]; ++k) {
-          int64_t jx = wrap(lo[0] + k, nc[0]);
-          int64_t jc = jx + nc[0] * (jy + nc[1] * jz);
-          for (int32_t s = start[jc]; s < start[jc + 1]; ++s) {
-            int64_t j = perm[s];
-            if (j == i) continue;
-            accumulate_pair(pos + 3 * i, pos + 3 * j, ti, type ? type[j] : 0, rc[i], L, &tab, shift, f, &ei, &wi, &np);
-          }
-        }
-      }
-    }
+    cells_one(i, pos, type, rc, L, l, nc, &tab, shift, cell, start, perm, f, &ei, &wi, &np);
     F[3 * i] = f[0];
     F[3 * i + 1] = f[1];
     F[3 * i + 2] = f[2];

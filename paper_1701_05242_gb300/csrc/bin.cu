@@ -1,0 +1,209 @@
+// Binning into cells (Sections 2.1 and 2.3): exact cell index, counts,
+// exclusive scan of the counts, and a stable scatter.
+//
+// Stability without a global sort: atomics give every particle a provisional
+// rank inside its cell, the scatter places it there, and one thread per cell
+// then insertion-sorts the cell's (few) entries by input index.  The result
+// is the unique stable order, independent of atomic timing.
+#include "dcm_internal.cuh"
+
+namespace dcm {
+
+template <typename R>
+__global__ void k_count(int64_t n, const typename RT<R>::R4* __restrict__ pos, Grid<R> g,
+                        int32_t* __restrict__ cell, int32_t* __restrict__ slot, int32_t* __restrict__ count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto p = ldg4(pos + i);
+  int cx = cell_coord<R>(p.x, g.edge, g.inv_edge, g.n[0]);
+  int cy = cell_coord<R>(p.y, g.edge, g.inv_edge, g.n[1]);
+  int cz = cell_coord<R>(p.z, g.edge, g.inv_edge, g.n[2]);
+  int c = cx + g.n[0] * (cy + g.n[1] * cz);
+  int r = atomicAdd(count + c, 1);
+  if (cell) cell[i] = c;
+  if (slot) slot[i] = r;
+}
+
+// Block-wide exclusive scan helpers (1024 threads, 32 warps).
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Returns the exclusive prefix of v over the block; *total receives the sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+  __shared__ int warp_sums[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+    s = warp_incl_scan(s);
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  int base = w > 0 ? warp_sums[w - 1] : 0;
+  *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+// Phase 1: exclusive scan inside each tile; tile sums to part[].
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                                           int64_t n, int32_t* __restrict__ part) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    sum += v[k];
+  }
+  int total;
+  int run = block_excl_scan(sum, &total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// Phase 2: one block scans the tile sums in chunks (exclusive, in place);
+// the grand total goes to out_total.
+__global__ void __launch_bounds__(kScanBlock) k_scan_parts(int32_t* part, int64_t nparts, int32_t* out_total) {
+  int carry = 0;
+  for (int64_t c0 = 0; c0 < nparts; c0 += kScanTile) {
+    int64_t base = c0 + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = (base + k < nparts) ? part[base + k] : 0;
+      sum += v[k];
+    }
+    int total;
+    int run = block_excl_scan(sum, &total) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < nparts) part[base + k] = run;
+      run += v[k];
+    }
+    carry += total;
+  }
+  if (threadIdx.x == 0) *out_total = carry;
+}
+
+// Phase 3: add the tile offsets.
+__global__ void k_scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* __restrict__ part) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] += part[i / kScanTile];
+}
+
+int exclusive_scan(dcm_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
+  int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles > ctx->scan_cap) return set_error(ctx, DCM_ERR_CAPACITY, "scan of %lld items exceeds scratch", (long long)n);
+  if (tiles == 0) {
+    DCM_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, sizeof(int32_t), st));
+    return DCM_OK;
+  }
+  DCM_LAUNCH(ctx, k_scan_tiles, (unsigned)tiles, kScanBlock, 0, st, in, out, n, ctx->scan_part);
+  DCM_LAUNCH(ctx, k_scan_parts, 1, kScanBlock, 0, st, ctx->scan_part, tiles, out + n);
+  DCM_LAUNCH(ctx, k_scan_add, (unsigned)((n + 255) / 256), 256, 0, st, out, n, ctx->scan_part);
+  return check_launch(ctx, "exclusive_scan");
+}
+
+__global__ void k_scatter(int64_t n, const int32_t* __restrict__ cell, const int32_t* __restrict__ slot,
+                          const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  perm[start[cell[i]] + slot[i]] = (int32_t)i;
+}
+
+// One thread per cell: insertion sort of the cell's entries by input index.
+__global__ void k_cell_sort(int64_t ncell, const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  int b = start[c], e = start[c + 1];
+  for (int k = b + 1; k < e; ++k) {
+    int v = perm[k];
+    int j = k - 1;
+    while (j >= b && perm[j] > v) {
+      perm[j + 1] = perm[j];
+      --j;
+    }
+    perm[j + 1] = v;
+  }
+}
+
+template <typename V>
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const V* __restrict__ src, V* __restrict__ dst) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  dst[k] = src[perm[k]];
+}
+
+template <typename R>
+int bin_particles(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const Grid<R>& grid, int32_t* cell,
+                  int32_t* cell_start, int32_t* perm, typename RT<R>::R4* pos_sorted, cudaStream_t st) {
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * grid.ncell, st));
+  if (n > 0) {
+    unsigned nb = (unsigned)((n + 255) / 256);
+    DCM_LAUNCH(ctx, k_count<R>, nb, 256, 0, st, n, pos, grid, cell, ctx->slot, ctx->cell_count);
+  }
+  int rc = exclusive_scan(ctx, ctx->cell_count, cell_start, grid.ncell, st);
+  if (rc) return rc;
+  if (n > 0) {
+    unsigned nb = (unsigned)((n + 255) / 256);
+    DCM_LAUNCH(ctx, k_scatter, nb, 256, 0, st, n, cell, ctx->slot, cell_start, perm);
+    DCM_LAUNCH(ctx, k_cell_sort, (unsigned)((grid.ncell + 255) / 256), 256, 0, st, grid.ncell, cell_start, perm);
+    if (pos_sorted) k_gather<typename RT<R>::R4><<<nb, 256, 0, st>>>(n, perm, pos, pos_sorted);
+  }
+  return check_launch(ctx, "bin_particles");
+}
+
+template <typename R>
+int histogram(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const Grid<R>& grid, int32_t* count,
+              cudaStream_t st) {
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(count, 0, sizeof(int32_t) * grid.ncell, st));
+  if (n > 0) DCM_LAUNCH(ctx, k_count<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, pos, grid, nullptr, nullptr, count);
+  return check_launch(ctx, "histogram");
+}
+
+template int bin_particles<float>(dcm_ctx*, int64_t, const float4*, const Grid<float>&, int32_t*, int32_t*,
+                                  int32_t*, float4*, cudaStream_t);
+template int bin_particles<double>(dcm_ctx*, int64_t, const dvec4*, const Grid<double>&, int32_t*, int32_t*,
+                                   int32_t*, dvec4*, cudaStream_t);
+template int histogram<float>(dcm_ctx*, int64_t, const float4*, const Grid<float>&, int32_t*, cudaStream_t);
+template int histogram<double>(dcm_ctx*, int64_t, const dvec4*, const Grid<double>&, int32_t*, cudaStream_t);
+
+// Gather of a per-particle payload into sorted order (used by step.cu).
+template <typename V>
+void gather(dcm_ctx* ctx, int64_t n, const int32_t* perm, const V* src, V* dst, cudaStream_t st) {
+  if (n > 0) DCM_LAUNCH(ctx, k_gather<V>, (unsigned)((n + 255) / 256), 256, 0, st, n, perm, src, dst);
+}
+template void gather<float4>(dcm_ctx*, int64_t, const int32_t*, const float4*, float4*, cudaStream_t);
+template void gather<dvec4>(dcm_ctx*, int64_t, const int32_t*, const dvec4*, dvec4*, cudaStream_t);
+template void gather<float>(dcm_ctx*, int64_t, const int32_t*, const float*, float*, cudaStream_t);
+template void gather<double>(dcm_ctx*, int64_t, const int32_t*, const double*, double*, cudaStream_t);
+template void gather<int32_t>(dcm_ctx*, int64_t, const int32_t*, const int32_t*, int32_t*, cudaStream_t);
+
+// Scatter + per-cell stable sort for callers that computed cell and slot
+// themselves (step.cu fuses the count into the drift kernel).
+int scatter_sort(dcm_ctx* ctx, int64_t n, const int32_t* cell, const int32_t* slot, const int32_t* cell_start,
+                 int64_t ncell, int32_t* perm, cudaStream_t st) {
+  if (n > 0) {
+    DCM_LAUNCH(ctx, k_scatter, (unsigned)((n + 255) / 256), 256, 0, st, n, cell, slot, cell_start, perm);
+    DCM_LAUNCH(ctx, k_cell_sort, (unsigned)((ncell + 255) / 256), 256, 0, st, ncell, cell_start, perm);
+  }
+  return check_launch(ctx, "scatter_sort");
+}
+
+}  // namespace dcm

@@ -1,0 +1,202 @@
+// Internal declarations shared by the CUDA translation units of libdcm.
+// Not part of the public ABI (see include/dcm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "../../include/dcm.h"
+
+namespace dcm {
+
+// ----------------------------------------------------------------------------
+// Precision traits.  The mixed form stores float4 / float, the FP64 form a
+// 32-byte aligned 4-vector of doubles (CUDA 13 deprecates double4).
+// ----------------------------------------------------------------------------
+struct __align__(32) dvec4 {
+  double x, y, z, w;
+};
+
+template <typename R>
+struct RT;
+template <>
+struct RT<float> {
+  using R4 = float4;
+  __device__ static float inf() { return __int_as_float(0x7f800000); }
+};
+template <>
+struct RT<double> {
+  using R4 = dvec4;
+  __device__ static double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+};
+
+__device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ dvec4 ldg4(const dvec4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return dvec4{a.x, a.y, b.x, b.y};
+}
+
+// Exact floor(x / l) for an edge l with a short mantissa (k * l exact), clamped
+// to [0, n-1].  One correction step suffices because x * (1/l) is within one
+// unit of the true quotient.
+template <typename R>
+__device__ __forceinline__ int cell_coord(R x, R l, R inv_l, int n) {
+  R q = floor(x * inv_l);
+  int k = (int)q;
+  if ((R)k * l > x)
+    --k;
+  else if ((R)(k + 1) * l <= x)
+    ++k;
+  k = k < 0 ? 0 : k;
+  return k > n - 1 ? n - 1 : k;
+}
+
+// ----------------------------------------------------------------------------
+// Geometry handed to kernels by value.
+// ----------------------------------------------------------------------------
+template <typename R>
+struct Grid {
+  int n[3];      // cells per dimension
+  R edge;        // cell edge
+  R inv_edge;
+  R L[3];        // box lengths (= n * edge exactly)
+  int64_t ncell;
+};
+
+struct LJTable {
+  int ntypes;
+  float eps24[16], eps4[16], sig2[16];   // FP32 copies
+  double deps24[16], deps4[16], dsig2[16];
+};
+
+// ----------------------------------------------------------------------------
+// Context.
+// ----------------------------------------------------------------------------
+}  // namespace dcm
+
+struct dcm_ctx {
+  dcm_params p;
+  int precision;
+  int64_t nc[3], ncell;     // force cells
+  int64_t nh[3], nbox;      // density boxes
+  int64_t n_max;
+  int device;
+  char err[512];
+  // device scratch
+  int32_t* status;          // [4]: first device-side error code, ...
+  int32_t* slot;            // n_max: rank of a particle inside its cell (atomics)
+  int32_t* cell;            // n_max: cell of each particle (step)
+  int32_t* perm;            // n_max
+  int32_t* cell_start;      // ncell + 1
+  int32_t* cell_count;      // ncell
+  int32_t* scan_part;       // scan block partials
+  int32_t* box_count;       // nbox
+  int32_t* g;               // nbox
+  int32_t* g_tmp;           // nbox
+  uint8_t* s;               // nbox
+  uint8_t* iface;           // nbox
+  void* D[2];               // nbox reals each
+  int32_t* flags;           // iter_max + 2 change flags of the distance sweeps
+  int32_t* hist;            // histogram of box sums
+  int32_t* thr;             // [8]: gmin, gmax, T, sweeps, ...
+  double* red;              // reduction partials
+  double* totals;           // [4]
+  int32_t* host_status;     // pinned host mirror
+  int64_t red_cap;          // number of partial slots in red (per quantity)
+  int64_t scan_cap;
+  int64_t launches;         // kernels launched through this context
+  // optional per-stage CUDA-event timing (dcm_set_timing)
+  int timing;
+  int ev_n[DCM_NSTAGES];
+  int ev_cap;                        // event pairs per stage
+  cudaEvent_t* ev;                   // [DCM_NSTAGES][ev_cap][2]
+};
+
+namespace dcm {
+
+constexpr int kHistCap = 1 << 20;
+constexpr int kScanBlock = 1024;       // threads of the scan kernels
+constexpr int kScanItems = 4;          // items per thread
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+int set_error(dcm_ctx* ctx, int code, const char* fmt, ...);
+
+// Stage timing: events recorded on the launching stream around a stage.
+void stage_begin(dcm_ctx* ctx, int stage, cudaStream_t st);
+void stage_end(dcm_ctx* ctx, int stage, cudaStream_t st);
+int check_launch(dcm_ctx* ctx, const char* what);
+
+// Grids from the context.
+template <typename R>
+Grid<R> cell_grid(const dcm_ctx* ctx);
+template <typename R>
+Grid<R> box_grid(const dcm_ctx* ctx);
+LJTable lj_table(const dcm_params& p);
+
+// ---- launchers (one per translation unit) ----------------------------------
+// bin.cu
+template <typename R>
+int bin_particles(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const Grid<R>& grid,
+                  int32_t* cell, int32_t* cell_start, int32_t* perm, typename RT<R>::R4* pos_sorted,
+                  cudaStream_t st);
+template <typename R>
+int histogram(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const Grid<R>& grid,
+              int32_t* count, cudaStream_t st);
+int exclusive_scan(dcm_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+template <typename V>
+void gather(dcm_ctx* ctx, int64_t n, const int32_t* perm, const V* src, V* dst, cudaStream_t st);
+int scatter_sort(dcm_ctx* ctx, int64_t n, const int32_t* cell, const int32_t* slot, const int32_t* cell_start,
+                 int64_t ncell, int32_t* perm, cudaStream_t st);
+
+// detect.cu
+int detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t* iface,
+                     int32_t* threshold, int32_t* g_out, cudaStream_t st);
+
+// distance.cu
+template <typename R>
+int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, int32_t* iters,
+                    bool host_check, cudaStream_t st);
+
+// cutoffs.cu
+template <typename R>
+int assign_cutoffs(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* D, R* rc,
+                   cudaStream_t st);
+
+// forces.cu
+template <typename R>
+int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc,
+              const int32_t* cell_start, typename RT<R>::R4* force, double* totals, cudaStream_t st);
+
+// step.cu
+template <typename R>
+int step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, cudaStream_t stream);
+template <typename R>
+int step_run(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int nsteps, cudaStream_t stream);
+
+// Deterministic reduction of per-block partials (nblk x nq doubles, quantity-
+// major) into out[0..nq) (device), optionally adding.  reduce.cu
+int reduce_partials(dcm_ctx* ctx, const double* part, int64_t nblk, int nq, double* out, bool accumulate,
+                    cudaStream_t st);
+
+// Device status word: first error wins.
+__device__ __forceinline__ void raise_status(int32_t* status, int code) { atomicCAS(status, 0, code); }
+
+}  // namespace dcm
+
+// Launch a kernel and count it.
+#define DCM_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)          \
+  do {                                                                  \
+    ++(ctx)->launches;                                                  \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);         \
+  } while (0)
+
+#define DCM_CUDA_TRY(ctx, call)                                                              \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return ::dcm::set_error((ctx), DCM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)

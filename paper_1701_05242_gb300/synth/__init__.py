@@ -257,10 +257,42 @@ class Slab:
         return tuple(float(v) for v in self.spec.box)
 
 
+def _cache_path(spec: SlabSpec):
+    import hashlib
+    import tempfile
+    if os.environ.get("DCM_SYNTH_CACHE", "1") == "0" or spec.n < 200000:
+        return None
+    key = repr((spec.box, spec.rho_l, spec.rho_v, spec.temperature, spec.liquid_fraction, spec.wave_amp,
+                spec.ntypes, spec.d_min, spec.seed, os.path.getmtime(_SRC)))
+    h = hashlib.sha256(key.encode()).hexdigest()[:24]
+    return os.path.join(tempfile.gettempdir(), "dcm_synth_cache", h + ".npz")
+
+
 def make_slab(spec: SlabSpec) -> Slab:
-    pos = make_positions(spec)
-    vel = make_velocities(pos.shape[0], spec.temperature, spec.seed)
-    types = make_types(pos.shape[0], spec.ntypes, spec.seed)
+    """Positions, velocities and types of one slab.  Large systems are cached
+    in the system temp directory (DCM_SYNTH_CACHE=0 disables the cache)."""
+    path = _cache_path(spec)
+    if path and os.path.exists(path):
+        try:
+            z = np.load(path)
+            pos, vel, types = z["pos"], z["vel"], z["types"]
+        except Exception:
+            path_ok = False
+            pos = None
+    else:
+        pos = None
+    if pos is None:
+        pos = make_positions(spec)
+        vel = make_velocities(pos.shape[0], spec.temperature, spec.seed)
+        types = make_types(pos.shape[0], spec.ntypes, spec.seed)
+        if path:
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                tmp = path + f".tmp{os.getpid()}.npz"
+                np.savez(tmp, pos=pos, vel=vel, types=types)
+                os.replace(tmp, path)
+            except OSError:
+                pass
     if spec.ntypes == 2:
         lj = {"eps": [1.0, 0.8], "sigma": [1.0, 1.1]}
     else:

@@ -1,0 +1,428 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated once, used below):
+  cells, counts, starts, permutation, box sums, threshold, S, interface: bit-exact
+  distances D: |dD| <= 1e-5 max(|D|, h) on finite values, identical +inf sets
+  cutoffs rc: |drc| <= 2e-6 (the ramp maps dD one to one into drc; FP32 ulp at 6 is 4.8e-7)
+  forces (mixed form): sqrt(sum|dF|^2 / sum|F|^2) <= 1e-5
+  energy E and virial W (mixed form): relative <= 1e-7
+  FP64 form: everything within 1e-12 relative (FP64 against FP64, different summation order)
+Pair-inclusion flips (r^2 within rounding of rc^2) are counted; they are bounded
+by the pairs lying within 1e-5 relative of a cutoff.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1701_05242_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+F_RMS_TOL = 1e-5
+EW_TOL = 1e-7
+D_TOL = 1e-5
+RC_TOL = 2e-6
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def D():
+    import paper_1701_05242_gb300.dcm as dcm
+    assert torch.cuda.is_available()
+    return dcm
+
+
+def make_ctx(D, box, n_max, precision=None, **kw):
+    prec = D.DCM_PREC_MIXED if precision is None else precision
+    p = D.make_params(box, n_max=int(n_max), precision=prec, **kw)
+    return D.Context(p)
+
+
+def real_of(D, prec):
+    return torch.float32 if prec == D.DCM_PREC_MIXED else torch.float64
+
+
+def pos4_of(D, pos, types, prec):
+    return D.to_real4(torch.from_numpy(np.asarray(pos, np.float32)),
+                      None if types is None else torch.from_numpy(np.asarray(types)), real_of(D, prec))
+
+
+def gpu_bin(D, ctx, pos4):
+    n = pos4.shape[0]
+    dev = pos4.device
+    cell = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    start = torch.empty(ctx.ncell + 1, dtype=torch.int32, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    ps = torch.empty_like(pos4) if n else torch.empty((1, 4), dtype=pos4.dtype, device=dev)
+    D.dcm_bin(ctx, n, pos4 if n else ps, cell, start, perm, ps)
+    torch.cuda.synchronize()
+    return cell[:n].cpu().numpy(), start.cpu().numpy(), perm[:n].cpu().numpy(), ps[:n]
+
+
+def rms_rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def near_cutoff_pairs(pos, rc, box, idx=None, rel=1e-5):
+    """Ordered pairs (i, j) with |r_ij^2 - rc_i^2| <= rel rc_i^2 (possible inclusion flips)."""
+    pos = np.asarray(pos, np.float64)
+    box = np.asarray(box, np.float64)
+    count = 0
+    for i in (range(len(pos)) if idx is None else idx):
+        d = pos[i] - pos
+        d -= box * np.round(d / box)
+        r2 = (d * d).sum(1)
+        r2[i] = -1
+        count += int((np.abs(r2 - rc[i] ** 2) <= rel * rc[i] ** 2).sum())
+    return count
+
+
+# --------------------------------------------------------------------------- binning
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("l", [1.5, 0.75])
+def test_bin_bit_exact(D, slab_1935, prec, l):
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, P, l=l)
+    pos4 = pos4_of(D, slab_1935.pos, None, P)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4)
+    oc, ocount, ostart, operm = O.bin_particles(slab_1935.pos, slab_1935.box, l)
+    assert np.array_equal(cell, oc)
+    assert np.array_equal(start, ostart)
+    assert np.array_equal(perm, operm)
+    assert torch.equal(ps.cpu(), pos4.cpu()[torch.from_numpy(operm).long()])
+
+
+def test_bin_edges_and_empty(D):
+    box = (12.0, 12.0, 12.0)
+    l = 1.5
+    xs = [0.0, 1.5, np.nextafter(np.float32(1.5), np.float32(0)), 3.0, 10.5, np.nextafter(np.float32(12), np.float32(0)),
+          6.0, 7.5]
+    pts = np.array([[x, y, z] for x in xs for y in xs[:3] for z in xs[-3:]], np.float32)
+    ctx = make_ctx(D, box, len(pts) + 10)
+    pos4 = pos4_of(D, pts, None, D.DCM_PREC_MIXED)
+    cell, start, perm, _ = gpu_bin(D, ctx, pos4)
+    oc, _, ostart, operm = O.bin_particles(pts, box, l)
+    assert np.array_equal(cell, oc) and np.array_equal(start, ostart) and np.array_equal(perm, operm)
+    # all particles in one cell keep their input order
+    same = np.full((37, 3), 4.0, np.float32) + np.linspace(0, 1.0, 37, dtype=np.float32)[:, None] * 0.4
+    cell, start, perm, _ = gpu_bin(D, ctx, pos4_of(D, same, None, D.DCM_PREC_MIXED))
+    assert np.array_equal(perm, np.arange(37)) and len(set(cell.tolist())) == 1
+    # no particles
+    cell, start, perm, _ = gpu_bin(D, ctx, torch.empty((0, 4), device="cuda"))
+    assert start.max() == 0 and start.shape[0] == ctx.ncell + 1
+
+
+def test_capacity_error(D, slab_1935):
+    ctx = make_ctx(D, slab_1935.box, 100)
+    pos4 = pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED)
+    with pytest.raises(D.DcmError) as e:
+        gpu_bin(D, ctx, pos4)
+    assert e.value.code == D.DCM_ERR_CAPACITY
+
+
+# ------------------------------------------------------------------- detection
+def gpu_detect(D, ctx, pos4):
+    n = pos4.shape[0]
+    bc = torch.empty(ctx.nbox, dtype=torch.int32, device="cuda")
+    D.dcm_box_counts(ctx, n, pos4, bc)
+    s = torch.empty(ctx.nbox, dtype=torch.uint8, device="cuda")
+    iface = torch.empty_like(s)
+    T = torch.empty(1, dtype=torch.int32, device="cuda")
+    g = torch.empty(ctx.nbox, dtype=torch.int32, device="cuda")
+    D.dcm_detect_interface(ctx, bc, s, iface, T, g)
+    torch.cuda.synchronize()
+    return bc.cpu().numpy(), g.cpu().numpy(), int(T.item()), s, iface
+
+
+@pytest.mark.parametrize("w,thr", [(2, -1), (1, -1), (0, -1), (2, 160)])
+def test_detect_bit_exact(D, slab_1935, w, thr):
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, smooth_w=w, threshold=thr)
+    pos4 = pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED)
+    bc, g, T, s, iface = gpu_detect(D, ctx, pos4)
+    nh = O.grid_dims(slab_1935.box, 1.5)
+    _, ocount, _, _ = O.bin_particles(slab_1935.pos, slab_1935.box, 1.5)
+    og, oT, os_, oif = O.detect_interface(ocount, nh, w, None if thr < 0 else thr)
+    assert np.array_equal(bc, ocount)
+    assert np.array_equal(g, og)
+    assert T == oT
+    assert np.array_equal(s.cpu().numpy(), os_) and np.array_equal(iface.cpu().numpy(), oif)
+
+
+def test_detect_single_phase_has_no_interface(D):
+    box = (12.0, 12.0, 12.0)
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(0, 12, size=(2000, 3)).astype(np.float32)
+    ctx = make_ctx(D, box, 2000, smooth_w=6)   # box sum over the whole periodic grid: all equal
+    _, g, T, s, iface = gpu_detect(D, ctx, pos4_of(D, pts, None, D.DCM_PREC_MIXED))
+    assert len(set(g.tolist())) == 1 and T == g[0] + 1 and int(iface.sum()) == 0
+
+
+# -------------------------------------------------------------------- distance
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_distance(D, slab_1935, prec):
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, P)
+    pos4 = pos4_of(D, slab_1935.pos, None, P)
+    _, _, _, s, iface = gpu_detect(D, ctx, pos4)
+    Dg = torch.empty(ctx.nbox, dtype=real_of(D, P), device="cuda")
+    it = torch.empty(1, dtype=torch.int32, device="cuda")
+    D.dcm_distance(ctx, s, iface, Dg, it)
+    Dg = Dg.cpu().numpy().astype(np.float64)
+    nh = O.grid_dims(slab_1935.box, 1.5)
+    Dj, itj = O.distance_jacobi(s.cpu().numpy(), iface.cpu().numpy(), nh, 1.5, ctx.params.r_grid or 6.0)
+    fin = np.isfinite(Dj)
+    assert np.array_equal(np.isfinite(Dg), fin)
+    tol = D_TOL if P == D.DCM_PREC_MIXED else FP64_TOL
+    assert np.all(np.abs(Dg[fin] - Dj[fin]) <= tol * np.maximum(Dj[fin], 1.5))
+    assert int(it.item()) == itj
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_distance_random_blobs(D, seed):
+    # hand-built S / interface volumes exercising diagonal fronts
+    rng = np.random.default_rng(seed)
+    box = (21.0, 18.0, 24.0)
+    nh = O.grid_dims(box, 1.5)
+    nb = int(np.prod(nh))
+    s = np.ones(nb, np.uint8)
+    iface = (rng.random(nb) < 0.004).astype(np.uint8)
+    s[rng.random(nb) < 0.002] = 0
+    ctx = make_ctx(D, box, 16, rc_min=3.0, rc_max=6.0, r_grid=7.5)
+    Dg = torch.empty(nb, dtype=torch.float32, device="cuda")
+    it = torch.empty(1, dtype=torch.int32, device="cuda")
+    D.dcm_distance(ctx, torch.from_numpy(s).cuda(), torch.from_numpy(iface).cuda(), Dg, it)
+    Dj, itj = O.distance_jacobi(s, iface, nh, 1.5, 7.5)
+    Dg = Dg.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(Dj)
+    assert np.array_equal(np.isfinite(Dg), fin)
+    assert np.all(np.abs(Dg[fin] - Dj[fin]) <= D_TOL * np.maximum(Dj[fin], 1.5))
+    assert int(it.item()) == itj
+
+
+def test_distance_not_converged_reports(D):
+    box = (6.0, 6.0, 60.0)
+    nh = O.grid_dims(box, 1.5)
+    nb = int(np.prod(nh))
+    s = np.ones(nb, np.uint8)
+    iface = np.zeros(nb, np.uint8)
+    iface[:16] = 1
+    ctx = make_ctx(D, box, 16, rc_min=1.5, rc_max=3.0, r_grid=100.0, iter_max=3)
+    Dg = torch.empty(nb, dtype=torch.float32, device="cuda")
+    with pytest.raises(D.DcmError) as e:
+        D.dcm_distance(ctx, torch.from_numpy(s).cuda(), torch.from_numpy(iface).cuda(), Dg)
+    assert e.value.code == D.DCM_ERR_NOT_CONVERGED
+    assert D.dcm_status(ctx) == D.DCM_ERR_NOT_CONVERGED
+    assert D.dcm_status(ctx) == D.DCM_OK   # cleared by the read
+
+
+# --------------------------------------------------------------------- cutoffs
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cutoffs(D, slab_1935, prec):
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, P)
+    pos4 = pos4_of(D, slab_1935.pos, None, P)
+    _, _, _, s, iface = gpu_detect(D, ctx, pos4)
+    Dg = torch.empty(ctx.nbox, dtype=real_of(D, P), device="cuda")
+    D.dcm_distance(ctx, s, iface, Dg)
+    rc = torch.empty(slab_1935.n, dtype=real_of(D, P), device="cuda")
+    D.dcm_cutoffs(ctx, slab_1935.n, pos4, Dg, rc)
+    p = O.Params(box=slab_1935.box)
+    a = O.assign_cutoffs(slab_1935.pos, p)
+    tol = RC_TOL if P == D.DCM_PREC_MIXED else FP64_TOL * 6
+    assert np.abs(rc.cpu().numpy().astype(np.float64) - a["rc"]).max() <= tol
+
+
+# ---------------------------------------------------------------------- forces
+def forces_case(D, slab, prec, rc64, types=None, eps=(1.0,), sigma=(1.0,), shift=0, l=1.5, box=None):
+    box = slab.box if box is None else box
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    kw = dict(ntypes=len(eps), eps=eps, sigma=sigma, shift_energy=shift, l=l)
+    ctx = make_ctx(D, box, slab.n, P, **kw)
+    real = real_of(D, P)
+    rc_in = rc64.astype(np.float32).astype(np.float64) if P == D.DCM_PREC_MIXED else rc64
+    pos4 = pos4_of(D, slab.pos, types, P)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4)
+    rcs = torch.from_numpy(rc_in[perm]).to(real).cuda()
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    D.dcm_forces(ctx, slab.n, ps, rcs, torch.from_numpy(start).cuda(), F, tot)
+    torch.cuda.synchronize()
+    Fs = F.cpu().numpy().astype(np.float64)
+    Fg = np.empty_like(Fs)
+    Fg[perm] = Fs
+    ref = O.forces_cells(slab.pos, rc_in, box, l, types, eps, sigma, bool(shift))
+    return Fg, tot.cpu().numpy(), ref, rc_in
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("l", [1.5, 1.0])
+def test_forces_dcm_cutoffs(D, slab_1935, prec, l):
+    p = O.Params(box=slab_1935.box)
+    rc64 = O.assign_cutoffs(slab_1935.pos, p)["rc"]
+    Fg, tot, ref, rc_in = forces_case(D, slab_1935, prec, rc64, l=l)
+    if prec == "mixed":
+        assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+        assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+        assert abs(tot[1] - ref.W) <= EW_TOL * abs(ref.W)
+        assert abs(Fg[:, 3] - ref.e).max() <= 1e-5 * np.abs(ref.e).max()
+        assert abs(int(tot[2]) - ref.npairs) <= near_cutoff_pairs(slab_1935.pos, rc_in, slab_1935.box)
+    else:
+        assert np.abs(Fg[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+        assert abs(tot[0] - ref.E) <= FP64_TOL * abs(ref.E)
+        assert abs(tot[1] - ref.W) <= FP64_TOL * abs(ref.W)
+        assert int(tot[2]) == ref.npairs
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_forces_uniform_and_shift(D, slab_1935, prec):
+    rc64 = np.full(slab_1935.n, 4.5)
+    Fg, tot, ref, _ = forces_case(D, slab_1935, prec, rc64, shift=1)
+    tol = F_RMS_TOL if prec == "mixed" else FP64_TOL
+    assert rms_rel(Fg[:, :3], ref.F) <= tol
+    assert abs(tot[0] - ref.E) <= (EW_TOL if prec == "mixed" else FP64_TOL) * abs(ref.E)
+    # uniform cutoff: Newton's third law makes the net force vanish (to rounding)
+    assert np.abs(Fg[:, :3].sum(0)).max() <= (1e-5 if prec == "mixed" else 1e-10) * np.abs(Fg[:, :3]).sum()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_forces_two_types(D, prec):
+    spec = synth.named("slab_256k_2types")
+    spec.box = (18.0, 18.0, 72.0)
+    slab = synth.make_slab(spec)
+    rng = np.random.default_rng(3)
+    rc64 = rng.uniform(3.0, 6.0, slab.n)
+    Fg, tot, ref, rc_in = forces_case(D, slab, prec, rc64, types=slab.types, eps=(1.0, 0.8), sigma=(1.0, 1.1))
+    if prec == "mixed":
+        assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+        assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+        assert abs(tot[1] - ref.W) <= EW_TOL * abs(ref.W)
+    else:
+        assert np.abs(Fg[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+        assert int(tot[2]) == ref.npairs
+
+
+def test_forces_tiny_box_and_ragged(D):
+    # rc_max = L/2 exactly (images on both sides), few particles, empty cells
+    rng = np.random.default_rng(11)
+    box = (12.0, 12.0, 12.0)
+    pts = rng.uniform(0, 12, size=(97, 3)).astype(np.float32)
+
+    class S:
+        pass
+    s = S()
+    s.pos, s.n, s.box = pts, 97, box
+    rc64 = rng.choice([3.0, 4.5, 6.0], 97)
+    Fg, tot, ref, rc_in = forces_case(D, s, "fp64", rc64)
+    assert np.abs(Fg[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+    assert int(tot[2]) == ref.npairs
+    Fg, tot, ref, rc_in = forces_case(D, s, "mixed", rc64)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+
+
+# ------------------------------------------------------------------------ step
+def run_gpu_steps(D, slab, P, nsteps, dt=0.005, K=1, per_step=True):
+    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K)
+    real = real_of(D, P)
+    pos4 = pos4_of(D, slab.pos, None, P)
+    vel4 = D.to_real4(torch.from_numpy(slab.vel), None, real)
+    st = D.State(ctx, pos4, vel4)
+    D.dcm_step_init(ctx, st)
+    out = [st.thermo.cpu().numpy().copy()]
+    for _ in range(nsteps if per_step else 1):
+        D.dcm_step(ctx, st, dt, 1 if per_step else nsteps)
+        out.append(st.thermo.cpu().numpy().copy())
+    assert D.dcm_status(ctx) == D.DCM_OK
+    return ctx, st, np.array(out)
+
+
+def test_step_fp64_matches_oracle_trajectory(D, slab_1935):
+    nsteps = 30
+    ctx, st, th = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, nsteps, K=1)
+    p = O.Params(box=slab_1935.box, recompute_every=1)
+    ost = O.init_state(slab_1935.pos, slab_1935.vel, p)
+    assert th[0, 0] == pytest.approx(ost.E, rel=1e-9)
+    assert th[0, 2] == pytest.approx(O.kinetic(slab_1935.vel.astype(np.float64)), rel=1e-12)
+    for k in range(nsteps):
+        ost = O.step(ost, 0.005, p)
+        assert th[k + 1, 0] == pytest.approx(ost.E, rel=1e-9), k
+        assert th[k + 1, 1] == pytest.approx(ost.W, rel=1e-9), k
+        assert th[k + 1, 2] == pytest.approx(O.kinetic(ost.vel), rel=1e-9), k
+    pos, vel, rc, ids = st.current()
+    ids = ids.cpu().numpy()
+    gp = np.empty((slab_1935.n, 3))
+    gp[ids] = pos.cpu().numpy()[:, :3]
+    d = np.abs(gp - ost.pos)
+    d = np.minimum(d, np.array(slab_1935.box) - d)
+    assert d.max() <= 1e-9
+
+
+def test_step_mixed_on_shared_inputs(D, slab_1935):
+    # one FP32 step; then the oracle re-evaluates forces at the GPU's own
+    # positions and cutoffs (shared inputs), since trajectories diverge
+    ctx, st, th = run_gpu_steps(D, slab_1935, D.DCM_PREC_MIXED, 3, K=1)
+    pos, vel, rc, ids = st.current()
+    pos = pos.cpu().numpy().astype(np.float64)
+    rcn = rc.cpu().numpy().astype(np.float64)
+    ref = O.forces_cells(pos[:, :3], rcn, slab_1935.box, 1.5)
+    Fg = st.force.cpu().numpy().astype(np.float64)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(th[-1, 0] - ref.E) <= EW_TOL * abs(ref.E)
+    # cutoffs recomputed at these positions
+    a = O.assign_cutoffs(pos[:, :3], O.Params(box=slab_1935.box))
+    assert np.abs(rcn - a["rc"]).max() <= RC_TOL
+
+
+def test_step_batched_call_equals_single_calls(D, slab_1935):
+    _, st1, th1 = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, 12, K=5, per_step=True)
+    _, st2, th2 = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, 12, K=5, per_step=False)
+    assert np.array_equal(th1[-1], th2[-1])
+    assert torch.equal(st1.current()[0], st2.current()[0])
+
+
+# ----------------------------------------------------------- full-size sample
+@pytest.fixture(scope="module")
+def slab_16m():
+    return synth.make_slab(synth.named("slab_16m"))
+
+
+def test_full_size_sampled(D, slab_16m):
+    """The 15.5M-particle workload in the configuration the benchmark times:
+    whole-grid stages compared in full, forces on a sample of particles."""
+    slab = slab_16m
+    n = slab.n
+    ctx = make_ctx(D, slab.box, n)
+    pos4 = pos4_of(D, slab.pos, None, D.DCM_PREC_MIXED)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4)
+    oc, ocount, ostart, operm = O.bin_particles(slab.pos, slab.box, 1.5)
+    assert np.array_equal(start, ostart) and np.array_equal(perm, operm)
+    bc, g, T, s, iface = gpu_detect(D, ctx, pos4)
+    nh = O.grid_dims(slab.box, 1.5)
+    og, oT, os_, oif = O.detect_interface(ocount, nh, 2)
+    assert T == oT and np.array_equal(g, og) and np.array_equal(iface.cpu().numpy(), oif)
+    Dg = torch.empty(ctx.nbox, dtype=torch.float32, device="cuda")
+    D.dcm_distance(ctx, s, iface, Dg)
+    Do, _ = O.cfsm(os_, oif, nh, 1.5, 6.0)
+    Dgn = Dg.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(Do)
+    assert np.array_equal(np.isfinite(Dgn), fin)
+    assert np.all(np.abs(Dgn[fin] - Do[fin]) <= D_TOL * np.maximum(Do[fin], 1.5))
+    rc = torch.empty(n, dtype=torch.float32, device="cuda")
+    D.dcm_cutoffs(ctx, n, ps, Dg, rc)
+    _, orc = O.cutoffs(slab.pos[operm], Do, nh, 1.5, 6.0, 3.0, 6.0, 3.0)
+    rcn = rc.cpu().numpy().astype(np.float64)
+    assert np.abs(rcn - orc).max() <= RC_TOL
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    D.dcm_forces(ctx, n, ps, rc, torch.from_numpy(start).cuda(), F, tot)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    # sample: random particles plus all of a few interface-region cells
+    idx = np.unique(np.concatenate([rng.choice(n, 3000, replace=False),
+                                    np.flatnonzero((rcn > 3.0) & (rcn < 6.0))[:1000]]))
+    spos = slab.pos[operm].astype(np.float64)
+    Fo, eo, wo, po = O.forces_subset(spos, rcn, slab.box, 1.5, idx, nthreads=8)
+    Fs = F.cpu().numpy().astype(np.float64)[idx]
+    assert rms_rel(Fs[:, :3], Fo) <= F_RMS_TOL
+    assert np.abs(Fs[:, 3] - eo).max() <= 1e-5 * np.abs(eo).max()
+    assert tot[0].item() != 0.0 and np.isfinite(tot.cpu().numpy()).all()
