@@ -216,7 +216,7 @@ struct ScratchPlan {
   int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags;
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
-           rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8;
+           2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256;
   }
 };
 
@@ -232,7 +232,7 @@ static ScratchPlan plan_of(const dcm_params* p) {
   s.nbox = nh[0] * nh[1] * nh[2];
   int64_t big = s.ncell > s.nbox ? s.ncell : s.nbox;
   s.scan_cap = (big + kScanTile - 1) / kScanTile + 1;
-  s.red_cap = (s.n_max + 127) / 128 + 1;
+  s.red_cap = (s.n_max + 31) / 32 + 1;      // one partial per warp
   s.rsize = p->precision == DCM_PREC_FP64 ? 8 : 4;
   s.flags = p->iter_max + 2;
   return s;
@@ -255,7 +255,7 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
   if (!ctx) return;
   void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
                  ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
-                 ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0]};
+                 ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -314,6 +314,7 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   alloc((void**)&ctx->thr, 4 * 8);
   alloc((void**)&ctx->red, 8 * 3 * s.red_cap);
   alloc((void**)&ctx->totals, 8 * 8);
+  alloc((void**)&ctx->red_tmp, 8 * 8 * 256);
   if (ok && cudaMallocHost((void**)&ctx->host_status, 16) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();

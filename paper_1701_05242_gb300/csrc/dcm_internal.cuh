@@ -104,6 +104,7 @@ struct dcm_ctx {
   int32_t* hist;            // histogram of box sums
   int32_t* thr;             // [8]: gmin, gmax, T, sweeps, ...
   double* red;              // reduction partials
+  double* red_tmp;          // [8 * 256] first-level chunk sums
   double* totals;           // [4]
   int32_t* host_status;     // pinned host mirror
   int64_t red_cap;          // number of partial slots in red (per quantity)

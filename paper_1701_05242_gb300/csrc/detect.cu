@@ -58,15 +58,31 @@ __global__ void k_minmax(const int32_t* __restrict__ g, int64_t nbox, int32_t* t
   }
 }
 
+// Histogram of the box sums over [gmin, gmax]: per-block shared-memory
+// histogram when the range fits (kSmemBins), else global atomics.
+constexpr int kSmemBins = 8192;
+
 __global__ void k_value_hist(const int32_t* __restrict__ g, int64_t nbox, const int32_t* thr, int32_t* hist,
                              int32_t* status) {
+  __shared__ int32_t sh[kSmemBins];
   int gmin = thr[0], gmax = thr[1];
   if ((int64_t)gmax - gmin >= kHistCap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, DCM_ERR_CAPACITY);
     return;
   }
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(hist + (g[b] - gmin), 1);
+  int range = gmax - gmin + 1;
+  if (range <= kSmemBins) {
+    for (int k = threadIdx.x; k < range; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += (int64_t)gridDim.x * blockDim.x)
+      atomicAdd(sh + (g[b] - gmin), 1);
+    __syncthreads();
+    for (int k = threadIdx.x; k < range; k += blockDim.x)
+      if (sh[k]) atomicAdd(hist + k, sh[k]);
+  } else {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += (int64_t)gridDim.x * blockDim.x)
+      atomicAdd(hist + (g[b] - gmin), 1);
+  }
 }
 
 __device__ long long block_sum_ll(long long v, long long* sh) {
@@ -175,7 +191,7 @@ int detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t
   DCM_LAUNCH(ctx, k_box_sum_axis<2>, nb, 256, 0, st, ctx->g_tmp, g, nx, ny, nz, w);
   if (ctx->p.threshold < 0) {
     DCM_LAUNCH(ctx, k_minmax_init, 1, 1, 0, st, ctx->thr);
-    int nred = (int)std::min<int64_t>((nbox + 255) / 256, 152 * 8);
+    int nred = (int)std::min<int64_t>((nbox + 255) / 256, 152 * 4);
     DCM_LAUNCH(ctx, k_minmax, nred, 256, 0, st, g, nbox, ctx->thr);
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->hist, 0, sizeof(int32_t) * kHistCap, st));
     DCM_LAUNCH(ctx, k_value_hist, nred, 256, 0, st, g, nbox, ctx->thr, ctx->hist, ctx->status);

@@ -54,12 +54,14 @@ template <typename R>
 __global__ void k_dist_sweep(const R* __restrict__ Din, R* __restrict__ Dout, int nx, int ny, int nz, R h, R r_grid,
                              int32_t* __restrict__ flags, int it) {
   if (it > 0 && flags[it - 1] == 0) return;  // the previous sweep changed nothing: converged
-  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t nxy = (int64_t)nx * ny;
-  if (b >= nxy * nz) return;
+  // grid: blockIdx.x over rows (ny * nz), blockIdx.y over chunks of one row
+  int x = blockIdx.y * blockDim.x + threadIdx.x;
+  int yz = blockIdx.x;
+  if (x >= nx) return;
+  int y = yz % ny, z = yz / ny;
+  int64_t b = x + (int64_t)nx * yz;
   R cur = Din[b];
   if (cur == (R)0) return;  // interface / low-density boxes are fixed at 0 in both buffers
-  int x = (int)(b % nx), y = (int)((b / nx) % ny), z = (int)(b / nxy);
   int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
@@ -97,6 +99,7 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
   R h = (R)ctx->p.h, rg = (R)ctx->p.r_grid;
   R* buf[2] = {D, (R*)ctx->D[1]};
   unsigned nb = (unsigned)((nbox + 255) / 256);
+  dim3 sg((unsigned)(ny * nz), (unsigned)((nx + 127) / 128));
   int iter_max = ctx->p.iter_max;
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(int32_t) * (size_t)(iter_max + 2), st));
   DCM_LAUNCH(ctx, k_dist_init<R>, nb, 256, 0, st, s, iface, nbox, buf[0], buf[1]);
@@ -108,7 +111,7 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
     while (done < iter_max && !converged) {
       int m = std::min(chunk, iter_max - done);
       for (int k = 0; k < m; ++k, ++done)
-        DCM_LAUNCH(ctx, k_dist_sweep<R>, nb, 256, 0, st, buf[done & 1], buf[(done + 1) & 1], nx, ny, nz, h, rg, ctx->flags, done);
+        DCM_LAUNCH(ctx, k_dist_sweep<R>, sg, 128, 0, st, buf[done & 1], buf[(done + 1) & 1], nx, ny, nz, h, rg, ctx->flags, done);
       DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status, ctx->flags + done - 1, sizeof(int32_t),
                                         cudaMemcpyDeviceToHost, st));
       DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -121,12 +124,15 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
       return set_error(ctx, DCM_ERR_NOT_CONVERGED, "fast sweeping did not converge in %d sweeps", iter_max);
     }
   } else {
-    // fixed even budget (result ends in buf[0] = D); Jacobi needs about
-    // 3 r_grid / h sweeps in the worst case seen, planar fronts r_grid / h
-    int budget = (int)std::ceil(3.0 * ctx->p.r_grid / ctx->p.h) + 6;
+    // fixed even budget (result ends in buf[0] = D).  Along a front the
+    // Godunov update can add arbitrarily little per box, so the sweep count is
+    // not bounded by r_grid / h; 8 r_grid / h + 8 leaves a wide margin over
+    // what wavy slab interfaces need (about 5 r_grid / h), and sweeps after
+    // convergence exit at once.
+    int budget = (int)std::ceil(8.0 * ctx->p.r_grid / ctx->p.h) + 8;
     budget = std::min(budget + (budget & 1), iter_max + (iter_max & 1));
     for (; done < budget; ++done)
-      DCM_LAUNCH(ctx, k_dist_sweep<R>, nb, 256, 0, st, buf[done & 1], buf[(done + 1) & 1], nx, ny, nz, h, rg, ctx->flags, done);
+      DCM_LAUNCH(ctx, k_dist_sweep<R>, sg, 128, 0, st, buf[done & 1], buf[(done + 1) & 1], nx, ny, nz, h, rg, ctx->flags, done);
     DCM_LAUNCH(ctx, k_dist_finish, 1, 1, 0, st, ctx->flags, done, iters, ctx->status);
   }
   return check_launch(ctx, "distance_sweeps");

@@ -55,31 +55,21 @@ __device__ __forceinline__ int ufloor(R v) {
   return (int)floor(v);
 }
 
+// Per-warp partial sums of (E, W, pairs): summed across the warp in the
+// working precision (32 terms), then stored as one FP64 partial per warp;
+// no block barrier, so warps that finish early do not wait.
 template <typename R>
-__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* part, int64_t nblk) {
-  __shared__ double sh[3][kForceBlock / 32];
+__device__ __forceinline__ void warp_partials3(R a, R b, int c, double* part, int64_t nslot) {
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
     c += __shfl_xor_sync(0xffffffffu, c, o);
   }
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[0][w] = a;
-    sh[1][w] = b;
-    sh[2][w] = c;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int k = 0; k < kForceBlock / 32; ++k) {
-      s0 += sh[0][k];
-      s1 += sh[1][k];
-      s2 += sh[2][k];
-    }
-    part[blockIdx.x] = s0;
-    part[nblk + blockIdx.x] = s1;
-    part[2 * nblk + blockIdx.x] = s2;
+  if ((threadIdx.x & 31) == 0) {
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    part[w] = (double)a;
+    part[nslot + w] = (double)b;
+    part[2 * nslot + w] = (double)c;
   }
 }
 
@@ -87,7 +77,7 @@ template <typename R, bool TYPED>
 __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                         const R* __restrict__ rc, const int32_t* __restrict__ start,
                                                         ForceArgs<R> a, typename RT<R>::R4* __restrict__ force,
-                                                        double* __restrict__ part, int64_t nblk) {
+                                                        double* __restrict__ part, int64_t nwarp) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   R fx = 0, fy = 0, fz = 0, en = 0, vir = 0;
   int npair = 0;
@@ -206,7 +196,7 @@ __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typenam
     out.w = (R)0.5 * en;
     force[i] = out;
   }
-  if (part) block_reduce3<R>((double)((R)0.5 * en), (double)((R)0.5 * vir), (double)npair, part, nblk);
+  if (part) warp_partials3<R>((R)0.5 * en, (R)0.5 * vir, npair, part, nwarp);
 }
 
 template <typename R>
@@ -228,16 +218,17 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   a.shift = ctx->p.shift_energy;
   a.rc_max = (R)ctx->p.rc_max;
   int64_t nblk = (n + kForceBlock - 1) / kForceBlock;
-  if (totals && nblk > ctx->red_cap)
-    return set_error(ctx, DCM_ERR_CAPACITY, "force reduction needs %lld partials", (long long)nblk);
+  int64_t nwarp = nblk * (kForceBlock / 32);
+  if (totals && nwarp > ctx->red_cap)
+    return set_error(ctx, DCM_ERR_CAPACITY, "force reduction needs %lld partials", (long long)nwarp);
   double* part = totals ? ctx->red : nullptr;
   auto kern = t.ntypes > 1 ? k_forces<R, true> : k_forces<R, false>;
   stage_begin(ctx, DCM_STAGE_FORCES, st);
-  DCM_LAUNCH(ctx, kern, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, a, force, part, nblk);
+  DCM_LAUNCH(ctx, kern, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, a, force, part, nwarp);
   stage_end(ctx, DCM_STAGE_FORCES, st);
   int r = check_launch(ctx, "lj_forces");
   if (r) return r;
-  if (totals) return reduce_partials(ctx, part, nblk, 3, totals, false, st);
+  if (totals) return reduce_partials(ctx, part, nwarp, 3, totals, false, st);
   return DCM_OK;
 }
 

@@ -46,11 +46,13 @@ __global__ void k_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__ p
   slot[i] = atomicAdd(count + c, 1);
 }
 
+// Second half kick and kinetic energy: per-thread and per-warp sums in the
+// working precision, one FP64 partial per warp.
 template <typename R>
 __global__ void k_kick_ke(int64_t n, typename RT<R>::R4* __restrict__ vel, const typename RT<R>::R4* __restrict__ force,
                           R half_dt, double* __restrict__ part) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double ke = 0.0;
+  R ke = 0;
   if (i < n) {
     auto v = vel[i];
     if (force) {
@@ -60,17 +62,25 @@ __global__ void k_kick_ke(int64_t n, typename RT<R>::R4* __restrict__ vel, const
       v.z += half_dt * f.z;
       vel[i] = v;
     }
-    ke = 0.5 * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+    ke = (R)0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
   }
   for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, o);
-  __shared__ double sh[8];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ke;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
-    part[blockIdx.x] = s;
-  }
+  if ((threadIdx.x & 31) == 0) part[i >> 5] = (double)ke;
+}
+
+// One pass over perm for the whole particle payload.
+template <typename R>
+__global__ void k_gather_state(int64_t n, const int32_t* __restrict__ perm, const typename RT<R>::R4* __restrict__ p0,
+                               typename RT<R>::R4* __restrict__ p1, const typename RT<R>::R4* __restrict__ v0,
+                               typename RT<R>::R4* __restrict__ v1, const R* __restrict__ r0, R* __restrict__ r1,
+                               const int32_t* __restrict__ id0, int32_t* __restrict__ id1) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int src = perm[k];
+  p1[k] = p0[src];
+  v1[k] = v0[src];
+  r1[k] = r0[src];
+  if (id0) id1[k] = id0[src];
 }
 
 __global__ void k_thermo(const double* totals, double* thermo) {
@@ -108,11 +118,11 @@ static int recompute_cutoffs(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* 
 template <typename R>
 static int finish_thermo(dcm_ctx* ctx, int64_t n, typename RT<R>::R4* vel, const typename RT<R>::R4* force, R half_dt,
                          double* thermo, cudaStream_t st) {
-  int64_t nblk = (n + 255) / 256;
-  if (nblk > ctx->red_cap) return set_error(ctx, DCM_ERR_CAPACITY, "kinetic reduction too large");
+  int64_t nblk = (n + 255) / 256, nwarp = nblk * 8;
+  if (nwarp > ctx->red_cap) return set_error(ctx, DCM_ERR_CAPACITY, "kinetic reduction too large");
   if (n > 0) {
     DCM_LAUNCH(ctx, k_kick_ke<R>, (unsigned)nblk, 256, 0, st, n, vel, force, half_dt, ctx->red);
-    int r = reduce_partials(ctx, ctx->red, nblk, 1, ctx->totals + 3, false, st);
+    int r = reduce_partials(ctx, ctx->red, nwarp, 1, ctx->totals + 3, false, st);
     if (r) return r;
   } else {
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->totals + 3, 0, sizeof(double), st));
@@ -125,10 +135,11 @@ template <typename R>
 static int gather_state(dcm_ctx* ctx, dcm_state* st, int64_t n, cudaStream_t s) {
   using R4 = typename RT<R>::R4;
   int c = st->cur, o = 1 - st->cur;
-  gather<R4>(ctx, n, ctx->perm, (const R4*)st->pos[c], (R4*)st->pos[o], s);
-  gather<R4>(ctx, n, ctx->perm, (const R4*)st->vel[c], (R4*)st->vel[o], s);
-  gather<R>(ctx, n, ctx->perm, (const R*)st->rc[c], (R*)st->rc[o], s);
-  if (st->id[c] && st->id[o]) gather<int32_t>(ctx, n, ctx->perm, st->id[c], st->id[o], s);
+  bool ids = st->id[c] && st->id[o];
+  if (n > 0)
+    DCM_LAUNCH(ctx, k_gather_state<R>, (unsigned)((n + 255) / 256), 256, 0, s, n, ctx->perm, (const R4*)st->pos[c],
+               (R4*)st->pos[o], (const R4*)st->vel[c], (R4*)st->vel[o], (const R*)st->rc[c], (R*)st->rc[o],
+               ids ? st->id[c] : nullptr, ids ? st->id[o] : nullptr);
   return check_launch(ctx, "gather_state");
 }
 

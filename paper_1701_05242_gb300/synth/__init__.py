@@ -119,6 +119,8 @@ def named(name: str) -> SlabSpec:
         return SlabSpec(box=(96.0, 96.0, 384.0), name=name)
     if name == "slab_16m":           # 240x240x960, N = 15,482,880, capillary waves 2.0 sigma
         return SlabSpec(box=(240.0, 240.0, 960.0), wave_amp=2.0, name=name)
+    if name == "slab_8m":            # 180x180x960, N = 8,709,120, capillary waves 2.0 sigma (profiling size)
+        return SlabSpec(box=(180.0, 180.0, 960.0), wave_amp=2.0, name=name)
     if name == "slab_256k_2types":   # 61.5x61.5x246, N = 260,522, two LJ types
         return SlabSpec(box=(61.5, 61.5, 246.0), ntypes=2, name=name)
     raise KeyError(name)

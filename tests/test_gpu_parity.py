@@ -60,6 +60,18 @@ def gpu_bin(D, ctx, pos4):
     return cell[:n].cpu().numpy(), start.cpu().numpy(), perm[:n].cpu().numpy(), ps[:n]
 
 
+def assert_distances(Dg, Do, r_grid, tol):
+    """Finite values within tol * max(D, h); the +inf sets agree except at the
+    acceptance threshold r_grid, where FP32 and FP64 may round a value of about
+    r_grid to either side."""
+    fin = np.isfinite(Do) & np.isfinite(Dg)
+    flip = np.isfinite(Do) != np.isfinite(Dg)
+    other = np.where(np.isfinite(Do), Do, Dg)
+    assert np.all(other[flip] >= r_grid * (1 - tol)), other[flip].min() if flip.any() else None
+    assert flip.sum() <= max(2, 1e-4 * flip.size)
+    assert np.all(np.abs(Dg[fin] - Do[fin]) <= tol * np.maximum(Do[fin], 1.5))
+
+
 def rms_rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
 
@@ -150,12 +162,13 @@ def test_detect_bit_exact(D, slab_1935, w, thr):
 
 
 def test_detect_single_phase_has_no_interface(D):
-    box = (12.0, 12.0, 12.0)
+    box = (13.5, 13.5, 13.5)                   # 9 boxes per dimension
     rng = np.random.default_rng(0)
-    pts = rng.uniform(0, 12, size=(2000, 3)).astype(np.float32)
-    ctx = make_ctx(D, box, 2000, smooth_w=6)   # box sum over the whole periodic grid: all equal
+    pts = rng.uniform(0, 13.5, size=(2000, 3)).astype(np.float32)
+    ctx = make_ctx(D, box, 2000, smooth_w=4)   # 9-wide box sum covers the periodic grid once: all equal
     _, g, T, s, iface = gpu_detect(D, ctx, pos4_of(D, pts, None, D.DCM_PREC_MIXED))
-    assert len(set(g.tolist())) == 1 and T == g[0] + 1 and int(iface.sum()) == 0
+    assert len(set(g.tolist())) == 1 and g[0] == 2000
+    assert T == g[0] + 1 and int(iface.sum()) == 0 and int(s.sum()) == 0
 
 
 # -------------------------------------------------------------------- distance
@@ -170,12 +183,10 @@ def test_distance(D, slab_1935, prec):
     D.dcm_distance(ctx, s, iface, Dg, it)
     Dg = Dg.cpu().numpy().astype(np.float64)
     nh = O.grid_dims(slab_1935.box, 1.5)
-    Dj, itj = O.distance_jacobi(s.cpu().numpy(), iface.cpu().numpy(), nh, 1.5, ctx.params.r_grid or 6.0)
-    fin = np.isfinite(Dj)
-    assert np.array_equal(np.isfinite(Dg), fin)
+    Dj, itj = O.distance_jacobi(s.cpu().numpy(), iface.cpu().numpy(), nh, 1.5, 6.0)
     tol = D_TOL if P == D.DCM_PREC_MIXED else FP64_TOL
-    assert np.all(np.abs(Dg[fin] - Dj[fin]) <= tol * np.maximum(Dj[fin], 1.5))
-    assert int(it.item()) == itj
+    assert_distances(Dg, Dj, 6.0, tol)
+    assert abs(int(it.item()) - itj) <= (2 if P == D.DCM_PREC_MIXED else 0)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -194,10 +205,9 @@ def test_distance_random_blobs(D, seed):
     D.dcm_distance(ctx, torch.from_numpy(s).cuda(), torch.from_numpy(iface).cuda(), Dg, it)
     Dj, itj = O.distance_jacobi(s, iface, nh, 1.5, 7.5)
     Dg = Dg.cpu().numpy().astype(np.float64)
-    fin = np.isfinite(Dj)
-    assert np.array_equal(np.isfinite(Dg), fin)
-    assert np.all(np.abs(Dg[fin] - Dj[fin]) <= D_TOL * np.maximum(Dj[fin], 1.5))
-    assert int(it.item()) == itj
+    assert_distances(Dg, Dj, 7.5, D_TOL)
+    # FP32 and FP64 sweeps may settle their last ulps one sweep apart
+    assert abs(int(it.item()) - itj) <= 2
 
 
 def test_distance_not_converged_reports(D):
@@ -404,9 +414,7 @@ def test_full_size_sampled(D, slab_16m):
     D.dcm_distance(ctx, s, iface, Dg)
     Do, _ = O.cfsm(os_, oif, nh, 1.5, 6.0)
     Dgn = Dg.cpu().numpy().astype(np.float64)
-    fin = np.isfinite(Do)
-    assert np.array_equal(np.isfinite(Dgn), fin)
-    assert np.all(np.abs(Dgn[fin] - Do[fin]) <= D_TOL * np.maximum(Do[fin], 1.5))
+    assert_distances(Dgn, Do, 6.0, D_TOL)
     rc = torch.empty(n, dtype=torch.float32, device="cuda")
     D.dcm_cutoffs(ctx, n, ps, Dg, rc)
     _, orc = O.cutoffs(slab.pos[operm], Do, nh, 1.5, 6.0, 3.0, 6.0, 3.0)
