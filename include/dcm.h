@@ -228,6 +228,26 @@ int dcm_step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, dcm_stream_t stream);
  * non-convergence is reported by dcm_status(). */
 int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, dcm_stream_t stream);
 
+/* Same result as dcm_distance, for callers that cannot allocate device
+ * memory: code whose device memory belongs to another allocator or
+ * framework, code running while a CUDA graph is captured, or a plugin that is
+ * only handed device buffers.  It needs no dcm_ctx (whose creation
+ * allocates) and calls no allocating routine.  The paper has no counterpart:
+ * this is a deployment variant of the same fast sweeping.
+ *   p      host pointer to the parameters (validated as by dcm_validate_params)
+ *   s, iface, D, iters: as for dcm_distance (device pointers; iters nullable)
+ * Scratch: one fixed 8 MiB device array compiled into the library (held by
+ * every GPU that loads it, until exit), holding the second Jacobi iterate
+ * (nboxes reals) and iter_max + 2 change flags; a grid or iter_max needing more
+ * returns DCM_ERR_CAPACITY before any launch (e.g. up to about 2.0M boxes in
+ * the mixed form, 1.0M in FP64).  The first call on each device looks up the
+ * array's device address with cudaGetSymbolAddress (device current) and
+ * caches it; make that first call before any stream capture.  Every call
+ * shares the array: calls whose kernels may overlap on the GPU race.
+ * SYNCHRONOUS like dcm_distance; returns DCM_ERR_NOT_CONVERGED likewise. */
+int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,
+                         dcm_stream_t stream);
+
 /* ---- instrumentation -------------------------------------------------- */
 
 /* Stages of dcm_step whose GPU time can be measured. */

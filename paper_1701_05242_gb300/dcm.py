@@ -74,6 +74,7 @@ _SIGS = {
     "dcm_forces": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dcm_step_init": (_i32, [_vp, ctypes.POINTER(dcm_state), _i64, _vp]),
     "dcm_step": (_i32, [_vp, ctypes.POINTER(dcm_state), _i64, ctypes.c_double, _i32, _vp]),
+    "dcm_distance_noalloc": (_i32, [ctypes.POINTER(dcm_params), _vp, _vp, _vp, _vp, _vp]),
     "dcm_set_timing": (_i32, [_vp, _i32]),
     "dcm_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "dcm_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
@@ -194,6 +195,13 @@ def dcm_detect_interface(ctx: Context, box_count, s, iface, threshold, g=None, s
 
 def dcm_distance(ctx: Context, s, iface, D, iters=None, stream=None):
     ctx.check(lib.dcm_distance(ctx.handle, _ptr(s), _ptr(iface), _ptr(D), _ptr(iters), _stream(stream)))
+
+
+def dcm_distance_noalloc(params: dcm_params, s, iface, D, iters=None, stream=None):
+    """dcm_distance without a context or any device allocation (fixed library
+    scratch); returns the status code (DCM_OK, DCM_ERR_CAPACITY, ...)."""
+    return lib.dcm_distance_noalloc(ctypes.byref(params), _ptr(s), _ptr(iface), _ptr(D), _ptr(iters),
+                                    _stream(stream))
 
 
 def dcm_cutoffs(ctx: Context, n, pos, D, rc, stream=None):
