@@ -46,9 +46,12 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="slab_16m")
+    ap.add_argument("--cell-edge", type=float, default=1.5, help="force-cell edge l (density grid h stays 1.5)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args(argv)
 
 
@@ -208,6 +211,50 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args, D, dev):
+    """64 independent replicas (N log-uniform in [2K, 200K]) stepped together:
+    autotuned cell edge and force block, one CUDA graph per recomputation
+    period, args.batch_steps timesteps timed."""
+    import numpy as np
+    import torch
+    from paper_1701_05242_gb300 import autotune, synth
+    specs = synth.batch_specs(64)
+    slabs = [synth.make_slab(s) for s in specs]
+    boxes = [s.box for s in slabs]
+    counts = [s.n for s in slabs]
+    pos = np.concatenate([s.pos for s in slabs])
+    vel = np.concatenate([s.vel for s in slabs])
+    best, table = autotune.tune(boxes, counts, pos, vel, K=K_RECOMPUTE, dt=DT)
+    b, st = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_MIXED, K_RECOMPUTE, best[0])
+    D.dcm_batch_set_force_block(b, best[1])
+    D.dcm_batch_step_init(b, st)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    D.dcm_batch_capture(b, st, DT, stream)
+    per = D.dcm_batch_graph_steps(b)
+    ngraphs = max(1, args.batch_steps // per)
+    D.dcm_batch_replay(b, st, 1, stream)
+    stream.synchronize()
+    D.dcm_batch_launch_count(b, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    D.dcm_batch_replay(b, st, ngraphs, stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps = ngraphs * per
+    status = D.dcm_batch_status(b, stream)
+    out = {"value": sum(counts) * steps / (ms / 1000.0), "unit": UNIT, "replicas": len(counts),
+           "particles": int(sum(counts)), "n_min": int(min(counts)), "n_max": int(max(counts)),
+           "timesteps": steps, "ms_per_timestep": ms / steps, "cuda_graph": True,
+           "graph_timesteps": per, "launches_per_timestep": D.dcm_batch_launch_count(b) / steps,
+           "autotuned": {"cell_edge": best[0], "force_block": best[1],
+                         "candidates_ms": {f"l={k[0]},block={k[1]}": v for k, v in table.items()}},
+           "device_status": status}
+    b.close()
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -226,7 +273,7 @@ def run_gb300(args):
     stream = torch.cuda.current_stream(dev)
 
     def new_state(prec):
-        p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE)
+        p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE, l=args.cell_edge)
         ctx = D.Context(p)
         real = ctx.real
         st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real, dev),
@@ -340,11 +387,19 @@ def run_gb300(args):
                "d2h_bytes_per_step": 2 * n * 16 + 32, "steps": ke,
                "note": "pinned host state in, dcm_step_init + 10 timesteps, state and thermo out"}
 
+    # ---------------- batched form: 64 replicas, autotuned, graph-captured
+    batch = None
+    if not args.skip_batch:
+        del st
+        ctx.close()
+        torch.cuda.empty_cache()
+        batch = run_batch(args, D, dev)
+
     # ---------------- CPU oracle on the host cores (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         nthreads = os.cpu_count() or 1
-        rate, n_s, secs, box = oracle_rate(args.workload, 30.0, 10, 1, nthreads)
+        rate, n_s, _, box = oracle_rate(args.workload, 30.0, 10, 1, nthreads)
         cpu = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                "sample": f"{n_s} particles: the {args.workload} recipe on a {box[0]:g}x{box[1]:g}x{box[2]:g} "
                          f"cross-section, 10 oracle timesteps incl. one cutoff recomputation (cell-list forces "
@@ -355,12 +410,12 @@ def run_gb300(args):
                "warmup": args.warmup, "ms_per_step": secs * 1000.0 / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "particles_per_gpu": n, "box": list(slab.box),
-                          "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": 1.5, "dt": DT,
+                          "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": args.cell_edge, "dt": DT,
                           "timesteps_per_step": K_RECOMPUTE, "recompute_every": K_RECOMPUTE,
                           "precision": "fp32 pair math, fp64 totals", "l2": "inputs larger than L2 (positions 248 MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "stage_ms_per_step": stage_ms, "fp64_form": fp64, "device_status": status,
+               "stage_ms_per_step": stage_ms, "fp64_form": fp64, "batched_form": batch, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}
         print(json.dumps(out), flush=True)

@@ -248,6 +248,52 @@ int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, 
 int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,
                          dcm_stream_t stream);
 
+/* ---- batched form: many independent systems in one launch per stage ---- */
+
+/* R independent replicas (the benchmark spec's batching form) that share every
+ * parameter in *p except the box and the particle count: replica r has box
+ * boxes[3r .. 3r+2] (host) and counts[r] particles (host).  Each replica is
+ * validated as a single system (dcm_validate_params).  The state arrays of
+ * dcm_state are the concatenation of the replicas: replica r owns slots
+ * [offset[r], offset[r+1]) (dcm_batch_offsets) and its particles stay there;
+ * thermo is double[4 R] = {E, W, KE, pairs} per replica.  Every stage of a
+ * step is one launch over all replicas (per-replica boxes, grids, thresholds
+ * and reductions are read from a device table).  Synchronous; allocates. */
+typedef struct dcm_batch dcm_batch;
+int dcm_batch_create(const dcm_params* p, int32_t R, const double* boxes, const int64_t* counts, dcm_batch** out);
+void dcm_batch_destroy(dcm_batch* b);
+const char* dcm_batch_last_error(const dcm_batch* b);
+
+/* offsets (host, R+1 entries): first slot of every replica and the total. */
+int dcm_batch_offsets(const dcm_batch* b, int64_t* offsets);
+
+/* Threads per block of the batched force kernel: 64, 128 (default) or 256
+ * (set by the autotuner).  Invalidates a captured graph. */
+int dcm_batch_set_force_block(dcm_batch* b, int32_t threads);
+
+/* As dcm_step_init / dcm_step for all replicas at once (asynchronous; the
+ * distance sweeps run a fixed budget and report non-convergence through
+ * dcm_batch_status). */
+int dcm_batch_step_init(dcm_batch* b, dcm_state* st, dcm_stream_t stream);
+int dcm_batch_step(dcm_batch* b, dcm_state* st, double dt, int32_t nsteps, dcm_stream_t stream);
+
+/* Capture one recomputation period (K steps, or 2K if K is odd so that the
+ * double buffers return to the same side) of dcm_batch_step into a CUDA graph
+ * on `stream` (must not be the legacy default stream); st->t must be a
+ * multiple of K.  The graph is bound to st's buffers.  Nothing is executed. */
+int dcm_batch_capture(dcm_batch* b, dcm_state* st, double dt, dcm_stream_t stream);
+
+/* Launch the captured graph ngraphs times (st->t advances by
+ * ngraphs * dcm_batch_graph_steps).  st must hold the captured buffers. */
+int dcm_batch_replay(dcm_batch* b, dcm_state* st, int32_t ngraphs, dcm_stream_t stream);
+int dcm_batch_graph_steps(const dcm_batch* b);
+
+/* As dcm_status, dcm_set_timing, dcm_stage_times, dcm_launch_count. */
+int dcm_batch_status(dcm_batch* b, dcm_stream_t stream);
+int dcm_batch_set_timing(dcm_batch* b, int32_t capacity);
+int dcm_batch_stage_times(dcm_batch* b, double* ms, int64_t* count);
+int dcm_batch_launch_count(dcm_batch* b, int64_t* count, int32_t reset);
+
 /* ---- instrumentation -------------------------------------------------- */
 
 /* Stages of dcm_step whose GPU time can be measured. */

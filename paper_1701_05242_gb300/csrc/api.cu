@@ -232,7 +232,7 @@ static ScratchPlan plan_of(const dcm_params* p) {
   s.nbox = nh[0] * nh[1] * nh[2];
   int64_t big = s.ncell > s.nbox ? s.ncell : s.nbox;
   s.scan_cap = (big + kScanTile - 1) / kScanTile + 1;
-  s.red_cap = (s.n_max + 31) / 32 + 1;      // one partial per warp
+  s.red_cap = ((s.n_max + 255) / 256 + 1) * 8;  // one partial per warp of the padded launches
   s.rsize = p->precision == DCM_PREC_FP64 ? 8 : 4;
   s.flags = p->iter_max + 2;
   return s;

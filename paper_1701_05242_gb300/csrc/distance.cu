@@ -50,32 +50,40 @@ __device__ __forceinline__ R godunov3(R a0, R a1, R a2, R h) {
   return d;
 }
 
+// One Jacobi sweep.  Grid-stride over (row, chunk) work items with a grid of
+// a few waves, so a sweep after convergence costs one short wave of blocks
+// that read the flag and leave.
 template <typename R>
 __global__ void k_dist_sweep(const R* __restrict__ Din, R* __restrict__ Dout, int nx, int ny, int nz, R h, R r_grid,
                              int32_t* __restrict__ flags, int it) {
   if (it > 0 && flags[it - 1] == 0) return;  // the previous sweep changed nothing: converged
-  // grid: blockIdx.x over rows (ny * nz), blockIdx.y over chunks of one row
-  int x = blockIdx.y * blockDim.x + threadIdx.x;
-  int yz = blockIdx.x;
-  if (x >= nx) return;
-  int y = yz % ny, z = yz / ny;
-  int64_t b = x + (int64_t)nx * yz;
-  R cur = Din[b];
-  if (cur == (R)0) return;  // interface / low-density boxes are fixed at 0 in both buffers
-  int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-  int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-  int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
-  R a0 = fmin(Din[row + xm], Din[row + xp]);
-  R a1 = fmin(Din[x + nx * (ym + (int64_t)ny * z)], Din[x + nx * (yp + (int64_t)ny * z)]);
-  R a2 = fmin(Din[x + nx * (y + (int64_t)ny * zm)], Din[x + nx * (y + (int64_t)ny * zp)]);
-  R d = godunov3<R>(a0, a1, a2, h);
-  R out = cur;
-  if (d < cur && d <= r_grid) {
-    out = d;
-    flags[it] = 1;
+  const int chunks = (nx + blockDim.x - 1) / blockDim.x;
+  const int64_t items = (int64_t)ny * nz * chunks;
+  bool changed = false;
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    int yz = (int)(w / chunks);
+    int x = (int)(w - (int64_t)yz * chunks) * blockDim.x + threadIdx.x;
+    if (x >= nx) continue;
+    int y = yz % ny, z = yz / ny;
+    int64_t b = x + (int64_t)nx * yz;
+    R cur = Din[b];
+    if (cur == (R)0) continue;  // interface / low-density boxes are fixed at 0 in both buffers
+    int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
+    R a0 = fmin(Din[row + xm], Din[row + xp]);
+    R a1 = fmin(Din[x + nx * (ym + (int64_t)ny * z)], Din[x + nx * (yp + (int64_t)ny * z)]);
+    R a2 = fmin(Din[x + nx * (y + (int64_t)ny * zm)], Din[x + nx * (y + (int64_t)ny * zp)]);
+    R d = godunov3<R>(a0, a1, a2, h);
+    R out = cur;
+    if (d < cur && d <= r_grid) {
+      out = d;
+      changed = true;
+    }
+    Dout[b] = out;
   }
-  Dout[b] = out;
+  if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
 }
 
 // iters = 1 + index of the first sweep that changed nothing (or -1), and a
@@ -99,7 +107,8 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
   R h = (R)ctx->p.h, rg = (R)ctx->p.r_grid;
   R* buf[2] = {D, (R*)ctx->D[1]};
   unsigned nb = (unsigned)((nbox + 255) / 256);
-  dim3 sg((unsigned)(ny * nz), (unsigned)((nx + 127) / 128));
+  int64_t items = (int64_t)ny * nz * ((nx + 127) / 128);
+  unsigned sg = (unsigned)std::min<int64_t>(items, 152 * 16);
   int iter_max = ctx->p.iter_max;
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(int32_t) * (size_t)(iter_max + 2), st));
   DCM_LAUNCH(ctx, k_dist_init<R>, nb, 256, 0, st, s, iface, nbox, buf[0], buf[1]);

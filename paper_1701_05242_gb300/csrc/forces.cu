@@ -18,42 +18,9 @@
 // zeroes every term.
 #include <algorithm>
 
-#include "dcm_internal.cuh"
+#include "forces_core.cuh"
 
 namespace dcm {
-
-constexpr int kForceBlock = 128;
-
-template <typename R>
-struct ForceArgs {
-  Grid<R> g;
-  R rc_max;
-  int ntypes;
-  R eps24[16], eps4[16], sig2[16];
-  int shift;
-};
-
-__device__ __forceinline__ float recip(float x) {
-  // hardware approximation refined by one Newton-Raphson step
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  float e = fmaf(-x, y, 1.0f);
-  return fmaf(y, e, y);
-}
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-
-// particle type stored as a number in w, clamped to [0, ntypes)
-template <typename R>
-__device__ __forceinline__ int type_of(R w, int ntypes) {
-  int t = (int)w;
-  return t < 0 ? 0 : (t >= ntypes ? ntypes - 1 : t);
-}
-
-// unwrapped cell index (no clamp) of a coordinate, used only for culling
-template <typename R>
-__device__ __forceinline__ int ufloor(R v) {
-  return (int)floor(v);
-}
 
 // Per-warp partial sums of (E, W, pairs): summed across the warp in the
 // working precision (32 terms), then stored as one FP64 partial per warp;
@@ -79,124 +46,10 @@ __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typenam
                                                         ForceArgs<R> a, typename RT<R>::R4* __restrict__ force,
                                                         double* __restrict__ part, int64_t nwarp) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  R fx = 0, fy = 0, fz = 0, en = 0, vir = 0;
-  int npair = 0;
-  if (i < n) {
-    const Grid<R>& g = a.g;
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const R l = g.edge, il = g.inv_edge;
-    auto pi = ldg4(pos + i);
-    // cutoffs outside [0, rc_max] (or NaN) are clamped: the stencil then never
-    // reaches past one periodic image, which keeps every cell index in range
-    R rci = rc[i];
-    if (!(rci <= a.rc_max)) rci = a.rc_max;
-    if (!(rci > (R)0)) rci = (R)0;
-    const R rc2 = rci * rci;
-    const R rc2s = rc2 * (R)1.000004;  // culling slack; the pair test below is exact
-    const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
-    R ushift[4] = {0, 0, 0, 0};
-    if (a.shift) {
-      for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
-        int tp = ti * a.ntypes + t;
-        R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
-        R s6 = s2 * s2 * s2;
-        ushift[t] = (TYPED ? a.eps4[tp] : (R)4) * s6 * (s6 - (R)1);
-      }
-    }
-    const int cx = cell_coord<R>(pi.x, l, il, nx);
-    const int cy = cell_coord<R>(pi.y, l, il, ny);
-    const int cz = cell_coord<R>(pi.z, l, il, nz);
-    const int H = (int)ceil(rci * il);
-    for (int uz = cz - H; uz <= cz + H; ++uz) {
-      R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
-      R gz2 = gz * gz;
-      if (gz2 >= rc2s) continue;
-      int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
-      R zi = uz >= nz ? pi.z - g.L[2] : pi.z;       // image +L: shift i
-      R zsh = uz < 0 ? -g.L[2] : (R)0;               // image -L: shift j
-      for (int uy = cy - H; uy <= cy + H; ++uy) {
-        R gy = uy > cy ? (R)uy * l - pi.y : (uy < cy ? pi.y - (R)(uy + 1) * l : (R)0);
-        R gyz2 = gz2 + gy * gy;
-        if (gyz2 >= rc2s) continue;
-        int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
-        R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
-        R ysh = uy < 0 ? -g.L[1] : (R)0;
-        R wx = sqrt(rc2s - gyz2);
-        int ulo = ufloor<R>((pi.x - wx) * il - (R)5e-4);
-        int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
-        ulo = max(ulo, cx - H);
-        uhi = min(uhi, cx + H);
-        const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
-        // up to three segments: u < 0 (image -L), 0 <= u < nx, u >= nx (image +L)
-#pragma unroll 1
-        for (int seg = 0; seg < 3; ++seg) {
-          int a0, a1;
-          R xi, xsh;
-          if (seg == 0) {
-            a0 = ulo;
-            a1 = min(uhi, -1);
-            xi = pi.x;
-            xsh = -g.L[0];
-          } else if (seg == 1) {
-            a0 = max(ulo, 0);
-            a1 = min(uhi, nx - 1);
-            xi = pi.x;
-            xsh = (R)0;
-          } else {
-            a0 = max(ulo, nx);
-            a1 = uhi;
-            xi = pi.x - g.L[0];
-            xsh = (R)0;
-          }
-          if (a0 > a1) continue;
-          int w0 = seg == 0 ? a0 + nx : (seg == 2 ? a0 - nx : a0);
-          int w1 = seg == 0 ? a1 + nx : (seg == 2 ? a1 - nx : a1);
-          int j0 = __ldg(start + row + w0), j1 = __ldg(start + row + w1 + 1);
-          for (int j = j0; j < j1; ++j) {
-            auto pj = ldg4(pos + j);
-            R dx = xi - (pj.x + xsh);
-            R dy = yi - (pj.y + ysh);
-            R dz = zi - (pj.z + zsh);
-            R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            bool acc = (r2 < rc2) && (j != (int)i);
-            R inv = recip(r2);
-            inv = acc ? inv : (R)0;
-            R s2, e24, e4, us;
-            if (TYPED) {
-              int tj = type_of(pj.w, a.ntypes);
-              int tp = ti * a.ntypes + tj;
-              s2 = a.sig2[tp] * inv;
-              e24 = a.eps24[tp];
-              e4 = a.eps4[tp];
-              us = tj == 0 ? ushift[0] : (tj == 1 ? ushift[1] : (tj == 2 ? ushift[2] : ushift[3]));
-            } else {
-              s2 = inv;
-              e24 = (R)24;
-              e4 = (R)4;
-              us = ushift[0];
-            }
-            R s6 = s2 * s2 * s2;
-            R pv = e24 * s6 * fma((R)2, s6, (R)-1);  // r . F_ij
-            R fs = pv * inv;
-            fx = fma(fs, dx, fx);
-            fy = fma(fs, dy, fy);
-            fz = fma(fs, dz, fz);
-            R u = e4 * s6 * (s6 - (R)1);
-            en += acc ? u - us : (R)0;
-            vir += pv;
-            npair += acc ? 1 : 0;
-          }
-        }
-      }
-    }
-    typename RT<R>::R4 out;
-    out.x = fx;
-    out.y = fy;
-    out.z = fz;
-    out.w = (R)0.5 * en;
-    force[i] = out;
-  }
-  if (part) warp_partials3<R>((R)0.5 * en, (R)0.5 * vir, npair, part, nwarp);
+  R e_out = 0, w_out = 0;
+  int np = 0;
+  if (i < n) force[i] = force_one<R, TYPED>(pos, start, a.g, a, (int)i, ldg4(pos + i), rc[i], e_out, w_out, np);
+  if (part) warp_partials3<R>(e_out, w_out, np, part, nwarp);
 }
 
 template <typename R>

@@ -1,0 +1,205 @@
+// Per-particle force core shared by the single-system and batched force kernels.
+#pragma once
+
+#include "dcm_internal.cuh"
+
+namespace dcm {
+
+constexpr int kForceBlock = 128;
+
+template <typename R>
+struct ForceArgs {
+  Grid<R> g;
+  R rc_max;
+  int ntypes;
+  R eps24[16], eps4[16], sig2[16];
+  int shift;
+};
+
+__device__ __forceinline__ float recip(float x) {
+  // hardware approximation refined by one Newton-Raphson step
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  float e = fmaf(-x, y, 1.0f);
+  return fmaf(y, e, y);
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// particle type stored as a number in w, clamped to [0, ntypes)
+template <typename R>
+__device__ __forceinline__ int type_of(R w, int ntypes) {
+  int t = (int)w;
+  return t < 0 ? 0 : (t >= ntypes ? ntypes - 1 : t);
+}
+
+// unwrapped cell index (no clamp) of a coordinate, used only for culling
+template <typename R>
+__device__ __forceinline__ int ufloor(R v) {
+  return (int)floor(v);
+}
+
+// Accumulators of one particle.  One type: the constant factors are taken
+// out of the pair loop: F = 24 sum s6 (2 s6 - 1) / r^2 r_ij, U = 4 sum
+// (s6^2 - s6), r.F = 24 sum s6 (2 s6 - 1), with s6 = (1/r^2)^3.  Each pair's
+// s6^2 - s6 is formed before summing: summing s6^2 and s6 separately and
+// subtracting at the end loses the cancellation near r = sigma.  Several
+// types: energy and virial per pair with the pair's eps and sigma.
+template <typename R>
+struct Acc {
+  R fx = 0, fy = 0, fz = 0;
+  R en = 0, vir = 0;
+  int np = 0;
+};
+
+// Pairs of particle i (coordinates xi, yi, zi in the image frame of the
+// segment) with sorted particles [lo, hi).  SJ: the segment's j coordinates
+// need the exact -L image shift (sh); otherwise they are used as loaded.
+template <typename R, bool SJ, bool TYPED>
+__device__ __forceinline__ void pair_range(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi,
+                                           R zi, R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a,
+                                           const R* ushift, Acc<R>& c) {
+#pragma unroll 2
+  for (int j = lo; j < hi; ++j) {
+    auto pj = ldg4(pos + j);
+    R dx, dy, dz;
+    if (SJ) {
+      dx = xi - (pj.x + shx);
+      dy = yi - (pj.y + shy);
+      dz = zi - (pj.z + shz);
+    } else {
+      dx = xi - pj.x;
+      dy = yi - pj.y;
+      dz = zi - pj.z;
+    }
+    R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    bool acc = r2 < rc2;
+    R inv = recip(r2);
+    inv = acc ? inv : (R)0;
+    if (TYPED) {
+      int tj = type_of(pj.w, a.ntypes);
+      int tp = ti * a.ntypes + tj;
+      R s2 = a.sig2[tp] * inv;
+      R s6 = s2 * s2 * s2;
+      R pv = a.eps24[tp] * s6 * fma((R)2, s6, (R)-1);  // r . F_ij
+      R fs = pv * inv;
+      c.fx = fma(fs, dx, c.fx);
+      c.fy = fma(fs, dy, c.fy);
+      c.fz = fma(fs, dz, c.fz);
+      R us = tj == 0 ? ushift[0] : (tj == 1 ? ushift[1] : (tj == 2 ? ushift[2] : ushift[3]));
+      R u = a.eps4[tp] * s6 * (s6 - (R)1);
+      c.en += acc ? u - us : (R)0;
+      c.vir += pv;
+    } else {
+      R s6 = inv * inv * inv;
+      R pv = s6 * fma((R)2, s6, (R)-1);  // r . F_ij / 24
+      R q = pv * inv;                    // |F_ij| / (24 r)
+      c.fx = fma(q, dx, c.fx);
+      c.fy = fma(q, dy, c.fy);
+      c.fz = fma(q, dz, c.fz);
+      c.en += fma(s6, s6, -s6);          // U / 4
+      c.vir += pv;
+    }
+    c.np += acc ? 1 : 0;
+  }
+}
+
+// Forces, energy and virial of particle `self` (position pi, cutoff rc_in)
+// over the cell grid g whose cell starts are start[0 .. ncell] (positions
+// pos, sorted by cell).  Returns the force and writes e_i, w_i, pairs.
+template <typename R, bool TYPED>
+__device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
+                                                        const int32_t* __restrict__ start, const Grid<R>& g,
+                                                        const ForceArgs<R>& a, int self,
+                                                        const typename RT<R>::R4& pi, R rc_in, R& e_out, R& w_out,
+                                                        int& np_out) {
+  Acc<R> c;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const R l = g.edge, il = g.inv_edge;
+  // cutoffs outside [0, rc_max] (or NaN) are clamped: the stencil then never
+  // reaches past one periodic image, which keeps every cell index in range
+  R rci = rc_in;
+  if (!(rci <= a.rc_max)) rci = a.rc_max;
+  if (!(rci > (R)0)) rci = (R)0;
+  const R rc2 = rci * rci;
+  const R rc2s = rc2 * (R)1.000004;  // culling slack; the pair test is exact
+  const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
+  R ushift[4] = {0, 0, 0, 0};
+  if (a.shift) {
+    for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
+      int tp = ti * a.ntypes + t;
+      R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
+      R s6 = s2 * s2 * s2;
+      ushift[t] = (TYPED ? a.eps4[tp] : (R)4) * s6 * (s6 - (R)1);
+    }
+  }
+  const int cx = cell_coord<R>(pi.x, l, il, nx);
+  const int cy = cell_coord<R>(pi.y, l, il, ny);
+  const int cz = cell_coord<R>(pi.z, l, il, nz);
+  const int H = (int)ceil(rci * il);
+  for (int uz = cz - H; uz <= cz + H; ++uz) {
+    R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
+    R gz2 = gz * gz;
+    if (gz2 >= rc2s) continue;
+    int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
+    R zi = uz >= nz ? pi.z - g.L[2] : pi.z;  // image +L: shift i
+    R zsh = uz < 0 ? -g.L[2] : (R)0;          // image -L: shift j
+    for (int uy = cy - H; uy <= cy + H; ++uy) {
+      R gy = uy > cy ? (R)uy * l - pi.y : (uy < cy ? pi.y - (R)(uy + 1) * l : (R)0);
+      R gyz2 = gz2 + gy * gy;
+      if (gyz2 >= rc2s) continue;
+      int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+      R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
+      R ysh = uy < 0 ? -g.L[1] : (R)0;
+      R wx = sqrt(rc2s - gyz2);
+      int ulo = ufloor<R>((pi.x - wx) * il - (R)5e-4);
+      int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
+      ulo = max(ulo, cx - H);
+      uhi = min(uhi, cx + H);
+      const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
+      // segment u < 0: image -L (shift j)
+      if (ulo < 0) {
+        int a1 = min(uhi, -1);
+        int j0 = __ldg(start + row + ulo + nx), j1 = __ldg(start + row + a1 + nx + 1);
+        pair_range<R, true, TYPED>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c);
+      }
+      // segment 0 <= u < nx: no x shift; the particle itself is skipped
+      {
+        int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
+        if (a0 <= a1) {
+          int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
+          if (ysh == (R)0 && zsh == (R)0) {
+            pair_range<R, false, TYPED>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c);
+            pair_range<R, false, TYPED>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c);
+          } else {
+            pair_range<R, true, TYPED>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c);
+          }
+        }
+      }
+      // segment u >= nx: image +L (shift i)
+      if (uhi >= nx) {
+        int a0 = max(ulo, nx);
+        int j0 = __ldg(start + row + a0 - nx), j1 = __ldg(start + row + uhi - nx + 1);
+        pair_range<R, true, TYPED>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c);
+      }
+    }
+  }
+  typename RT<R>::R4 out;
+  if (TYPED) {
+    out.x = c.fx;
+    out.y = c.fy;
+    out.z = c.fz;
+    e_out = (R)0.5 * c.en;
+    w_out = (R)0.5 * c.vir;
+  } else {
+    out.x = (R)24 * c.fx;
+    out.y = (R)24 * c.fy;
+    out.z = (R)24 * c.fz;
+    e_out = (R)2 * c.en - (R)0.5 * (R)c.np * ushift[0];
+    w_out = (R)12 * c.vir;
+  }
+  out.w = e_out;
+  np_out = c.np;
+  return out;
+}
+
+}  // namespace dcm

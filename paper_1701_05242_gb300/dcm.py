@@ -75,6 +75,21 @@ _SIGS = {
     "dcm_step_init": (_i32, [_vp, ctypes.POINTER(dcm_state), _i64, _vp]),
     "dcm_step": (_i32, [_vp, ctypes.POINTER(dcm_state), _i64, ctypes.c_double, _i32, _vp]),
     "dcm_distance_noalloc": (_i32, [ctypes.POINTER(dcm_params), _vp, _vp, _vp, _vp, _vp]),
+    "dcm_batch_create": (_i32, [ctypes.POINTER(dcm_params), _i32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(_i64), ctypes.POINTER(_vp)]),
+    "dcm_batch_destroy": (None, [_vp]),
+    "dcm_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "dcm_batch_offsets": (_i32, [_vp, ctypes.POINTER(_i64)]),
+    "dcm_batch_set_force_block": (_i32, [_vp, _i32]),
+    "dcm_batch_step_init": (_i32, [_vp, ctypes.POINTER(dcm_state), _vp]),
+    "dcm_batch_step": (_i32, [_vp, ctypes.POINTER(dcm_state), ctypes.c_double, _i32, _vp]),
+    "dcm_batch_capture": (_i32, [_vp, ctypes.POINTER(dcm_state), ctypes.c_double, _vp]),
+    "dcm_batch_replay": (_i32, [_vp, ctypes.POINTER(dcm_state), _i32, _vp]),
+    "dcm_batch_graph_steps": (_i32, [_vp]),
+    "dcm_batch_status": (_i32, [_vp, _vp]),
+    "dcm_batch_set_timing": (_i32, [_vp, _i32]),
+    "dcm_batch_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
+    "dcm_batch_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
     "dcm_set_timing": (_i32, [_vp, _i32]),
     "dcm_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "dcm_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
@@ -216,7 +231,7 @@ def dcm_forces(ctx: Context, n, pos_sorted, rc, cell_start, force, totals=None, 
 class State:
     """Double-buffered device state for dcm_step (tensors kept alive here)."""
 
-    def __init__(self, ctx: Context, pos4, vel4, ids=None):
+    def __init__(self, ctx, pos4, vel4, ids=None):
         n = pos4.shape[0]
         dev = pos4.device
         real = ctx.real
@@ -283,4 +298,94 @@ def dcm_stage_times(ctx: Context):
 def dcm_launch_count(ctx: Context, reset: bool = False) -> int:
     c = _i64()
     ctx.check(lib.dcm_launch_count(ctx.handle, ctypes.byref(c), 1 if reset else 0))
+    return c.value
+
+
+# ---------------------------------------------------------------- batched form
+class Batch:
+    """Owns one dcm_batch: R replicas sharing params except box and size."""
+
+    def __init__(self, params: dcm_params, boxes, counts):
+        self.params = params
+        self.R = len(counts)
+        bx = (ctypes.c_double * (3 * self.R))(*[float(v) for b in boxes for v in b])
+        cn = (_i64 * self.R)(*[int(c) for c in counts])
+        h = ctypes.c_void_p()
+        rc = lib.dcm_batch_create(ctypes.byref(params), self.R, bx, cn, ctypes.byref(h))
+        if rc != DCM_OK:
+            raise DcmError(rc, "dcm_batch_create failed")
+        self.handle = h
+        off = (_i64 * (self.R + 1))()
+        lib.dcm_batch_offsets(h, off)
+        self.offsets = list(off)
+        self.n = self.offsets[-1]
+        self.real = torch.float32 if params.precision == DCM_PREC_MIXED else torch.float64
+
+    def check(self, rc):
+        if rc != DCM_OK:
+            raise DcmError(rc, lib.dcm_batch_last_error(self.handle).decode())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.dcm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchState(State):
+    """Concatenated double-buffered state of a Batch; thermo has 4 R entries."""
+
+    def __init__(self, batch: Batch, pos4, vel4, ids=None):
+        super().__init__(batch, pos4, vel4, ids)
+        self.thermo = torch.zeros(4 * batch.R, dtype=torch.float64, device=pos4.device)
+        self.c.thermo = self.thermo.data_ptr()
+
+
+def dcm_batch_set_force_block(b: Batch, threads: int):
+    b.check(lib.dcm_batch_set_force_block(b.handle, int(threads)))
+
+
+def dcm_batch_step_init(b: Batch, st: BatchState, stream=None):
+    b.check(lib.dcm_batch_step_init(b.handle, ctypes.byref(st.c), _stream(stream)))
+
+
+def dcm_batch_step(b: Batch, st: BatchState, dt: float, nsteps: int = 1, stream=None):
+    b.check(lib.dcm_batch_step(b.handle, ctypes.byref(st.c), float(dt), int(nsteps), _stream(stream)))
+
+
+def dcm_batch_capture(b: Batch, st: BatchState, dt: float, stream):
+    b.check(lib.dcm_batch_capture(b.handle, ctypes.byref(st.c), float(dt), _stream(stream)))
+
+
+def dcm_batch_replay(b: Batch, st: BatchState, ngraphs: int, stream):
+    b.check(lib.dcm_batch_replay(b.handle, ctypes.byref(st.c), int(ngraphs), _stream(stream)))
+
+
+def dcm_batch_graph_steps(b: Batch) -> int:
+    return lib.dcm_batch_graph_steps(b.handle)
+
+
+def dcm_batch_status(b: Batch, stream=None):
+    return lib.dcm_batch_status(b.handle, _stream(stream))
+
+
+def dcm_batch_set_timing(b: Batch, capacity: int = 4096):
+    b.check(lib.dcm_batch_set_timing(b.handle, int(capacity)))
+
+
+def dcm_batch_stage_times(b: Batch):
+    ms = (ctypes.c_double * len(STAGES))()
+    cnt = (_i64 * len(STAGES))()
+    b.check(lib.dcm_batch_stage_times(b.handle, ms, cnt))
+    return {name: (ms[k], cnt[k]) for k, name in enumerate(STAGES)}
+
+
+def dcm_batch_launch_count(b: Batch, reset: bool = False) -> int:
+    c = _i64()
+    b.check(lib.dcm_batch_launch_count(b.handle, ctypes.byref(c), 1 if reset else 0))
     return c.value

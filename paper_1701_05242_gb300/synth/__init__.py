@@ -302,9 +302,12 @@ def make_slab(spec: SlabSpec) -> Slab:
     return Slab(spec, pos, vel, types, lj)
 
 
-def batch_specs(count: int = 64, n_lo: int = 2000, n_hi: int = 200000):
-    """Independent replicas: N log-uniform in [n_lo, n_hi], aspect 1:1:4, rho_l ~ U[0.7, 0.85],
-    T* ~ U[0.65, 0.85], rho_v = 0.02, seeds 0..count-1."""
+def batch_specs(count: int = 64, n_lo: int = 2000, n_hi: int = 200000, edge: float = 1.5):
+    """Independent replicas: target N log-uniform in [n_lo, n_hi], aspect
+    1:1:4, rho_l ~ U[0.7, 0.85], T* ~ U[0.65, 0.85], rho_v = 0.02, seeds
+    0..count-1.  The box edge is rounded to a multiple of `edge` (at least 8
+    edges, so that a cutoff of 6 fits half the box); N then follows from the
+    densities."""
     out = []
     for s in range(count):
         u = uniform(100000 + s, 3)
@@ -313,6 +316,6 @@ def batch_specs(count: int = 64, n_lo: int = 2000, n_hi: int = 200000):
         temp = 0.65 + 0.2 * u[2]
         # N = L^2 * 4L * (rho_l/3 + 2 rho_v/3)
         L = (n_target / (4.0 * (rho_l + 2.0 * 0.02) / 3.0)) ** (1.0 / 3.0)
-        out.append(SlabSpec(box=(L, L, 4.0 * L), rho_l=rho_l, temperature=temp, seed=s,
-                            name=f"replica_{s}"))
+        L = edge * max(8, int(round(L / edge)))
+        out.append(SlabSpec(box=(L, L, 4.0 * L), rho_l=rho_l, temperature=temp, seed=s, name=f"replica_{s}"))
     return out

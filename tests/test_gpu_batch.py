@@ -1,0 +1,126 @@
+"""Batched form: independent replicas stepped in one launch per stage.
+
+Each replica of a batch must evolve exactly as the same system stepped alone
+through dcm_step (the per-particle arithmetic is the same; only the order of
+the per-replica energy sums differs), a captured CUDA graph must replay the
+same trajectory as direct stepping, and the FP64 batch must track the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1701_05242_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+K = 5
+DT = 0.005
+
+
+@pytest.fixture(scope="module")
+def D():
+    import paper_1701_05242_gb300.dcm as dcm
+    return dcm
+
+
+@pytest.fixture(scope="module")
+def replicas():
+    out = []
+    for r, (L, rho) in enumerate([(12.0, 0.8), (13.5, 0.7), (15.0, 0.85)]):
+        spec = synth.SlabSpec(box=(L, L, 4 * L), rho_l=rho, seed=r, name=f"rep{r}")
+        out.append(synth.make_slab(spec))
+    return out
+
+
+def batch_state(D, reps, prec):
+    real = torch.float32 if prec == D.DCM_PREC_MIXED else torch.float64
+    p = D.make_params((1, 1, 1), precision=prec, recompute_every=K)
+    b = D.Batch(p, [s.box for s in reps], [s.n for s in reps])
+    pos = np.concatenate([s.pos for s in reps])
+    vel = np.concatenate([s.vel for s in reps])
+    st = D.BatchState(b, D.to_real4(torch.from_numpy(pos), None, real), D.to_real4(torch.from_numpy(vel), None, real))
+    return b, st
+
+
+def single_run(D, slab, prec, nsteps):
+    real = torch.float32 if prec == D.DCM_PREC_MIXED else torch.float64
+    ctx = D.Context(D.make_params(slab.box, n_max=slab.n, precision=prec, recompute_every=K))
+    st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real), D.to_real4(torch.from_numpy(slab.vel), None, real))
+    D.dcm_step_init(ctx, st)
+    D.dcm_step(ctx, st, DT, nsteps)
+    pos, vel, rc, ids = st.current()
+    order = torch.argsort(ids.long())
+    return pos[order].cpu().numpy(), st.thermo.cpu().numpy()
+
+
+def by_id(st, b, r):
+    pos, vel, rc, ids = st.current()
+    a, e = b.offsets[r], b.offsets[r + 1]
+    idr = ids[a:e].long() - a
+    out = torch.empty_like(pos[a:e])
+    out[idr] = pos[a:e]
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_matches_single_systems(D, replicas, prec):
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    nsteps = 2 * K + 2
+    b, st = batch_state(D, replicas, P)
+    D.dcm_batch_step_init(b, st)
+    D.dcm_batch_step(b, st, DT, nsteps)
+    assert D.dcm_batch_status(b) == D.DCM_OK
+    th = st.thermo.cpu().numpy().reshape(-1, 4)
+    for r, slab in enumerate(replicas):
+        pos1, th1 = single_run(D, slab, P, nsteps)
+        pb = by_id(st, b, r)
+        assert np.abs(pb - pos1).max() <= (1e-12 if prec == "fp64" else 1e-5)
+        tol = 1e-10 if prec == "fp64" else 1e-6
+        for q in range(3):
+            assert th[r, q] == pytest.approx(th1[q], rel=tol, abs=1e-9)
+        assert th[r, 3] == th1[3]
+
+
+def test_batch_graph_replay_equals_stepping(D, replicas):
+    P = D.DCM_PREC_MIXED
+    b1, s1 = batch_state(D, replicas, P)
+    D.dcm_batch_step_init(b1, s1)
+    D.dcm_batch_step(b1, s1, DT, 2 * K)
+    b2, s2 = batch_state(D, replicas, P)
+    D.dcm_batch_step_init(b2, s2)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    D.dcm_batch_capture(b2, s2, DT, stream)
+    assert D.dcm_batch_graph_steps(b2) == (2 * K if K % 2 else K)
+    reps = (2 * K) // D.dcm_batch_graph_steps(b2)
+    D.dcm_batch_replay(b2, s2, reps, stream)
+    stream.synchronize()
+    assert s2.c.t == s1.c.t == 2 * K
+    assert torch.equal(s1.current()[0], s2.current()[0])
+    assert torch.equal(s1.thermo, s2.thermo)
+    assert D.dcm_batch_status(b2) == D.DCM_OK
+
+
+def test_batch_fp64_tracks_oracle(D, replicas):
+    b, st = batch_state(D, replicas, D.DCM_PREC_FP64)
+    D.dcm_batch_step_init(b, st)
+    D.dcm_batch_step(b, st, DT, 3)
+    th = st.thermo.cpu().numpy().reshape(-1, 4)
+    for r, slab in enumerate(replicas):
+        p = O.Params(box=slab.box, recompute_every=K)
+        o = O.init_state(slab.pos, slab.vel, p)
+        for _ in range(3):
+            o = O.step(o, DT, p)
+        assert th[r, 0] == pytest.approx(o.E, rel=1e-9)
+        assert th[r, 2] == pytest.approx(O.kinetic(o.vel), rel=1e-9)
+        pb = by_id(st, b, r)
+        d = np.abs(pb[:, :3] - o.pos)
+        d = np.minimum(d, np.array(slab.box) - d)
+        assert d.max() <= 1e-9
+
+
+def test_batch_rejects_bad_replica(D):
+    p = D.make_params((1, 1, 1))
+    with pytest.raises(D.DcmError):
+        D.Batch(p, [(12.0, 12.0, 48.0), (12.0, 12.0, 47.0)], [10, 10])
