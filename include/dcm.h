@@ -213,6 +213,24 @@ int dcm_cutoffs(dcm_ctx* ctx, int64_t n, const void* pos, const void* D, void* r
 int dcm_forces(dcm_ctx* ctx, int64_t n, const void* pos_sorted, const void* rc,
                const int32_t* cell_start, void* force, double* totals, dcm_stream_t stream);
 
+/* Replace the LJ parameters of ctx (host-side only, validated; takes effect
+ * for later calls).  Used when eps and sigma are being optimised. */
+int dcm_set_lj(dcm_ctx* ctx, int32_t ntypes, const double* eps, const double* sigma);
+
+/* Adjoint of dcm_forces (differentiation form; the paper has no gradient: this
+ * differentiates its force and energy, Section 2.4, with the cutoffs held
+ * fixed).  For a scalar loss L(F, E) with upstream dL_dF = dL/dF (real4[n],
+ * w ignored) and dL_dE = dL/dE:
+ *   dL_dpos[k] = sum_{j in N(k)} [J(r_kj) A_k - dL_dE/2 phi_kj]
+ *              + sum_{j : k in N(j)} [-J(r_kj) A_j - dL_dE/2 phi_kj]
+ * with N(i) = {j != i : |r_ij| < rc_i}, phi_ij the pair force on i and J its
+ * Jacobian (the second sum runs over the particles whose own cutoff reaches
+ * k, so the stencil has radius rc_max).  dL_dparams (device double[2 ntypes],
+ * nullable) receives dL/deps_a then dL/dsigma_a, chained through
+ * Lorentz-Berthelot mixing.  Inputs as for dcm_forces (sorted order). */
+int dcm_forces_backward(dcm_ctx* ctx, int64_t n, const void* pos_sorted, const void* rc, const int32_t* cell_start,
+                        const void* dL_dF, double dL_dE, void* dL_dpos, double* dL_dparams, dcm_stream_t stream);
+
 /* Initial evaluation before the first step: bin (state reordered into buffer
  * 1-cur), interface, distances, cutoffs and forces for the current positions;
  * sets t = 0 and thermo.  Synchronous only if distance sweeps need a host

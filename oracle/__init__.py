@@ -79,6 +79,8 @@ def _load():
                                             _f64p, I32, I32, _f64p, _f64p, _f64p, _i64p]),
                 "orc_forces_subset": (None, [I64, _f64p, _i32p, _f64p, _f64p, _f64p, _i64p, I32, _f64p, _f64p,
                                              I32, I64, _i64p, I32, _f64p, _f64p, _f64p, _i64p]),
+                "orc_adjoint_brute": (None, [I64, _f64p, _i32p, _f64p, _f64p, I32, _f64p, _f64p, I32, _f64p, D,
+                                             _f64p, _f64p, _f64p]),
                 "orc_kick": (None, [I64, _f64p, _f64p, D]),
                 "orc_drift": (None, [I64, _f64p, _f64p, D, _f64p]),
                 "orc_kinetic": (D, [I64, _f64p]),
@@ -300,6 +302,50 @@ def forces_subset(pos, rc, box, l, idx, types=None, eps=(1.0,), sigma=(1.0,), sh
                               _p(sigma, _f64p), int(shift), m, _p(idx, _i64p), int(nthreads), _p(F, _f64p),
                               _p(e, _f64p), _p(w, _f64p), _p(npairs, _i64p))
     return F[:m], e[:m], w[:m], npairs[:m]
+
+
+def adjoint(pos, rc, box, A, dLdE, types=None, eps=(1.0,), sigma=(1.0,), shift=False):
+    """Gradient of a loss L(F, E) with respect to positions and per-type LJ
+    parameters, cutoffs held fixed (O(N^2), FP64).  A = dL/dF (N x 3),
+    dLdE = dL/dE.  Returns (dL/dpos (N x 3), dL/deps (ntypes), dL/dsigma
+    (ntypes)); the type-pair sums are chained through Lorentz-Berthelot
+    mixing, eps_ab = sqrt(eps_a eps_b), sigma_ab = (sigma_a + sigma_b) / 2."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    rc = _f64(np.broadcast_to(rc, (n,)))
+    A = _f64(A).reshape(-1, 3)
+    eps, sigma = _lj_arrays(eps, sigma)
+    nt = eps.size
+    t = None if types is None else np.ascontiguousarray(types, dtype=np.int32)
+    G = np.empty((max(n, 1), 3))
+    dep = np.empty(nt * nt)
+    dsp = np.empty(nt * nt)
+    _load().orc_adjoint_brute(n, _p(pos, _f64p), None if t is None else _p(t, _i32p), _p(rc, _f64p),
+                              _p(_vec3(box), _f64p), nt, _p(eps, _f64p), _p(sigma, _f64p), int(shift),
+                              _p(A, _f64p), float(dLdE), _p(G, _f64p), _p(dep, _f64p), _p(dsp, _f64p))
+    de, ds = mix_chain(dep, dsp, eps)
+    return G[:n], de, ds
+
+
+def mix_chain(deps_pair, dsig_pair, eps):
+    """Chain per-type-pair parameter gradients to per-type gradients through
+    eps_ab = sqrt(eps_a eps_b) and sigma_ab = (sigma_a + sigma_b) / 2."""
+    eps = np.asarray(eps, np.float64)
+    nt = eps.size
+    de = np.zeros(nt)
+    ds = np.zeros(nt)
+    for a in range(nt):
+        for b in range(nt):
+            p = a * nt + b
+            if a == b:
+                de[a] += deps_pair[p]
+                ds[a] += dsig_pair[p]
+            else:
+                de[a] += deps_pair[p] * 0.5 * math.sqrt(eps[b] / eps[a])
+                de[b] += deps_pair[p] * 0.5 * math.sqrt(eps[a] / eps[b])
+                ds[a] += 0.5 * dsig_pair[p]
+                ds[b] += 0.5 * dsig_pair[p]
+    return de, ds
 
 
 def lj_pair(r, eps=1.0, sigma=1.0):

@@ -591,6 +591,81 @@ void orc_forces_cells(int64_t n, const double* pos, const int32_t* type, const d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Adjoint of the force/energy map (extension for differentiation).          */
+/* For a scalar loss L(F, E) with upstream A_i = dL/dF_i and dLdE = dL/dE,    */
+/* cutoffs held fixed:                                                       */
+/*   dL/dr_k = sum_{j in N(k)} [ J(r_kj) A_k - dLdE/2 phi_kj ]               */
+/*           + sum_{j : k in N(j)} [ -J(r_kj) A_j - dLdE/2 phi_kj ]          */
+/* with N(i) = {j != i : |r_ij| < rc_i}, phi_ij = g(r) r_ij the force on i   */
+/* from j, g(r) = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2 and the (symmetric)    */
+/* Jacobian J(r) = d phi / d r_i = g I + (g'(r) / r) r r^T,                  */
+/* g'(r) / r = 24 eps [-28 (s/r)^12 + 8 (s/r)^6] / r^4.                       */
+/* Per type pair p = (a, b) of a forward pair (i, j in N(i)):                */
+/*   dL/deps_p   += A_i . phi_ij / eps_p + dLdE/2 (U - Ushift) / eps_p        */
+/*   dL/dsigma_p += A_i . dphi/dsigma + dLdE/2 d(U - Ushift)/dsigma           */
+/* with dg/dsigma = (24 eps / sigma) [24 (s/r)^12 - 6 (s/r)^6] / r^2 and      */
+/* dU/dsigma = (4 eps / sigma) [12 (s/r)^12 - 6 (s/r)^6] (Ushift = U(rc_i)).  */
+/* O(N^2) over all ordered pairs.                                            */
+/* ------------------------------------------------------------------------ */
+static void lj_terms(double r2, double eps, double sig2, double* g, double* gpr, double* u) {
+  double s2 = sig2 / r2;
+  double s6 = s2 * s2 * s2, s12 = s6 * s6;
+  *g = 24.0 * eps * (2.0 * s12 - s6) / r2;
+  *gpr = 24.0 * eps * (-28.0 * s12 + 8.0 * s6) / (r2 * r2);
+  *u = 4.0 * eps * (s12 - s6);
+}
+
+void orc_adjoint_brute(int64_t n, const double* pos, const int32_t* type, const double* rc, const double* L,
+                       int ntypes, const double* eps, const double* sigma, int shift, const double* A,
+                       double dLdE, double* G, double* deps_pair, double* dsig_pair) {
+  ljtab_t tab;
+  lj_table(ntypes, eps, sigma, &tab);
+  for (int p = 0; p < ntypes * ntypes; ++p) deps_pair[p] = dsig_pair[p] = 0.0;
+  for (int64_t k = 0; k < n; ++k) {
+    double gk[3] = {0, 0, 0};
+    int tk = type ? type[k] : 0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == k) continue;
+      int tj = type ? type[j] : 0;
+      double r[3] = {min_image(pos[3 * k] - pos[3 * j], L[0]), min_image(pos[3 * k + 1] - pos[3 * j + 1], L[1]),
+                     min_image(pos[3 * k + 2] - pos[3 * j + 2], L[2])};
+      double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      int p = tk * ntypes + tj;
+      double g, gpr, u;
+      lj_terms(r2, tab.eps[p], tab.sig2[p], &g, &gpr, &u);
+      int fwd = r2 < rc[k] * rc[k];  /* j in N(k)  */
+      int rev = r2 < rc[j] * rc[j];  /* k in N(j)  */
+      if (fwd) {
+        const double* a = A + 3 * k;
+        double ra = r[0] * a[0] + r[1] * a[1] + r[2] * a[2];
+        for (int d = 0; d < 3; ++d) gk[d] += g * a[d] + gpr * ra * r[d] - 0.5 * dLdE * g * r[d];
+        /* parameter gradients of the forward pair (k, j) */
+        double e = tab.eps[p], sg = sqrt(tab.sig2[p]);
+        double s2 = tab.sig2[p] / r2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+        double dg_dsig = 24.0 * e / sg * (24.0 * s12 - 6.0 * s6) / r2;
+        double du_dsig = 4.0 * e / sg * (12.0 * s12 - 6.0 * s6);
+        double uc = 0.0, duc_dsig = 0.0;
+        if (shift) {
+          double c2 = tab.sig2[p] / (rc[k] * rc[k]), c6 = c2 * c2 * c2, c12 = c6 * c6;
+          uc = 4.0 * e * (c12 - c6);
+          duc_dsig = 4.0 * e / sg * (12.0 * c12 - 6.0 * c6);
+        }
+        deps_pair[p] += (g * ra) / e + 0.5 * dLdE * (u - uc) / e;
+        dsig_pair[p] += dg_dsig * ra + 0.5 * dLdE * (du_dsig - duc_dsig);
+      }
+      if (rev) {
+        const double* a = A + 3 * j;
+        double ra = r[0] * a[0] + r[1] * a[1] + r[2] * a[2];
+        for (int d = 0; d < 3; ++d) gk[d] += -(g * a[d] + gpr * ra * r[d]) - 0.5 * dLdE * g * r[d];
+      }
+    }
+    G[3 * k] = gk[0];
+    G[3 * k + 1] = gk[1];
+    G[3 * k + 2] = gk[2];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Velocity Verlet (Section 2, box 5 of Fig. 3), unit masses.                */
 /* ------------------------------------------------------------------------ */
 void orc_kick(int64_t n, double* vel, const double* F, double half_dt) {

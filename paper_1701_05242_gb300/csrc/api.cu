@@ -216,7 +216,8 @@ struct ScratchPlan {
   int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags;
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
-           2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256;
+           2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
+           8 * 32 * red_cap + 8 * 48;
   }
 };
 
@@ -255,7 +256,7 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
   if (!ctx) return;
   void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
                  ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
-                 ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp};
+                 ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -315,6 +316,8 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   alloc((void**)&ctx->red, 8 * 3 * s.red_cap);
   alloc((void**)&ctx->totals, 8 * 8);
   alloc((void**)&ctx->red_tmp, 8 * 8 * 256);
+  alloc((void**)&ctx->adj_part, 8 * 32 * s.red_cap);
+  alloc((void**)&ctx->adj_pairs, 8 * 48);
   if (ok && cudaMallocHost((void**)&ctx->host_status, 16) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
@@ -507,4 +510,41 @@ extern "C" int dcm_launch_count(dcm_ctx* ctx, int64_t* count, int32_t reset) {
   *count = ctx->launches;
   if (reset) ctx->launches = 0;
   return DCM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// differentiation
+// ---------------------------------------------------------------------------
+extern "C" int dcm_set_lj(dcm_ctx* ctx, int32_t ntypes, const double* eps, const double* sigma) {
+  if (!ctx || !eps || !sigma) return DCM_ERR_INVALID_ARG;
+  dcm_params q = ctx->p;
+  q.ntypes = ntypes;
+  for (int k = 0; k < 4; ++k) {
+    q.eps[k] = k < ntypes ? eps[k] : 1.0;
+    q.sigma[k] = k < ntypes ? sigma[k] : 1.0;
+  }
+  char msg[256];
+  int r = dcm_validate_params(&q, msg, sizeof(msg));
+  if (r) return set_error(ctx, r, "%s", msg);
+  ctx->p.ntypes = ntypes;
+  for (int k = 0; k < 4; ++k) {
+    ctx->p.eps[k] = q.eps[k];
+    ctx->p.sigma[k] = q.sigma[k];
+  }
+  return DCM_OK;
+}
+
+extern "C" int dcm_forces_backward(dcm_ctx* ctx, int64_t n, const void* pos_sorted, const void* rc,
+                                   const int32_t* cell_start, const void* dL_dF, double dL_dE, void* dL_dpos,
+                                   double* dL_dparams, dcm_stream_t stream) {
+  if (!ctx) return DCM_ERR_INVALID_ARG;
+  int r = check_n(ctx, n);
+  if (r) return r;
+  REQUIRE(cell_start && (n == 0 || (pos_sorted && rc && dL_dF && dL_dpos)), "dcm_forces_backward: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->precision == DCM_PREC_MIXED)
+    return lj_adjoint<float>(ctx, n, (const float4*)pos_sorted, (const float*)rc, cell_start, (const float4*)dL_dF,
+                             dL_dE, (float4*)dL_dpos, dL_dparams, st);
+  return lj_adjoint<double>(ctx, n, (const dvec4*)pos_sorted, (const double*)rc, cell_start, (const dvec4*)dL_dF,
+                            dL_dE, (dvec4*)dL_dpos, dL_dparams, st);
 }

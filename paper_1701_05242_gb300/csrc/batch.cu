@@ -561,7 +561,7 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     a.shift = b->p.shift_energy;
     a.rc_max = (R)b->p.rc_max;
     int bs = b->force_block;
-    auto kern = t.ntypes > 1 ? k_b_forces<R, true> : k_b_forces<R, false>;
+    auto kern = lj_general(t) ? k_b_forces<R, true> : k_b_forces<R, false>;
     stage_begin(ctx, DCM_STAGE_FORCES, st);
     DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
                b->rep_of_particle, force, (R*)b->w_i, b->np_i);

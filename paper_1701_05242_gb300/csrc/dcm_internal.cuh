@@ -105,6 +105,8 @@ struct dcm_ctx {
   int32_t* thr;             // [8]: gmin, gmax, T, sweeps, ...
   double* red;              // reduction partials
   double* red_tmp;          // [8 * 256] first-level chunk sums
+  double* adj_part;         // [32][red_cap] adjoint parameter-gradient partials
+  double* adj_pairs;        // [48]: per-pair eps sums, per-pair sigma sums, eps values
   double* totals;           // [4]
   int32_t* host_status;     // pinned host mirror
   int64_t red_cap;          // number of partial slots in red (per quantity)
@@ -137,6 +139,11 @@ Grid<R> cell_grid(const dcm_ctx* ctx);
 template <typename R>
 Grid<R> box_grid(const dcm_ctx* ctx);
 LJTable lj_table(const dcm_params& p);
+// The one-type kernels take eps = sigma = 1 as constants; anything else uses
+// the per-pair parameter path.
+inline bool lj_general(const LJTable& t) {
+  return t.ntypes > 1 || t.deps24[0] != 24.0 || t.dsig2[0] != 1.0;
+}
 
 // ---- launchers (one per translation unit) ----------------------------------
 // bin.cu
@@ -171,6 +178,11 @@ int assign_cutoffs(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const
 template <typename R>
 int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc,
               const int32_t* cell_start, typename RT<R>::R4* force, double* totals, cudaStream_t st);
+
+// adjoint.cu
+template <typename R>
+int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, const int32_t* cell_start,
+               const typename RT<R>::R4* A, double dlde, typename RT<R>::R4* G, double* dparams, cudaStream_t st);
 
 // step.cu
 template <typename R>

@@ -75,7 +75,7 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   if (totals && nwarp > ctx->red_cap)
     return set_error(ctx, DCM_ERR_CAPACITY, "force reduction needs %lld partials", (long long)nwarp);
   double* part = totals ? ctx->red : nullptr;
-  auto kern = t.ntypes > 1 ? k_forces<R, true> : k_forces<R, false>;
+  auto kern = lj_general(t) ? k_forces<R, true> : k_forces<R, false>;
   stage_begin(ctx, DCM_STAGE_FORCES, st);
   DCM_LAUNCH(ctx, kern, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, a, force, part, nwarp);
   stage_end(ctx, DCM_STAGE_FORCES, st);

@@ -90,6 +90,8 @@ _SIGS = {
     "dcm_batch_set_timing": (_i32, [_vp, _i32]),
     "dcm_batch_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "dcm_batch_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
+    "dcm_set_lj": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "dcm_forces_backward": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "dcm_set_timing": (_i32, [_vp, _i32]),
     "dcm_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "dcm_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
@@ -226,6 +228,19 @@ def dcm_cutoffs(ctx: Context, n, pos, D, rc, stream=None):
 def dcm_forces(ctx: Context, n, pos_sorted, rc, cell_start, force, totals=None, stream=None):
     ctx.check(lib.dcm_forces(ctx.handle, n, _ptr(pos_sorted), _ptr(rc), _ptr(cell_start), _ptr(force),
                              _ptr(totals), _stream(stream)))
+
+
+def dcm_set_lj(ctx: Context, eps, sigma):
+    nt = len(eps)
+    e = (ctypes.c_double * nt)(*[float(x) for x in eps])
+    sg = (ctypes.c_double * nt)(*[float(x) for x in sigma])
+    ctx.check(lib.dcm_set_lj(ctx.handle, nt, e, sg))
+
+
+def dcm_forces_backward(ctx: Context, n, pos_sorted, rc, cell_start, dL_dF, dL_dE, dL_dpos, dL_dparams=None,
+                        stream=None):
+    ctx.check(lib.dcm_forces_backward(ctx.handle, n, _ptr(pos_sorted), _ptr(rc), _ptr(cell_start), _ptr(dL_dF),
+                                      float(dL_dE), _ptr(dL_dpos), _ptr(dL_dparams), _stream(stream)))
 
 
 class State:
