@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="slab_16m")
     ap.add_argument("--cell-edge", type=float, default=1.5, help="force-cell edge l (density grid h stays 1.5)")
+    ap.add_argument("--skin", type=float, default=0.0, help="Verlet-list skin (0: forces from cell lists every step)")
+    ap.add_argument("--force-kernel", type=int, default=0, help="cell-list force kernel (DCM_FORCE_*; 0: auto)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -273,7 +275,8 @@ def run_gb300(args):
     stream = torch.cuda.current_stream(dev)
 
     def new_state(prec):
-        p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE, l=args.cell_edge)
+        p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE, l=args.cell_edge,
+                          skin=args.skin, force_kernel=args.force_kernel)
         ctx = D.Context(p)
         real = ctx.real
         st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real, dev),
@@ -323,7 +326,8 @@ def run_gb300(args):
     peak_tinstr = sms * FP32_LANES_PER_SM * fmax * 1e6 / 1e12
     f_avg_s = (f_ms / max(f_cnt, 1)) / 1000.0
     achieved = pairs * FLOP_PER_PAIR / f_avg_s / 1e12 if f_avg_s > 0 else None
-    roof = {"bound": "alu", "kernel": "k_forces", "achieved": achieved, "peak": peak_tinstr,
+    fkern = "k_forces_list" if args.skin > 0 else D.FORCE_KERNEL_NAMES[D.dcm_force_kernel(ctx)]
+    roof = {"bound": "alu", "kernel": fkern, "achieved": achieved, "peak": peak_tinstr,
             "unit": "T FP32-instr/s", "frac": (achieved / peak_tinstr) if achieved else None,
             "traffic": recorded_traffic(args.workload), "avg_launch_ms": f_ms / max(f_cnt, 1),
             "pairs_per_launch": pairs, "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
@@ -410,7 +414,7 @@ def run_gb300(args):
                "warmup": args.warmup, "ms_per_step": secs * 1000.0 / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "particles_per_gpu": n, "box": list(slab.box),
-                          "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": args.cell_edge, "dt": DT,
+                          "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": args.cell_edge, "skin": args.skin, "dt": DT,
                           "timesteps_per_step": K_RECOMPUTE, "recompute_every": K_RECOMPUTE,
                           "precision": "fp32 pair math, fp64 totals", "l2": "inputs larger than L2 (positions 248 MB)",
                           "parallelism": f"replicas x{world}"},

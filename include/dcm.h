@@ -65,6 +65,17 @@ enum dcm_status_code {
   DCM_ERR_NOMEM = 6          /* scratch allocation failed in dcm_create */
 };
 
+/* Cell-list force kernels (all compute the same pairs; they differ in how
+ * work is spread over threads).  Kernels 2 and 3 serve one-type FP32 runs
+ * with eps = sigma = 1 and fall back to kernel 1 otherwise; kernel 3 also
+ * needs ceil(rc_max / l) <= 4. */
+enum {
+  DCM_FORCE_AUTO = 0,        /* the fastest measured choice for the configuration */
+  DCM_FORCE_THREAD = 1,      /* one thread per particle i */
+  DCM_FORCE_TWO_PHASE = 2,   /* per-lane shared-memory buffers of accepted pairs */
+  DCM_FORCE_WARP = 3         /* one warp per particle i, ballot-compacted pair queue */
+};
+
 enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };
 
 /* Parameters of one system.  dcm_params_default() fills the defaults used for
@@ -86,8 +97,12 @@ typedef struct dcm_params {
   int32_t shift_energy;   /* 1: pair energy U(r) - U(rc_i); forces unchanged. Default 0 */
   int32_t precision;      /* DCM_PREC_MIXED (default) or DCM_PREC_FP64 */
   int32_t recompute_every;/* K: interface, distances and cutoffs every K steps. Default 10 */
-  int32_t reserved;
+  int32_t force_kernel;   /* cell-list force kernel (DCM_FORCE_*); DCM_FORCE_AUTO (0) by default */
   int64_t n_max;          /* largest particle count any call on this context will pass */
+  double skin;            /* > 0: dcm_step keeps Verlet neighbour lists of radius rc_i + skin
+                             (Algorithm 2.2) and rebuilds them only when a particle has moved
+                             more than skin / 2 since the last build or the cutoffs are
+                             recomputed; 0 (default): forces straight from the cell lists */
 } dcm_params;
 
 typedef struct dcm_ctx dcm_ctx;
@@ -121,7 +136,8 @@ int dcm_params_default(dcm_params* p);
  * into fewer than 65536 cells; 0 < rc_min <= rc_max <= min(L)/2 (so at most
  * one periodic image of a particle lies within any cutoff); 1 <= ntypes <= 4;
  * eps, sigma > 0; smooth_w >= 0; 1 <= iter_max <= 100000; recompute_every
- * >= 1; 0 <= n_max < 2^31.
+ * >= 1; force_kernel one of DCM_FORCE_*; 0 <= n_max < 2^31; skin >= 0 with rc_max + skin <= min(L)/2 and
+ * n_max < 2^26 when skin > 0.
  * On failure writes a message to msg (if msg_len > 0) and returns
  * DCM_ERR_BOX or DCM_ERR_INVALID_ARG. */
 int dcm_validate_params(const dcm_params* p, char* msg, int32_t msg_len);
@@ -242,8 +258,13 @@ int dcm_step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, dcm_stream_t stream);
  *   if t % K == 0: box counts, interface, distances, cutoffs;
  *   forces;  v += dt/2 F;  thermo = {E, W, KE, pairs}.
  * Masses are 1.  The distance sweeps run a fixed budget of iterations with a
- * device-side convergence flag, so the call never waits on the host;
- * non-convergence is reported by dcm_status(). */
+ * device-side convergence flag; non-convergence is reported by dcm_status().
+ * With params.skin == 0 the call never waits on the host.  With skin > 0
+ * (Verlet lists) each step reads the largest displacement back to the host
+ * to decide whether to rebin and rebuild the lists (so it synchronises the
+ * stream once per step, may grow the list storage, and leaves the state in
+ * buffer cur unchanged on steps without a rebuild; between rebuilds positions
+ * are not wrapped into the box). */
 int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, dcm_stream_t stream);
 
 /* Same result as dcm_distance, for callers that cannot allocate device
@@ -276,7 +297,8 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
  * [offset[r], offset[r+1]) (dcm_batch_offsets) and its particles stay there;
  * thermo is double[4 R] = {E, W, KE, pairs} per replica.  Every stage of a
  * step is one launch over all replicas (per-replica boxes, grids, thresholds
- * and reductions are read from a device table).  Synchronous; allocates. */
+ * and reductions are read from a device table).  The batched form steps over
+ * cell lists: p->skin must be 0.  Synchronous; allocates. */
 typedef struct dcm_batch dcm_batch;
 int dcm_batch_create(const dcm_params* p, int32_t R, const double* boxes, const int64_t* counts, dcm_batch** out);
 void dcm_batch_destroy(dcm_batch* b);
@@ -323,7 +345,8 @@ enum dcm_stage {
   DCM_STAGE_CUTOFFS = 4,    /* dcm_cutoffs */
   DCM_STAGE_FORCES = 5,     /* dcm_forces kernel (without the final reduction) */
   DCM_STAGE_KICK = 6,       /* second half kick and kinetic energy */
-  DCM_NSTAGES = 7
+  DCM_STAGE_LISTS = 7,      /* Verlet list build (params.skin > 0) */
+  DCM_NSTAGES = 8
 };
 
 /* capacity > 0: every later stage run on ctx records a CUDA event pair on the
@@ -342,6 +365,11 @@ int dcm_stage_times(dcm_ctx* ctx, double* ms, int64_t* count);
 
 /* Number of CUDA kernels this context has launched; reset if reset != 0. */
 int dcm_launch_count(dcm_ctx* ctx, int64_t* count, int32_t reset);
+
+/* The DCM_FORCE_* kernel that dcm_forces and dcm_step run on the cell lists
+ * for this context's parameters (params.force_kernel with AUTO and the
+ * kernels' limits resolved), written to *kernel.  Host only. */
+int dcm_force_kernel(const dcm_ctx* ctx, int32_t* kernel);
 
 #ifdef __cplusplus
 }

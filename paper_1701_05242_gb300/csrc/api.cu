@@ -19,6 +19,10 @@ int set_error(dcm_ctx* ctx, int code, const char* fmt, ...) {
   return code;
 }
 
+int force_kernel_choice(const dcm_params& p) {
+  return p.force_kernel == DCM_FORCE_AUTO ? DCM_FORCE_THREAD : p.force_kernel;
+}
+
 int check_launch(dcm_ctx* ctx, const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(ctx, DCM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -188,6 +192,8 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
   if (p->iter_max < 1 || p->iter_max > 100000)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "iter_max must be in 1..100000");
   if (p->recompute_every < 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "recompute_every must be >= 1");
+  if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_WARP)
+    return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "precision must be DCM_PREC_FP64 or DCM_PREC_MIXED");
   if (p->n_max < 0 || p->n_max > 0x7fffffffLL) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "n_max out of range");
@@ -200,6 +206,13 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
     return msg_out(msg, len, DCM_ERR_BOX, "grid too large for 32-bit cell indices");
   dcm_params q = resolved(p);
   if (!(q.r_grid > 0.0)) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "r_grid must be positive");
+  if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "skin must be >= 0");
+  if (p->skin > 0.0) {
+    if (p->rc_max + p->skin > 0.5 * Lmin)
+      return msg_out(msg, len, DCM_ERR_BOX, "rc_max + skin = %g exceeds half the smallest box length %g",
+                     p->rc_max + p->skin, Lmin);
+    if (p->n_max >= (int64_t)1 << 26) return msg_out(msg, len, DCM_ERR_CAPACITY, "Verlet lists need n_max < 2^26");
+  }
   return DCM_OK;
 }
 
@@ -214,10 +227,11 @@ extern "C" int dcm_grid_dims(const dcm_params* p, int64_t* cells3, int64_t* boxe
 
 struct ScratchPlan {
   int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags;
+  double skin;
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
-           8 * 32 * red_cap + 8 * 48;
+           8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 4 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 16 : 0);
   }
 };
 
@@ -236,6 +250,7 @@ static ScratchPlan plan_of(const dcm_params* p) {
   s.red_cap = ((s.n_max + 255) / 256 + 1) * 8;  // one partial per warp of the padded launches
   s.rsize = p->precision == DCM_PREC_FP64 ? 8 : 4;
   s.flags = p->iter_max + 2;
+  s.skin = p->skin;
   return s;
 }
 
@@ -256,7 +271,8 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
   if (!ctx) return;
   void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
                  ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
-                 ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs};
+                 ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
+                 ctx->nnb, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -317,6 +333,14 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   alloc((void**)&ctx->totals, 8 * 8);
   alloc((void**)&ctx->red_tmp, 8 * 8 * 256);
   alloc((void**)&ctx->adj_part, 8 * 32 * s.red_cap);
+  if (p->skin > 0.0) {
+    alloc((void**)&ctx->nnb, 4 * nm);
+    alloc((void**)&ctx->capw, 4 * (nm / 32 + 16));
+    alloc((void**)&ctx->offw, 4 * (nm / 32 + 16));
+    alloc(&ctx->xbuild, 4 * s.rsize * nm);
+    alloc((void**)&ctx->dmax, 16);
+    alloc((void**)&ctx->lflag, 16);
+  }
   alloc((void**)&ctx->adj_pairs, 8 * 48);
   if (ok && cudaMallocHost((void**)&ctx->host_status, 16) != cudaSuccess) ok = false;
   if (!ok) {
@@ -509,6 +533,12 @@ extern "C" int dcm_launch_count(dcm_ctx* ctx, int64_t* count, int32_t reset) {
   if (!ctx || !count) return DCM_ERR_INVALID_ARG;
   *count = ctx->launches;
   if (reset) ctx->launches = 0;
+  return DCM_OK;
+}
+
+extern "C" int dcm_force_kernel(const dcm_ctx* ctx, int32_t* kernel) {
+  if (!ctx || !kernel) return DCM_ERR_INVALID_ARG;
+  *kernel = resolve_force_kernel(ctx);
   return DCM_OK;
 }
 

@@ -112,6 +112,16 @@ struct dcm_ctx {
   int64_t red_cap;          // number of partial slots in red (per quantity)
   int64_t scan_cap;
   int64_t launches;         // kernels launched through this context
+  // Verlet lists (params.skin > 0)
+  int32_t* nnb;             // n_max: list length of each particle
+  int32_t* capw;            // per warp: longest list of its 32 particles
+  int32_t* offw;            // exclusive scan of capw (units of 32 entries)
+  uint32_t* list;           // interleaved lists (grown on demand)
+  int64_t list_cap;
+  void* xbuild;             // positions at the last build
+  int32_t* dmax;            // largest squared displacement (float bits)
+  int32_t* lflag;           // list overflow flag of the single-walk build
+  int list_valid;
   // optional per-stage CUDA-event timing (dcm_set_timing)
   int timing;
   int ev_n[DCM_NSTAGES];
@@ -127,6 +137,11 @@ constexpr int kScanItems = 4;          // items per thread
 constexpr int kScanTile = kScanBlock * kScanItems;
 
 int set_error(dcm_ctx* ctx, int code, const char* fmt, ...);
+
+// Force kernel used for one-type FP32 systems: 1 = single-pass (default),
+// 2 = two-phase.  DCM_FORCE_KERNEL in the environment overrides it (read once).
+int force_kernel_choice(const dcm_params& p);  // DCM_FORCE_* with AUTO resolved
+int resolve_force_kernel(const dcm_ctx* ctx);  // ... and each kernel's limits applied
 
 // Stage timing: events recorded on the launching stream around a stage.
 void stage_begin(dcm_ctx* ctx, int stage, cudaStream_t st);
@@ -183,6 +198,17 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
 template <typename R>
 int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, const int32_t* cell_start,
                const typename RT<R>::R4* A, double dlde, typename RT<R>::R4* G, double* dparams, cudaStream_t st);
+
+// verlet.cu
+template <typename R>
+int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, cudaStream_t st);
+template <typename R>
+int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, typename RT<R>::R4* force,
+                double* totals, cudaStream_t st);
+template <typename R>
+int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, bool* rebuild, cudaStream_t st);
+template <typename R>
+int list_wrap_count(dcm_ctx* ctx, dcm_state* s, int64_t n, cudaStream_t st);
 
 // step.cu
 template <typename R>

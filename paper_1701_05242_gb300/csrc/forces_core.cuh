@@ -124,7 +124,7 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
   const R rc2s = rc2 * (R)1.000004;  // culling slack; the pair test is exact
   const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
   R ushift[4] = {0, 0, 0, 0};
-  if (a.shift) {
+  if (a.shift && rc2 > (R)0) {  // no pairs at rc = 0: no shift either
     for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
       int tp = ti * a.ntypes + t;
       R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;

@@ -152,18 +152,69 @@ int step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, cudaStream_t s) {
   if (r) return r;
   if ((r = gather_state<R>(ctx, st, n, s))) return r;
   if ((r = recompute_cutoffs<R>(ctx, n, (const R4*)st->pos[o], (R*)st->rc[o], s))) return r;
-  if ((r = lj_forces<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], ctx->cell_start, (R4*)st->force,
-                        ctx->totals, s)))
-    return r;
+  if (ctx->p.skin > 0.0) {
+    if ((r = list_build<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], s))) return r;
+    r = list_forces<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], (R4*)st->force, ctx->totals, s);
+  } else {
+    r = lj_forces<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], ctx->cell_start, (R4*)st->force,
+                     ctx->totals, s);
+  }
+  if (r) return r;
   if ((r = finish_thermo<R>(ctx, n, (R4*)st->vel[o], nullptr, (R)0, st->thermo, s))) return r;
   st->cur = o;
   st->t = 0;
   return DCM_OK;
 }
 
+// Steps with Verlet lists: rebin and rebuild only when needed.
+template <typename R>
+static int step_run_lists(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int nsteps, cudaStream_t s) {
+  using R4 = typename RT<R>::R4;
+  Grid<R> g = cell_grid<R>(ctx);
+  R hdt = (R)(0.5 * dt), rdt = (R)dt;
+  int K = ctx->p.recompute_every;
+  for (int k = 0; k < nsteps; ++k) {
+    int r;
+    bool recompute = (st->t + 1) % K == 0;
+    bool rebuild = recompute || !ctx->list_valid;
+    stage_begin(ctx, DCM_STAGE_KICK_DRIFT, s);
+    if (rebuild) {
+      DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s));
+      if (n > 0)
+        DCM_LAUNCH(ctx, k_kick_drift_count<R>, (unsigned)((n + 255) / 256), 256, 0, s, n, (R4*)st->pos[st->cur],
+                   (R4*)st->vel[st->cur], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count);
+    } else {
+      if ((r = list_kick_drift<R>(ctx, st, n, hdt, rdt, &rebuild, s))) return r;
+      if (rebuild && (r = list_wrap_count<R>(ctx, st, n, s))) return r;
+    }
+    stage_end(ctx, DCM_STAGE_KICK_DRIFT, s);
+    st->t += 1;
+    if (rebuild) {
+      int o = 1 - st->cur;
+      stage_begin(ctx, DCM_STAGE_BIN, s);
+      if ((r = exclusive_scan(ctx, ctx->cell_count, ctx->cell_start, ctx->ncell, s))) return r;
+      if ((r = scatter_sort(ctx, n, ctx->cell, ctx->slot, ctx->cell_start, ctx->ncell, ctx->perm, s))) return r;
+      if ((r = gather_state<R>(ctx, st, n, s))) return r;
+      stage_end(ctx, DCM_STAGE_BIN, s);
+      if (recompute)
+        if ((r = recompute_cutoffs<R>(ctx, n, (const R4*)st->pos[o], (R*)st->rc[o], s))) return r;
+      if ((r = list_build<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], s))) return r;
+      st->cur = o;
+    }
+    int c = st->cur;
+    if ((r = list_forces<R>(ctx, n, (const R4*)st->pos[c], (const R*)st->rc[c], (R4*)st->force, ctx->totals, s)))
+      return r;
+    stage_begin(ctx, DCM_STAGE_KICK, s);
+    if ((r = finish_thermo<R>(ctx, n, (R4*)st->vel[c], (const R4*)st->force, hdt, st->thermo, s))) return r;
+    stage_end(ctx, DCM_STAGE_KICK, s);
+  }
+  return DCM_OK;
+}
+
 template <typename R>
 int step_run(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int nsteps, cudaStream_t s) {
   using R4 = typename RT<R>::R4;
+  if (ctx->p.skin > 0.0) return step_run_lists<R>(ctx, st, n, dt, nsteps, s);
   Grid<R> g = cell_grid<R>(ctx);
   R hdt = (R)(0.5 * dt), rdt = (R)dt;
   int K = ctx->p.recompute_every;

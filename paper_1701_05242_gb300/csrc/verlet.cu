@@ -1,0 +1,473 @@
+// Verlet neighbour lists with a skin (Algorithm 2.2) and forces over them
+// (Algorithm 2.3), used by dcm_step when params.skin > 0.
+//
+// Build (at a rebuild): for every particle i, the j != i with
+// |r_ij| < rc_i + skin, found by the same culled cell-row walk as the
+// cell-list force kernel.  A count pass sizes the lists; the lists of the 32
+// particles of a warp are interleaved (entry k of lane l at base + 32 k + l,
+// base = 32 x the sum of the earlier warps' longest lists) so that the force
+// loop reads them coalesced.  An entry is j | image code << 26: per dimension
+// 0 = same image, 1 = j taken at x_j - L, 2 = i taken at x_i - L, so that the
+// force loop forms every r_ij with one rounding, exactly as the cell walk.
+//
+// Between rebuilds particles are not rebinned and positions are not wrapped
+// (the image codes stay valid); dcm_step rebuilds when the largest
+// displacement since the build exceeds skin / 2 (then no pair can have moved
+// from beyond rc_i + skin to within rc_i), and whenever the cutoffs are
+// recomputed.
+#include <algorithm>
+
+#include "forces_core.cuh"
+
+namespace dcm {
+
+constexpr uint32_t kIdxBits = 26;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1;
+
+// Walk the cell rows of particle i within radius sqrt(rl2) and call f(j, code)
+// for every j != i with r_ij^2 < rl2.
+template <typename R, typename F>
+__device__ __forceinline__ void walk(const typename RT<R>::R4* __restrict__ pos, const int32_t* __restrict__ start,
+                                     const Grid<R>& g, int self, const typename RT<R>::R4& pi, R rl, F&& f) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const R l = g.edge, il = g.inv_edge;
+  const R rl2 = rl * rl;
+  const R rl2s = rl2 * (R)1.000004;
+  const int cx = cell_coord<R>(pi.x, l, il, nx);
+  const int cy = cell_coord<R>(pi.y, l, il, ny);
+  const int cz = cell_coord<R>(pi.z, l, il, nz);
+  const int H = (int)ceil(rl * il);
+  for (int uz = cz - H; uz <= cz + H; ++uz) {
+    R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
+    R gz2 = gz * gz;
+    if (gz2 >= rl2s) continue;
+    int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
+    uint32_t zc = uz < 0 ? 1u : (uz >= nz ? 2u : 0u);
+    R zi = zc == 2 ? pi.z - g.L[2] : pi.z;
+    R zsh = zc == 1 ? -g.L[2] : (R)0;
+    for (int uy = cy - H; uy <= cy + H; ++uy) {
+      R gy = uy > cy ? (R)uy * l - pi.y : (uy < cy ? pi.y - (R)(uy + 1) * l : (R)0);
+      R gyz2 = gz2 + gy * gy;
+      if (gyz2 >= rl2s) continue;
+      int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+      uint32_t yc = uy < 0 ? 1u : (uy >= ny ? 2u : 0u);
+      R yi = yc == 2 ? pi.y - g.L[1] : pi.y;
+      R ysh = yc == 1 ? -g.L[1] : (R)0;
+      R wx = sqrt(rl2s - gyz2);
+      int ulo = max(ufloor<R>((pi.x - wx) * il - (R)5e-4), cx - H);
+      int uhi = min(ufloor<R>((pi.x + wx) * il + (R)5e-4), cx + H);
+      const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
+      for (int seg = 0; seg < 3; ++seg) {
+        int a0, a1;
+        uint32_t xc;
+        if (seg == 0) {
+          a0 = ulo;
+          a1 = min(uhi, -1);
+          xc = 1;
+        } else if (seg == 1) {
+          a0 = max(ulo, 0);
+          a1 = min(uhi, nx - 1);
+          xc = 0;
+        } else {
+          a0 = max(ulo, nx);
+          a1 = uhi;
+          xc = 2;
+        }
+        if (a0 > a1) continue;
+        int w0 = seg == 0 ? a0 + nx : (seg == 2 ? a0 - nx : a0);
+        int w1 = seg == 0 ? a1 + nx : (seg == 2 ? a1 - nx : a1);
+        int j0 = __ldg(start + row + w0), j1 = __ldg(start + row + w1 + 1);
+        R xi = xc == 2 ? pi.x - g.L[0] : pi.x;
+        R xsh = xc == 1 ? -g.L[0] : (R)0;
+        uint32_t code = xc | (yc << 2) | (zc << 4);
+        for (int j = j0; j < j1; ++j) {
+          if (j == self && code == 0) continue;
+          auto pj = ldg4(pos + j);
+          R dx = xi - (pj.x + xsh);
+          R dy = yi - (pj.y + ysh);
+          R dz = zi - (pj.z + zsh);
+          R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+          if (r2 < rl2) f(j, code);
+        }
+      }
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R list_radius(R rc, R rc_max, R skin) {
+  if (!(rc <= rc_max)) rc = rc_max;
+  if (!(rc > (R)0)) rc = (R)0;
+  return rc + skin;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_list_count(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                    const R* __restrict__ rc, const int32_t* __restrict__ start,
+                                                    Grid<R> g, R rc_max, R skin, int32_t* __restrict__ nnb,
+                                                    int32_t* __restrict__ capw) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = 0;
+  if (i < n) {
+    auto pi = ldg4(pos + i);
+    walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int, uint32_t) { ++cnt; });
+    nnb[i] = cnt;
+  }
+  int m = cnt;
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) capw[i >> 5] = m;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_list_fill(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                   const R* __restrict__ rc, const int32_t* __restrict__ start,
+                                                   Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ offw,
+                                                   uint32_t* __restrict__ list) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t* out = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
+  int k = 0;
+  auto pi = ldg4(pos + i);
+  walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int j, uint32_t code) {
+    out[(int64_t)k * 32] = (uint32_t)j | (code << kIdxBits);
+    ++k;
+  });
+}
+
+// Capacity bound of a list of radius R: the particles a sphere of radius R can
+// hold at number density 1.3 (well above any liquid state of the workloads),
+// plus a margin; a build that exceeds it is detected and redone exactly.
+template <typename R>
+__device__ __forceinline__ int list_cap_bound(R rl) {
+  R v = (R)(4.18879020478639) * rl * rl * rl;  // 4/3 pi R^3
+  return (int)(v * (R)1.3) + 24;
+}
+
+template <typename R>
+__global__ void k_list_caps(int64_t n, const R* __restrict__ rc, R rc_max, R skin, int32_t* __restrict__ capw) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int cap = i < n ? list_cap_bound<R>(list_radius<R>(rc[i], rc_max, skin)) : 0;
+  for (int o = 16; o > 0; o >>= 1) cap = max(cap, __shfl_xor_sync(0xffffffffu, cap, o));
+  if ((threadIdx.x & 31) == 0) capw[i >> 5] = cap;
+}
+
+// One walk: writes the list into the bounded space and its length; a list
+// longer than its warp's capacity raises the overflow flag (the caller then
+// counts exactly and fills again).
+template <typename R>
+__global__ void __launch_bounds__(128) k_list_fill1(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                    const R* __restrict__ rc, const int32_t* __restrict__ start,
+                                                    Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ capw,
+                                                    const int32_t* __restrict__ offw, uint32_t* __restrict__ list,
+                                                    int32_t* __restrict__ nnb, int32_t* __restrict__ flag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cap = capw[i >> 5];
+  uint32_t* out = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
+  int k = 0;
+  auto pi = ldg4(pos + i);
+  walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int j, uint32_t code) {
+    if (k < cap) out[(int64_t)k * 32] = (uint32_t)j | (code << kIdxBits);
+    ++k;
+  });
+  nnb[i] = k;
+  if (k > cap) atomicExch(flag, 1);
+}
+
+// Per-warp partials (E, W, pairs) as in the cell-list kernel.
+template <typename R>
+__device__ __forceinline__ void list_partials(R a, R b, int c, double* part, int64_t nslot) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    part[w] = (double)a;
+    part[nslot + w] = (double)b;
+    part[2 * nslot + w] = (double)c;
+  }
+}
+
+// Forces over the lists: the pair rule |r_ij| < rc_i is applied to every
+// entry (the list holds the j within rc_i + skin at build time).
+template <typename R, bool TYPED>
+__global__ void __launch_bounds__(128) k_forces_list(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                     const R* __restrict__ rc, const int32_t* __restrict__ nnb,
+                                                     const int32_t* __restrict__ offw,
+                                                     const uint32_t* __restrict__ list, ForceArgs<R> a,
+                                                     typename RT<R>::R4* __restrict__ force, double* __restrict__ part,
+                                                     int64_t nwarp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  Acc<R> c;
+  R e_out = 0, w_out = 0;
+  if (i < n) {
+    auto pi = ldg4(pos + i);
+    R rci = rc[i];
+    if (!(rci <= a.rc_max)) rci = a.rc_max;
+    if (!(rci > (R)0)) rci = (R)0;
+    const R rc2 = rci * rci;
+    const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
+    R ushift[4] = {0, 0, 0, 0};
+    if (a.shift) {
+      for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
+        int tp = ti * a.ntypes + t;
+        R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
+        R s6 = s2 * s2 * s2;
+        ushift[t] = (TYPED ? a.eps4[tp] : (R)4) * s6 * (s6 - (R)1);
+      }
+    }
+    const uint32_t* lp = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
+    const int m = nnb[i];
+    const R Lx = a.g.L[0], Ly = a.g.L[1], Lz = a.g.L[2];
+#pragma unroll 2
+    for (int k = 0; k < m; ++k) {
+      uint32_t e = __ldg(lp + (int64_t)k * 32);
+      int j = (int)(e & kIdxMask);
+      uint32_t code = e >> kIdxBits;
+      auto pj = ldg4(pos + j);
+      R dx, dy, dz;
+      if (code == 0) {
+        dx = pi.x - pj.x;
+        dy = pi.y - pj.y;
+        dz = pi.z - pj.z;
+      } else {
+        uint32_t xc = code & 3, yc = (code >> 2) & 3, zc = code >> 4;
+        dx = (xc == 2 ? pi.x - Lx : pi.x) - (xc == 1 ? pj.x - Lx : pj.x);
+        dy = (yc == 2 ? pi.y - Ly : pi.y) - (yc == 1 ? pj.y - Ly : pj.y);
+        dz = (zc == 2 ? pi.z - Lz : pi.z) - (zc == 1 ? pj.z - Lz : pj.z);
+      }
+      R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      bool acc = r2 < rc2;
+      R inv = recip(r2);
+      inv = acc ? inv : (R)0;
+      if (TYPED) {
+        int tj = type_of(pj.w, a.ntypes);
+        int tp = ti * a.ntypes + tj;
+        R s2 = a.sig2[tp] * inv;
+        R s6 = s2 * s2 * s2;
+        R pv = a.eps24[tp] * s6 * fma((R)2, s6, (R)-1);
+        R fs = pv * inv;
+        c.fx = fma(fs, dx, c.fx);
+        c.fy = fma(fs, dy, c.fy);
+        c.fz = fma(fs, dz, c.fz);
+        R us = tj == 0 ? ushift[0] : (tj == 1 ? ushift[1] : (tj == 2 ? ushift[2] : ushift[3]));
+        R u = a.eps4[tp] * s6 * (s6 - (R)1);
+        c.en += acc ? u - us : (R)0;
+        c.vir += pv;
+      } else {
+        R s6 = inv * inv * inv;
+        R pv = s6 * fma((R)2, s6, (R)-1);
+        R q = pv * inv;
+        c.fx = fma(q, dx, c.fx);
+        c.fy = fma(q, dy, c.fy);
+        c.fz = fma(q, dz, c.fz);
+        c.en += fma(s6, s6, -s6);
+        c.vir += pv;
+      }
+      c.np += acc ? 1 : 0;
+    }
+    typename RT<R>::R4 out;
+    if (TYPED) {
+      out.x = c.fx;
+      out.y = c.fy;
+      out.z = c.fz;
+      e_out = (R)0.5 * c.en;
+      w_out = (R)0.5 * c.vir;
+    } else {
+      out.x = (R)24 * c.fx;
+      out.y = (R)24 * c.fy;
+      out.z = (R)24 * c.fz;
+      e_out = (R)2 * c.en - (R)0.5 * (R)c.np * ushift[0];
+      w_out = (R)12 * c.vir;
+    }
+    out.w = e_out;
+    force[i] = out;
+  }
+  if (part) list_partials<R>(e_out, w_out, c.np, part, nwarp);
+}
+
+// Half kick and drift without wrapping (the list's image codes stay valid),
+// with the largest squared displacement since the build (as float bits; the
+// values are non-negative, so integer max orders them).
+template <typename R>
+__global__ void k_kick_drift_nowrap(int64_t n, typename RT<R>::R4* __restrict__ pos, typename RT<R>::R4* __restrict__ vel,
+                                    const typename RT<R>::R4* __restrict__ force,
+                                    const typename RT<R>::R4* __restrict__ xb, R half_dt, R dt,
+                                    int32_t* __restrict__ dmax) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float d2 = 0.f;
+  if (i < n) {
+    auto p = pos[i];
+    auto v = vel[i];
+    auto f = force[i];
+    v.x += half_dt * f.x;
+    v.y += half_dt * f.y;
+    v.z += half_dt * f.z;
+    p.x += dt * v.x;
+    p.y += dt * v.y;
+    p.z += dt * v.z;
+    pos[i] = p;
+    vel[i] = v;
+    auto b = xb[i];
+    R dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
+    d2 = (float)(dx * dx + dy * dy + dz * dz);
+    if (!(d2 == d2)) d2 = 3.0e38f;  // NaN: force a rebuild
+  }
+  for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dmax, __float_as_int(d2));
+}
+
+// Wrap drifted positions into [0, L) and count cells (the rebuild's binning).
+template <typename R>
+__global__ void k_wrap_count(int64_t n, typename RT<R>::R4* __restrict__ pos, Grid<R> g, int32_t* __restrict__ cell,
+                             int32_t* __restrict__ slot, int32_t* __restrict__ count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto p = pos[i];
+  R* c3[3] = {&p.x, &p.y, &p.z};
+  for (int d = 0; d < 3; ++d) {
+    R x = *c3[d];
+    R L = g.L[d];
+    if (x >= L) x -= L;
+    if (x < (R)0) {
+      x += L;
+      if (x >= L) x = (R)0;
+    }
+    *c3[d] = x;
+  }
+  pos[i] = p;
+  int cx = cell_coord<R>(p.x, g.edge, g.inv_edge, g.n[0]);
+  int cy = cell_coord<R>(p.y, g.edge, g.inv_edge, g.n[1]);
+  int cz = cell_coord<R>(p.z, g.edge, g.inv_edge, g.n[2]);
+  int c = cx + g.n[0] * (cy + g.n[1] * cz);
+  cell[i] = c;
+  slot[i] = atomicAdd(count + c, 1);
+}
+
+// ---- launchers -------------------------------------------------------------------
+
+static int ensure_list_capacity(dcm_ctx* ctx, int64_t need) {
+  if (need <= ctx->list_cap) return DCM_OK;
+  if (ctx->list) cudaFree(ctx->list);
+  ctx->list = nullptr;
+  ctx->list_cap = 0;
+  int64_t cap = need + need / 8 + 1024;
+  if (cudaMalloc((void**)&ctx->list, sizeof(uint32_t) * cap) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ctx, DCM_ERR_NOMEM, "neighbour lists need %lld entries", (long long)need);
+  }
+  ctx->list_cap = cap;
+  return DCM_OK;
+}
+
+// Build: bounded capacities -> one walk; on overflow, exact count + fill.
+template <typename R>
+int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, cudaStream_t st) {
+  Grid<R> g = cell_grid<R>(ctx);
+  R skin = (R)ctx->p.skin, rcm = (R)ctx->p.rc_max;
+  int64_t nblk = (n + 127) / 128, nw = nblk * 4;
+  stage_begin(ctx, DCM_STAGE_LISTS, st);
+  if (n > 0) DCM_LAUNCH(ctx, k_list_caps<R>, (unsigned)nblk, 128, 0, st, n, rc, rcm, skin, ctx->capw);
+  int r = exclusive_scan(ctx, ctx->capw, ctx->offw, nw, st);
+  if (r) return r;
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->lflag, 0, sizeof(int32_t), st));
+  DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 1, ctx->offw + nw, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if ((r = ensure_list_capacity(ctx, (int64_t)ctx->host_status[1] * 32))) return r;
+  if (n > 0)
+    DCM_LAUNCH(ctx, k_list_fill1<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, ctx->capw,
+               ctx->offw, ctx->list, ctx->nnb, ctx->lflag);
+  DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 3, ctx->lflag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (ctx->host_status[3]) {
+    // some list outgrew its bound: count exactly, then fill
+    if (n > 0)
+      DCM_LAUNCH(ctx, k_list_count<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin,
+                 ctx->nnb, ctx->capw);
+    if ((r = exclusive_scan(ctx, ctx->capw, ctx->offw, nw, st))) return r;
+    DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 1, ctx->offw + nw, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if ((r = ensure_list_capacity(ctx, (int64_t)ctx->host_status[1] * 32))) return r;
+    if (n > 0)
+      DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin,
+                 ctx->offw, ctx->list);
+  }
+  DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->xbuild, pos, sizeof(typename RT<R>::R4) * n, cudaMemcpyDeviceToDevice, st));
+  stage_end(ctx, DCM_STAGE_LISTS, st);
+  ctx->list_valid = 1;
+  return check_launch(ctx, "list_build");
+}
+
+template <typename R>
+int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, typename RT<R>::R4* force,
+                double* totals, cudaStream_t st) {
+  if (n <= 0) {
+    if (totals) DCM_CUDA_TRY(ctx, cudaMemsetAsync(totals, 0, 3 * sizeof(double), st));
+    return DCM_OK;
+  }
+  ForceArgs<R> a;
+  a.g = cell_grid<R>(ctx);
+  LJTable t = lj_table(ctx->p);
+  a.ntypes = t.ntypes;
+  for (int k = 0; k < 16; ++k) {
+    a.eps24[k] = (R)t.deps24[k];
+    a.eps4[k] = (R)t.deps4[k];
+    a.sig2[k] = (R)t.dsig2[k];
+  }
+  a.shift = ctx->p.shift_energy;
+  a.rc_max = (R)ctx->p.rc_max;
+  int64_t nblk = (n + 127) / 128, nwarp = nblk * 4;
+  if (totals && nwarp > ctx->red_cap) return set_error(ctx, DCM_ERR_CAPACITY, "force reduction too large");
+  double* part = totals ? ctx->red : nullptr;
+  auto kern = lj_general(t) ? k_forces_list<R, true> : k_forces_list<R, false>;
+  stage_begin(ctx, DCM_STAGE_FORCES, st);
+  DCM_LAUNCH(ctx, kern, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->offw, ctx->list, a, force, part, nwarp);
+  stage_end(ctx, DCM_STAGE_FORCES, st);
+  int r = check_launch(ctx, "list_forces");
+  if (r) return r;
+  if (totals) return reduce_partials(ctx, part, nwarp, 3, totals, false, st);
+  return DCM_OK;
+}
+
+// Half kick + drift (no wrap); returns through *rebuild whether the largest
+// displacement since the build exceeds skin / 2 (synchronous read).
+template <typename R>
+int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, bool* rebuild, cudaStream_t st) {
+  using R4 = typename RT<R>::R4;
+  int c = s->cur;
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dmax, 0, sizeof(int32_t), st));
+  if (n > 0)
+    DCM_LAUNCH(ctx, k_kick_drift_nowrap<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, (R4*)s->pos[c],
+               (R4*)s->vel[c], (const R4*)s->force, (const R4*)ctx->xbuild, hdt, dt, ctx->dmax);
+  DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 2, ctx->dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  int bits = ctx->host_status[2];
+  float d2;
+  memcpy(&d2, &bits, sizeof(d2));
+  double half = 0.5 * ctx->p.skin;
+  *rebuild = !((double)d2 <= half * half);
+  return check_launch(ctx, "list_kick_drift");
+}
+
+template <typename R>
+int list_wrap_count(dcm_ctx* ctx, dcm_state* s, int64_t n, cudaStream_t st) {
+  using R4 = typename RT<R>::R4;
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, st));
+  if (n > 0)
+    DCM_LAUNCH(ctx, k_wrap_count<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, (R4*)s->pos[s->cur],
+               cell_grid<R>(ctx), ctx->cell, ctx->slot, ctx->cell_count);
+  return check_launch(ctx, "list_wrap_count");
+}
+
+template int list_build<float>(dcm_ctx*, int64_t, const float4*, const float*, cudaStream_t);
+template int list_build<double>(dcm_ctx*, int64_t, const dvec4*, const double*, cudaStream_t);
+template int list_forces<float>(dcm_ctx*, int64_t, const float4*, const float*, float4*, double*, cudaStream_t);
+template int list_forces<double>(dcm_ctx*, int64_t, const dvec4*, const double*, dvec4*, double*, cudaStream_t);
+template int list_kick_drift<float>(dcm_ctx*, dcm_state*, int64_t, float, float, bool*, cudaStream_t);
+template int list_kick_drift<double>(dcm_ctx*, dcm_state*, int64_t, double, double, bool*, cudaStream_t);
+template int list_wrap_count<float>(dcm_ctx*, dcm_state*, int64_t, cudaStream_t);
+template int list_wrap_count<double>(dcm_ctx*, dcm_state*, int64_t, cudaStream_t);
+
+}  // namespace dcm

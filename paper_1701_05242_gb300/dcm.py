@@ -28,6 +28,10 @@ DCM_ERR_CAPACITY = 5
 DCM_ERR_NOMEM = 6
 DCM_PREC_FP64 = 0
 DCM_PREC_MIXED = 1
+DCM_FORCE_AUTO = 0
+DCM_FORCE_THREAD = 1
+DCM_FORCE_TWO_PHASE = 2
+DCM_FORCE_WARP = 3
 
 _ERRNAMES = {1: "INVALID_ARG", 2: "BOX", 3: "CUDA", 4: "NOT_CONVERGED", 5: "CAPACITY", 6: "NOMEM"}
 
@@ -44,7 +48,8 @@ class dcm_params(ctypes.Structure):
                 ("r_grid", ctypes.c_double), ("smooth_w", ctypes.c_int32), ("threshold", ctypes.c_int32),
                 ("iter_max", ctypes.c_int32), ("ntypes", ctypes.c_int32), ("eps", ctypes.c_double * 4),
                 ("sigma", ctypes.c_double * 4), ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("recompute_every", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_max", ctypes.c_int64)]
+                ("recompute_every", ctypes.c_int32), ("force_kernel", ctypes.c_int32), ("n_max", ctypes.c_int64),
+                ("skin", ctypes.c_double)]
 
 
 class dcm_state(ctypes.Structure):
@@ -95,9 +100,10 @@ _SIGS = {
     "dcm_set_timing": (_i32, [_vp, _i32]),
     "dcm_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "dcm_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
+    "dcm_force_kernel": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32)]),
 }
 
-STAGES = ("kick_drift", "bin", "detect", "distance", "cutoffs", "forces", "kick")
+STAGES = ("kick_drift", "bin", "detect", "distance", "cutoffs", "forces", "kick", "lists")
 
 
 def _load_library():
@@ -314,6 +320,15 @@ def dcm_launch_count(ctx: Context, reset: bool = False) -> int:
     c = _i64()
     ctx.check(lib.dcm_launch_count(ctx.handle, ctypes.byref(c), 1 if reset else 0))
     return c.value
+
+
+def dcm_force_kernel(ctx: Context) -> int:
+    k = ctypes.c_int32()
+    ctx.check(lib.dcm_force_kernel(ctx.handle, ctypes.byref(k)))
+    return k.value
+
+
+FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_TWO_PHASE: "k_forces2", DCM_FORCE_WARP: "k_forces_wp"}
 
 
 # ---------------------------------------------------------------- batched form

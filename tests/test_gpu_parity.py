@@ -244,10 +244,10 @@ def test_cutoffs(D, slab_1935, prec):
 
 
 # ---------------------------------------------------------------------- forces
-def forces_case(D, slab, prec, rc64, types=None, eps=(1.0,), sigma=(1.0,), shift=0, l=1.5, box=None):
+def forces_case(D, slab, prec, rc64, types=None, eps=(1.0,), sigma=(1.0,), shift=0, l=1.5, box=None, kernel=0):
     box = slab.box if box is None else box
     P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
-    kw = dict(ntypes=len(eps), eps=eps, sigma=sigma, shift_energy=shift, l=l)
+    kw = dict(ntypes=len(eps), eps=eps, sigma=sigma, shift_energy=shift, l=l, force_kernel=kernel)
     ctx = make_ctx(D, box, slab.n, P, **kw)
     real = real_of(D, P)
     rc_in = rc64.astype(np.float32).astype(np.float64) if P == D.DCM_PREC_MIXED else rc64
@@ -310,6 +310,49 @@ def test_forces_two_types(D, prec):
     else:
         assert np.abs(Fg[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
         assert int(tot[2]) == ref.npairs
+
+
+@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("l", [1.5, 1.0])
+def test_forces_kernel_variants(D, slab_1935, kernel, l):
+    """Every cell-list force kernel against the oracle (mixed, one type); at
+    l = 1.0 the warp kernel's stencil limit sends it to the thread kernel."""
+    p = O.Params(box=slab_1935.box)
+    rc64 = O.assign_cutoffs(slab_1935.pos, p)["rc"]
+    Fg, tot, ref, rc_in = forces_case(D, slab_1935, "mixed", rc64, l=l, kernel=kernel)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+    assert abs(tot[1] - ref.W) <= EW_TOL * abs(ref.W)
+    assert abs(Fg[:, 3] - ref.e).max() <= 1e-5 * np.abs(ref.e).max()
+    assert abs(int(tot[2]) - ref.npairs) <= near_cutoff_pairs(slab_1935.pos, rc_in, slab_1935.box)
+    # uniform cutoff with the shifted energy
+    Fg, tot, ref, _ = forces_case(D, slab_1935, "mixed", np.full(slab_1935.n, 4.5), shift=1, l=l, kernel=kernel)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+
+
+def test_forces_kernel_rejects_unknown(D):
+    with pytest.raises(D.DcmError):
+        make_ctx(D, (12.0, 12.0, 48.0), 10, force_kernel=4)
+
+
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_forces_tiny_box_and_ragged_kernels(D, kernel):
+    """rc_max = L/2 (pieces on both image sides of a row), 97 particles."""
+    rng = np.random.default_rng(12)
+    box = (12.0, 12.0, 12.0)
+    pts = rng.uniform(0, 12, size=(97, 3)).astype(np.float32)
+
+    class S:
+        pass
+    s = S()
+    s.pos, s.n, s.box = pts, 97, box
+    rc64 = rng.choice([0.0, 3.0, 4.5, 6.0], 97)
+    Fg, tot, ref, rc_in = forces_case(D, s, "mixed", rc64, kernel=kernel, shift=1)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+    assert int(tot[2]) == ref.npairs
+    assert np.isfinite(Fg).all()
 
 
 def test_forces_tiny_box_and_ragged(D):
@@ -390,6 +433,69 @@ def test_step_batched_call_equals_single_calls(D, slab_1935):
     assert torch.equal(st1.current()[0], st2.current()[0])
 
 
+def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5):
+    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, skin=skin, rc_max=rc_max)
+    real = real_of(D, P)
+    st = D.State(ctx, pos4_of(D, slab.pos, None, P), D.to_real4(torch.from_numpy(slab.vel), None, real))
+    D.dcm_step_init(ctx, st)
+    out = [st.thermo.cpu().numpy().copy()]
+    for _ in range(nsteps):
+        D.dcm_step(ctx, st, dt, 1)
+        out.append(st.thermo.cpu().numpy().copy())
+    assert D.dcm_status(ctx) == D.DCM_OK
+    return ctx, st, np.array(out)
+
+
+def test_step_verlet_lists_fp64_matches_oracle(D, slab_1935):
+    # Verlet lists (Algorithm 2.2) with skin: same trajectory as the oracle's
+    # cell-list steps (rebuilds on displacement and at every cutoff recomputation)
+    nsteps = 24
+    ctx, st, th = run_gpu_steps_list(D, slab_1935, D.DCM_PREC_FP64, nsteps, skin=0.3, K=10)
+    p = O.Params(box=slab_1935.box, recompute_every=10, rc_max=5.5)
+    ost = O.init_state(slab_1935.pos, slab_1935.vel, p)
+    for k in range(nsteps):
+        ost = O.step(ost, 0.005, p)
+        assert th[k + 1, 0] == pytest.approx(ost.E, rel=1e-9), k
+        assert th[k + 1, 1] == pytest.approx(ost.W, rel=1e-9), k
+        assert th[k + 1, 2] == pytest.approx(O.kinetic(ost.vel), rel=1e-9), k
+        assert th[k + 1, 3] == ost_pairs(ost, p), k
+    pos, vel, rc, ids = st.current()
+    gp = np.empty((slab_1935.n, 3))
+    gp[ids.cpu().numpy()] = pos.cpu().numpy()[:, :3]
+    d = np.abs(np.mod(gp - ost.pos + 0.5 * np.array(slab_1935.box), slab_1935.box) - 0.5 * np.array(slab_1935.box))
+    assert d.max() <= 1e-9
+
+
+def ost_pairs(ost, p):
+    return O.forces(ost.pos, ost.rc, p).npairs
+
+
+def test_step_verlet_lists_mixed_close_to_cells(D, slab_1935):
+    _, st_l, th_l = run_gpu_steps_list(D, slab_1935, D.DCM_PREC_MIXED, 12, skin=0.4, K=5)
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, D.DCM_PREC_MIXED, recompute_every=5, rc_max=5.5)
+    st = D.State(ctx, pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED),
+                 D.to_real4(torch.from_numpy(slab_1935.vel), None, torch.float32))
+    D.dcm_step_init(ctx, st)
+    for _ in range(12):
+        D.dcm_step(ctx, st, 0.005, 1)
+    th_c = st.thermo.cpu().numpy()
+    assert th_l[-1, 0] == pytest.approx(th_c[0], rel=1e-4)
+    assert th_l[-1, 2] == pytest.approx(th_c[2], rel=1e-4)
+    # forces on shared inputs: the list path's positions and cutoffs given to the oracle
+    pos, vel, rc, ids = st_l.current()
+    pw = np.mod(pos.cpu().numpy()[:, :3].astype(np.float64), slab_1935.box)
+    ref = O.forces_cells(pw, rc.cpu().numpy().astype(np.float64), slab_1935.box, 1.5)
+    Fg = st_l.force.cpu().numpy().astype(np.float64)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(th_l[-1, 0] - ref.E) <= EW_TOL * abs(ref.E)
+
+
+def test_skin_validation(D):
+    p = D.make_params((12.0, 12.0, 48.0), skin=0.5)   # rc_max 6 + 0.5 > 12 / 2
+    rc, msg = D.dcm_validate_params(p)
+    assert rc == D.DCM_ERR_BOX and "skin" in msg
+
+
 # ----------------------------------------------------------- full-size sample
 @pytest.fixture(scope="module")
 def slab_16m():
@@ -420,17 +526,28 @@ def test_full_size_sampled(D, slab_16m):
     _, orc = O.cutoffs(slab.pos[operm], Do, nh, 1.5, 6.0, 3.0, 6.0, 3.0)
     rcn = rc.cpu().numpy().astype(np.float64)
     assert np.abs(rcn - orc).max() <= RC_TOL
-    F = torch.empty_like(ps)
-    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
-    D.dcm_forces(ctx, n, ps, rc, torch.from_numpy(start).cuda(), F, tot)
-    torch.cuda.synchronize()
     rng = np.random.default_rng(7)
     # sample: random particles plus all of a few interface-region cells
     idx = np.unique(np.concatenate([rng.choice(n, 3000, replace=False),
                                     np.flatnonzero((rcn > 3.0) & (rcn < 6.0))[:1000]]))
     spos = slab.pos[operm].astype(np.float64)
     Fo, eo, wo, po = O.forces_subset(spos, rcn, slab.box, 1.5, idx, nthreads=8)
-    Fs = F.cpu().numpy().astype(np.float64)[idx]
-    assert rms_rel(Fs[:, :3], Fo) <= F_RMS_TOL
-    assert np.abs(Fs[:, 3] - eo).max() <= 1e-5 * np.abs(eo).max()
-    assert tot[0].item() != 0.0 and np.isfinite(tot.cpu().numpy()).all()
+    totals = []
+    for kernel in (0, 1, 2, 3):  # every cell-list kernel on the same sorted input
+        kctx = make_ctx(D, slab.box, n, force_kernel=kernel)
+        F = torch.empty_like(ps)
+        tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+        D.dcm_forces(kctx, n, ps, rc, torch.from_numpy(start).cuda(), F, tot)
+        torch.cuda.synchronize()
+        Fs = F.cpu().numpy().astype(np.float64)[idx]
+        assert rms_rel(Fs[:, :3], Fo) <= F_RMS_TOL
+        assert np.abs(Fs[:, 3] - eo).max() <= 1e-5 * np.abs(eo).max()
+        tot = tot.cpu().numpy()
+        assert tot[0] != 0.0 and np.isfinite(tot).all()
+        totals.append(tot)
+        del F, kctx
+    # the kernels accept the same pairs up to cutoff ties and agree on the totals
+    for t in totals[1:]:
+        assert abs(t[2] - totals[0][2]) <= 1e-6 * totals[0][2]
+        assert abs(t[0] - totals[0][0]) <= EW_TOL * abs(totals[0][0])
+        assert abs(t[1] - totals[0][1]) <= EW_TOL * abs(totals[0][1])
