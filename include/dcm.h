@@ -65,15 +65,15 @@ enum dcm_status_code {
   DCM_ERR_NOMEM = 6          /* scratch allocation failed in dcm_create */
 };
 
-/* Cell-list force kernels (all compute the same pairs; they differ in how
- * work is spread over threads).  Kernels 2 and 3 serve one-type FP32 runs
- * with eps = sigma = 1 and fall back to kernel 1 otherwise; kernel 3 also
- * needs ceil(rc_max / l) <= 4. */
+/* Cell-list force kernels (all walk the same culled cell rows and accept the
+ * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2
+ * and 3 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
+ * ntypes = 1) and fall back to kernel 1 otherwise. */
 enum {
-  DCM_FORCE_AUTO = 0,        /* the fastest measured choice for the configuration */
-  DCM_FORCE_THREAD = 1,      /* one thread per particle i */
+  DCM_FORCE_AUTO = 0,        /* kernel 3 where it applies, else kernel 1 */
+  DCM_FORCE_THREAD = 1,      /* one thread per particle i, one candidate per instruction */
   DCM_FORCE_TWO_PHASE = 2,   /* per-lane shared-memory buffers of accepted pairs */
-  DCM_FORCE_WARP = 3         /* one warp per particle i, ballot-compacted pair queue */
+  DCM_FORCE_PACKED = 3       /* one thread per particle i, two candidates per FP32x2 instruction */
 };
 
 enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };

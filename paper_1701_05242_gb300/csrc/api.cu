@@ -20,7 +20,7 @@ int set_error(dcm_ctx* ctx, int code, const char* fmt, ...) {
 }
 
 int force_kernel_choice(const dcm_params& p) {
-  return p.force_kernel == DCM_FORCE_AUTO ? DCM_FORCE_THREAD : p.force_kernel;
+  return p.force_kernel == DCM_FORCE_AUTO ? DCM_FORCE_PACKED : p.force_kernel;
 }
 
 int check_launch(dcm_ctx* ctx, const char* what) {
@@ -192,7 +192,7 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
   if (p->iter_max < 1 || p->iter_max > 100000)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "iter_max must be in 1..100000");
   if (p->recompute_every < 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "recompute_every must be >= 1");
-  if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_WARP)
+  if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_PACKED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "precision must be DCM_PREC_FP64 or DCM_PREC_MIXED");
@@ -231,7 +231,7 @@ struct ScratchPlan {
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
-           8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 4 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 16 : 0);
+           8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0);
   }
 };
 
@@ -272,7 +272,7 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
   void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
                  ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
-                 ctx->nnb, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag};
+                 ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -335,6 +335,7 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   alloc((void**)&ctx->adj_part, 8 * 32 * s.red_cap);
   if (p->skin > 0.0) {
     alloc((void**)&ctx->nnb, 4 * nm);
+    alloc((void**)&ctx->nimg, 4 * nm);
     alloc((void**)&ctx->capw, 4 * (nm / 32 + 16));
     alloc((void**)&ctx->offw, 4 * (nm / 32 + 16));
     alloc(&ctx->xbuild, 4 * s.rsize * nm);

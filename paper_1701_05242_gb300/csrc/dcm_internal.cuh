@@ -113,7 +113,8 @@ struct dcm_ctx {
   int64_t scan_cap;
   int64_t launches;         // kernels launched through this context
   // Verlet lists (params.skin > 0)
-  int32_t* nnb;             // n_max: list length of each particle
+  int32_t* nnb;             // n_max: same-image entries of each list (from the front)
+  int32_t* nimg;            // n_max: periodic-image entries of each list (from the back)
   int32_t* capw;            // per warp: longest list of its 32 particles
   int32_t* offw;            // exclusive scan of capw (units of 32 entries)
   uint32_t* list;           // interleaved lists (grown on demand)

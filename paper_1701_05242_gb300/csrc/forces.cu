@@ -53,6 +53,20 @@ __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typenam
   if (part) warp_partials3<R>(e_out, w_out, np, part, nwarp);
 }
 
+// The same walk with the packed two-candidates-per-instruction pair loop
+// (one type, FP32, eps = sigma = 1).
+__global__ void __launch_bounds__(kForceBlock) k_forces_x2(int64_t n, const float4* __restrict__ pos,
+                                                           const float* __restrict__ rc,
+                                                           const int32_t* __restrict__ start, ForceArgs<float> a,
+                                                           float4* __restrict__ force, double* __restrict__ part,
+                                                           int64_t nwarp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float e_out = 0, w_out = 0;
+  int np = 0;
+  if (i < n) force[i] = force_one<float, false, true>(pos, start, a.g, a, (int)i, __ldg(pos + i), rc[i], e_out, w_out, np);
+  if (part) warp_partials3<float>(e_out, w_out, np, part, nwarp);
+}
+
 // ----------------------------------------------------------------------------
 // Two-phase force kernel (one type, FP32, eps = sigma = 1): every lane first
 // filters its candidates row by row and appends the accepted ones (r_ij and
@@ -232,216 +246,11 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
   if (part) warp_partials3<float>(e_out, w_out, c.np, part, nwarp);
 }
 
-// ----------------------------------------------------------------------------
-// Warp-per-particle force kernel (one type, FP32, eps = sigma = 1).
-//
-// A warp takes one particle i at a time.  Its lanes first cut i's culled
-// stencil into pieces (a row window, split where it wraps around the box; at
-// most 3 per row) and write them, with running candidate offsets, to shared
-// memory.  The flattened candidate sequence is then split into 32 equal
-// contiguous blocks, one per lane, so every lane runs the same number of
-// iterations.  A candidate j inside rc_i is appended (r_ij, r^2) to the
-// warp's ring queue with one ballot; whenever 32 are queued all lanes evaluate
-// one pair each, so the pair arithmetic never runs on rejected candidates or
-// idle lanes.  All queued pairs belong to i, so the lanes' partial sums are
-// simply reduced across the warp at the end.
-// ----------------------------------------------------------------------------
-constexpr int kWpWarps = 4;        // warps per block
-constexpr int kWpMaxHalf = 4;     // stencil half-width in cells (H = ceil(rc / l))
-constexpr int kMaxPieces = 3 * (2 * kWpMaxHalf + 1) * (2 * kWpMaxHalf + 1);  // up to 3 pieces a row
-constexpr int kQ = 64;             // ring queue per warp
-
-struct Piece {
-  int j0;      // first sorted slot
-  int len;     // candidates
-  int cum;     // candidates before this piece
-  int code;    // image code: x 0/1/2, y << 2, z << 4 (1: j - L, 2: i - L)
-};
-
-__device__ __forceinline__ void wp_pair(const float4 e, Acc<float>& c) {
-  float inv = recip(e.w);
-  float s6 = inv * inv * inv;
-  float pv = s6 * fmaf(2.0f, s6, -1.0f);
-  float q = pv * inv;
-  c.fx = fmaf(q, e.x, c.fx);
-  c.fy = fmaf(q, e.y, c.fy);
-  c.fz = fmaf(q, e.z, c.fz);
-  c.en += fmaf(s6, s6, -s6);
-  c.vir += pv;
-}
-
-__global__ void __launch_bounds__(32 * kWpWarps) k_forces_wp(int64_t n, const float4* __restrict__ pos,
-                                                             const float* __restrict__ rc,
-                                                             const int32_t* __restrict__ start, ForceArgs<float> a,
-                                                             float4* __restrict__ force, double* __restrict__ part) {
-  __shared__ Piece pcs[kWpWarps][kMaxPieces];
-  __shared__ float4 que[kWpWarps][kQ];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  Piece* P = pcs[wid];
-  float4* Q = que[wid];
-  const Grid<float>& g = a.g;
-  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const float l = g.edge, il = g.inv_edge;
-  const int64_t gw = (int64_t)blockIdx.x * kWpWarps + wid, tw = (int64_t)gridDim.x * kWpWarps;
-  double esum = 0.0, wsum = 0.0;  // lane 0's running sums over its particles
-  int64_t psum = 0;
-  for (int64_t i = gw; i < n; i += tw) {
-    const float4 pi = __ldg(pos + i);
-    float rci = __ldg(rc + i);
-    if (!(rci <= a.rc_max)) rci = a.rc_max;
-    if (!(rci > 0.f)) rci = 0.f;
-    const float rc2 = rci * rci, rc2s = rc2 * 1.000004f;
-    const int cx = cell_coord<float>(pi.x, l, il, nx);
-    const int cy = cell_coord<float>(pi.y, l, il, ny);
-    const int cz = cell_coord<float>(pi.z, l, il, nz);
-    const int H = (int)ceilf(rci * il);
-    const int side = 2 * H + 1, nrow = side * side;
-    // ---- pieces of the culled stencil, in row order
-    int npc = 0, total = 0;
-    for (int r0 = 0; r0 < nrow; r0 += 32) {
-      int r = r0 + lane;
-      // up to three pieces of this row: image -L, no image, image +L in x
-      int ja = 0, la = 0, jb = 0, lb = 0, jc = 0, lc = 0, yzc = 0;
-      if (r < nrow) {
-        int uz = cz - H + r / side, uy = cy - H + r % side;
-        float gz = uz > cz ? (float)uz * l - pi.z : (uz < cz ? pi.z - (float)(uz + 1) * l : 0.f);
-        float gy = uy > cy ? (float)uy * l - pi.y : (uy < cy ? pi.y - (float)(uy + 1) * l : 0.f);
-        float gyz2 = fmaf(gz, gz, gy * gy);
-        if (gyz2 < rc2s) {
-          int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
-          int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
-          yzc = ((uy < 0 ? 1 : (uy >= ny ? 2 : 0)) << 2) | ((uz < 0 ? 1 : (uz >= nz ? 2 : 0)) << 4);
-          float wx = sqrtf(rc2s - gyz2);
-          int ulo = max(ufloor<float>((pi.x - wx) * il - 5e-4f), cx - H);
-          int uhi = min(ufloor<float>((pi.x + wx) * il + 5e-4f), cx + H);
-          const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
-          if (ulo < 0) {
-            int a1 = min(uhi, -1);
-            ja = __ldg(start + row + ulo + nx);
-            la = __ldg(start + row + a1 + nx + 1) - ja;
-          }
-          int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
-          if (a0 <= a1) {
-            jb = __ldg(start + row + a0);
-            lb = __ldg(start + row + a1 + 1) - jb;
-          }
-          if (uhi >= nx) {
-            int c0 = max(ulo, nx);
-            jc = __ldg(start + row + c0 - nx);
-            lc = __ldg(start + row + uhi - nx + 1) - jc;
-          }
-        }
-      }
-      // warp scans of piece counts and candidate counts, then store
-      const int cnt = (la > 0) + (lb > 0) + (lc > 0), mylen = la + lb + lc;
-      int pcnt = cnt, plsum = mylen;
-      for (int o = 1; o < 32; o <<= 1) {
-        int t1 = __shfl_up_sync(0xffffffffu, pcnt, o), t2 = __shfl_up_sync(0xffffffffu, plsum, o);
-        if (lane >= o) { pcnt += t1; plsum += t2; }
-      }
-      int k = npc + pcnt - cnt, cb = total + plsum - mylen;
-      if (la > 0) { P[k++] = Piece{ja, la, cb, yzc | 1}; cb += la; }
-      if (lb > 0) { P[k++] = Piece{jb, lb, cb, yzc}; cb += lb; }
-      if (lc > 0) P[k] = Piece{jc, lc, cb, yzc | 2};
-      npc += __shfl_sync(0xffffffffu, pcnt, 31);
-      total += __shfl_sync(0xffffffffu, plsum, 31);
-    }
-    __syncwarp();
-    // ---- each lane: a contiguous block of the flattened candidates
-    const int S = (total + 31) >> 5;
-    int c = lane * S, cend = min(total, c + S);
-    // first piece of the block: binary search on cum
-    int lo = 0, hi = npc - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (P[mid].cum <= c) lo = mid; else hi = mid - 1;
-    }
-    int pk = lo;
-    Piece cur = npc > 0 ? P[pk] : Piece{0, 0, 0, 0};
-    float xi = pi.x, yi = pi.y, zi = pi.z, sx = 0.f, sy = 0.f, sz = 0.f;
-    auto set_frame = [&](int code) {
-      int xc = code & 3, yc = (code >> 2) & 3, zc = code >> 4;
-      xi = xc == 2 ? pi.x - g.L[0] : pi.x;
-      yi = yc == 2 ? pi.y - g.L[1] : pi.y;
-      zi = zc == 2 ? pi.z - g.L[2] : pi.z;
-      sx = xc == 1 ? -g.L[0] : 0.f;
-      sy = yc == 1 ? -g.L[1] : 0.f;
-      sz = zc == 1 ? -g.L[2] : 0.f;
-    };
-    set_frame(cur.code);
-    Acc<float> acc;
-    int head = 0, tail = 0;  // ring queue indices (warp-uniform)
-    for (int t = 0; t < S; ++t, ++c) {
-      bool ok = c < cend;
-      if (ok && c >= cur.cum + cur.len) {
-        do { cur = P[++pk]; } while (c >= cur.cum + cur.len);
-        set_frame(cur.code);
-      }
-      bool take = false;
-      float4 e;
-      if (ok) {
-        int j = cur.j0 + (c - cur.cum);
-        float4 pj = __ldg(pos + j);
-        e.x = xi - (pj.x + sx);
-        e.y = yi - (pj.y + sy);
-        e.z = zi - (pj.z + sz);
-        e.w = fmaf(e.x, e.x, fmaf(e.y, e.y, e.z * e.z));
-        take = e.w < rc2 && !(j == (int)i && cur.code == 0);
-      }
-      unsigned m = __ballot_sync(0xffffffffu, take);
-      if (take) Q[(tail + __popc(m & lt)) & (kQ - 1)] = e;
-      tail += __popc(m);
-      if (tail - head >= 32) {
-        __syncwarp();
-        wp_pair(Q[(head + lane) & (kQ - 1)], acc);
-        head += 32;
-        acc.np += 1;
-        __syncwarp();
-      }
-    }
-    __syncwarp();
-    if (lane < tail - head) {
-      wp_pair(Q[(head + lane) & (kQ - 1)], acc);
-      acc.np += 1;
-    }
-    __syncwarp();
-    // ---- reduce the lanes' partial sums of particle i
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.fx += __shfl_xor_sync(0xffffffffu, acc.fx, o);
-      acc.fy += __shfl_xor_sync(0xffffffffu, acc.fy, o);
-      acc.fz += __shfl_xor_sync(0xffffffffu, acc.fz, o);
-      acc.en += __shfl_xor_sync(0xffffffffu, acc.en, o);
-      acc.vir += __shfl_xor_sync(0xffffffffu, acc.vir, o);
-      acc.np += __shfl_xor_sync(0xffffffffu, acc.np, o);
-    }
-    float ush = 0.f;
-    if (a.shift && rc2 > 0.f) {
-      float s2 = 1.f / rc2, s6 = s2 * s2 * s2;
-      ush = 4.f * s6 * (s6 - 1.f);
-    }
-    float e_i = 2.f * acc.en - 0.5f * (float)acc.np * ush;
-    float w_i = 12.f * acc.vir;
-    if (lane == 0) force[i] = make_float4(24.f * acc.fx, 24.f * acc.fy, 24.f * acc.fz, e_i);
-    esum += (double)e_i;
-    wsum += (double)w_i;
-    psum += acc.np;
-    __syncwarp();
-  }
-  if (part && lane == 0) {
-    part[gw] = esum;
-    part[tw + gw] = wsum;
-    part[2 * tw + gw] = (double)psum;
-  }
-}
-
-// Kernels 2 and 3 serve one-type mixed-precision runs with eps = sigma = 1;
-// kernel 3's piece table holds stencils of up to 9 x 9 rows.
+// Kernels 2 and 3 serve one-type mixed-precision runs with eps = sigma = 1.
 int resolve_force_kernel(const dcm_ctx* ctx) {
   int k = force_kernel_choice(ctx->p);
   if (k == DCM_FORCE_THREAD) return k;
   if (ctx->p.precision != DCM_PREC_MIXED || lj_general(lj_table(ctx->p))) return DCM_FORCE_THREAD;
-  if (k == DCM_FORCE_WARP && std::ceil(ctx->p.rc_max / ctx->p.l) > (double)kWpMaxHalf) return DCM_FORCE_THREAD;
   return k;
 }
 
@@ -473,14 +282,11 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   bool done = false;
   if constexpr (sizeof(R) == 4) {
     const ForceArgs<float>& af = a;
-    if (resolve_force_kernel(ctx) == DCM_FORCE_WARP) {
-      // a grid of 16 waves of blocks strides over the particles
-      int64_t nblk_wp = std::min<int64_t>((n + kWpWarps - 1) / kWpWarps, (int64_t)152 * 16 * 4);
-      if (totals) nblk_wp = std::min<int64_t>(nblk_wp, ctx->red_cap / kWpWarps);
-      DCM_LAUNCH(ctx, k_forces_wp, (unsigned)nblk_wp, 32 * kWpWarps, 0, st, n, pos, rc, cell_start, af, force, part);
-      nwarp = nblk_wp * kWpWarps;
+    const int kind = resolve_force_kernel(ctx);
+    if (kind == DCM_FORCE_PACKED) {
+      DCM_LAUNCH(ctx, k_forces_x2, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part, nwarp);
       done = true;
-    } else if (resolve_force_kernel(ctx) == DCM_FORCE_TWO_PHASE) {
+    } else if (kind == DCM_FORCE_TWO_PHASE) {
       static_assert(kF2Block == kForceBlock, "partials layout assumes equal blocks");
       DCM_LAUNCH(ctx, k_forces2, (unsigned)nblk, kF2Block, 0, st, n, pos, rc, cell_start, af, force, part, nwarp);
       done = true;

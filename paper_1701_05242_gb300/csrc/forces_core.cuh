@@ -103,16 +103,83 @@ __device__ __forceinline__ void pair_range(const typename RT<R>::R4* __restrict_
   }
 }
 
+// Packed form of the one-type FP32 pair loop: candidates j and j + 1 of a
+// segment share every arithmetic instruction that has an FP32x2 form (FMA,
+// MUL, ADD); the comparison, the hardware reciprocal and the select stay
+// scalar.  An odd segment's last pair slot repeats its last candidate and is
+// masked out.  Signs: with d = r_j - r_i (no packed operand needs negating),
+// y = 1/r^2 (zero when rejected) and s6 = y^3,
+//   r.F/24 = s6 (2 s6 - 1),   -F_i/24 = sum (r.F/24) y d,   U/4 = s6 (s6 - 1),
+// and the reciprocal is refined exactly as recip() does.
+struct Acc2 {
+  float2 fx = {0.f, 0.f}, fy = {0.f, 0.f}, fz = {0.f, 0.f};
+  float2 en = {0.f, 0.f}, vir = {0.f, 0.f};
+  int np = 0;
+};
+
+template <bool SJ>
+__device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
+                                              float zi, float shx, float shy, float shz, float rc2, Acc2& c) {
+  const float2 two = make_float2(2.f, 2.f), m1 = make_float2(-1.f, -1.f);
+  for (int j = lo; j < hi; j += 2) {
+    const bool has1 = j + 1 < hi;
+    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + (has1 ? j + 1 : j));
+    float2 dx, dy, dz;
+    if (SJ) {
+      dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
+      dy = make_float2((p0.y + shy) - yi, (p1.y + shy) - yi);
+      dz = make_float2((p0.z + shz) - zi, (p1.z + shz) - zi);
+    } else {
+      dx = make_float2(p0.x - xi, p1.x - xi);
+      dy = make_float2(p0.y - yi, p1.y - yi);
+      dz = make_float2(p0.z - zi, p1.z - zi);
+    }
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float y0, y1;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+    const float2 e = make_float2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
+    float2 y = make_float2(y0, y1);
+    y = __ffma2_rn(y, e, y);
+    const bool a0 = r2.x < rc2, a1 = has1 && r2.y < rc2;
+    y = make_float2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
+    const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+    const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1));  // r.F / 24
+    const float2 q = __fmul2_rn(pv, y);
+    c.fx = __ffma2_rn(q, dx, c.fx);
+    c.fy = __ffma2_rn(q, dy, c.fy);
+    c.fz = __ffma2_rn(q, dz, c.fz);
+    c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1), c.en);
+    c.vir = __fadd2_rn(c.vir, pv);
+    c.np += (int)a0 + (int)a1;
+  }
+}
+
+// Segment dispatch: the packed loop for one-type FP32, the scalar loop
+// otherwise.
+template <typename R, bool SJ, bool TYPED, bool X2>
+__device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi, R zi,
+                                        R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a, const R* ushift,
+                                        Acc<R>& c, Acc2& c2) {
+  if constexpr (X2) {
+    pair_range_x2<SJ>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2);
+  } else {
+    pair_range<R, SJ, TYPED>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
+  }
+}
+
 // Forces, energy and virial of particle `self` (position pi, cutoff rc_in)
 // over the cell grid g whose cell starts are start[0 .. ncell] (positions
 // pos, sorted by cell).  Returns the force and writes e_i, w_i, pairs.
-template <typename R, bool TYPED>
+template <typename R, bool TYPED, bool X2 = false>
 __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
                                                         const int32_t* __restrict__ start, const Grid<R>& g,
                                                         const ForceArgs<R>& a, int self,
                                                         const typename RT<R>::R4& pi, R rc_in, R& e_out, R& w_out,
                                                         int& np_out) {
+  static_assert(!X2 || (sizeof(R) == 4 && !TYPED), "the packed loop serves one-type FP32 only");
   Acc<R> c;
+  Acc2 c2;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const R l = g.edge, il = g.inv_edge;
   // cutoffs outside [0, rc_max] (or NaN) are clamped: the stencil then never
@@ -160,7 +227,7 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       if (ulo < 0) {
         int a1 = min(uhi, -1);
         int j0 = __ldg(start + row + ulo + nx), j1 = __ldg(start + row + a1 + nx + 1);
-        pair_range<R, true, TYPED>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c);
+        segment<R, true, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2);
       }
       // segment 0 <= u < nx: no x shift; the particle itself is skipped
       {
@@ -168,10 +235,11 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
         if (a0 <= a1) {
           int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
           if (ysh == (R)0 && zsh == (R)0) {
-            pair_range<R, false, TYPED>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c);
-            pair_range<R, false, TYPED>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c);
+            segment<R, false, TYPED, X2>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2);
+            segment<R, false, TYPED, X2>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
+                                         c2);
           } else {
-            pair_range<R, true, TYPED>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c);
+            segment<R, true, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2);
           }
         }
       }
@@ -179,9 +247,17 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       if (uhi >= nx) {
         int a0 = max(ulo, nx);
         int j0 = __ldg(start + row + a0 - nx), j1 = __ldg(start + row + uhi - nx + 1);
-        pair_range<R, true, TYPED>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c);
+        segment<R, true, TYPED, X2>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2);
       }
     }
+  }
+  if constexpr (X2) {  // fold the two packed lanes (and the sign of d) into c
+    c.fx = -(c2.fx.x + c2.fx.y);
+    c.fy = -(c2.fy.x + c2.fy.y);
+    c.fz = -(c2.fz.x + c2.fz.y);
+    c.en = c2.en.x + c2.en.y;
+    c.vir = c2.vir.x + c2.vir.y;
+    c.np = c2.np;
   }
   typename RT<R>::R4 out;
   if (TYPED) {

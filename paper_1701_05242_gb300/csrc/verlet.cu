@@ -3,12 +3,16 @@
 //
 // Build (at a rebuild): for every particle i, the j != i with
 // |r_ij| < rc_i + skin, found by the same culled cell-row walk as the
-// cell-list force kernel.  A count pass sizes the lists; the lists of the 32
-// particles of a warp are interleaved (entry k of lane l at base + 32 k + l,
-// base = 32 x the sum of the earlier warps' longest lists) so that the force
-// loop reads them coalesced.  An entry is j | image code << 26: per dimension
-// 0 = same image, 1 = j taken at x_j - L, 2 = i taken at x_i - L, so that the
-// force loop forms every r_ij with one rounding, exactly as the cell walk.
+// cell-list force kernel.  The lists of the 32 particles of a warp share one
+// interleaved region (entry k of lane l at base + 32 k + l, base = 32 x the
+// sum of the earlier warps' capacities) so that the force loop reads them
+// coalesced.  Same-image neighbours are stored from the front of a lane's
+// column as plain indices j; neighbours across the periodic boundary from the
+// back as j | image code << 26, the code per dimension 0 = same image, 1 = j
+// taken at x_j - L, 2 = i taken at x_i - L, so that every r_ij is formed
+// with one rounding, exactly as in the cell walk.  The force loop therefore
+// runs over plain entries without decoding and treats the few image entries
+// apart.
 //
 // Between rebuilds particles are not rebinned and positions are not wrapped
 // (the image codes stay valid); dcm_step rebuilds when the largest
@@ -104,34 +108,46 @@ __device__ __forceinline__ R list_radius(R rc, R rc_max, R skin) {
 template <typename R>
 __global__ void __launch_bounds__(128) k_list_count(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                     const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                    Grid<R> g, R rc_max, R skin, int32_t* __restrict__ nnb,
-                                                    int32_t* __restrict__ capw) {
+                                                    Grid<R> g, R rc_max, R skin, int32_t* __restrict__ capw) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int cnt = 0;
   if (i < n) {
     auto pi = ldg4(pos + i);
     walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int, uint32_t) { ++cnt; });
-    nnb[i] = cnt;
   }
   int m = cnt;
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) capw[i >> 5] = m;
 }
 
+// Fill lane columns of capacity capw[warp]: plain entries from the front,
+// image entries from the back.  More than capw entries raise *flag (the lists
+// are then incomplete and the caller counts exactly and fills again).
 template <typename R>
 __global__ void __launch_bounds__(128) k_list_fill(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                    const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                   Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ offw,
-                                                   uint32_t* __restrict__ list) {
+                                                   Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ capw,
+                                                   const int32_t* __restrict__ offw, uint32_t* __restrict__ list,
+                                                   int32_t* __restrict__ nnb, int32_t* __restrict__ nimg,
+                                                   int32_t* __restrict__ flag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int cap = capw[i >> 5];
   uint32_t* out = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
-  int k = 0;
+  int kf = 0, kb = 0;
   auto pi = ldg4(pos + i);
   walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int j, uint32_t code) {
-    out[(int64_t)k * 32] = (uint32_t)j | (code << kIdxBits);
-    ++k;
+    if (code == 0) {
+      if (kf + kb < cap) out[(int64_t)kf * 32] = (uint32_t)j;
+      ++kf;
+    } else {
+      if (kf + kb < cap) out[(int64_t)(cap - 1 - kb) * 32] = (uint32_t)j | (code << kIdxBits);
+      ++kb;
+    }
   });
+  nnb[i] = kf;
+  nimg[i] = kb;
+  if (kf + kb > cap) atomicExch(flag, 1);
 }
 
 // Capacity bound of a list of radius R: the particles a sphere of radius R can
@@ -151,29 +167,6 @@ __global__ void k_list_caps(int64_t n, const R* __restrict__ rc, R rc_max, R ski
   if ((threadIdx.x & 31) == 0) capw[i >> 5] = cap;
 }
 
-// One walk: writes the list into the bounded space and its length; a list
-// longer than its warp's capacity raises the overflow flag (the caller then
-// counts exactly and fills again).
-template <typename R>
-__global__ void __launch_bounds__(128) k_list_fill1(int64_t n, const typename RT<R>::R4* __restrict__ pos,
-                                                    const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                    Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ capw,
-                                                    const int32_t* __restrict__ offw, uint32_t* __restrict__ list,
-                                                    int32_t* __restrict__ nnb, int32_t* __restrict__ flag) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int cap = capw[i >> 5];
-  uint32_t* out = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
-  int k = 0;
-  auto pi = ldg4(pos + i);
-  walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int j, uint32_t code) {
-    if (k < cap) out[(int64_t)k * 32] = (uint32_t)j | (code << kIdxBits);
-    ++k;
-  });
-  nnb[i] = k;
-  if (k > cap) atomicExch(flag, 1);
-}
-
 // Per-warp partials (E, W, pairs) as in the cell-list kernel.
 template <typename R>
 __device__ __forceinline__ void list_partials(R a, R b, int c, double* part, int64_t nslot) {
@@ -190,11 +183,79 @@ __device__ __forceinline__ void list_partials(R a, R b, int c, double* part, int
   }
 }
 
-// Forces over the lists: the pair rule |r_ij| < rc_i is applied to every
-// entry (the list holds the j within rc_i + skin at build time).
+// Pair term of the list kernels: accumulates j's contribution to i for the
+// components (dx, dy, dz) of r_ij (rejected beyond rc_i).
+template <typename R, bool TYPED>
+__device__ __forceinline__ void list_pair(R dx, R dy, R dz, R rc2, int ti, R pjw, const ForceArgs<R>& a,
+                                          const R* ushift, Acc<R>& c) {
+  R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+  bool acc = r2 < rc2;
+  R inv = recip(r2);
+  inv = acc ? inv : (R)0;
+  if (TYPED) {
+    int tj = type_of(pjw, a.ntypes);
+    int tp = ti * a.ntypes + tj;
+    R s2 = a.sig2[tp] * inv;
+    R s6 = s2 * s2 * s2;
+    R pv = a.eps24[tp] * s6 * fma((R)2, s6, (R)-1);
+    R fs = pv * inv;
+    c.fx = fma(fs, dx, c.fx);
+    c.fy = fma(fs, dy, c.fy);
+    c.fz = fma(fs, dz, c.fz);
+    R us = tj == 0 ? ushift[0] : (tj == 1 ? ushift[1] : (tj == 2 ? ushift[2] : ushift[3]));
+    R u = a.eps4[tp] * s6 * (s6 - (R)1);
+    c.en += acc ? u - us : (R)0;
+    c.vir += pv;
+  } else {
+    R s6 = inv * inv * inv;
+    R pv = s6 * fma((R)2, s6, (R)-1);
+    R q = pv * inv;
+    c.fx = fma(q, dx, c.fx);
+    c.fy = fma(q, dy, c.fy);
+    c.fz = fma(q, dz, c.fz);
+    c.en += fma(s6, s6, -s6);
+    c.vir += pv;
+  }
+  c.np += acc ? 1 : 0;
+}
+
+// r_ij of an image entry (code != 0), one rounding per component.
+template <typename R>
+__device__ __forceinline__ void image_delta(uint32_t code, const typename RT<R>::R4& pi,
+                                            const typename RT<R>::R4& pj, const Grid<R>& g, R& dx, R& dy, R& dz) {
+  uint32_t xc = code & 3, yc = (code >> 2) & 3, zc = code >> 4;
+  dx = (xc == 2 ? pi.x - g.L[0] : pi.x) - (xc == 1 ? pj.x - g.L[0] : pj.x);
+  dy = (yc == 2 ? pi.y - g.L[1] : pi.y) - (yc == 1 ? pj.y - g.L[1] : pj.y);
+  dz = (zc == 2 ? pi.z - g.L[2] : pi.z) - (zc == 1 ? pj.z - g.L[2] : pj.z);
+}
+
+template <typename R, bool TYPED>
+__device__ __forceinline__ void list_finish(const Acc<R>& c, const R* ushift, typename RT<R>::R4& out, R& e_out,
+                                            R& w_out) {
+  if (TYPED) {
+    out.x = c.fx;
+    out.y = c.fy;
+    out.z = c.fz;
+    e_out = (R)0.5 * c.en;
+    w_out = (R)0.5 * c.vir;
+  } else {
+    out.x = (R)24 * c.fx;
+    out.y = (R)24 * c.fy;
+    out.z = (R)24 * c.fz;
+    e_out = (R)2 * c.en - (R)0.5 * (R)c.np * ushift[0];
+    w_out = (R)12 * c.vir;
+  }
+  out.w = e_out;
+}
+
+// Forces over the lists (general form: any types, FP32 or FP64): the pair
+// rule |r_ij| < rc_i is applied to every entry (the list holds the j within
+// rc_i + skin at build time).
 template <typename R, bool TYPED>
 __global__ void __launch_bounds__(128) k_forces_list(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                      const R* __restrict__ rc, const int32_t* __restrict__ nnb,
+                                                     const int32_t* __restrict__ nimg,
+                                                     const int32_t* __restrict__ capw,
                                                      const int32_t* __restrict__ offw,
                                                      const uint32_t* __restrict__ list, ForceArgs<R> a,
                                                      typename RT<R>::R4* __restrict__ force, double* __restrict__ part,
@@ -210,7 +271,7 @@ __global__ void __launch_bounds__(128) k_forces_list(int64_t n, const typename R
     const R rc2 = rci * rci;
     const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
     R ushift[4] = {0, 0, 0, 0};
-    if (a.shift) {
+    if (a.shift && rc2 > (R)0) {
       for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
         int tp = ti * a.ntypes + t;
         R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
@@ -219,73 +280,115 @@ __global__ void __launch_bounds__(128) k_forces_list(int64_t n, const typename R
       }
     }
     const uint32_t* lp = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
-    const int m = nnb[i];
-    const R Lx = a.g.L[0], Ly = a.g.L[1], Lz = a.g.L[2];
+    const int m = nnb[i], cap = capw[i >> 5], mb = nimg[i];
 #pragma unroll 2
     for (int k = 0; k < m; ++k) {
-      uint32_t e = __ldg(lp + (int64_t)k * 32);
-      int j = (int)(e & kIdxMask);
-      uint32_t code = e >> kIdxBits;
+      int j = (int)__ldg(lp + (int64_t)k * 32);
       auto pj = ldg4(pos + j);
+      list_pair<R, TYPED>(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, rc2, ti, pj.w, a, ushift, c);
+    }
+    for (int k = cap - mb; k < cap; ++k) {
+      uint32_t e = __ldg(lp + (int64_t)k * 32);
+      auto pj = ldg4(pos + (e & kIdxMask));
       R dx, dy, dz;
-      if (code == 0) {
-        dx = pi.x - pj.x;
-        dy = pi.y - pj.y;
-        dz = pi.z - pj.z;
-      } else {
-        uint32_t xc = code & 3, yc = (code >> 2) & 3, zc = code >> 4;
-        dx = (xc == 2 ? pi.x - Lx : pi.x) - (xc == 1 ? pj.x - Lx : pj.x);
-        dy = (yc == 2 ? pi.y - Ly : pi.y) - (yc == 1 ? pj.y - Ly : pj.y);
-        dz = (zc == 2 ? pi.z - Lz : pi.z) - (zc == 1 ? pj.z - Lz : pj.z);
-      }
-      R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-      bool acc = r2 < rc2;
-      R inv = recip(r2);
-      inv = acc ? inv : (R)0;
-      if (TYPED) {
-        int tj = type_of(pj.w, a.ntypes);
-        int tp = ti * a.ntypes + tj;
-        R s2 = a.sig2[tp] * inv;
-        R s6 = s2 * s2 * s2;
-        R pv = a.eps24[tp] * s6 * fma((R)2, s6, (R)-1);
-        R fs = pv * inv;
-        c.fx = fma(fs, dx, c.fx);
-        c.fy = fma(fs, dy, c.fy);
-        c.fz = fma(fs, dz, c.fz);
-        R us = tj == 0 ? ushift[0] : (tj == 1 ? ushift[1] : (tj == 2 ? ushift[2] : ushift[3]));
-        R u = a.eps4[tp] * s6 * (s6 - (R)1);
-        c.en += acc ? u - us : (R)0;
-        c.vir += pv;
-      } else {
-        R s6 = inv * inv * inv;
-        R pv = s6 * fma((R)2, s6, (R)-1);
-        R q = pv * inv;
-        c.fx = fma(q, dx, c.fx);
-        c.fy = fma(q, dy, c.fy);
-        c.fz = fma(q, dz, c.fz);
-        c.en += fma(s6, s6, -s6);
-        c.vir += pv;
-      }
-      c.np += acc ? 1 : 0;
+      image_delta<R>(e >> kIdxBits, pi, pj, a.g, dx, dy, dz);
+      list_pair<R, TYPED>(dx, dy, dz, rc2, ti, pj.w, a, ushift, c);
     }
     typename RT<R>::R4 out;
-    if (TYPED) {
-      out.x = c.fx;
-      out.y = c.fy;
-      out.z = c.fz;
-      e_out = (R)0.5 * c.en;
-      w_out = (R)0.5 * c.vir;
-    } else {
-      out.x = (R)24 * c.fx;
-      out.y = (R)24 * c.fy;
-      out.z = (R)24 * c.fz;
-      e_out = (R)2 * c.en - (R)0.5 * (R)c.np * ushift[0];
-      w_out = (R)12 * c.vir;
-    }
-    out.w = e_out;
+    list_finish<R, TYPED>(c, ushift, out, e_out, w_out);
     force[i] = out;
   }
   if (part) list_partials<R>(e_out, w_out, c.np, part, nwarp);
+}
+
+// Forces over the lists, one type with eps = sigma = 1, FP32: the plain
+// entries are taken two at a time with packed FP32x2 arithmetic (one
+// instruction for both pairs wherever the operation allows), which halves the
+// issue slots of the pair math.  With d = r_j - r_i (so that no packed operand
+// needs negating), y = 1/r^2 (zero beyond rc_i) and s6 = y^3:
+//   r.F/24 = s6 (2 s6 - 1),   -F_i/24 = sum (r.F/24) y d,   U/4 = s6 (s6 - 1).
+// The reciprocal is refined exactly as in the cell kernel (one Newton step on
+// the hardware approximation, the residual 1 - r^2 y0 formed by an FMA).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__global__ void __launch_bounds__(128) k_forces_list_x2(int64_t n, const float4* __restrict__ pos,
+                                                        const float* __restrict__ rc, const int32_t* __restrict__ nnb,
+                                                        const int32_t* __restrict__ nimg,
+                                                        const int32_t* __restrict__ capw,
+                                                        const int32_t* __restrict__ offw,
+                                                        const uint32_t* __restrict__ list, ForceArgs<float> a,
+                                                        float4* __restrict__ force, double* __restrict__ part,
+                                                        int64_t nwarp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float e_out = 0.f, w_out = 0.f;
+  int np = 0;
+  if (i < n) {
+    const float4 pi = __ldg(pos + i);
+    float rci = __ldg(rc + i);
+    if (!(rci <= a.rc_max)) rci = a.rc_max;
+    if (!(rci > 0.f)) rci = 0.f;
+    const float rc2 = rci * rci;
+    const uint32_t* lp = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
+    const int m = nnb[i], cap = capw[i >> 5], mb = nimg[i];
+    const float2 two = f2(2.f, 2.f), m1 = f2(-1.f, -1.f);
+    float2 fx = f2(0.f, 0.f), fy = fx, fz = fx, en = fx, vir = fx;
+    int k = 0;
+    for (; k + 1 < m; k += 2) {
+      const int j0 = (int)__ldg(lp + (int64_t)k * 32), j1 = (int)__ldg(lp + (int64_t)(k + 1) * 32);
+      const float4 p0 = __ldg(pos + j0), p1 = __ldg(pos + j1);
+      const float2 dx = f2(p0.x - pi.x, p1.x - pi.x);
+      const float2 dy = f2(p0.y - pi.y, p1.y - pi.y);
+      const float2 dz = f2(p0.z - pi.z, p1.z - pi.z);
+      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float y0, y1;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+      const float2 e = f2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
+      float2 y = f2(y0, y1);
+      y = __ffma2_rn(y, e, y);
+      const bool a0 = r2.x < rc2, a1 = r2.y < rc2;
+      y = f2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
+      const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+      const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1));  // r.F / 24
+      const float2 q = __fmul2_rn(pv, y);
+      fx = __ffma2_rn(q, dx, fx);
+      fy = __ffma2_rn(q, dy, fy);
+      fz = __ffma2_rn(q, dz, fz);
+      en = __ffma2_rn(s6, __fadd2_rn(s6, m1), en);
+      vir = __fadd2_rn(vir, pv);
+      np += (int)a0 + (int)a1;
+    }
+    Acc<float> c;
+    c.fx = -(fx.x + fx.y);
+    c.fy = -(fy.x + fy.y);
+    c.fz = -(fz.x + fz.y);
+    c.en = en.x + en.y;
+    c.vir = vir.x + vir.y;
+    c.np = np;
+    const float ushift0 = 0.f;
+    if (k < m) {
+      const int j = (int)__ldg(lp + (int64_t)k * 32);
+      const float4 pj = __ldg(pos + j);
+      list_pair<float, false>(pi.x - pj.x, pi.y - pj.y, pi.z - pj.z, rc2, 0, pj.w, a, &ushift0, c);
+    }
+    for (int kk = cap - mb; kk < cap; ++kk) {
+      const uint32_t e = __ldg(lp + (int64_t)kk * 32);
+      const float4 pj = __ldg(pos + (e & kIdxMask));
+      float dx, dy, dz;
+      image_delta<float>(e >> kIdxBits, pi, pj, a.g, dx, dy, dz);
+      list_pair<float, false>(dx, dy, dz, rc2, 0, pj.w, a, &ushift0, c);
+    }
+    float ushift[4] = {0.f, 0.f, 0.f, 0.f};
+    if (a.shift && rc2 > 0.f) {
+      float s2 = 1.f / rc2, s6 = s2 * s2 * s2;
+      ushift[0] = 4.f * s6 * (s6 - 1.f);
+    }
+    float4 out;
+    list_finish<float, false>(c, ushift, out, e_out, w_out);
+    force[i] = out;
+    np = c.np;
+  }
+  if (part) list_partials<float>(e_out, w_out, np, part, nwarp);
 }
 
 // Half kick and drift without wrapping (the list's image codes stay valid),
@@ -377,22 +480,23 @@ int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   if ((r = ensure_list_capacity(ctx, (int64_t)ctx->host_status[1] * 32))) return r;
   if (n > 0)
-    DCM_LAUNCH(ctx, k_list_fill1<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, ctx->capw,
-               ctx->offw, ctx->list, ctx->nnb, ctx->lflag);
+    DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, ctx->capw,
+               ctx->offw, ctx->list, ctx->nnb, ctx->nimg, ctx->lflag);
   DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 3, ctx->lflag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   if (ctx->host_status[3]) {
-    // some list outgrew its bound: count exactly, then fill
+    // some list outgrew its bound: count exactly, then fill again
     if (n > 0)
       DCM_LAUNCH(ctx, k_list_count<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin,
-                 ctx->nnb, ctx->capw);
+                 ctx->capw);
     if ((r = exclusive_scan(ctx, ctx->capw, ctx->offw, nw, st))) return r;
+    DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->lflag, 0, sizeof(int32_t), st));
     DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 1, ctx->offw + nw, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     if ((r = ensure_list_capacity(ctx, (int64_t)ctx->host_status[1] * 32))) return r;
     if (n > 0)
       DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin,
-                 ctx->offw, ctx->list);
+                 ctx->capw, ctx->offw, ctx->list, ctx->nnb, ctx->nimg, ctx->lflag);
   }
   DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->xbuild, pos, sizeof(typename RT<R>::R4) * n, cudaMemcpyDeviceToDevice, st));
   stage_end(ctx, DCM_STAGE_LISTS, st);
@@ -423,7 +527,17 @@ int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R*
   double* part = totals ? ctx->red : nullptr;
   auto kern = lj_general(t) ? k_forces_list<R, true> : k_forces_list<R, false>;
   stage_begin(ctx, DCM_STAGE_FORCES, st);
-  DCM_LAUNCH(ctx, kern, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->offw, ctx->list, a, force, part, nwarp);
+  bool packed = false;
+  if constexpr (sizeof(R) == 4) {
+    if (!lj_general(t)) {
+      DCM_LAUNCH(ctx, k_forces_list_x2, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->nimg, ctx->capw,
+                 ctx->offw, ctx->list, a, force, part, nwarp);
+      packed = true;
+    }
+  }
+  if (!packed)
+    DCM_LAUNCH(ctx, kern, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->nimg, ctx->capw, ctx->offw,
+               ctx->list, a, force, part, nwarp);
   stage_end(ctx, DCM_STAGE_FORCES, st);
   int r = check_launch(ctx, "list_forces");
   if (r) return r;

@@ -31,7 +31,7 @@ DCM_PREC_MIXED = 1
 DCM_FORCE_AUTO = 0
 DCM_FORCE_THREAD = 1
 DCM_FORCE_TWO_PHASE = 2
-DCM_FORCE_WARP = 3
+DCM_FORCE_PACKED = 3
 
 _ERRNAMES = {1: "INVALID_ARG", 2: "BOX", 3: "CUDA", 4: "NOT_CONVERGED", 5: "CAPACITY", 6: "NOMEM"}
 
@@ -328,7 +328,7 @@ def dcm_force_kernel(ctx: Context) -> int:
     return k.value
 
 
-FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_TWO_PHASE: "k_forces2", DCM_FORCE_WARP: "k_forces_wp"}
+FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_TWO_PHASE: "k_forces2", DCM_FORCE_PACKED: "k_forces_x2"}
 
 
 # ---------------------------------------------------------------- batched form
