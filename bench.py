@@ -74,6 +74,15 @@ def dist_init(world, local, backend):
     return None
 
 
+def rank_spec(workload: str, rank: int):
+    """Each rank steps its own replica of the workload: the same recipe and
+    sizes, seeded with the rank (independent systems, no exchange)."""
+    from paper_1701_05242_gb300 import synth
+    spec = synth.named(workload)
+    spec.seed = rank
+    return spec
+
+
 def aggregate(dist, units: float, seconds: float):
     """Whole-job throughput: units summed over ranks, time = max over ranks."""
     if dist is None:
@@ -267,9 +276,7 @@ def run_gb300(args):
     import paper_1701_05242_gb300.dcm as D
     from paper_1701_05242_gb300 import synth
 
-    spec = synth.named(args.workload)
-    spec.seed = rank
-    slab = synth.make_slab(spec)
+    slab = synth.make_slab(rank_spec(args.workload, rank))
     n = slab.n
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -416,7 +423,7 @@ def run_gb300(args):
                "config": {"workload": args.workload, "particles_per_gpu": n, "box": list(slab.box),
                           "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": args.cell_edge, "skin": args.skin, "dt": DT,
                           "timesteps_per_step": K_RECOMPUTE, "recompute_every": K_RECOMPUTE,
-                          "precision": "fp32 pair math, fp64 totals", "l2": "inputs larger than L2 (positions 248 MB)",
+                          "precision": "fp32 pair math, fp64 totals", "l2": f"inputs larger than L2 (positions {16 * n / 1e6:.0f} MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "stage_ms_per_step": stage_ms, "fp64_form": fp64, "batched_form": batch, "device_status": status,

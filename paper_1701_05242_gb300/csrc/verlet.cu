@@ -28,15 +28,18 @@ namespace dcm {
 constexpr uint32_t kIdxBits = 26;
 constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1;
 
-// Walk the cell rows of particle i within radius sqrt(rl2) and call f(j, code)
-// for every j != i with r_ij^2 < rl2.
-template <typename R, typename F>
-__device__ __forceinline__ void walk(const typename RT<R>::R4* __restrict__ pos, const int32_t* __restrict__ start,
-                                     const Grid<R>& g, int self, const typename RT<R>::R4& pi, R rl, F&& f) {
+// Walk the culled cell rows of particle i for radius rl and hand each row
+// segment to the segment visitor v: v.plain(j0, j1, xi, yi, zi) for
+// segments in i's own image (with i itself cut out) and v.image(j0, j1, xi,
+// yi, zi, shx, shy, shz, code) for segments across the periodic boundary
+// (xi.. the i coordinates and sh.. the j shifts of that image, code as stored
+// in the lists).  The visitor tests r_ij^2 < rl^2 itself.
+template <typename R, typename V>
+__device__ __forceinline__ void walk_segments(const int32_t* __restrict__ start, const Grid<R>& g, int self,
+                                              const typename RT<R>::R4& pi, R rl, V& v) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const R l = g.edge, il = g.inv_edge;
-  const R rl2 = rl * rl;
-  const R rl2s = rl2 * (R)1.000004;
+  const R rl2s = rl * rl * (R)1.000004;  // culling slack; the pair test is exact
   const int cx = cell_coord<R>(pi.x, l, il, nx);
   const int cy = cell_coord<R>(pi.y, l, il, ny);
   const int cz = cell_coord<R>(pi.z, l, il, nz);
@@ -61,42 +64,87 @@ __device__ __forceinline__ void walk(const typename RT<R>::R4* __restrict__ pos,
       int ulo = max(ufloor<R>((pi.x - wx) * il - (R)5e-4), cx - H);
       int uhi = min(ufloor<R>((pi.x + wx) * il + (R)5e-4), cx + H);
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
-      for (int seg = 0; seg < 3; ++seg) {
-        int a0, a1;
-        uint32_t xc;
-        if (seg == 0) {
-          a0 = ulo;
-          a1 = min(uhi, -1);
-          xc = 1;
-        } else if (seg == 1) {
-          a0 = max(ulo, 0);
-          a1 = min(uhi, nx - 1);
-          xc = 0;
-        } else {
-          a0 = max(ulo, nx);
-          a1 = uhi;
-          xc = 2;
+      const uint32_t yzc = (yc << 2) | (zc << 4);
+      if (ulo < 0) {  // image -L in x: shift j
+        int a1 = min(uhi, -1);
+        int j0 = __ldg(start + row + ulo + nx), j1 = __ldg(start + row + a1 + nx + 1);
+        v.image(j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, yzc | 1u);
+      }
+      {
+        int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
+        if (a0 <= a1) {
+          int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
+          if (yzc == 0) {
+            v.plain(j0, min(j1, self), pi.x, yi, zi);
+            v.plain(max(j0, self + 1), j1, pi.x, yi, zi);
+          } else {
+            v.image(j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, yzc);
+          }
         }
-        if (a0 > a1) continue;
-        int w0 = seg == 0 ? a0 + nx : (seg == 2 ? a0 - nx : a0);
-        int w1 = seg == 0 ? a1 + nx : (seg == 2 ? a1 - nx : a1);
-        int j0 = __ldg(start + row + w0), j1 = __ldg(start + row + w1 + 1);
-        R xi = xc == 2 ? pi.x - g.L[0] : pi.x;
-        R xsh = xc == 1 ? -g.L[0] : (R)0;
-        uint32_t code = xc | (yc << 2) | (zc << 4);
-        for (int j = j0; j < j1; ++j) {
-          if (j == self && code == 0) continue;
-          auto pj = ldg4(pos + j);
-          R dx = xi - (pj.x + xsh);
-          R dy = yi - (pj.y + ysh);
-          R dz = zi - (pj.z + zsh);
-          R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-          if (r2 < rl2) f(j, code);
-        }
+      }
+      if (uhi >= nx) {  // image +L in x: shift i
+        int a0 = max(ulo, nx);
+        int j0 = __ldg(start + row + a0 - nx), j1 = __ldg(start + row + uhi - nx + 1);
+        v.image(j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, yzc | 2u);
       }
     }
   }
 }
+
+// Segment visitors of the build: counting, and filling a lane's column
+// (plain entries from the front, image entries from the back, nothing
+// written past the column's capacity).
+template <typename R>
+struct CountVisitor {
+  const typename RT<R>::R4* __restrict__ pos;
+  R rl2;
+  int cnt;
+  __device__ __forceinline__ void plain(int j0, int j1, R xi, R yi, R zi) {
+    for (int j = j0; j < j1; ++j) {
+      auto pj = ldg4(pos + j);
+      R dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+      cnt += fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 ? 1 : 0;
+    }
+  }
+  __device__ __forceinline__ void image(int j0, int j1, R xi, R yi, R zi, R shx, R shy, R shz, uint32_t) {
+    for (int j = j0; j < j1; ++j) {
+      auto pj = ldg4(pos + j);
+      R dx = xi - (pj.x + shx), dy = yi - (pj.y + shy), dz = zi - (pj.z + shz);
+      cnt += fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 ? 1 : 0;
+    }
+  }
+};
+
+template <typename R>
+struct FillVisitor {
+  const typename RT<R>::R4* __restrict__ pos;
+  uint32_t* __restrict__ out;  // the lane's column: entry k at out[32 k]
+  R rl2;
+  int cap, kf, kb;
+  __device__ __forceinline__ void plain(int j0, int j1, R xi, R yi, R zi) {
+    const int lim = cap - kb;
+    int k = kf;
+    for (int j = j0; j < j1; ++j) {
+      auto pj = ldg4(pos + j);
+      R dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
+      if (fma(dx, dx, fma(dy, dy, dz * dz)) < rl2) {
+        if (k < lim) out[(int64_t)k * 32] = (uint32_t)j;
+        ++k;
+      }
+    }
+    kf = k;
+  }
+  __device__ __forceinline__ void image(int j0, int j1, R xi, R yi, R zi, R shx, R shy, R shz, uint32_t code) {
+    for (int j = j0; j < j1; ++j) {
+      auto pj = ldg4(pos + j);
+      R dx = xi - (pj.x + shx), dy = yi - (pj.y + shy), dz = zi - (pj.z + shz);
+      if (fma(dx, dx, fma(dy, dy, dz * dz)) < rl2) {
+        if (kf + kb < cap) out[(int64_t)(cap - 1 - kb) * 32] = (uint32_t)j | (code << kIdxBits);
+        ++kb;
+      }
+    }
+  }
+};
 
 template <typename R>
 __device__ __forceinline__ R list_radius(R rc, R rc_max, R skin) {
@@ -113,7 +161,10 @@ __global__ void __launch_bounds__(128) k_list_count(int64_t n, const typename RT
   int cnt = 0;
   if (i < n) {
     auto pi = ldg4(pos + i);
-    walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int, uint32_t) { ++cnt; });
+    R rl = list_radius<R>(rc[i], rc_max, skin);
+    CountVisitor<R> v{pos, rl * rl, 0};
+    walk_segments<R>(start, g, (int)i, pi, rl, v);
+    cnt = v.cnt;
   }
   int m = cnt;
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -132,22 +183,13 @@ __global__ void __launch_bounds__(128) k_list_fill(int64_t n, const typename RT<
                                                    int32_t* __restrict__ flag) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int cap = capw[i >> 5];
-  uint32_t* out = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
-  int kf = 0, kb = 0;
   auto pi = ldg4(pos + i);
-  walk<R>(pos, start, g, (int)i, pi, list_radius<R>(rc[i], rc_max, skin), [&](int j, uint32_t code) {
-    if (code == 0) {
-      if (kf + kb < cap) out[(int64_t)kf * 32] = (uint32_t)j;
-      ++kf;
-    } else {
-      if (kf + kb < cap) out[(int64_t)(cap - 1 - kb) * 32] = (uint32_t)j | (code << kIdxBits);
-      ++kb;
-    }
-  });
-  nnb[i] = kf;
-  nimg[i] = kb;
-  if (kf + kb > cap) atomicExch(flag, 1);
+  R rl = list_radius<R>(rc[i], rc_max, skin);
+  FillVisitor<R> v{pos, list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31), rl * rl, capw[i >> 5], 0, 0};
+  walk_segments<R>(start, g, (int)i, pi, rl, v);
+  nnb[i] = v.kf;
+  nimg[i] = v.kb;
+  if (v.kf + v.kb > v.cap) atomicExch(flag, 1);
 }
 
 // Capacity bound of a list of radius R: the particles a sphere of radius R can
@@ -311,6 +353,38 @@ __global__ void __launch_bounds__(128) k_forces_list(int64_t n, const typename R
 // the hardware approximation, the residual 1 - r^2 y0 formed by an FMA).
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+struct PackedAcc {
+  float2 fx, fy, fz, en, vir;
+  int np;
+};
+
+// Two same-image neighbours p0, p1 of the particle at pi (cutoff^2 rc2).
+__device__ __forceinline__ void packed_pair(const float4& pi, const float4& p0, const float4& p1, float rc2,
+                                            PackedAcc& c) {
+  const float2 two = f2(2.f, 2.f), m1 = f2(-1.f, -1.f);
+  const float2 dx = f2(p0.x - pi.x, p1.x - pi.x);
+  const float2 dy = f2(p0.y - pi.y, p1.y - pi.y);
+  const float2 dz = f2(p0.z - pi.z, p1.z - pi.z);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  float y0, y1;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+  const float2 e = f2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
+  float2 y = f2(y0, y1);
+  y = __ffma2_rn(y, e, y);
+  const bool a0 = r2.x < rc2, a1 = r2.y < rc2;
+  y = f2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
+  const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+  const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1));  // r.F / 24
+  const float2 q = __fmul2_rn(pv, y);
+  c.fx = __ffma2_rn(q, dx, c.fx);
+  c.fy = __ffma2_rn(q, dy, c.fy);
+  c.fz = __ffma2_rn(q, dz, c.fz);
+  c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1), c.en);
+  c.vir = __fadd2_rn(c.vir, pv);
+  c.np += (int)a0 + (int)a1;
+}
+
 __global__ void __launch_bounds__(128) k_forces_list_x2(int64_t n, const float4* __restrict__ pos,
                                                         const float* __restrict__ rc, const int32_t* __restrict__ nnb,
                                                         const int32_t* __restrict__ nimg,
@@ -330,34 +404,26 @@ __global__ void __launch_bounds__(128) k_forces_list_x2(int64_t n, const float4*
     const float rc2 = rci * rci;
     const uint32_t* lp = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
     const int m = nnb[i], cap = capw[i >> 5], mb = nimg[i];
-    const float2 two = f2(2.f, 2.f), m1 = f2(-1.f, -1.f);
-    float2 fx = f2(0.f, 0.f), fy = fx, fz = fx, en = fx, vir = fx;
+    PackedAcc pc;
+    pc.fx = pc.fy = pc.fz = pc.en = pc.vir = f2(0.f, 0.f);
+    pc.np = 0;
     int k = 0;
-    for (; k + 1 < m; k += 2) {
-      const int j0 = (int)__ldg(lp + (int64_t)k * 32), j1 = (int)__ldg(lp + (int64_t)(k + 1) * 32);
-      const float4 p0 = __ldg(pos + j0), p1 = __ldg(pos + j1);
-      const float2 dx = f2(p0.x - pi.x, p1.x - pi.x);
-      const float2 dy = f2(p0.y - pi.y, p1.y - pi.y);
-      const float2 dz = f2(p0.z - pi.z, p1.z - pi.z);
-      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-      float y0, y1;
-      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
-      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
-      const float2 e = f2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
-      float2 y = f2(y0, y1);
-      y = __ffma2_rn(y, e, y);
-      const bool a0 = r2.x < rc2, a1 = r2.y < rc2;
-      y = f2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
-      const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
-      const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1));  // r.F / 24
-      const float2 q = __fmul2_rn(pv, y);
-      fx = __ffma2_rn(q, dx, fx);
-      fy = __ffma2_rn(q, dy, fy);
-      fz = __ffma2_rn(q, dz, fz);
-      en = __ffma2_rn(s6, __fadd2_rn(s6, m1), en);
-      vir = __fadd2_rn(vir, pv);
-      np += (int)a0 + (int)a1;
+    // four entries per iteration: their indices, then their positions, are
+    // all requested before any arithmetic, so that the loads overlap
+    for (; k + 3 < m; k += 4) {
+      const uint32_t* q = lp + (int64_t)k * 32;
+      const int j0 = (int)__ldg(q), j1 = (int)__ldg(q + 32), j2 = (int)__ldg(q + 64), j3 = (int)__ldg(q + 96);
+      const float4 p0 = __ldg(pos + j0), p1 = __ldg(pos + j1), p2 = __ldg(pos + j2), p3 = __ldg(pos + j3);
+      packed_pair(pi, p0, p1, rc2, pc);
+      packed_pair(pi, p2, p3, rc2, pc);
     }
+    if (k + 1 < m) {
+      const int j0 = (int)__ldg(lp + (int64_t)k * 32), j1 = (int)__ldg(lp + (int64_t)(k + 1) * 32);
+      packed_pair(pi, __ldg(pos + j0), __ldg(pos + j1), rc2, pc);
+      k += 2;
+    }
+    const float2 fx = pc.fx, fy = pc.fy, fz = pc.fz, en = pc.en, vir = pc.vir;
+    np = pc.np;
     Acc<float> c;
     c.fx = -(fx.x + fx.y);
     c.fy = -(fy.x + fy.y);
