@@ -147,19 +147,27 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- profiles
+FORCE_SOURCES = ("forces_core.cuh", "forces.cu")
+
+
+def force_source_sha():
+    """SHA-256 of the cell-list force kernel's sources (core, then kernels)."""
+    h = hashlib.sha256()
+    for name in FORCE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1701_05242_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def recorded_traffic(workload):
     """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the current force kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1701_05242_gb300", "csrc", "forces.cu")
+    taken on the current force kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"forces_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    h = re.search(r"forces_cu_sha256:\s*([0-9a-f]{64})", txt)
-    if not m or not h:
-        return None
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+    h = re.search(r"forces_src_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h or h.group(1) != force_source_sha():
         return None
     return float(m.group(1))
 

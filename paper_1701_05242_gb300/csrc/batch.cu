@@ -431,7 +431,7 @@ __global__ void k_b_cutoffs(int64_t n, const typename RT<R>::R4* __restrict__ po
 }
 
 // ---- forces -----------------------------------------------------------------------
-template <typename R, bool TYPED>
+template <typename R, bool TYPED, bool X2>
 __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
                            const int32_t* __restrict__ start, ForceArgs<R> a, const RepGeom* __restrict__ geom,
                            const uint16_t* __restrict__ rep, typename RT<R>::R4* __restrict__ force,
@@ -442,7 +442,7 @@ __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos
   Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge);
   R e = 0, w = 0;
   int np = 0;
-  force[i] = force_one<R, TYPED>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
+  force[i] = force_one<R, TYPED, X2>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
   w_i[i] = w;
   np_i[i] = np;
 }
@@ -561,7 +561,9 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     a.shift = b->p.shift_energy;
     a.rc_max = (R)b->p.rc_max;
     int bs = b->force_block;
-    auto kern = lj_general(t) ? k_b_forces<R, true> : k_b_forces<R, false>;
+    // one type in FP32: the packed two-candidates-per-instruction pair loop
+    auto kern = lj_general(t) ? k_b_forces<R, true, false>
+                              : (sizeof(R) == 4 ? k_b_forces<R, false, sizeof(R) == 4> : k_b_forces<R, false, false>);
     stage_begin(ctx, DCM_STAGE_FORCES, st);
     DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
                b->rep_of_particle, force, (R*)b->w_i, b->np_i);
