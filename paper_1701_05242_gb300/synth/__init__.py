@@ -8,7 +8,9 @@ sides start from bit-identical FP32 states.
 Recipe (all seeded, deterministic):
   * Geometry: periodic box (Lx, Ly, Lz); the liquid slab fills the central
     third in z (the planar system of the paper's Section 3, Fig. 5a), the vapor
-    the rest.  Particle counts are N_phase = floor(rho * V_phase + 0.5).
+    the rest.  Or (``cylinder_radius > 0``) a liquid cylinder of that radius
+    along x with its axis at (Ly/2, Lz/2) (the curved interface of Fig. 5b).
+    Particle counts are N_phase = floor(rho * V_phase + 0.5).
   * Optional capillary waves on each of the two surfaces: 16 modes
     (1 <= kx, ky <= 4), amplitude proportional to 1/|k|, random phases, scaled
     so that the largest excursion over the xy plane equals ``wave_amp``.
@@ -61,6 +63,9 @@ def _load():
                                            ctypes.c_int, pd, pd, pd, pd, d,
                                            ctypes.c_int, pd, pd, pd, pd, d,
                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_float)]
+            lib.synth_rsa_cylinder.restype = ctypes.c_int
+            lib.synth_rsa_cylinder.argtypes = [d, d, d, ctypes.c_int, pi64, pi64, d, ctypes.c_uint64, d, d, d,
+                                               ctypes.c_int64, ctypes.POINTER(ctypes.c_float)]
             lib.synth_uniform.restype = None
             lib.synth_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, pd]
             _lib = lib
@@ -87,6 +92,14 @@ class SlabSpec:
     d_min: float = 0.85
     seed: int = 0
     name: str = ""
+    cylinder_radius: float = 0.0
+
+    @property
+    def liquid_volume(self) -> float:
+        if self.cylinder_radius > 0:
+            return math.pi * self.cylinder_radius ** 2 * self.box[0]
+        z0, z1 = self.liquid_bounds
+        return self.box[0] * self.box[1] * (z1 - z0)
 
     @property
     def liquid_bounds(self):
@@ -97,13 +110,11 @@ class SlabSpec:
 
     @property
     def n_liquid(self) -> int:
-        z0, z1 = self.liquid_bounds
-        return int(math.floor(self.rho_l * self.box[0] * self.box[1] * (z1 - z0) + 0.5))
+        return int(math.floor(self.rho_l * self.liquid_volume + 0.5))
 
     @property
     def n_vapor(self) -> int:
-        z0, z1 = self.liquid_bounds
-        v = self.box[0] * self.box[1] * (self.box[2] - (z1 - z0))
+        v = self.box[0] * self.box[1] * self.box[2] - self.liquid_volume
         return int(math.floor(self.rho_v * v + 0.5))
 
     @property
@@ -123,6 +134,10 @@ def named(name: str) -> SlabSpec:
         return SlabSpec(box=(180.0, 180.0, 960.0), wave_amp=2.0, name=name)
     if name == "slab_256k_2types":   # 61.5x61.5x246, N = 260,522, two LJ types
         return SlabSpec(box=(61.5, 61.5, 246.0), ntypes=2, name=name)
+    if name == "cylinder_2393":      # 24^3, liquid cylinder of radius 6 along x, N = 2,393
+        return SlabSpec(box=(24.0, 24.0, 24.0), cylinder_radius=6.0, name=name)
+    if name == "cylinder_299k":      # 120^3, liquid cylinder of radius 30 along x, N = 299,208
+        return SlabSpec(box=(120.0, 120.0, 120.0), cylinder_radius=30.0, name=name)
     raise KeyError(name)
 
 
@@ -200,10 +215,42 @@ def slab_quotas(spec: SlabSpec, nslab: int):
     return ql, qv, lo, hi
 
 
+def cylinder_quotas(spec: SlabSpec, nslab: int):
+    """Per-z-slab counts for the liquid cylinder: rho times the phase volume of
+    the slab (the circle's chord integrated in closed form), rounded by
+    largest remainder to the exact totals."""
+    Lx, Ly, Lz = (float(v) for v in spec.box)
+    r, zc = spec.cylinder_radius, 0.5 * Lz
+
+    def area_below(z):  # area of the disc's part with z' < z
+        t = min(max((z - zc) / r, -1.0), 1.0)
+        return r * r * (t * math.sqrt(1.0 - t * t) + math.asin(t) + 0.5 * math.pi)
+
+    edges = Lz * np.arange(nslab + 1) / nslab
+    vliq = np.array([Lx * (area_below(edges[k + 1]) - area_below(edges[k])) for k in range(nslab)])
+    vslab = Lx * Ly * np.diff(edges)
+    ql = _largest_remainder(spec.rho_l * vliq, spec.n_liquid)
+    qv = _largest_remainder(spec.rho_v * (vslab - vliq), spec.n_vapor)
+    return ql, qv
+
+
 def make_positions(spec: SlabSpec) -> np.ndarray:
     """RSA positions (float32, shape (N, 3), each coordinate in [0, L)); liquid
     particles first, then vapor."""
     Lx, Ly, Lz = (float(v) for v in spec.box)
+    if spec.cylinder_radius > 0:
+        if not 2.0 * spec.cylinder_radius < min(Ly, Lz):
+            raise ValueError("the cylinder must fit in the y-z cross-section")
+        nslab = max(1, int(round(Lz / 2.0)))
+        ql, qv = cylinder_quotas(spec, nslab)
+        pos = np.empty((int(ql.sum() + qv.sum()), 3), dtype=np.float32)
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        rc = _load().synth_rsa_cylinder(Lx, Ly, Lz, nslab, ql.ctypes.data_as(pi64), qv.ctypes.data_as(pi64),
+                                        spec.d_min, spec.seed, spec.cylinder_radius, 0.5 * Ly, 0.5 * Lz,
+                                        1000000, pos.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if rc != 0:
+            raise RuntimeError(f"synth_rsa_cylinder failed ({rc}) for {spec}")
+        return pos
     z0, z1 = spec.liquid_bounds
     nslab = max(1, int(round(Lz / 2.0)))
     ql, qv, lo, hi = slab_quotas(spec, nslab)
@@ -265,7 +312,7 @@ def _cache_path(spec: SlabSpec):
     if os.environ.get("DCM_SYNTH_CACHE", "1") == "0" or spec.n < 200000:
         return None
     key = repr((spec.box, spec.rho_l, spec.rho_v, spec.temperature, spec.liquid_fraction, spec.wave_amp,
-                spec.ntypes, spec.d_min, spec.seed, os.path.getmtime(_SRC)))
+                spec.ntypes, spec.d_min, spec.seed, spec.cylinder_radius, os.path.getmtime(_SRC)))
     h = hashlib.sha256(key.encode()).hexdigest()[:24]
     return os.path.join(tempfile.gettempdir(), "dcm_synth_cache", h + ".npz")
 

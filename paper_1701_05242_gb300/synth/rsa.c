@@ -111,14 +111,69 @@ static int too_close(const grid_t* g, const float* pos, double x, double y, doub
  * order) and returns 0; -1 if max_tries_per_particle consecutive proposals
  * failed (density too high for d_min), -2 on allocation failure.
  */
+/* Liquid region: a slab between two surfaces (cyl_r <= 0), or the cylinder
+ * (y - cyl_y)^2 + (z - cyl_z)^2 < cyl_r^2 along x (cyl_r > 0). */
+typedef struct {
+  surface_t lo, hi;
+  double reach_lo, reach_hi;
+  double cyl_r, cyl_y, cyl_z;
+  double Lx, Ly;
+} region_t;
+
+static int in_liquid(const region_t* q, double x, double y, double z) {
+  if (q->cyl_r > 0.0) {
+    double dy = y - q->cyl_y, dz = z - q->cyl_z;
+    return dy * dy + dz * dz < q->cyl_r * q->cyl_r;
+  }
+  if (z >= q->lo.z0 + q->reach_lo && z < q->hi.z0 - q->reach_hi) return 1;
+  if (z < q->lo.z0 - q->reach_lo || z >= q->hi.z0 + q->reach_hi) return 0;
+  double zl = surface_z(&q->lo, x, y, q->Lx, q->Ly), zh = surface_z(&q->hi, x, y, q->Lx, q->Ly);
+  return z >= zl && z < zh;
+}
+
+static int rsa_fill(double Lx, double Ly, double Lz, int nslab, const int64_t* q_liq, const int64_t* q_vap,
+                    double d_min, uint64_t seed, const region_t* region, int64_t max_tries_per_particle,
+                    float* pos);
+
 int synth_rsa_slab(double Lx, double Ly, double Lz, int nslab, const int64_t* q_liq,
                    const int64_t* q_vap, double d_min, uint64_t seed, int nm_lo,
                    const double* kx_lo, const double* ky_lo, const double* amp_lo,
                    const double* ph_lo, double z0_lo, int nm_hi, const double* kx_hi,
                    const double* ky_hi, const double* amp_hi, const double* ph_hi, double z0_hi,
                    int64_t max_tries_per_particle, float* pos) {
-  surface_t slo = {nm_lo, kx_lo, ky_lo, amp_lo, ph_lo, z0_lo};
-  surface_t shi = {nm_hi, kx_hi, ky_hi, amp_hi, ph_hi, z0_hi};
+  region_t q;
+  q.lo = (surface_t){nm_lo, kx_lo, ky_lo, amp_lo, ph_lo, z0_lo};
+  q.hi = (surface_t){nm_hi, kx_hi, ky_hi, amp_hi, ph_hi, z0_hi};
+  q.reach_lo = 1e-12;
+  q.reach_hi = 1e-12;
+  for (int m = 0; m < nm_lo; ++m) q.reach_lo += fabs(amp_lo[m]);
+  for (int m = 0; m < nm_hi; ++m) q.reach_hi += fabs(amp_hi[m]);
+  q.cyl_r = 0.0;
+  q.cyl_y = q.cyl_z = 0.0;
+  q.Lx = Lx;
+  q.Ly = Ly;
+  return rsa_fill(Lx, Ly, Lz, nslab, q_liq, q_vap, d_min, seed, &q, max_tries_per_particle, pos);
+}
+
+/* The same fill with a liquid cylinder of radius r along x, axis at (y0, z0). */
+int synth_rsa_cylinder(double Lx, double Ly, double Lz, int nslab, const int64_t* q_liq, const int64_t* q_vap,
+                       double d_min, uint64_t seed, double r, double y0, double z0,
+                       int64_t max_tries_per_particle, float* pos) {
+  region_t q;
+  q.lo = (surface_t){0, 0, 0, 0, 0, 0.0};
+  q.hi = q.lo;
+  q.reach_lo = q.reach_hi = 0.0;
+  q.cyl_r = r;
+  q.cyl_y = y0;
+  q.cyl_z = z0;
+  q.Lx = Lx;
+  q.Ly = Ly;
+  return rsa_fill(Lx, Ly, Lz, nslab, q_liq, q_vap, d_min, seed, &q, max_tries_per_particle, pos);
+}
+
+static int rsa_fill(double Lx, double Ly, double Lz, int nslab, const int64_t* q_liq, const int64_t* q_vap,
+                    double d_min, uint64_t seed, const region_t* region, int64_t max_tries_per_particle,
+                    float* pos) {
   grid_t g;
   g.nx = (int)floor(Lx / d_min);
   g.ny = (int)floor(Ly / d_min);
@@ -143,9 +198,6 @@ int synth_rsa_slab(double Lx, double Ly, double Lz, int nslab, const int64_t* q_
     return -2;
   }
   for (int64_t c = 0; c < ncell; ++c) g.head[c] = -1;
-  double reach_lo = 1e-12, reach_hi = 1e-12;
-  for (int m = 0; m < nm_lo; ++m) reach_lo += fabs(amp_lo[m]);
-  for (int m = 0; m < nm_hi; ++m) reach_hi += fabs(amp_hi[m]);
   rng_t r = {sm64_mix(seed ^ 0x5851f42d4c957f2dULL), 0};
   double dmin2 = d_min * d_min;
   int64_t next_liq = 0, next_vap = n_liq; /* output slots */
@@ -164,16 +216,7 @@ int synth_rsa_slab(double Lx, double Ly, double Lz, int nslab, const int64_t* q_
       to_float_coord(x, Lx, &fx);
       to_float_coord(y, Ly, &fy);
       to_float_coord(z, Lz, &fz);
-      double zz = fz;
-      int inside;
-      if (zz >= z0_lo + reach_lo && zz < z0_hi - reach_hi)
-        inside = 1;
-      else if (zz < z0_lo - reach_lo || zz >= z0_hi + reach_hi)
-        inside = 0;
-      else {
-        double zl = surface_z(&slo, fx, fy, Lx, Ly), zh = surface_z(&shi, fx, fy, Lx, Ly);
-        inside = (zz >= zl && zz < zh);
-      }
+      int inside = in_liquid(region, fx, fy, fz);
       if (inside ? left_liq == 0 : left_vap == 0) continue;
       if (too_close(&g, pos, fx, fy, fz, Lx, Ly, Lz, dmin2)) continue;
       int64_t slot = inside ? next_liq++ : next_vap++;

@@ -579,3 +579,64 @@ def test_full_size_sampled(D, slab_16m):
         assert abs(t[2] - totals[0][2]) <= 1e-6 * totals[0][2]
         assert abs(t[0] - totals[0][0]) <= EW_TOL * abs(totals[0][0])
         assert abs(t[1] - totals[0][1]) <= EW_TOL * abs(totals[0][1])
+
+
+# ------------------------------------------------- curved interface (cylinder)
+@pytest.fixture(scope="module")
+def cyl_small():
+    return synth.make_slab(synth.named("cylinder_2393"))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cylinder_pipeline(D, cyl_small, prec):
+    """A liquid cylinder in vapor (a curved interface, Fig. 5b): detection
+    bit-exact, distances, cutoffs and forces against the oracle."""
+    slab = cyl_small
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    ctx = make_ctx(D, slab.box, slab.n, P)
+    pos4 = pos4_of(D, slab.pos, None, P)
+    bc, g, T, s, iface = gpu_detect(D, ctx, pos4)
+    nh = O.grid_dims(slab.box, 1.5)
+    _, ocount, _, _ = O.bin_particles(slab.pos, slab.box, 1.5)
+    og, oT, os_, oif = O.detect_interface(ocount, nh, 2)
+    assert np.array_equal(bc, ocount) and np.array_equal(g, og) and T == oT
+    assert np.array_equal(s.cpu().numpy(), os_) and np.array_equal(iface.cpu().numpy(), oif)
+    assert oif.sum() > 0
+    Dg = torch.empty(ctx.nbox, dtype=real_of(D, P), device="cuda")
+    D.dcm_distance(ctx, s, iface, Dg)
+    Dj, _ = O.distance_jacobi(os_, oif, nh, 1.5, 6.0)
+    assert_distances(Dg.cpu().numpy().astype(np.float64), Dj, 6.0, D_TOL if prec == "mixed" else FP64_TOL)
+    rc = torch.empty(slab.n, dtype=real_of(D, P), device="cuda")
+    D.dcm_cutoffs(ctx, slab.n, pos4, Dg, rc)
+    a = O.assign_cutoffs(slab.pos, O.Params(box=slab.box))
+    tol = RC_TOL if prec == "mixed" else FP64_TOL * 6
+    assert np.abs(rc.cpu().numpy().astype(np.float64) - a["rc"]).max() <= tol
+    Fg, tot, ref, rc_in = forces_case(D, slab, prec, a["rc"])
+    if prec == "mixed":
+        assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+        assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+    else:
+        assert np.abs(Fg[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+        assert int(tot[2]) == ref.npairs
+
+
+def test_cylinder_299k_step_on_shared_inputs(D):
+    """dcm_step_init on the 299k-particle cylinder (mixed): the oracle
+    recomputes cutoffs and forces at the GPU's own sorted positions."""
+    slab = synth.make_slab(synth.named("cylinder_299k"))
+    ctx = make_ctx(D, slab.box, slab.n, D.DCM_PREC_MIXED, recompute_every=10)
+    st = D.State(ctx, pos4_of(D, slab.pos, None, D.DCM_PREC_MIXED),
+                 D.to_real4(torch.from_numpy(slab.vel), None, torch.float32))
+    D.dcm_step_init(ctx, st)
+    th = st.thermo.cpu().numpy()
+    pos, vel, rc, ids = st.current()
+    pos = pos.cpu().numpy().astype(np.float64)[:, :3]
+    rcn = rc.cpu().numpy().astype(np.float64)
+    a = O.assign_cutoffs(pos, O.Params(box=slab.box))
+    assert np.abs(rcn - a["rc"]).max() <= RC_TOL
+    ref = O.forces_cells(pos, rcn, slab.box, 1.5)
+    Fg = st.force.cpu().numpy().astype(np.float64)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(th[0] - ref.E) <= EW_TOL * abs(ref.E)
+    assert abs(th[1] - ref.W) <= EW_TOL * abs(ref.W)
+    assert abs(int(th[3]) - ref.npairs) <= near_cutoff_pairs(pos, rcn, slab.box)
