@@ -36,6 +36,7 @@ struct RepGeom {
 };
 
 constexpr int kBatchHistBins = 4096;  // per-replica histogram of box sums
+constexpr int64_t kThermoChunk = 4096;  // particles per block of the per-replica sums
 
 }  // namespace dcm
 
@@ -54,6 +55,10 @@ struct dcm_batch {
   void* w_i;          // per-particle virial (real)
   void* ke_i;         // per-particle kinetic energy (real)
   int32_t* np_i;      // per-particle accepted pairs
+  int32_t nchunk;     // thermo reduction: chunks of at most kThermoChunk particles of one replica
+  int64_t* chunk;     // [nchunk][2]: first, end particle
+  int32_t* chunk0;    // [R + 1]: first chunk of each replica
+  double* tpart;      // [4][nchunk]: per-chunk E, W, KE, pairs
   int force_block;    // threads per block of the force kernel
   cudaGraphExec_t graph;
   int graph_steps;
@@ -464,31 +469,47 @@ __global__ void k_b_kick(int64_t n, typename RT<R>::R4* __restrict__ vel, const 
   ke_i[i] = (R)0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
 }
 
-// one block per replica: thermo[4 r + {0,1,2,3}] = {E, W, KE, pairs}
+// Per-replica thermo in two fixed-order levels: one block per chunk of at
+// most kThermoChunk particles of one replica (FP64 sums), then one warp per
+// replica over its chunks.  thermo[4 r + {0,1,2,3}] = {E, W, KE, pairs}.
 template <typename R>
-__global__ void k_b_thermo(const RepGeom* __restrict__ geom, const typename RT<R>::R4* __restrict__ force,
-                           const R* __restrict__ w_i, const R* __restrict__ ke_i, const int32_t* __restrict__ np_i,
-                           double* __restrict__ thermo) {
-  __shared__ double sh[4][256];
-  const RepGeom& G = geom[blockIdx.x];
-  double e = 0, w = 0, k = 0, p = 0;
-  for (int64_t i = G.p0 + threadIdx.x; i < G.p1; i += blockDim.x) {
-    e += (double)force[i].w;
-    w += (double)w_i[i];
-    k += (double)ke_i[i];
-    p += (double)np_i[i];
+__global__ void k_b_thermo_chunks(const int64_t* __restrict__ chunk, int32_t nchunk,
+                                  const typename RT<R>::R4* __restrict__ force, const R* __restrict__ w_i,
+                                  const R* __restrict__ ke_i, const int32_t* __restrict__ np_i,
+                                  double* __restrict__ tpart) {
+  __shared__ double sh[4][8];
+  const int64_t p0 = chunk[2 * blockIdx.x], p1 = chunk[2 * blockIdx.x + 1];
+  double v[4] = {0, 0, 0, 0};
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+    v[0] += (double)force[i].w;
+    v[1] += (double)w_i[i];
+    v[2] += (double)ke_i[i];
+    v[3] += (double)np_i[i];
   }
-  sh[0][threadIdx.x] = e;
-  sh[1][threadIdx.x] = w;
-  sh[2][threadIdx.x] = k;
-  sh[3][threadIdx.x] = p;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 4; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) sh[q][wid] = v[q];
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
-    __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[threadIdx.x][k];
+    tpart[(int64_t)threadIdx.x * nchunk + blockIdx.x] = t;
   }
-  if (threadIdx.x < 4) thermo[4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_b_thermo_sum(const int32_t* __restrict__ chunk0, int R, int32_t nchunk,
+                               const double* __restrict__ tpart, double* __restrict__ thermo) {
+  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (r >= R) return;
+  const int c0 = chunk0[r], c1 = chunk0[r + 1];
+  for (int q = 0; q < 4; ++q) {
+    double t = 0;
+    for (int c = c0 + lane; c < c1; c += 32) t += tpart[(int64_t)q * nchunk + c];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) thermo[4 * r + q] = t;
+  }
 }
 
 // ---- orchestration ------------------------------------------------------------------
@@ -571,8 +592,11 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     stage_begin(ctx, DCM_STAGE_KICK, st);
     DCM_LAUNCH(ctx, k_b_kick<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, vel, kick ? force : nullptr, half_dt,
                (R*)b->ke_i);
-    DCM_LAUNCH(ctx, k_b_thermo<R>, (unsigned)b->R, 256, 0, st, b->geom, force, (const R*)b->w_i,
-               (const R*)b->ke_i, b->np_i, thermo);
+    if (b->nchunk > 0)
+      DCM_LAUNCH(ctx, k_b_thermo_chunks<R>, (unsigned)b->nchunk, 256, 0, st, b->chunk, b->nchunk, force,
+                 (const R*)b->w_i, (const R*)b->ke_i, b->np_i, b->tpart);
+    DCM_LAUNCH(ctx, k_b_thermo_sum, (unsigned)((b->R + 7) / 8), 256, 0, st, b->chunk0, b->R, b->nchunk, b->tpart,
+               thermo);
     stage_end(ctx, DCM_STAGE_KICK, st);
   }
   return check_launch(ctx, "batch forces");
@@ -653,7 +677,7 @@ extern "C" void dcm_batch_destroy(dcm_batch* b) {
   void* dev[] = {c->status, c->slot,  c->cell,  c->perm,   c->cell_start, c->cell_count, c->scan_part,
                  c->box_count, c->g,   c->g_tmp, c->s,      c->iface,      c->D[0],       c->D[1],
                  c->flags,  c->red,   c->red_tmp, c->totals, b->geom,       b->rep_of_particle, b->rep_of_box,
-                 b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i};
+                 b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (c->host_status) cudaFreeHost(c->host_status);
@@ -715,6 +739,10 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   b->hist = nullptr;
   b->w_i = b->ke_i = nullptr;
   b->np_i = nullptr;
+  b->nchunk = 0;
+  b->chunk = nullptr;
+  b->chunk0 = nullptr;
+  b->tpart = nullptr;
   b->force_block = 128;
   b->graph = nullptr;
   b->graph_steps = 0;
@@ -762,6 +790,20 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   alloc(&b->w_i, rs * nm);
   alloc(&b->ke_i, rs * nm);
   alloc((void**)&b->np_i, 4 * nm);
+  std::vector<int64_t> ch;
+  std::vector<int32_t> ch0((size_t)R + 1, 0);
+  for (int r = 0; r < R; ++r) {
+    ch0[(size_t)r] = (int32_t)(ch.size() / 2);
+    for (int64_t a = geom[(size_t)r].p0; a < geom[(size_t)r].p1; a += kThermoChunk) {
+      ch.push_back(a);
+      ch.push_back(std::min(a + kThermoChunk, geom[(size_t)r].p1));
+    }
+  }
+  b->nchunk = (int32_t)(ch.size() / 2);
+  ch0[(size_t)R] = b->nchunk;
+  alloc((void**)&b->chunk, 8 * (int64_t)ch.size());
+  alloc((void**)&b->chunk0, 4 * ((int64_t)R + 1));
+  alloc((void**)&b->tpart, 8 * 4 * (int64_t)std::max<int32_t>(b->nchunk, 1));
   if (ok && cudaMallocHost((void**)&c->host_status, 16) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
@@ -777,6 +819,8 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   if (cudaMemcpy(b->geom, geom.data(), sizeof(RepGeom) * R, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->rep_of_particle, rp.data(), 2 * rp.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->rep_of_box, rb.data(), 2 * (size_t)nbtot, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!ch.empty() && cudaMemcpy(b->chunk, ch.data(), 8 * ch.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(b->chunk0, ch0.data(), 4 * ch0.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(c->status, 0, 16) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     dcm_batch_destroy(b);

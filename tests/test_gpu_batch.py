@@ -120,6 +120,23 @@ def test_batch_fp64_tracks_oracle(D, replicas):
         assert d.max() <= 1e-9
 
 
+def test_batch_thermo_over_several_chunks(D):
+    """A replica larger than one reduction chunk (4096 particles) between two
+    small ones: per-replica E, W, KE and pairs equal the systems stepped alone."""
+    reps = [synth.make_slab(synth.SlabSpec(box=b, seed=s, name=f"c{s}"))
+            for s, b in enumerate([(12.0, 12.0, 48.0), (24.0, 24.0, 96.0), (13.5, 13.5, 54.0)])]
+    assert reps[1].n > 2 * 4096
+    b, st = batch_state(D, reps, D.DCM_PREC_FP64)
+    D.dcm_batch_step_init(b, st)
+    D.dcm_batch_step(b, st, DT, 3)
+    th = st.thermo.cpu().numpy().reshape(-1, 4)
+    for r, slab in enumerate(reps):
+        _, th1 = single_run(D, slab, D.DCM_PREC_FP64, 3)
+        for q in range(3):
+            assert th[r, q] == pytest.approx(th1[q], rel=1e-10, abs=1e-9)
+        assert th[r, 3] == th1[3]
+
+
 def test_batch_rejects_bad_replica(D):
     p = D.make_params((1, 1, 1))
     with pytest.raises(D.DcmError):
