@@ -640,3 +640,53 @@ def test_cylinder_299k_step_on_shared_inputs(D):
     assert abs(th[0] - ref.E) <= EW_TOL * abs(ref.E)
     assert abs(th[1] - ref.W) <= EW_TOL * abs(ref.W)
     assert abs(int(th[3]) - ref.npairs) <= near_cutoff_pairs(pos, rcn, slab.box)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("skin", [0.0, 0.5])
+def test_empty_system_steps(D, prec, skin):
+    """N = 0: every stage runs on empty arrays, the totals are zero."""
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    real = real_of(D, P)
+    ctx = make_ctx(D, (12.0, 12.0, 48.0), 8, P, skin=skin, rc_max=5.5)
+    st = D.State(ctx, torch.empty((0, 4), dtype=real, device="cuda"), torch.empty((0, 4), dtype=real, device="cuda"))
+    D.dcm_step_init(ctx, st)
+    D.dcm_step(ctx, st, 0.005, 3)
+    assert D.dcm_status(ctx) == D.DCM_OK
+    assert torch.count_nonzero(st.thermo).item() == 0
+
+
+def two_particles(D, r, rc, prec="mixed"):
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    real = real_of(D, P)
+    pts = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]], np.float32)
+    ctx = make_ctx(D, (12.0, 12.0, 12.0), 2, P)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, pts, None, P))
+    rcs = torch.tensor([rc, rc], dtype=real, device="cuda")
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    D.dcm_forces(ctx, 2, ps, rcs, torch.from_numpy(start).cuda(), F, tot)
+    torch.cuda.synchronize()
+    return F.cpu().numpy().astype(np.float64), tot.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_pair_rule_is_strict_at_the_cutoff(D, prec):
+    """|r_ij| < rc_i: a pair exactly at rc is out, one ulp beyond rc is in."""
+    F, tot = two_particles(D, 3.0, 3.0, prec)
+    assert tot[2] == 0 and np.abs(F).max() == 0.0
+    rc_up = float(np.nextafter(np.float32(3.0), np.float32(4.0)))
+    F, tot = two_particles(D, 3.0, rc_up, prec)
+    assert tot[2] == 2
+    # U(3) = 4 (3^-12 - 3^-6); each particle carries half, the force is 24 (2 r^-13 - r^-7)
+    u = 4.0 * (3.0 ** -12 - 3.0 ** -6)
+    assert tot[0] == pytest.approx(u, rel=1e-6)
+    f = 24.0 * (2 * 3.0 ** -13 - 3.0 ** -7)    # < 0: attraction
+    assert F[0, 0] == pytest.approx(-f, rel=1e-6) and F[1, 0] == pytest.approx(f, rel=1e-6)
+    assert F[0, 0] == pytest.approx(-F[1, 0], rel=1e-12) and np.abs(F[:, 1:3]).max() == 0.0
+
+
+def test_single_particle_has_no_pairs(D):
+    F, tot = two_particles(D, 6.0, 5.9)       # the other one (and its images) beyond rc
+    assert tot[2] == 0 and tot[0] == 0.0 and np.abs(F).max() == 0.0
