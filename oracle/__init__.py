@@ -68,6 +68,8 @@ def _load():
                 "orc_smooth": (None, [_i32p, _i64p, I32, _i32p]),
                 "orc_two_means": (I64, [_i32p, I64, I32]),
                 "orc_segment": (None, [_i32p, _i64p, I64, _u8p, _u8p]),
+                "orc_interface": (None, [_u8p, _i64p, _u8p]),
+                "orc_remove_small_components": (I64, [_u8p, _i64p, I64, _u8p]),
                 "orc_cfsm": (I32, [_u8p, _u8p, _i64p, D, D, I32, _f64p]),
                 "orc_distance_jacobi": (I32, [_u8p, _u8p, _i64p, D, D, I32, _f64p]),
                 "orc_distance_sweep8": (I32, [_u8p, _u8p, _i64p, D, D, I32, _f64p]),
@@ -172,11 +174,36 @@ def segment(g, nh, T: int):
     return s, iface
 
 
-def detect_interface(count, nh, w: int = 2, threshold=None):
-    """count -> (g, T, s, iface).  ``threshold`` fixes T instead of 2-means."""
+def interface(s, nh):
+    """Liquid-side interface boxes of a segmented volume S."""
+    nh = np.asarray(nh, dtype=np.int64)
+    s = np.ascontiguousarray(s, dtype=np.uint8)
+    iface = np.empty(s.size, np.uint8)
+    _load().orc_interface(_p(s, _u8p), _p(nh, _i64p), _p(iface, _u8p))
+    return iface
+
+
+def remove_small_components(s, nh, min_boxes: int):
+    """Section 2.1's bubble filter (reading): every face-connected periodic
+    component of either phase with fewer than ``min_boxes`` boxes takes the
+    other value.  Returns (s_filtered, number of flipped components)."""
+    nh = np.asarray(nh, dtype=np.int64)
+    s = np.ascontiguousarray(s, dtype=np.uint8)
+    out = np.empty_like(s)
+    k = _load().orc_remove_small_components(_p(s, _u8p), _p(nh, _i64p), int(min_boxes), _p(out, _u8p))
+    return out, int(k)
+
+
+def detect_interface(count, nh, w: int = 2, threshold=None, min_component: int = 0):
+    """count -> (g, T, s, iface).  ``threshold`` fixes T instead of 2-means;
+    ``min_component > 0`` removes smaller components of either phase from S
+    before the interface boxes are taken."""
     g = smooth(count, nh, w)
     T = two_means(g) if threshold is None else int(threshold)
     s, iface = segment(g, nh, T)
+    if min_component > 0:
+        s, _ = remove_small_components(s, nh, min_component)
+        iface = interface(s, nh)
     return g, T, s, iface
 
 
@@ -373,6 +400,7 @@ class Params:
     sigma: tuple = (1.0,)
     shift: bool = False
     recompute_every: int = 1  # K: interface/distance/cutoffs every K steps
+    min_component: int = 0    # > 0: remove smaller components of S (Section 2.1's bubble filter)
 
     def __post_init__(self):
         if self.ramp is None:
@@ -386,7 +414,7 @@ def assign_cutoffs(pos, p: Params):
     Returns dict(count, g, T, s, iface, D, passes, delta, rc)."""
     nh = grid_dims(p.box, p.h)
     _, count, _, _ = bin_particles(pos, p.box, p.h)
-    g, T, s, iface = detect_interface(count, nh, p.smooth_w, p.threshold)
+    g, T, s, iface = detect_interface(count, nh, p.smooth_w, p.threshold, p.min_component)
     D, passes = cfsm(s, iface, nh, p.h, p.r_grid, p.iter_max)
     delta, rc = cutoffs(pos, D, nh, p.h, p.r_grid, p.rc_min, p.rc_max, p.ramp)
     return dict(count=count, g=g, T=T, s=s, iface=iface, D=D, passes=passes, delta=delta, rc=rc)

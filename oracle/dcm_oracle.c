@@ -155,6 +155,67 @@ void orc_segment(const int32_t* g, const int64_t* nh, int64_t T, uint8_t* s, uin
       }
 }
 
+/* Interface boxes of a given segmented volume S: high-density boxes with a
+ * low-density face neighbour (the same rule as orc_segment). */
+void orc_interface(const uint8_t* s, const int64_t* nh, uint8_t* iface) {
+  for (int64_t z = 0; z < nh[2]; ++z)
+    for (int64_t y = 0; y < nh[1]; ++y)
+      for (int64_t x = 0; x < nh[0]; ++x) {
+        int64_t b = x + nh[0] * (y + nh[1] * z);
+        int f = 0;
+        if (s[b]) {
+          f |= !s[wrap(x - 1, nh[0]) + nh[0] * (y + nh[1] * z)];
+          f |= !s[wrap(x + 1, nh[0]) + nh[0] * (y + nh[1] * z)];
+          f |= !s[x + nh[0] * (wrap(y - 1, nh[1]) + nh[1] * z)];
+          f |= !s[x + nh[0] * (wrap(y + 1, nh[1]) + nh[1] * z)];
+          f |= !s[x + nh[0] * (y + nh[1] * wrap(z - 1, nh[2]))];
+          f |= !s[x + nh[0] * (y + nh[1] * wrap(z + 1, nh[2]))];
+        }
+        iface[b] = (uint8_t)f;
+      }
+}
+
+/* Removal of small connected components (Section 2.1: "bubbles" of either
+ * phase inside the other are filtered out by volume; the filter itself is in
+ * the paper's reference [25], not available).  Reading: components are sets
+ * of boxes of equal S joined through faces (6-connectivity, periodic); every
+ * component of fewer than min_boxes boxes, of either phase, takes the other
+ * value; all components are found on the input volume and flipped together.
+ * Plain breadth-first search.  Returns the number of flipped components. */
+int64_t orc_remove_small_components(const uint8_t* s_in, const int64_t* nh, int64_t min_boxes, uint8_t* s_out) {
+  int64_t nbox = nh[0] * nh[1] * nh[2];
+  int64_t* comp = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbox);
+  int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)nbox);
+  for (int64_t b = 0; b < nbox; ++b) comp[b] = -1;
+  int64_t flipped = 0;
+  for (int64_t seed = 0; seed < nbox; ++seed) {
+    if (comp[seed] >= 0) continue;
+    /* breadth-first search from the seed over equal-valued face neighbours */
+    int64_t head = 0, tail = 0;
+    queue[tail++] = seed;
+    comp[seed] = seed;
+    while (head < tail) {
+      int64_t b = queue[head++];
+      int64_t x = b % nh[0], y = (b / nh[0]) % nh[1], z = b / (nh[0] * nh[1]);
+      int64_t nb[6] = {wrap(x - 1, nh[0]) + nh[0] * (y + nh[1] * z), wrap(x + 1, nh[0]) + nh[0] * (y + nh[1] * z),
+                       x + nh[0] * (wrap(y - 1, nh[1]) + nh[1] * z), x + nh[0] * (wrap(y + 1, nh[1]) + nh[1] * z),
+                       x + nh[0] * (y + nh[1] * wrap(z - 1, nh[2])), x + nh[0] * (y + nh[1] * wrap(z + 1, nh[2]))};
+      for (int k = 0; k < 6; ++k)
+        if (comp[nb[k]] < 0 && s_in[nb[k]] == s_in[seed]) {
+          comp[nb[k]] = seed;
+          queue[tail++] = nb[k];
+        }
+    }
+    /* the queue now holds exactly this component (tail boxes) */
+    int flip = tail < min_boxes;
+    flipped += flip;
+    for (int64_t q = 0; q < tail; ++q) s_out[queue[q]] = (uint8_t)(flip ? !s_in[seed] : s_in[seed]);
+  }
+  free(comp);
+  free(queue);
+  return flipped;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Box-interface distances (Section 2.2).                                    */
 /* ------------------------------------------------------------------------ */

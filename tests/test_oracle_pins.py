@@ -434,3 +434,74 @@ def test_kick_drift_wrap():
     assert out[0, 2] == pytest.approx(0.01, abs=1e-12)
     v = O.kick(vel, np.array([[2.0, 2.0, 2.0]]), 0.5)
     assert np.array_equal(v, [[-3.0, 1.0, 5.0]])
+
+
+# ------------------------------------------------------------ bubble filter
+def _uf_components(s, nh):
+    """Independent check: union-find over face links (periodic), pure Python."""
+    nx, ny, nz = (int(v) for v in nh)
+    parent = list(range(s.size))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                b = x + nx * (y + ny * z)
+                for n in (((x + 1) % nx) + nx * (y + ny * z), x + nx * (((y + 1) % ny) + ny * z),
+                          x + nx * (y + ny * ((z + 1) % nz))):
+                    if s[n] == s[b]:
+                        ra, rb = find(b), find(n)
+                        if ra != rb:
+                            parent[max(ra, rb)] = min(ra, rb)
+    roots = np.array([find(b) for b in range(s.size)])
+    return roots, np.bincount(roots, minlength=s.size)
+
+
+def test_bubble_filter_hand_built():
+    nh = np.array([10, 10, 10])
+    s = np.zeros((10, 10, 10), np.uint8)        # [z, y, x]
+    s[2:8] = 1                                  # liquid slab
+    s[4:6, 4:6, 4:6] = 0                        # vapor bubble of 8 boxes
+    s[3:6, 1:4, 7:10] = 0                       # vapor bubble of 27 boxes
+    s[0, 5, 5] = 1                              # liquid droplet of 1 box in vapor
+    out, k = O.remove_small_components(s.ravel(), nh, 10)
+    exp = np.zeros_like(s)
+    exp[2:8] = 1
+    exp[3:6, 1:4, 7:10] = 0                     # the large bubble stays
+    assert k == 2 and np.array_equal(out.reshape(s.shape), exp)
+    # interface of the filtered volume: the slab faces and the large bubble's skin
+    iface = O.interface(out, nh).reshape(s.shape)
+    assert iface[2].all() and iface[7].all() and iface[6, 2, 8] == 1 and iface[4, 4, 4] == 0
+
+
+def test_bubble_filter_periodic_and_strict():
+    nh = np.array([8, 6, 6])
+    s = np.ones((6, 6, 8), np.uint8)
+    s[2:4, 2, 0] = 0
+    s[2:4, 2, 7] = 0                            # one 4-box bubble across the x boundary
+    out4, k4 = O.remove_small_components(s.ravel(), nh, 4)
+    out5, k5 = O.remove_small_components(s.ravel(), nh, 5)
+    assert k4 == 0 and np.array_equal(out4, s.ravel())     # size 4 is not < 4
+    assert k5 == 1 and out5.all()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bubble_filter_matches_union_find(seed):
+    rng = np.random.default_rng(seed)
+    nh = np.array([7, 6, 5])
+    s = (rng.random(210) < 0.55).astype(np.uint8)
+    roots, size = _uf_components(s, nh)
+    for m in (2, 4, 9):
+        out, k = O.remove_small_components(s, nh, m)
+        small = size[roots] < m
+        assert np.array_equal(out, np.where(small, 1 - s, s))
+        assert k == len(set(roots[small].tolist()))
+    # translation invariance
+    sh = np.roll(s.reshape(5, 6, 7), (1, 2, 3), axis=(0, 1, 2)).ravel()
+    o1, _ = O.remove_small_components(s, nh, 4)
+    o2, _ = O.remove_small_components(sh, nh, 4)
+    assert np.array_equal(np.roll(o1.reshape(5, 6, 7), (1, 2, 3), axis=(0, 1, 2)).ravel(), o2)
