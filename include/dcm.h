@@ -103,6 +103,10 @@ typedef struct dcm_params {
                              (Algorithm 2.2) and rebuilds them only when a particle has moved
                              more than skin / 2 since the last build or the cutoffs are
                              recomputed; 0 (default): forces straight from the cell lists */
+  int32_t min_component;  /* > 0: remove connected components of S (6-connected, periodic, either
+                             phase) of fewer boxes before the interface is taken (Section 2.1's
+                             bubble filter); 0 (default): off.  Single-system contexts only */
+  int32_t reserved2;
 } dcm_params;
 
 typedef struct dcm_ctx dcm_ctx;
@@ -136,7 +140,7 @@ int dcm_params_default(dcm_params* p);
  * into fewer than 65536 cells; 0 < rc_min <= rc_max <= min(L)/2 (so at most
  * one periodic image of a particle lies within any cutoff); 1 <= ntypes <= 4;
  * eps, sigma > 0; smooth_w >= 0; 1 <= iter_max <= 100000; recompute_every
- * >= 1; force_kernel one of DCM_FORCE_*; 0 <= n_max < 2^31; skin >= 0 with rc_max + skin <= min(L)/2 and
+ * >= 1; force_kernel one of DCM_FORCE_*; min_component >= 0; 0 <= n_max < 2^31; skin >= 0 with rc_max + skin <= min(L)/2 and
  * n_max < 2^26 when skin > 0.
  * On failure writes a message to msg (if msg_len > 0) and returns
  * DCM_ERR_BOX or DCM_ERR_INVALID_ARG. */
@@ -189,12 +193,25 @@ int dcm_box_counts(dcm_ctx* ctx, int64_t n, const void* pos, int32_t* box_count,
 
 /* Interface detection, Section 2.1 and Eq. 4.  g = box sum of box_count over
  * the (2w+1)^3 periodic neighbourhood; T = integer 2-means threshold of g (or
- * the fixed params.threshold); s = (g >= T); iface = s AND some face
- * neighbour has s = 0.  If one phase is empty, T = max(g) + 1 (no interface).
+ * the fixed params.threshold); s = (g >= T), then (params.min_component > 0)
+ * without its small components (dcm_remove_small_components); iface = s AND
+ * some face neighbour has s = 0.  If one phase is empty, T = max(g) + 1 (no
+ * interface).
  *   box_count int32[nboxes] in;  s, iface uint8[nboxes] out;
  *   threshold int32[1] out (device);  g int32[nboxes] out (nullable). */
 int dcm_detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t* iface,
                          int32_t* threshold, int32_t* g, dcm_stream_t stream);
+
+/* Section 2.1's bubble filter: every connected component of s_in (boxes of
+ * equal value joined through faces, periodic) with fewer than
+ * params.min_component boxes takes the other value; s_out gets the result and
+ * iface its interface boxes (as in dcm_detect_interface).  s_in, s_out, iface
+ * uint8[nboxes] on the device; s_in and s_out must not overlap.  Needs a
+ * context created with params.min_component > 0 (else DCM_ERR_INVALID_ARG).
+ * Labelling runs at most 64 hook passes; more raise DCM_ERR_NOT_CONVERGED in
+ * the device status.  Asynchronous. */
+int dcm_remove_small_components(dcm_ctx* ctx, const uint8_t* s_in, uint8_t* s_out, uint8_t* iface,
+                                dcm_stream_t stream);
 
 /* Box-interface distances, Section 2.2 and Algorithm 2.1.  D = 0 on boxes
  * with s = 0 or iface = 1, +inf elsewhere; then Godunov fast-sweeping updates
@@ -298,7 +315,8 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
  * thermo is double[4 R] = {E, W, KE, pairs} per replica.  Every stage of a
  * step is one launch over all replicas (per-replica boxes, grids, thresholds
  * and reductions are read from a device table).  The batched form steps over
- * cell lists: p->skin must be 0.  Synchronous; allocates. */
+ * cell lists: p->skin must be 0, and p->min_component 0 (no bubble filter).
+ * Synchronous; allocates. */
 typedef struct dcm_batch dcm_batch;
 int dcm_batch_create(const dcm_params* p, int32_t R, const double* boxes, const int64_t* counts, dcm_batch** out);
 void dcm_batch_destroy(dcm_batch* b);

@@ -192,6 +192,7 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
   if (p->iter_max < 1 || p->iter_max > 100000)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "iter_max must be in 1..100000");
   if (p->recompute_every < 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "recompute_every must be >= 1");
+  if (p->min_component < 0) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "min_component must be >= 0");
   if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_PACKED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
@@ -228,10 +229,12 @@ extern "C" int dcm_grid_dims(const dcm_params* p, int64_t* cells3, int64_t* boxe
 struct ScratchPlan {
   int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags;
   double skin;
+  int32_t min_component;
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
-           8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0);
+           8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
+           (min_component > 0 ? 9 * nbox + 4 * 80 : 0);
   }
 };
 
@@ -251,6 +254,7 @@ static ScratchPlan plan_of(const dcm_params* p) {
   s.rsize = p->precision == DCM_PREC_FP64 ? 8 : 4;
   s.flags = p->iter_max + 2;
   s.skin = p->skin;
+  s.min_component = p->min_component;
   return s;
 }
 
@@ -272,7 +276,8 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
   void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
                  ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
-                 ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag};
+                 ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
+                 ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -341,6 +346,12 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
     alloc(&ctx->xbuild, 4 * s.rsize * nm);
     alloc((void**)&ctx->dmax, 16);
     alloc((void**)&ctx->lflag, 16);
+  }
+  if (p->min_component > 0) {
+    alloc((void**)&ctx->cc_lab, 4 * s.nbox);
+    alloc((void**)&ctx->cc_cnt, 4 * s.nbox);
+    alloc((void**)&ctx->cc_flags, 4 * 80);
+    alloc((void**)&ctx->cc_s0, s.nbox);
   }
   alloc((void**)&ctx->adj_pairs, 8 * 48);
   if (ok && cudaMallocHost((void**)&ctx->host_status, 16) != cudaSuccess) ok = false;
@@ -417,6 +428,13 @@ extern "C" int dcm_detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint
   if (!ctx) return DCM_ERR_INVALID_ARG;
   REQUIRE(box_count && s && iface && threshold, "dcm_detect_interface: null argument");
   return detect_interface(ctx, box_count, s, iface, threshold, g, (cudaStream_t)stream);
+}
+
+extern "C" int dcm_remove_small_components(dcm_ctx* ctx, const uint8_t* s_in, uint8_t* s_out, uint8_t* iface,
+                                           dcm_stream_t stream) {
+  if (!ctx) return DCM_ERR_INVALID_ARG;
+  REQUIRE(s_in && s_out && iface && s_in != s_out, "dcm_remove_small_components: null or aliased argument");
+  return remove_small_components(ctx, s_in, s_out, iface, (cudaStream_t)stream);
 }
 
 extern "C" int dcm_distance(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,

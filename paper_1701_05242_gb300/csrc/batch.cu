@@ -694,6 +694,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   if (!p || !boxes || !counts || !out || R < 1 || R > 65535) return DCM_ERR_INVALID_ARG;
   *out = nullptr;
   if (p->skin != 0.0) return DCM_ERR_INVALID_ARG;  // the batched form steps over cell lists only
+  if (p->min_component != 0) return DCM_ERR_INVALID_ARG;  // no bubble filter in the batched form
   std::vector<RepGeom> geom((size_t)R);
   int64_t ntot = 0, nctot = 0, nbtot = 0;
   for (int r = 0; r < R; ++r) {

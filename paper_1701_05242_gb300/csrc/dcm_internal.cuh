@@ -115,6 +115,11 @@ struct dcm_ctx {
   // Verlet lists (params.skin > 0)
   int32_t* nnb;             // n_max: same-image entries of each list (from the front)
   int32_t* nimg;            // n_max: periodic-image entries of each list (from the back)
+  // bubble filter (params.min_component > 0)
+  int32_t* cc_lab;          // nbox: component tree parents
+  int32_t* cc_cnt;          // nbox: component sizes at the roots
+  int32_t* cc_flags;        // hook passes that changed a parent
+  uint8_t* cc_s0;           // nbox: S before the filter
   int32_t* capw;            // per warp: longest list of its 32 particles
   int32_t* offw;            // exclusive scan of capw (units of 32 entries)
   uint32_t* list;           // interleaved lists (grown on demand)
@@ -177,6 +182,9 @@ int scatter_sort(dcm_ctx* ctx, int64_t n, const int32_t* cell, const int32_t* sl
                  int64_t ncell, int32_t* perm, cudaStream_t st);
 
 // detect.cu
+// Section 2.1's bubble filter on S (params.min_component > 0): s_out and the
+// interface boxes of s_out (components.cu).
+int remove_small_components(dcm_ctx* ctx, const uint8_t* s_in, uint8_t* s_out, uint8_t* iface, cudaStream_t st);
 int detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t* iface,
                      int32_t* threshold, int32_t* g_out, cudaStream_t st);
 

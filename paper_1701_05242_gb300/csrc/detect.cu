@@ -197,6 +197,13 @@ int detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t
     DCM_LAUNCH(ctx, k_value_hist, nred, 256, 0, st, g, nbox, ctx->thr, ctx->hist, ctx->status);
   }
   DCM_LAUNCH(ctx, k_two_means, 1, 1024, 0, st, ctx->hist, ctx->thr, 64, ctx->p.threshold, threshold);
+  if (ctx->p.min_component > 0) {
+    // segment into scratch, then the filtered S and its interface into s, iface
+    DCM_LAUNCH(ctx, k_segment, nb, 256, 0, st, g, nx, ny, nz, ctx->thr, ctx->cc_s0, iface);
+    int r = check_launch(ctx, "detect_interface");
+    if (r) return r;
+    return remove_small_components(ctx, ctx->cc_s0, s, iface, st);
+  }
   DCM_LAUNCH(ctx, k_segment, nb, 256, 0, st, g, nx, ny, nz, ctx->thr, s, iface);
   return check_launch(ctx, "detect_interface");
 }

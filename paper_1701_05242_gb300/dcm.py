@@ -49,7 +49,7 @@ class dcm_params(ctypes.Structure):
                 ("iter_max", ctypes.c_int32), ("ntypes", ctypes.c_int32), ("eps", ctypes.c_double * 4),
                 ("sigma", ctypes.c_double * 4), ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("force_kernel", ctypes.c_int32), ("n_max", ctypes.c_int64),
-                ("skin", ctypes.c_double)]
+                ("skin", ctypes.c_double), ("min_component", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class dcm_state(ctypes.Structure):
@@ -74,6 +74,7 @@ _SIGS = {
     "dcm_bin": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "dcm_box_counts": (_i32, [_vp, _i64, _vp, _vp, _vp]),
     "dcm_detect_interface": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "dcm_remove_small_components": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "dcm_distance": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "dcm_cutoffs": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
     "dcm_forces": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -214,6 +215,10 @@ def dcm_box_counts(ctx: Context, n, pos, box_count, stream=None):
 def dcm_detect_interface(ctx: Context, box_count, s, iface, threshold, g=None, stream=None):
     ctx.check(lib.dcm_detect_interface(ctx.handle, _ptr(box_count), _ptr(s), _ptr(iface), _ptr(threshold), _ptr(g),
                                        _stream(stream)))
+
+
+def dcm_remove_small_components(ctx: Context, s_in, s_out, iface, stream=None):
+    ctx.check(lib.dcm_remove_small_components(ctx.handle, _ptr(s_in), _ptr(s_out), _ptr(iface), _stream(stream)))
 
 
 def dcm_distance(ctx: Context, s, iface, D, iters=None, stream=None):

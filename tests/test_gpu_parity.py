@@ -690,3 +690,76 @@ def test_pair_rule_is_strict_at_the_cutoff(D, prec):
 def test_single_particle_has_no_pairs(D):
     F, tot = two_particles(D, 6.0, 5.9)       # the other one (and its images) beyond rc
     assert tot[2] == 0 and tot[0] == 0.0 and np.abs(F).max() == 0.0
+
+
+# -------------------------------------------------------------- bubble filter
+def gpu_filter(D, s_np, box, min_component):
+    ctx = make_ctx(D, box, 16, min_component=min_component)
+    s_in = torch.from_numpy(np.ascontiguousarray(s_np, dtype=np.uint8)).cuda()
+    s_out = torch.empty_like(s_in)
+    iface = torch.empty_like(s_in)
+    D.dcm_remove_small_components(ctx, s_in, s_out, iface)
+    torch.cuda.synchronize()
+    assert D.dcm_status(ctx) == D.DCM_OK
+    return s_out.cpu().numpy(), iface.cpu().numpy()
+
+
+def test_bubble_filter_hand_built_gpu(D):
+    s = np.zeros((10, 10, 10), np.uint8)
+    s[2:8] = 1
+    s[4:6, 4:6, 4:6] = 0
+    s[3:6, 1:4, 7:10] = 0
+    s[0, 5, 5] = 1
+    nh = np.array([10, 10, 10])
+    so, io = gpu_filter(D, s.ravel(), (15.0, 15.0, 15.0), 10)
+    ref, k = O.remove_small_components(s.ravel(), nh, 10)
+    assert k == 2 and np.array_equal(so, ref) and np.array_equal(io, O.interface(ref, nh))
+
+
+@pytest.mark.parametrize("seed,min_c", [(0, 3), (1, 8), (2, 40)])
+def test_bubble_filter_random_volumes(D, seed, min_c):
+    # noisy volumes: thousands of components of every size, long periodic ones included
+    rng = np.random.default_rng(seed)
+    nh = np.array([40, 36, 30])
+    s = (rng.random(int(np.prod(nh))) < 0.5).astype(np.uint8)
+    so, io = gpu_filter(D, s, tuple(1.5 * nh), min_c)
+    ref, _ = O.remove_small_components(s, nh, min_c)
+    assert np.array_equal(so, ref) and np.array_equal(io, O.interface(ref, nh))
+
+
+def test_detect_with_filter_on_noisy_segmentation(D, slab_1935):
+    # w = 0: the raw counts give a noisy S with small components in both phases
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, smooth_w=0, min_component=6)
+    bc, g, T, s, iface = gpu_detect(D, ctx, pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED))
+    nh = O.grid_dims(slab_1935.box, 1.5)
+    og, oT, os_, oif = O.detect_interface(bc, nh, 0, None, 6)
+    _, _, raw, _ = O.detect_interface(bc, nh, 0)
+    assert T == oT and np.array_equal(s.cpu().numpy(), os_) and np.array_equal(iface.cpu().numpy(), oif)
+    assert not np.array_equal(raw, os_)     # the filter changed something here
+
+
+def test_step_with_filter_fp64_matches_oracle(D, slab_1935):
+    nsteps = 4
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, D.DCM_PREC_FP64, recompute_every=1, smooth_w=1, min_component=5)
+    st = D.State(ctx, pos4_of(D, slab_1935.pos, None, D.DCM_PREC_FP64),
+                 D.to_real4(torch.from_numpy(slab_1935.vel), None, torch.float64))
+    D.dcm_step_init(ctx, st)
+    p = O.Params(box=slab_1935.box, recompute_every=1, smooth_w=1, min_component=5)
+    ost = O.init_state(slab_1935.pos, slab_1935.vel, p)
+    for k in range(nsteps):
+        D.dcm_step(ctx, st, 0.005, 1)
+        ost = O.step(ost, 0.005, p)
+        th = st.thermo.cpu().numpy()
+        assert th[0] == pytest.approx(ost.E, rel=1e-9), k
+        assert th[3] == ost_pairs(ost, p), k
+    assert D.dcm_status(ctx) == D.DCM_OK
+
+
+def test_full_size_detection_with_filter(D, slab_16m):
+    slab = slab_16m
+    ctx = make_ctx(D, slab.box, slab.n, smooth_w=1, min_component=8)
+    bc, g, T, s, iface = gpu_detect(D, ctx, pos4_of(D, slab.pos, None, D.DCM_PREC_MIXED))
+    nh = O.grid_dims(slab.box, 1.5)
+    og, oT, os_, oif = O.detect_interface(bc, nh, 1, None, 8)
+    assert T == oT and np.array_equal(s.cpu().numpy(), os_) and np.array_equal(iface.cpu().numpy(), oif)
+    assert D.dcm_status(ctx) == D.DCM_OK
