@@ -35,7 +35,7 @@ METRIC = "DCM step particle-steps/s at N=16M"
 UNIT = "particle-steps/s"
 K_RECOMPUTE = 10
 DT = 0.005
-FLOP_PER_PAIR = 18          # FP32-pipe instructions per accepted pair
+FLOP_PER_PAIR = 18          # FP32-pipe instructions of the pair arithmetic per accepted pair
 FP32_LANES_PER_SM = 128
 
 

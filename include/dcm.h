@@ -306,7 +306,7 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
 
 /* ---- batched form: many independent systems in one launch per stage ---- */
 
-/* R independent replicas (the benchmark spec's batching form) that share every
+/* R independent replicas (the batching form) that share every
  * parameter in *p except the box and the particle count: replica r has box
  * boxes[3r .. 3r+2] (host) and counts[r] particles (host).  Each replica is
  * validated as a single system (dcm_validate_params).  The state arrays of
