@@ -234,7 +234,7 @@ struct ScratchPlan {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
            8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
-           (min_component > 0 ? 9 * nbox + 4 * 80 : 0);
+           (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2);
   }
 };
 
@@ -277,7 +277,8 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
                  ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
                  ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
-                 ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0};
+                 ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0, ctx->dq[0], ctx->dq[1], ctx->dqlen,
+                 ctx->dstamp, ctx->dfixed};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -347,6 +348,11 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
     alloc((void**)&ctx->dmax, 16);
     alloc((void**)&ctx->lflag, 16);
   }
+  alloc((void**)&ctx->dq[0], 4 * s.nbox);
+  alloc((void**)&ctx->dq[1], 4 * s.nbox);
+  alloc((void**)&ctx->dqlen, 4 * (int64_t)(p->iter_max + 2));
+  alloc((void**)&ctx->dstamp, 4 * s.nbox);
+  alloc((void**)&ctx->dfixed, s.nbox);
   if (p->min_component > 0) {
     alloc((void**)&ctx->cc_lab, 4 * s.nbox);
     alloc((void**)&ctx->cc_cnt, 4 * s.nbox);

@@ -115,6 +115,12 @@ struct dcm_ctx {
   // Verlet lists (params.skin > 0)
   int32_t* nnb;             // n_max: same-image entries of each list (from the front)
   int32_t* nimg;            // n_max: periodic-image entries of each list (from the back)
+  // distance sweeps: queues of boxes to re-solve, their lengths per sweep,
+  // the last sweep each box was queued for, and the boxes fixed at 0
+  int32_t* dq[2];
+  int32_t* dqlen;
+  int32_t* dstamp;
+  uint8_t* dfixed;
   // bubble filter (params.min_component > 0)
   int32_t* cc_lab;          // nbox: component tree parents
   int32_t* cc_cnt;          // nbox: component sizes at the roots

@@ -5,12 +5,15 @@
 // until the largest change of a pass is below epsilon; its result is the
 // fixed point of the local fast-sweeping update restricted to distances
 // <= r_grid, whatever the visiting order.  On the GPU the same fixed point is
-// reached by Jacobi sweeps: every box of the high-density phase re-solves the
-// Godunov update from the previous iterate (double buffered, so the result is
-// deterministic), and a per-sweep device flag records whether any box
-// changed; a sweep that finds its predecessor's flag clear exits at once, so
-// a fixed budget of launches costs little once converged.  The MPI_Allreduce
-// of the paper's version becomes that flag.
+// reached by Jacobi sweeps (double buffered, so the result is deterministic):
+// sweep 0 re-solves every box of the high-density phase; every later sweep
+// re-solves only the boxes of its queue — the boxes that changed in the
+// previous sweep and their six neighbours — which are exactly the boxes
+// whose update can differ from the previous sweep's, so the iterates are
+// those of full Jacobi sweeps while the work follows the moving front (the
+// paper's queue Q).  A sweep whose queue is empty exits at once, so a fixed
+// budget of launches costs little once converged; the MPI_Allreduce of the
+// paper's version becomes the queue length in device memory.
 #include <algorithm>
 
 #include "dcm_internal.cuh"
@@ -19,12 +22,16 @@ namespace dcm {
 
 template <typename R>
 __global__ void k_dist_init(const uint8_t* __restrict__ s, const uint8_t* __restrict__ iface, int64_t nbox,
-                            R* __restrict__ D0, R* __restrict__ D1) {
+                            R* __restrict__ D0, R* __restrict__ D1, uint8_t* __restrict__ fixed0,
+                            int32_t* __restrict__ stamp) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbox) return;
-  R v = (!s[b] || iface[b]) ? (R)0 : RT<R>::inf();
+  bool z = !s[b] || iface[b];
+  R v = z ? (R)0 : RT<R>::inf();
   D0[b] = v;
   D1[b] = v;
+  fixed0[b] = (uint8_t)z;
+  stamp[b] = -1;
 }
 
 // Godunov upwind update of |grad d| = 1 with spacing h from the three axis
@@ -50,13 +57,49 @@ __device__ __forceinline__ R godunov3(R a0, R a1, R a2, R h) {
   return d;
 }
 
-// One Jacobi sweep.  Grid-stride over (row, chunk) work items with a grid of
-// a few waves, so a sweep after convergence costs one short wave of blocks
-// that read the flag and leave.
+// Queue the high-density boxes among b and its six neighbours for sweep it+1
+// (each box once: stamp holds the last sweep a box was queued for).
+__device__ __forceinline__ void dist_push(int64_t b, int x, int y, int z, int nx, int ny, int nz,
+                                          const uint8_t* __restrict__ fixed0, int32_t* __restrict__ stamp,
+                                          int32_t* __restrict__ qout, int32_t* __restrict__ qlen, int it) {
+  const int64_t nxy = (int64_t)nx * ny;
+  int64_t nb[7] = {b,
+                   x == 0 ? b + nx - 1 : b - 1,
+                   x == nx - 1 ? b - x : b + 1,
+                   y == 0 ? b + (int64_t)(ny - 1) * nx : b - nx,
+                   y == ny - 1 ? b - (int64_t)y * nx : b + nx,
+                   z == 0 ? b + (int64_t)(nz - 1) * nxy : b - nxy,
+                   z == nz - 1 ? b - (int64_t)z * nxy : b + nxy};
+  for (int k = 0; k < 7; ++k) {
+    int64_t q = nb[k];
+    if (fixed0[q]) continue;
+    if (atomicExch(stamp + q, it + 1) != it + 1) qout[atomicAdd(qlen + it + 1, 1)] = (int32_t)q;
+  }
+}
+
+// Update of one box from the previous iterate; true if it changed.
 template <typename R>
-__global__ void k_dist_sweep(const R* __restrict__ Din, R* __restrict__ Dout, int nx, int ny, int nz, R h, R r_grid,
-                             int32_t* __restrict__ flags, int it) {
-  if (it > 0 && flags[it - 1] == 0) return;  // the previous sweep changed nothing: converged
+__device__ __forceinline__ bool dist_update(const R* __restrict__ Din, R* __restrict__ Dout, int64_t b, int x, int y,
+                                            int z, int nx, int ny, int nz, R h, R r_grid) {
+  R cur = Din[b];
+  int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+  int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
+  R a0 = fmin(Din[row + xm], Din[row + xp]);
+  R a1 = fmin(Din[x + nx * (ym + (int64_t)ny * z)], Din[x + nx * (yp + (int64_t)ny * z)]);
+  R a2 = fmin(Din[x + nx * (y + (int64_t)ny * zm)], Din[x + nx * (y + (int64_t)ny * zp)]);
+  R d = godunov3<R>(a0, a1, a2, h);
+  bool ch = d < cur && d <= r_grid;
+  Dout[b] = ch ? d : cur;
+  return ch;
+}
+
+// Sweep 0 over the whole grid.  Grid-stride over (row, chunk) work items.
+template <typename R>
+__global__ void k_dist_sweep0(const R* __restrict__ Din, R* __restrict__ Dout, int nx, int ny, int nz, R h, R r_grid,
+                              const uint8_t* __restrict__ fixed0, int32_t* __restrict__ stamp,
+                              int32_t* __restrict__ qout, int32_t* __restrict__ qlen, int32_t* __restrict__ flags) {
   const int chunks = (nx + blockDim.x - 1) / blockDim.x;
   const int64_t items = (int64_t)ny * nz * chunks;
   bool changed = false;
@@ -66,22 +109,31 @@ __global__ void k_dist_sweep(const R* __restrict__ Din, R* __restrict__ Dout, in
     if (x >= nx) continue;
     int y = yz % ny, z = yz / ny;
     int64_t b = x + (int64_t)nx * yz;
-    R cur = Din[b];
-    if (cur == (R)0) continue;  // interface / low-density boxes are fixed at 0 in both buffers
-    int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
-    R a0 = fmin(Din[row + xm], Din[row + xp]);
-    R a1 = fmin(Din[x + nx * (ym + (int64_t)ny * z)], Din[x + nx * (yp + (int64_t)ny * z)]);
-    R a2 = fmin(Din[x + nx * (y + (int64_t)ny * zm)], Din[x + nx * (y + (int64_t)ny * zp)]);
-    R d = godunov3<R>(a0, a1, a2, h);
-    R out = cur;
-    if (d < cur && d <= r_grid) {
-      out = d;
+    if (fixed0[b]) continue;  // interface / low-density boxes are fixed at 0 in both buffers
+    if (dist_update<R>(Din, Dout, b, x, y, z, nx, ny, nz, h, r_grid)) {
       changed = true;
+      dist_push(b, x, y, z, nx, ny, nz, fixed0, stamp, qout, qlen, 0);
     }
-    Dout[b] = out;
+  }
+  if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[0] = 1;
+}
+
+// Sweep it >= 1 over its queue (grid-stride; an empty queue means converged).
+template <typename R>
+__global__ void k_dist_sweep_queue(const R* __restrict__ Din, R* __restrict__ Dout, int nx, int ny, int nz, R h,
+                                   R r_grid, const uint8_t* __restrict__ fixed0, int32_t* __restrict__ stamp,
+                                   const int32_t* __restrict__ qin, int32_t* __restrict__ qout,
+                                   int32_t* __restrict__ qlen, int32_t* __restrict__ flags, int it) {
+  const int32_t n = qlen[it];
+  bool changed = false;
+  const int64_t nxy = (int64_t)nx * ny;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = qin[k];
+    int x = (int)(b % nx), y = (int)((b / nx) % ny), z = (int)(b / nxy);
+    if (dist_update<R>(Din, Dout, b, x, y, z, nx, ny, nz, h, r_grid)) {
+      changed = true;
+      dist_push(b, x, y, z, nx, ny, nz, fixed0, stamp, qout, qlen, it);
+    }
   }
   if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
 }
@@ -106,12 +158,24 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
   int64_t nbox = ctx->nbox;
   R h = (R)ctx->p.h, rg = (R)ctx->p.r_grid;
   R* buf[2] = {D, (R*)ctx->D[1]};
+  int32_t* q[2] = {ctx->dq[0], ctx->dq[1]};
   unsigned nb = (unsigned)((nbox + 255) / 256);
   int64_t items = (int64_t)ny * nz * ((nx + 127) / 128);
   unsigned sg = (unsigned)std::min<int64_t>(items, 152 * 16);
+  const unsigned qg = 152 * 8;  // queue sweeps: grid-stride over the queue length read on the device
   int iter_max = ctx->p.iter_max;
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(int32_t) * (size_t)(iter_max + 2), st));
-  DCM_LAUNCH(ctx, k_dist_init<R>, nb, 256, 0, st, s, iface, nbox, buf[0], buf[1]);
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dqlen, 0, sizeof(int32_t) * (size_t)(iter_max + 2), st));
+  DCM_LAUNCH(ctx, k_dist_init<R>, nb, 256, 0, st, s, iface, nbox, buf[0], buf[1], ctx->dfixed, ctx->dstamp);
+  auto sweep = [&](int it) -> int {
+    if (it == 0)
+      DCM_LAUNCH(ctx, k_dist_sweep0<R>, sg, 128, 0, st, buf[0], buf[1], nx, ny, nz, h, rg, ctx->dfixed, ctx->dstamp,
+                 q[1], ctx->dqlen, ctx->flags);
+    else
+      DCM_LAUNCH(ctx, k_dist_sweep_queue<R>, qg, 256, 0, st, buf[it & 1], buf[(it + 1) & 1], nx, ny, nz, h, rg,
+                 ctx->dfixed, ctx->dstamp, q[it & 1], q[(it + 1) & 1], ctx->dqlen, ctx->flags, it);
+    return DCM_OK;
+  };
   int done = 0;
   if (host_check) {
     // chunks of 8 sweeps, then look at the last flag of the chunk on the host
@@ -119,8 +183,7 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
     bool converged = false;
     while (done < iter_max && !converged) {
       int m = std::min(chunk, iter_max - done);
-      for (int k = 0; k < m; ++k, ++done)
-        DCM_LAUNCH(ctx, k_dist_sweep<R>, sg, 128, 0, st, buf[done & 1], buf[(done + 1) & 1], nx, ny, nz, h, rg, ctx->flags, done);
+      for (int k = 0; k < m; ++k, ++done) sweep(done);
       DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status, ctx->flags + done - 1, sizeof(int32_t),
                                         cudaMemcpyDeviceToHost, st));
       DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -140,8 +203,7 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
     // convergence exit at once.
     int budget = (int)std::ceil(8.0 * ctx->p.r_grid / ctx->p.h) + 8;
     budget = std::min(budget + (budget & 1), iter_max + (iter_max & 1));
-    for (; done < budget; ++done)
-      DCM_LAUNCH(ctx, k_dist_sweep<R>, sg, 128, 0, st, buf[done & 1], buf[(done + 1) & 1], nx, ny, nz, h, rg, ctx->flags, done);
+    for (; done < budget; ++done) sweep(done);
     DCM_LAUNCH(ctx, k_dist_finish, 1, 1, 0, st, ctx->flags, done, iters, ctx->status);
   }
   return check_launch(ctx, "distance_sweeps");
