@@ -21,18 +21,24 @@ __device__ __forceinline__ R wrap_coord(R x, R L) {
   return x;
 }
 
+// kicks = 1: the first half kick of a step; kicks = 2: also the second half
+// kick of the previous step (the same two roundings as two launches), used
+// inside a multi-step call where that step's kinetic energy is not reported.
 template <typename R>
 __global__ void k_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__ pos, typename RT<R>::R4* __restrict__ vel,
                                    const typename RT<R>::R4* __restrict__ force, R half_dt, R dt, Grid<R> g,
-                                   int32_t* __restrict__ cell, int32_t* __restrict__ slot, int32_t* __restrict__ count) {
+                                   int32_t* __restrict__ cell, int32_t* __restrict__ slot, int32_t* __restrict__ count,
+                                   int kicks) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   auto p = pos[i];
   auto v = vel[i];
   auto f = force[i];
-  v.x += half_dt * f.x;
-  v.y += half_dt * f.y;
-  v.z += half_dt * f.z;
+  for (int k = 0; k < kicks; ++k) {
+    v.x += half_dt * f.x;
+    v.y += half_dt * f.y;
+    v.z += half_dt * f.z;
+  }
   p.x = wrap_coord<R>(p.x + dt * v.x, g.L[0]);
   p.y = wrap_coord<R>(p.y + dt * v.y, g.L[1]);
   p.z = wrap_coord<R>(p.z + dt * v.z, g.L[2]);
@@ -182,7 +188,7 @@ static int step_run_lists(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int
       DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s));
       if (n > 0)
         DCM_LAUNCH(ctx, k_kick_drift_count<R>, (unsigned)((n + 255) / 256), 256, 0, s, n, (R4*)st->pos[st->cur],
-                   (R4*)st->vel[st->cur], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count);
+                   (R4*)st->vel[st->cur], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count, 1);
     } else {
       if ((r = list_kick_drift<R>(ctx, st, n, hdt, rdt, &rebuild, s))) return r;
       if (rebuild && (r = list_wrap_count<R>(ctx, st, n, s))) return r;
@@ -220,11 +226,15 @@ int step_run(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int nsteps, cuda
   int K = ctx->p.recompute_every;
   for (int k = 0; k < nsteps; ++k) {
     int c = st->cur, o = 1 - c;
+    // only the last step of the call reports thermo: the second half kick of
+    // the others is applied by the next step's kick-drift launch
+    const bool last = k == nsteps - 1;
     stage_begin(ctx, DCM_STAGE_KICK_DRIFT, s);
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s));
     if (n > 0)
       DCM_LAUNCH(ctx, k_kick_drift_count<R>, (unsigned)((n + 255) / 256), 256, 0, s, n, (R4*)st->pos[c],
-                 (R4*)st->vel[c], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count);
+                 (R4*)st->vel[c], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count,
+                 k == 0 ? 1 : 2);
     stage_end(ctx, DCM_STAGE_KICK_DRIFT, s);
     stage_begin(ctx, DCM_STAGE_BIN, s);
     int r = exclusive_scan(ctx, ctx->cell_count, ctx->cell_start, ctx->ncell, s);
@@ -236,11 +246,13 @@ int step_run(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int nsteps, cuda
     if (st->t % K == 0)
       if ((r = recompute_cutoffs<R>(ctx, n, (const R4*)st->pos[o], (R*)st->rc[o], s))) return r;
     if ((r = lj_forces<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], ctx->cell_start, (R4*)st->force,
-                          ctx->totals, s)))
+                          last ? ctx->totals : nullptr, s)))
       return r;
-    stage_begin(ctx, DCM_STAGE_KICK, s);
-    if ((r = finish_thermo<R>(ctx, n, (R4*)st->vel[o], (const R4*)st->force, hdt, st->thermo, s))) return r;
-    stage_end(ctx, DCM_STAGE_KICK, s);
+    if (last) {
+      stage_begin(ctx, DCM_STAGE_KICK, s);
+      if ((r = finish_thermo<R>(ctx, n, (R4*)st->vel[o], (const R4*)st->force, hdt, st->thermo, s))) return r;
+      stage_end(ctx, DCM_STAGE_KICK, s);
+    }
     st->cur = o;
   }
   return DCM_OK;

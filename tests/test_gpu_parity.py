@@ -436,11 +436,16 @@ def test_step_mixed_on_shared_inputs(D, slab_1935):
     assert np.abs(rcn - a["rc"]).max() <= RC_TOL
 
 
-def test_step_batched_call_equals_single_calls(D, slab_1935):
-    _, st1, th1 = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, 12, K=5, per_step=True)
-    _, st2, th2 = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, 12, K=5, per_step=False)
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_step_batched_call_equals_single_calls(D, slab_1935, prec):
+    # one call of 12 steps (the second half kicks fused into the next steps'
+    # kick-drift, thermo of the last step only) == 12 calls of one step, bit for bit
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    _, st1, th1 = run_gpu_steps(D, slab_1935, P, 12, K=5, per_step=True)
+    _, st2, th2 = run_gpu_steps(D, slab_1935, P, 12, K=5, per_step=False)
     assert np.array_equal(th1[-1], th2[-1])
     assert torch.equal(st1.current()[0], st2.current()[0])
+    assert torch.equal(st1.current()[1], st2.current()[1])
 
 
 def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5):
