@@ -66,14 +66,15 @@ enum dcm_status_code {
 };
 
 /* Cell-list force kernels (all walk the same culled cell rows and accept the
- * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2
- * and 3 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
+ * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2,
+ * 3 and 4 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
  * ntypes = 1) and fall back to kernel 1 otherwise. */
 enum {
   DCM_FORCE_AUTO = 0,        /* kernel 3 where it applies, else kernel 1 */
   DCM_FORCE_THREAD = 1,      /* one thread per particle i, one candidate per instruction */
   DCM_FORCE_TWO_PHASE = 2,   /* per-lane shared-memory buffers of accepted pairs */
-  DCM_FORCE_PACKED = 3       /* one thread per particle i, two candidates per FP32x2 instruction */
+  DCM_FORCE_PACKED = 3,      /* one thread per particle i, two candidates per FP32x2 instruction */
+  DCM_FORCE_TILE = 4         /* as 3, with each warp's row windows staged in shared memory */
 };
 
 enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };

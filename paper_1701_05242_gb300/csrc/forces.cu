@@ -17,6 +17,7 @@
 // Pair arithmetic is branch-free: rejected candidates get 1/r^2 = 0, which
 // zeroes every term.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "forces_core.cuh"
@@ -64,6 +65,125 @@ __global__ void __launch_bounds__(kForceBlock) k_forces_x2(int64_t n, const floa
   float e_out = 0, w_out = 0;
   int np = 0;
   if (i < n) force[i] = force_one<float, false, true>(pos, start, a.g, a, (int)i, __ldg(pos + i), rc[i], e_out, w_out, np);
+  if (part) warp_partials3<float>(e_out, w_out, np, part, nwarp);
+}
+
+// ----------------------------------------------------------------------------
+// Tile kernel (one type, FP32): the warp's 32 particles share one x-line of
+// cells, so for every row offset (dy, dz) their windows lie in one grid row;
+// the warp stages the union of the windows (and the cell starts around it)
+// in shared memory with coalesced loads, then every lane runs the packed pair
+// loop of its own window from the tile.  Warps whose particles span two
+// x-lines, or whose stencil reaches a periodic boundary or a tile overflows,
+// take the cell-row walk of k_forces_x2.
+// ----------------------------------------------------------------------------
+constexpr int kTileWarps = 4;
+constexpr int kTileCap = 128;   // staged particles per warp and row
+constexpr int kTileCells = 40;  // staged cell starts per warp and row
+
+__global__ void __launch_bounds__(32 * kTileWarps) k_forces_tile(int64_t n, const float4* __restrict__ pos,
+                                                                 const float* __restrict__ rc,
+                                                                 const int32_t* __restrict__ start,
+                                                                 ForceArgs<float> a, float4* __restrict__ force,
+                                                                 double* __restrict__ part, int64_t nwarp) {
+  __shared__ float4 tile[kTileWarps][kTileCap];
+  __shared__ int32_t cst[kTileWarps][kTileCells];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  const Grid<float>& g = a.g;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const float l = g.edge, il = g.inv_edge;
+  const float4 pi = valid ? __ldg(pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float rc_in = valid ? __ldg(rc + i) : 0.f;
+  float rci = rc_in;
+  if (!(rci <= a.rc_max)) rci = a.rc_max;
+  if (!(rci > 0.f)) rci = 0.f;
+  const int cx = cell_coord<float>(pi.x, l, il, nx), cy = cell_coord<float>(pi.y, l, il, ny),
+            cz = cell_coord<float>(pi.z, l, il, nz);
+  const int H = (int)ceilf(rci * il);
+  int Hm = H, cmin = cx, cmax = cx;
+  for (int o = 16; o > 0; o >>= 1) {
+    Hm = max(Hm, __shfl_xor_sync(FULL, Hm, o));
+    cmin = min(cmin, __shfl_xor_sync(FULL, cmin, o));
+    cmax = max(cmax, __shfl_xor_sync(FULL, cmax, o));
+  }
+  const int cy0 = __shfl_sync(FULL, cy, 0), cz0 = __shfl_sync(FULL, cz, 0);
+  const bool tiled = __all_sync(FULL, valid && cy == cy0 && cz == cz0) && cmin - Hm >= 0 && cmax + Hm < nx &&
+                     cy0 - Hm >= 0 && cy0 + Hm < ny && cz0 - Hm >= 0 && cz0 + Hm < nz &&
+                     (cmax - cmin) + 2 * Hm + 2 <= kTileCells;
+  float e_out = 0.f, w_out = 0.f;
+  int np = 0;
+  if (!tiled) {
+    if (valid) force[i] = force_one<float, false, true>(pos, start, g, a, (int)i, pi, rc_in, e_out, w_out, np);
+  } else {
+    Acc2 c2;
+    const float rc2 = rci * rci, rc2s = rc2 * 1.000004f;
+    const int self = (int)i;
+    for (int dz = -Hm; dz <= Hm; ++dz) {
+      const int uz = cz0 + dz;
+      const float gz = uz > cz ? (float)uz * l - pi.z : (uz < cz ? pi.z - (float)(uz + 1) * l : 0.f);
+      for (int dy = -Hm; dy <= Hm; ++dy) {
+        const int uy = cy0 + dy;
+        const float gy = uy > cy ? (float)uy * l - pi.y : (uy < cy ? pi.y - (float)(uy + 1) * l : 0.f);
+        const float gyz2 = gz * gz + gy * gy;
+        bool has = dz >= -H && dz <= H && dy >= -H && dy <= H && gyz2 < rc2s;
+        int ulo = 0, uhi = -1;
+        if (has) {
+          const float wx = sqrtf(rc2s - gyz2);
+          ulo = max(ufloor<float>((pi.x - wx) * il - 5e-4f), cx - H);
+          uhi = min(ufloor<float>((pi.x + wx) * il + 5e-4f), cx + H);
+          has = ulo <= uhi;
+        }
+        if (__ballot_sync(FULL, has) == 0) continue;
+        int umin = has ? ulo : INT_MAX, umax = has ? uhi : INT_MIN;
+        for (int o = 16; o > 0; o >>= 1) {
+          umin = min(umin, __shfl_xor_sync(FULL, umin, o));
+          umax = max(umax, __shfl_xor_sync(FULL, umax, o));
+        }
+        const int64_t row = (int64_t)nx * (uy + (int64_t)ny * uz);
+        const int ncs = umax - umin + 2;  // <= kTileCells: the stencil spans at most that many cells
+        __syncwarp();                     // the previous row's tile is no longer read
+        for (int k = lane; k < ncs; k += 32) cst[wid][k] = __ldg(start + row + umin + k);
+        __syncwarp();
+        const int base = cst[wid][0], cnt = cst[wid][ncs - 1] - base;
+        const int j0 = has ? cst[wid][ulo - umin] : 0, j1 = has ? cst[wid][uhi - umin + 1] : 0;
+        const bool centre = dz == 0 && dy == 0;
+        if (cnt <= kTileCap) {
+          for (int k = lane; k < cnt; k += 32) tile[wid][k] = __ldg(pos + base + k);
+          __syncwarp();
+          if (has) {
+            const float4* tp = tile[wid] - base;  // indexed by the global slot j
+            if (centre) {
+              pair_range_x2<false, true>(tp, j0, self, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+              pair_range_x2<false, true>(tp, self + 1, j1, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+            } else {
+              pair_range_x2<false, true>(tp, j0, j1, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+            }
+          }
+        } else if (has) {  // too many to stage: read this row from global memory
+          if (centre) {
+            pair_range_x2<false>(pos, j0, self, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+            pair_range_x2<false>(pos, self + 1, j1, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+          } else {
+            pair_range_x2<false>(pos, j0, j1, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+          }
+        }
+      }
+    }
+    float ush = 0.f;
+    if (a.shift && rc2 > 0.f) {
+      const float s2 = 1.f / rc2, s6 = s2 * s2 * s2;
+      ush = 4.f * s6 * (s6 - 1.f);
+    }
+    const float en = c2.en.x + c2.en.y;
+    np = c2.np;
+    e_out = 2.f * en - 0.5f * (float)np * ush;
+    w_out = 12.f * (c2.vir.x + c2.vir.y);
+    force[i] = make_float4(-24.f * (c2.fx.x + c2.fx.y), -24.f * (c2.fy.x + c2.fy.y), -24.f * (c2.fz.x + c2.fz.y),
+                           e_out);
+  }
   if (part) warp_partials3<float>(e_out, w_out, np, part, nwarp);
 }
 
@@ -246,7 +366,7 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
   if (part) warp_partials3<float>(e_out, w_out, c.np, part, nwarp);
 }
 
-// Kernels 2 and 3 serve one-type mixed-precision runs with eps = sigma = 1.
+// Kernels 2, 3 and 4 serve one-type mixed-precision runs with eps = sigma = 1.
 int resolve_force_kernel(const dcm_ctx* ctx) {
   int k = force_kernel_choice(ctx->p);
   if (k == DCM_FORCE_THREAD) return k;
@@ -283,7 +403,12 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   if constexpr (sizeof(R) == 4) {
     const ForceArgs<float>& af = a;
     const int kind = resolve_force_kernel(ctx);
-    if (kind == DCM_FORCE_PACKED) {
+    if (kind == DCM_FORCE_TILE) {
+      static_assert(32 * kTileWarps == kForceBlock, "partials layout assumes equal blocks");
+      DCM_LAUNCH(ctx, k_forces_tile, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part,
+                 nwarp);
+      done = true;
+    } else if (kind == DCM_FORCE_PACKED) {
       DCM_LAUNCH(ctx, k_forces_x2, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part, nwarp);
       done = true;
     } else if (kind == DCM_FORCE_TWO_PHASE) {

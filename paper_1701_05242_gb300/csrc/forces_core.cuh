@@ -117,13 +117,16 @@ struct Acc2 {
   int np = 0;
 };
 
-template <bool SJ>
+// STAGED: pos points into a shared-memory tile (plain loads) instead of
+// global memory (read-only cached loads).
+template <bool SJ, bool STAGED = false>
 __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                               float zi, float shx, float shy, float shz, float rc2, Acc2& c) {
   const float2 two = make_float2(2.f, 2.f), m1 = make_float2(-1.f, -1.f);
   for (int j = lo; j < hi; j += 2) {
     const bool has1 = j + 1 < hi;
-    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + (has1 ? j + 1 : j));
+    const int j1 = has1 ? j + 1 : j;
+    const float4 p0 = STAGED ? pos[j] : __ldg(pos + j), p1 = STAGED ? pos[j1] : __ldg(pos + j1);
     float2 dx, dy, dz;
     if (SJ) {
       dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);

@@ -319,7 +319,7 @@ def test_forces_two_types(D, prec):
         assert int(tot[2]) == ref.npairs
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 @pytest.mark.parametrize("l", [1.5, 1.0])
 def test_forces_kernel_variants(D, slab_1935, kernel, l):
     """Every cell-list force kernel against the oracle (mixed, one type)."""
@@ -337,12 +337,13 @@ def test_forces_kernel_variants(D, slab_1935, kernel, l):
     assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
 
 
-def test_forces_kernel_rejects_unknown(D):
+@pytest.mark.parametrize("k", [-1, 5])
+def test_forces_kernel_rejects_unknown(D, k):
     with pytest.raises(D.DcmError):
-        make_ctx(D, (12.0, 12.0, 48.0), 10, force_kernel=4)
+        make_ctx(D, (12.0, 12.0, 48.0), 10, force_kernel=k)
 
 
-@pytest.mark.parametrize("kernel", [1, 3])
+@pytest.mark.parametrize("kernel", [1, 3, 4])
 def test_forces_tiny_box_and_ragged_kernels(D, kernel):
     """rc_max = L/2 (rows reaching both periodic images), 97 particles,
     some cutoffs 0 (no pairs, no shift)."""
@@ -566,7 +567,7 @@ def test_full_size_sampled(D, slab_16m):
     spos = slab.pos[operm].astype(np.float64)
     Fo, eo, wo, po = O.forces_subset(spos, rcn, slab.box, 1.5, idx, nthreads=8)
     totals = []
-    for kernel in (0, 1, 2, 3):  # every cell-list kernel on the same sorted input
+    for kernel in (0, 1, 2, 3, 4):  # every cell-list kernel on the same sorted input
         kctx = make_ctx(D, slab.box, n, force_kernel=kernel)
         F = torch.empty_like(ps)
         tot = torch.zeros(3, dtype=torch.float64, device="cuda")
