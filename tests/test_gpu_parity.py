@@ -769,3 +769,32 @@ def test_full_size_detection_with_filter(D, slab_16m):
     og, oT, os_, oif = O.detect_interface(bc, nh, 1, None, 8)
     assert T == oT and np.array_equal(s.cpu().numpy(), os_) and np.array_equal(iface.cpu().numpy(), oif)
     assert D.dcm_status(ctx) == D.DCM_OK
+
+
+def test_verlet_list_overflow_falls_back_to_exact_lists(D):
+    """A blob at density 2.4 holds more neighbours within rc + skin than the
+    list capacity bound (density 1.3): the build must detect the overflow,
+    count exactly and fill again; forces then match the oracle."""
+    g = np.arange(10) * 0.75 + 5.0
+    blob = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(4)
+    gas = rng.uniform(0, 18.0, size=(400, 3))
+    far = np.abs(gas[:, None, :] - blob[None, :, :]).max(-1).min(1) > 1.5
+    pts = np.concatenate([blob, gas[far]]).astype(np.float32)
+    box = (18.0, 18.0, 18.0)
+    n = len(pts)
+    # uniform cutoff 3: bound = 1.3 x (4/3) pi 3.5^3 + 24 = 257 < ~360 neighbours in the blob
+    ctx = make_ctx(D, box, n, D.DCM_PREC_FP64, skin=0.5, rc_min=3.0, rc_max=3.0, recompute_every=1000)
+    st = D.State(ctx, pos4_of(D, pts, None, D.DCM_PREC_FP64), torch.zeros((n, 4), dtype=torch.float64, device="cuda"))
+    D.dcm_step_init(ctx, st)
+    assert D.dcm_status(ctx) == D.DCM_OK
+    pos, vel, rc, ids = st.current()
+    p = pos.cpu().numpy()[:, :3]
+    rcn = rc.cpu().numpy()
+    assert (rcn == 3.0).all()
+    ref = O.forces_cells(np.mod(p, box), rcn, box, 1.5)
+    dc = blob - blob[555]
+    assert (np.sqrt((dc * dc).sum(1)) < 3.5).sum() - 1 > int(4.18879020478639 * 3.5 ** 3 * 1.3) + 24
+    F = st.force.cpu().numpy()[:, :3]
+    assert np.abs(F - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+    assert st.thermo[3].item() == ref.npairs
