@@ -115,6 +115,13 @@ struct CountVisitor {
   }
 };
 
+// Predicated 32-bit store (no branch around it in the candidate loop).
+__device__ __forceinline__ void store_if(bool p, uint32_t* addr, uint32_t v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}" ::"l"(addr), "r"(v),
+               "r"((uint32_t)p)
+               : "memory");
+}
+
 template <typename R>
 struct FillVisitor {
   const typename RT<R>::R4* __restrict__ pos;
@@ -127,10 +134,9 @@ struct FillVisitor {
     for (int j = j0; j < j1; ++j) {
       auto pj = ldg4(pos + j);
       R dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-      if (fma(dx, dx, fma(dy, dy, dz * dz)) < rl2) {
-        if (k < lim) out[(int64_t)k * 32] = (uint32_t)j;
-        ++k;
-      }
+      const bool acc = fma(dx, dx, fma(dy, dy, dz * dz)) < rl2;
+      store_if(acc && k < lim, out + (int64_t)k * 32, (uint32_t)j);
+      k += acc ? 1 : 0;
     }
     kf = k;
   }
@@ -408,14 +414,23 @@ __global__ void __launch_bounds__(128) k_forces_list_x2(int64_t n, const float4*
     pc.fx = pc.fy = pc.fz = pc.en = pc.vir = f2(0.f, 0.f);
     pc.np = 0;
     int k = 0;
-    // four entries per iteration: their indices, then their positions, are
-    // all requested before any arithmetic, so that the loads overlap
-    for (; k + 3 < m; k += 4) {
-      const uint32_t* q = lp + (int64_t)k * 32;
-      const int j0 = (int)__ldg(q), j1 = (int)__ldg(q + 32), j2 = (int)__ldg(q + 64), j3 = (int)__ldg(q + 96);
-      const float4 p0 = __ldg(pos + j0), p1 = __ldg(pos + j1), p2 = __ldg(pos + j2), p3 = __ldg(pos + j3);
-      packed_pair(pi, p0, p1, rc2, pc);
-      packed_pair(pi, p2, p3, rc2, pc);
+    // four entries per iteration; the next four indices are requested before
+    // this iteration's arithmetic (the list streams from DRAM once, so its
+    // loads bypass L1 and leave it to the positions)
+    if (k + 3 < m) {
+      int e0 = (int)__ldcs(lp), e1 = (int)__ldcs(lp + 32), e2 = (int)__ldcs(lp + 64), e3 = (int)__ldcs(lp + 96);
+      for (; k + 3 < m; k += 4) {
+        const float4 p0 = __ldg(pos + e0), p1 = __ldg(pos + e1), p2 = __ldg(pos + e2), p3 = __ldg(pos + e3);
+        if (k + 7 < m) {
+          const uint32_t* q = lp + (int64_t)(k + 4) * 32;
+          e0 = (int)__ldcs(q);
+          e1 = (int)__ldcs(q + 32);
+          e2 = (int)__ldcs(q + 64);
+          e3 = (int)__ldcs(q + 96);
+        }
+        packed_pair(pi, p0, p1, rc2, pc);
+        packed_pair(pi, p2, p3, rc2, pc);
+      }
     }
     if (k + 1 < m) {
       const int j0 = (int)__ldg(lp + (int64_t)k * 32), j1 = (int)__ldg(lp + (int64_t)(k + 1) * 32);
