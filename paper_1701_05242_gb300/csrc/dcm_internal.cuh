@@ -221,7 +221,7 @@ template <typename R>
 int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, typename RT<R>::R4* force,
                 double* totals, cudaStream_t st);
 template <typename R>
-int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, bool* rebuild, cudaStream_t st);
+int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, int kicks, bool* rebuild, cudaStream_t st);
 template <typename R>
 int list_wrap_count(dcm_ctx* ctx, dcm_state* s, int64_t n, cudaStream_t st);
 

@@ -183,14 +183,19 @@ static int step_run_lists(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int
     int r;
     bool recompute = (st->t + 1) % K == 0;
     bool rebuild = recompute || !ctx->list_valid;
+    // as in step_run: only the last step of the call reports thermo, the
+    // others' second half kick rides on the next step's kick-drift launch
+    const bool last = k == nsteps - 1;
+    const int kicks = k == 0 ? 1 : 2;
     stage_begin(ctx, DCM_STAGE_KICK_DRIFT, s);
     if (rebuild) {
       DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * ctx->ncell, s));
       if (n > 0)
         DCM_LAUNCH(ctx, k_kick_drift_count<R>, (unsigned)((n + 255) / 256), 256, 0, s, n, (R4*)st->pos[st->cur],
-                   (R4*)st->vel[st->cur], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count, 1);
+                   (R4*)st->vel[st->cur], (const R4*)st->force, hdt, rdt, g, ctx->cell, ctx->slot, ctx->cell_count,
+                   kicks);
     } else {
-      if ((r = list_kick_drift<R>(ctx, st, n, hdt, rdt, &rebuild, s))) return r;
+      if ((r = list_kick_drift<R>(ctx, st, n, hdt, rdt, kicks, &rebuild, s))) return r;
       if (rebuild && (r = list_wrap_count<R>(ctx, st, n, s))) return r;
     }
     stage_end(ctx, DCM_STAGE_KICK_DRIFT, s);
@@ -208,11 +213,14 @@ static int step_run_lists(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int
       st->cur = o;
     }
     int c = st->cur;
-    if ((r = list_forces<R>(ctx, n, (const R4*)st->pos[c], (const R*)st->rc[c], (R4*)st->force, ctx->totals, s)))
+    if ((r = list_forces<R>(ctx, n, (const R4*)st->pos[c], (const R*)st->rc[c], (R4*)st->force,
+                            last ? ctx->totals : nullptr, s)))
       return r;
-    stage_begin(ctx, DCM_STAGE_KICK, s);
-    if ((r = finish_thermo<R>(ctx, n, (R4*)st->vel[c], (const R4*)st->force, hdt, st->thermo, s))) return r;
-    stage_end(ctx, DCM_STAGE_KICK, s);
+    if (last) {
+      stage_begin(ctx, DCM_STAGE_KICK, s);
+      if ((r = finish_thermo<R>(ctx, n, (R4*)st->vel[c], (const R4*)st->force, hdt, st->thermo, s))) return r;
+      stage_end(ctx, DCM_STAGE_KICK, s);
+    }
   }
   return DCM_OK;
 }

@@ -131,7 +131,21 @@ struct FillVisitor {
   __device__ __forceinline__ void plain(int j0, int j1, R xi, R yi, R zi) {
     const int lim = cap - kb;
     int k = kf;
-    for (int j = j0; j < j1; ++j) {
+    int j = j0;
+    if constexpr (sizeof(R) == 4) {  // two candidates per packed r^2 (the same roundings as one at a time)
+      for (; j + 1 < j1; j += 2) {
+        const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j + 1);
+        const float2 dx = make_float2(xi - p0.x, xi - p1.x), dy = make_float2(yi - p0.y, yi - p1.y),
+                     dz = make_float2(zi - p0.z, zi - p1.z);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const bool a0 = r2.x < rl2, a1 = r2.y < rl2;
+        store_if(a0 && k < lim, out + (int64_t)k * 32, (uint32_t)j);
+        k += a0 ? 1 : 0;
+        store_if(a1 && k < lim, out + (int64_t)k * 32, (uint32_t)(j + 1));
+        k += a1 ? 1 : 0;
+      }
+    }
+    for (; j < j1; ++j) {
       auto pj = ldg4(pos + j);
       R dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
       const bool acc = fma(dx, dx, fma(dy, dy, dz * dz)) < rl2;
@@ -479,16 +493,18 @@ template <typename R>
 __global__ void k_kick_drift_nowrap(int64_t n, typename RT<R>::R4* __restrict__ pos, typename RT<R>::R4* __restrict__ vel,
                                     const typename RT<R>::R4* __restrict__ force,
                                     const typename RT<R>::R4* __restrict__ xb, R half_dt, R dt,
-                                    int32_t* __restrict__ dmax) {
+                                    int32_t* __restrict__ dmax, int kicks) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.f;
   if (i < n) {
     auto p = pos[i];
     auto v = vel[i];
     auto f = force[i];
-    v.x += half_dt * f.x;
-    v.y += half_dt * f.y;
-    v.z += half_dt * f.z;
+    for (int k = 0; k < kicks; ++k) {  // 2: also the previous step's second half kick
+      v.x += half_dt * f.x;
+      v.y += half_dt * f.y;
+      v.z += half_dt * f.z;
+    }
     p.x += dt * v.x;
     p.y += dt * v.y;
     p.z += dt * v.z;
@@ -629,13 +645,13 @@ int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R*
 // Half kick + drift (no wrap); returns through *rebuild whether the largest
 // displacement since the build exceeds skin / 2 (synchronous read).
 template <typename R>
-int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, bool* rebuild, cudaStream_t st) {
+int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, int kicks, bool* rebuild, cudaStream_t st) {
   using R4 = typename RT<R>::R4;
   int c = s->cur;
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->dmax, 0, sizeof(int32_t), st));
   if (n > 0)
     DCM_LAUNCH(ctx, k_kick_drift_nowrap<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, (R4*)s->pos[c],
-               (R4*)s->vel[c], (const R4*)s->force, (const R4*)ctx->xbuild, hdt, dt, ctx->dmax);
+               (R4*)s->vel[c], (const R4*)s->force, (const R4*)ctx->xbuild, hdt, dt, ctx->dmax, kicks);
   DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 2, ctx->dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   int bits = ctx->host_status[2];
@@ -660,8 +676,8 @@ template int list_build<float>(dcm_ctx*, int64_t, const float4*, const float*, c
 template int list_build<double>(dcm_ctx*, int64_t, const dvec4*, const double*, cudaStream_t);
 template int list_forces<float>(dcm_ctx*, int64_t, const float4*, const float*, float4*, double*, cudaStream_t);
 template int list_forces<double>(dcm_ctx*, int64_t, const dvec4*, const double*, dvec4*, double*, cudaStream_t);
-template int list_kick_drift<float>(dcm_ctx*, dcm_state*, int64_t, float, float, bool*, cudaStream_t);
-template int list_kick_drift<double>(dcm_ctx*, dcm_state*, int64_t, double, double, bool*, cudaStream_t);
+template int list_kick_drift<float>(dcm_ctx*, dcm_state*, int64_t, float, float, int, bool*, cudaStream_t);
+template int list_kick_drift<double>(dcm_ctx*, dcm_state*, int64_t, double, double, int, bool*, cudaStream_t);
 template int list_wrap_count<float>(dcm_ctx*, dcm_state*, int64_t, cudaStream_t);
 template int list_wrap_count<double>(dcm_ctx*, dcm_state*, int64_t, cudaStream_t);
 

@@ -524,6 +524,20 @@ def test_step_verlet_lists_mixed_medium_box(D):
     assert abs(int(th[-1, 3]) - ref.npairs) <= near_cutoff_pairs(pw, rc.cpu().numpy().astype(np.float64), slab.box)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_step_lists_batched_call_equals_single_calls(D, slab_1935, prec):
+    # Verlet-list path: one call of 12 steps == 12 calls of one step, bit for bit
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    ctx1, st1, th1 = run_gpu_steps_list(D, slab_1935, P, 12, skin=0.4, K=5)
+    ctx2 = make_ctx(D, slab_1935.box, slab_1935.n, P, recompute_every=5, skin=0.4, rc_max=5.5)
+    st2 = D.State(ctx2, pos4_of(D, slab_1935.pos, None, P),
+                  D.to_real4(torch.from_numpy(slab_1935.vel), None, real_of(D, P)))
+    D.dcm_step_init(ctx2, st2)
+    D.dcm_step(ctx2, st2, 0.005, 12)
+    assert np.array_equal(th1[-1], st2.thermo.cpu().numpy())
+    assert torch.equal(st1.current()[0], st2.current()[0]) and torch.equal(st1.current()[1], st2.current()[1])
+
+
 def test_skin_validation(D):
     p = D.make_params((12.0, 12.0, 48.0), skin=0.5)   # rc_max 6 + 0.5 > 12 / 2
     rc, msg = D.dcm_validate_params(p)
