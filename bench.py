@@ -35,6 +35,7 @@ METRIC = "DCM step particle-steps/s at N=16M"
 UNIT = "particle-steps/s"
 K_RECOMPUTE = 10
 DT = 0.005
+LIST_SKIN = 0.5             # Verlet-list skin of the lists form (the fastest measured on the 16M slab)
 FLOP_PER_PAIR = 18          # FP32-pipe instructions of the pair arithmetic per accepted pair
 FP32_LANES_PER_SM = 128
 
@@ -53,6 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-lists", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args(argv)
 
@@ -289,9 +291,9 @@ def run_gb300(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    def new_state(prec):
+    def new_state(prec, skin=None):
         p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE, l=args.cell_edge,
-                          skin=args.skin, force_kernel=args.force_kernel)
+                          skin=args.skin if skin is None else skin, force_kernel=args.force_kernel)
         ctx = D.Context(p)
         real = ctx.real
         st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real, dev),
@@ -406,6 +408,41 @@ def run_gb300(args):
                "d2h_bytes_per_step": 2 * n * 16 + 32, "steps": ke,
                "note": "pinned host state in, dcm_step_init + 10 timesteps, state and thermo out"}
 
+    # ---------------- Verlet-list form (Alg. 2.2/2.3 with skin) on the same system
+    lists = None
+    if not args.skip_lists and args.skin == 0.0:
+        del st
+        ctx.close()
+        torch.cuda.empty_cache()
+        cl, sl = new_state(D.DCM_PREC_MIXED, skin=LIST_SKIN)
+        for _ in range(args.warmup):
+            D.dcm_step(cl, sl, DT, K_RECOMPUTE)
+        kl = max(1, min(10, args.steps))
+        barrier()
+        D.dcm_set_timing(cl, kl * K_RECOMPUTE * 2 + 8)
+        e0.record(stream)
+        for _ in range(kl):
+            D.dcm_step(cl, sl, DT, K_RECOMPUTE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msl = e0.elapsed_time(e1)
+        lst = D.dcm_stage_times(cl)
+        pl = float(sl.thermo[3].item())
+        ul, tl = aggregate(dist, float(n) * kl * K_RECOMPUTE, msl / 1000.0)
+        lf_ms, lf_cnt = lst["forces"]
+        lf_avg = lf_ms / max(lf_cnt, 1)
+        lists = {"value": ul / tl, "unit": UNIT, "steps": kl, "ms_per_step": msl / kl, "skin": LIST_SKIN,
+                 "force_kernel": "k_forces_list_x2", "force_avg_launch_ms": lf_avg,
+                 "force_frac_fp32": pl * FLOP_PER_PAIR / (lf_avg / 1000.0) / 1e12 / peak_tinstr if lf_avg > 0 else None,
+                 "list_builds": int(lst["lists"][1]), "build_avg_ms": lst["lists"][0] / max(lst["lists"][1], 1),
+                 "stage_ms_per_step": {k: v[0] / kl for k, v in lst.items()}, "pairs_last": pl,
+                 "note": "neighbour lists of radius rc_i + skin, rebuilt (with rebinning) when a particle moved "
+                         "more than skin/2 or the cutoffs were recomputed"}
+        del sl
+        cl.close()
+        torch.cuda.empty_cache()
+        ctx, st = new_state(D.DCM_PREC_MIXED)
+
     # ---------------- batched form: 64 replicas, autotuned, graph-captured
     batch = None
     if not args.skip_batch:
@@ -434,7 +471,7 @@ def run_gb300(args):
                           "precision": "fp32 pair math, fp64 totals", "l2": f"inputs larger than L2 (positions {16 * n / 1e6:.0f} MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "stage_ms_per_step": stage_ms, "fp64_form": fp64, "batched_form": batch, "device_status": status,
+               "stage_ms_per_step": stage_ms, "fp64_form": fp64, "lists_form": lists, "batched_form": batch, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}
         print(json.dumps(out), flush=True)
