@@ -118,8 +118,7 @@ struct CountVisitor {
 // Predicated 32-bit store (no branch around it in the candidate loop).
 __device__ __forceinline__ void store_if(bool p, uint32_t* addr, uint32_t v) {
   asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}" ::"l"(addr), "r"(v),
-               "r"((uint32_t)p)
-               : "memory");
+               "r"((uint32_t)p));  // no memory clobber: nothing in the build reads the lists back
 }
 
 template <typename R>
@@ -195,7 +194,7 @@ __global__ void __launch_bounds__(128) k_list_count(int64_t n, const typename RT
 // image entries from the back.  More than capw entries raise *flag (the lists
 // are then incomplete and the caller counts exactly and fills again).
 template <typename R>
-__global__ void __launch_bounds__(128) k_list_fill(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+__global__ void __maxnreg__(80) k_list_fill(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                    const R* __restrict__ rc, const int32_t* __restrict__ start,
                                                    Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ capw,
                                                    const int32_t* __restrict__ offw, uint32_t* __restrict__ list,
