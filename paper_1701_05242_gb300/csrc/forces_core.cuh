@@ -237,10 +237,12 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
         int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
         if (a0 <= a1) {
           int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
-          if (ysh == (R)0 && zsh == (R)0) {
+          if (uy == cy && uz == cz) {  // the particle's own row: cut it out
             segment<R, false, TYPED, X2>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2);
             segment<R, false, TYPED, X2>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
                                          c2);
+          } else if (ysh == (R)0 && zsh == (R)0) {
+            segment<R, false, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2);
           } else {
             segment<R, true, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2);
           }
