@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_forces_tile(int64_t n, cons
         bool has = dz >= -H && dz <= H && dy >= -H && dy <= H && gyz2 < rc2s;
         int ulo = 0, uhi = -1;
         if (has) {
-          const float wx = sqrtf(rc2s - gyz2);
+          const float wx = window_half_width(rc2s - gyz2);
           ulo = max(ufloor<float>((pi.x - wx) * il - 5e-4f), cx - H);
           uhi = min(ufloor<float>((pi.x + wx) * il + 5e-4f), cx + H);
           has = ulo <= uhi;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
         int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
         yi = uy >= ny ? pi.y - g.L[1] : pi.y;
         ysh = uy < 0 ? -g.L[1] : 0.f;
-        float wx = sqrtf(rc2s - gyz2);
+        float wx = window_half_width(rc2s - gyz2);
         ulo = max((int)floorf((pi.x - wx) * il - 5e-4f), cx - H);
         uhi = min((int)floorf((pi.x + wx) * il + 5e-4f), cx + H);
         row = (int64_t)nx * (wy + (int64_t)ny * wz);

@@ -60,7 +60,7 @@ __device__ __forceinline__ void walk_segments(const int32_t* __restrict__ start,
       uint32_t yc = uy < 0 ? 1u : (uy >= ny ? 2u : 0u);
       R yi = yc == 2 ? pi.y - g.L[1] : pi.y;
       R ysh = yc == 1 ? -g.L[1] : (R)0;
-      R wx = sqrt(rl2s - gyz2);
+      R wx = window_half_width(rl2s - gyz2);
       int ulo = max(ufloor<R>((pi.x - wx) * il - (R)5e-4), cx - H);
       int uhi = min(ufloor<R>((pi.x + wx) * il + (R)5e-4), cx + H);
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
