@@ -138,13 +138,14 @@ int dcm_params_default(dcm_params* p);
 
 /* Check *p without touching the GPU.  Rules: box > 0; h and l have at most 8
  * significant bits (so k*l is exact in FP32) and divide every box length
- * into fewer than 65536 cells; 0 < rc_min <= rc_max <= min(L)/2 (so at most
- * one periodic image of a particle lies within any cutoff); 1 <= ntypes <= 4;
- * eps, sigma > 0; smooth_w >= 0; 1 <= iter_max <= 100000; recompute_every
- * >= 1; force_kernel one of DCM_FORCE_*; min_component >= 0; 0 <= n_max < 2^31; skin >= 0 with rc_max + skin <= min(L)/2 and
- * n_max < 2^26 when skin > 0.
+ * into fewer than 65536 cells, fewer than 2^31 cells (and boxes) in all;
+ * 0 < rc_min <= rc_max <= min(L)/2 (so at most one periodic image of a
+ * particle lies within any cutoff); 1 <= ntypes <= 4; eps, sigma > 0;
+ * smooth_w >= 0; 1 <= iter_max <= 100000; recompute_every >= 1;
+ * force_kernel one of DCM_FORCE_*; min_component >= 0; 0 <= n_max < 2^31;
+ * skin >= 0 with rc_max + skin <= min(L)/2 and n_max < 2^26 when skin > 0.
  * On failure writes a message to msg (if msg_len > 0) and returns
- * DCM_ERR_BOX or DCM_ERR_INVALID_ARG. */
+ * DCM_ERR_BOX, DCM_ERR_INVALID_ARG or DCM_ERR_CAPACITY. */
 int dcm_validate_params(const dcm_params* p, char* msg, int32_t msg_len);
 
 /* Grid shapes for a parameter set: cells3 = force cells per dimension (L/l),

@@ -65,6 +65,14 @@ def test_params_default_and_validate(lib):
     (dict(recompute_every=0), 1),
     (dict(precision=7), 1),
     (dict(n_max=-1), 1),
+    (dict(n_max=2 ** 31), 1),
+    (dict(box=(4000.5, 4000.5, 4000.5)), 2),    # each axis < 65536 cells, 2^31 or more in all
+    (dict(box=(99000.0, 12.0, 48.0)), 2),       # 66000 cells along x
+    (dict(min_component=-1), 1),
+    (dict(force_kernel=9), 1),
+    (dict(skin=-0.1), 1),
+    (dict(skin=0.5, rc_max=5.8), 2),             # rc_max + skin > L/2
+    (dict(skin=0.3, rc_max=5.5, n_max=2 ** 26), 5),  # list entries keep 26 index bits
 ])
 def test_params_rejected(lib, kw, code):
     D, p = _params(lib, **kw)
