@@ -35,6 +35,9 @@ METRIC = "DCM step particle-steps/s at N=16M"
 UNIT = "particle-steps/s"
 K_RECOMPUTE = 10
 DT = 0.005
+REST_BYTES = 197            # HBM bytes per particle and timestep of every stage but the forces:
+                            # binning + permutation 96, cell counts/scan 13, velocity Verlet 80,
+                            # interface/distances/cutoffs 8 (amortised over the cadence)
 LIST_SKIN = 0.5             # Verlet-list skin of the lists form (the fastest measured on the 16M slab)
 FLOP_PER_PAIR = 18          # FP32-pipe instructions of the pair arithmetic per accepted pair
 FP32_LANES_PER_SM = 128
@@ -349,6 +352,16 @@ def run_gb300(args):
             "traffic": recorded_traffic(args.workload), "avg_launch_ms": f_ms / max(f_cnt, 1),
             "pairs_per_launch": pairs, "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
     stage_ms = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
+    # step roofline: the force kernel at the FP32-pipe peak plus every other
+    # stage at the measured HBM bandwidth (REST_BYTES per particle per timestep)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    f_ideal = pairs * FLOP_PER_PAIR / (peak_tinstr * 1e12) * 1e3
+    r_ideal = n * REST_BYTES / (hbm * 1e9) * 1e3
+    t_meas = ms / max(args.steps * K_RECOMPUTE, 1)
+    step_roof = {"force_ideal_ms": f_ideal, "rest_ideal_ms": r_ideal, "ideal_ms_per_timestep": f_ideal + r_ideal,
+                 "measured_ms_per_timestep": t_meas, "frac": (f_ideal + r_ideal) / t_meas if t_meas > 0 else None,
+                 "basis": f"pairs x {FLOP_PER_PAIR} FP32-pipe instr at the peak above + {REST_BYTES} B/particle "
+                          f"at {hbm:g} GB/s (measured copy bandwidth)"}
 
     # ---------------- plain FP64 form on the same GPU (per-step launches)
     fp64 = None
@@ -456,10 +469,12 @@ def run_gb300(args):
     if rank == 0 and world == 1 and not args.skip_cpu:
         nthreads = os.cpu_count() or 1
         rate, n_s, _, box = oracle_rate(args.workload, 30.0, 10, 1, nthreads)
+        rate1, _, _, _ = oracle_rate(args.workload, 30.0, 3, 1, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                "sample": f"{n_s} particles: the {args.workload} recipe on a {box[0]:g}x{box[1]:g}x{box[2]:g} "
                          f"cross-section, 10 oracle timesteps incl. one cutoff recomputation (cell-list forces "
-                         f"threaded with dynamic(20), other stages single-threaded)"}
+                         f"threaded with dynamic(20), other stages single-threaded)",
+               "single_thread_value": rate1}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -471,7 +486,7 @@ def run_gb300(args):
                           "precision": "fp32 pair math, fp64 totals", "l2": f"inputs larger than L2 (positions {16 * n / 1e6:.0f} MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "stage_ms_per_step": stage_ms, "fp64_form": fp64, "lists_form": lists, "batched_form": batch, "device_status": status,
+               "stage_ms_per_step": stage_ms, "step_roofline": step_roof, "fp64_form": fp64, "lists_form": lists, "batched_form": batch, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}
         print(json.dumps(out), flush=True)
