@@ -122,8 +122,7 @@ def grid_dims(box, edge) -> np.ndarray:
 # Binning
 # --------------------------------------------------------------------------
 def bin_particles(pos, box, l):
-    """Counting sort by cell (Sections 2.1, 2.3), within a cell by x (ties in
-    input order).
+    """Stable counting sort by cell (Sections 2.1, 2.3).
 
     Returns (cell[N], count[ncell], start[ncell+1], perm[N]) as int32, with the
     cell of a particle c = cx + nx (cy + ny cz), cx = floor(x / l) exactly.

@@ -53,12 +53,9 @@ int64_t orc_cell_of(const double* p, const double* l, const int64_t* nc) {
   return cx + nc[0] * (cy + nc[1] * cz);
 }
 
-/* Counting sort of particles by cell, then each cell's particles by x (ties
- * kept in input order).  cell[i]: cell of input particle i; count[c];
- * start[c] = exclusive prefix sum (start[ncell] = n); perm[k]: input index of
- * the particle in sorted slot k.  Ordering a cell by x lets a neighbour walk
- * skip the part of a cell on the far side of a sphere (reading: the paper
- * leaves the order within a bin open). */
+/* Stable counting sort of particles by cell.  cell[i]: cell of input particle
+ * i; count[c]; start[c] = exclusive prefix sum (start[ncell] = n); perm[k]:
+ * input index of the particle in sorted slot k (ties kept in input order). */
 void orc_bin(int64_t n, const double* pos, const double* l, const int64_t* nc, int32_t* cell,
              int32_t* count, int32_t* start, int32_t* perm) {
   int64_t ncell = nc[0] * nc[1] * nc[2];
@@ -80,17 +77,6 @@ void orc_bin(int64_t n, const double* pos, const double* l, const int64_t* nc, i
     fill[c]++;
   }
   free(fill);
-  /* within each cell: insertion sort by (x, input index) */
-  for (int64_t c = 0; c < ncell; ++c)
-    for (int32_t k = start[c] + 1; k < start[c + 1]; ++k) {
-      int32_t v = perm[k];
-      int32_t m = k - 1;
-      while (m >= start[c] && (pos[3 * perm[m]] > pos[3 * v] || (pos[3 * perm[m]] == pos[3 * v] && perm[m] > v))) {
-        perm[m + 1] = perm[m];
-        --m;
-      }
-      perm[m + 1] = v;
-    }
 }
 
 /* ------------------------------------------------------------------------ */
