@@ -812,3 +812,37 @@ def test_verlet_list_overflow_falls_back_to_exact_lists(D):
     F = st.force.cpu().numpy()[:, :3]
     assert np.abs(F - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
     assert st.thermo[3].item() == ref.npairs
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_forces_on_cells_in_any_order(D, slab_1935, prec):
+    """dcm_forces takes any order of the particles inside a cell (callers may
+    bin with their own sort): with every cell shuffled the accepted pairs and
+    forces must match the oracle."""
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    real = real_of(D, P)
+    box = slab_1935.box
+    rc64 = O.assign_cutoffs(slab_1935.pos, O.Params(box=box))["rc"]
+    rc_in = rc64.astype(np.float32).astype(np.float64) if prec == "mixed" else rc64
+    cell, count, start, perm = O.bin_particles(slab_1935.pos, box, 1.5)
+    rng = np.random.default_rng(2)
+    perm = perm.copy()
+    for c in np.flatnonzero(count > 1):
+        seg = perm[start[c]:start[c + 1]]
+        perm[start[c]:start[c + 1]] = seg[rng.permutation(len(seg))]
+    ctx = make_ctx(D, box, slab_1935.n, P)
+    ps = pos4_of(D, slab_1935.pos[perm], None, P)
+    rcs = torch.from_numpy(rc_in[perm]).to(real).cuda()
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    D.dcm_forces(ctx, slab_1935.n, ps, rcs, torch.from_numpy(start).cuda(), F, tot)
+    torch.cuda.synchronize()
+    Fg = np.empty((slab_1935.n, 3))
+    Fg[perm] = F.cpu().numpy()[:, :3]
+    ref = O.forces_cells(slab_1935.pos, rc_in, box, 1.5)
+    if prec == "fp64":
+        assert np.abs(Fg - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+        assert int(tot[2].item()) == ref.npairs
+    else:
+        assert rms_rel(Fg, ref.F) <= F_RMS_TOL
+        assert abs(int(tot[2].item()) - ref.npairs) <= near_cutoff_pairs(slab_1935.pos, rc_in, box)
