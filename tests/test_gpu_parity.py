@@ -846,3 +846,37 @@ def test_forces_on_cells_in_any_order(D, slab_1935, prec):
     else:
         assert rms_rel(Fg, ref.F) <= F_RMS_TOL
         assert abs(int(tot[2].item()) - ref.npairs) <= near_cutoff_pairs(slab_1935.pos, rc_in, box)
+
+
+@pytest.mark.parametrize("case", ["single_phase", "uniform_cutoff"])
+def test_degenerate_pipelines(D, slab_1935, case):
+    """The method's degenerate cases through dcm_step_init: a single-phase
+    system has no interface, so every particle keeps rc_max; rc_min = rc_max
+    is plain cutoff LJ.  Cutoffs and forces against the oracle."""
+    if case == "single_phase":
+        # 9 boxes per axis and a 9-wide box sum: every gray value is the total
+        # count, so the 2-means threshold finds one phase and no interface
+        rng = np.random.default_rng(8)
+        box = (13.5, 13.5, 13.5)
+        pos = rng.uniform(0, 13.5, size=(2000, 3)).astype(np.float32)
+        vel = np.zeros((2000, 3), np.float32)
+        kw, okw = dict(smooth_w=4), dict(smooth_w=4)
+    else:
+        box, pos, vel = slab_1935.box, slab_1935.pos, slab_1935.vel
+        kw, okw = dict(rc_min=4.5, rc_max=4.5), dict(rc_min=4.5, rc_max=4.5)
+    n = len(pos)
+    ctx = make_ctx(D, box, n, D.DCM_PREC_FP64, **kw)
+    st = D.State(ctx, pos4_of(D, pos, None, D.DCM_PREC_FP64), D.to_real4(torch.from_numpy(vel), None, torch.float64))
+    D.dcm_step_init(ctx, st)
+    p_, v_, rc, ids = st.current()
+    p_ = p_.cpu().numpy()[:, :3]
+    rcn = rc.cpu().numpy()
+    a = O.assign_cutoffs(p_, O.Params(box=box, **okw))
+    assert np.abs(rcn - a["rc"]).max() <= 1e-12
+    assert (rcn == (6.0 if case == "single_phase" else 4.5)).all()
+    if case == "single_phase":
+        assert a["iface"].sum() == 0
+    ref = O.forces_cells(p_, rcn, box, 1.5)
+    F = st.force.cpu().numpy()[:, :3]
+    assert np.abs(F - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+    assert st.thermo[3].item() == ref.npairs
