@@ -210,3 +210,59 @@ def test_autograd_function_and_finite_differences(small2):
         if checked == 6:
             break
     assert checked == 6
+
+
+@pytest.mark.gpu
+def test_adjoint_full_two_type_workload():
+    """The 260,522-particle two-type workload: the mixed-precision adjoint
+    against the FP64 one (itself checked against the oracle above), and the
+    FP64 position gradient against central differences of the GPU FP64
+    forward at a few particles."""
+    import paper_1701_05242_gb300.dcm as D
+    slab = synth.make_slab(synth.named("slab_256k_2types"))
+    rng = np.random.default_rng(5)
+    rc = rng.choice([3.0, 4.0, 5.0, 6.0], slab.n)
+    out = {}
+    for prec in (D.DCM_PREC_FP64, D.DCM_PREC_MIXED):
+        ctx, ps, rcs, start, perm, rc_in = gpu_setup(D, slab, rc, prec)
+        F = torch.empty_like(ps)
+        D.dcm_forces(ctx, slab.n, ps, rcs, start, F)
+        A = torch.zeros_like(ps)
+        A[:, :3] = 2 * F[:, :3]
+        G = torch.empty_like(ps)
+        dpar = torch.zeros(4, dtype=torch.float64, device="cuda")
+        D.dcm_forces_backward(ctx, slab.n, ps, rcs, start, A, 1.0, G, dpar)
+        torch.cuda.synchronize()
+        out[prec] = (G.cpu().numpy().astype(np.float64)[:, :3], dpar.cpu().numpy(), perm, ctx, ps, rcs, start)
+    G64, d64, perm, ctx, ps, rcs, start = out[D.DCM_PREC_FP64]
+    G32, d32 = out[D.DCM_PREC_MIXED][0], out[D.DCM_PREC_MIXED][1]
+    assert np.array_equal(out[D.DCM_PREC_MIXED][2], perm)
+    assert np.sqrt(((G32 - G64) ** 2).sum() / (G64 ** 2).sum()) <= 1e-4
+    assert np.allclose(d32, d64, rtol=1e-4)
+
+    def L_at(p4):
+        F = torch.empty_like(p4)
+        tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+        D.dcm_forces(ctx, slab.n, p4, rcs, start, F, tot)
+        return float((F[:, :3] ** 2).sum() + tot[0])
+    h = 1e-4
+    spos = slab.pos[perm].astype(np.float64)
+    rch = rcs.cpu().numpy()
+    checked = 0
+    for k in rng.permutation(slab.n)[:200]:
+        if crosses(spos, k, rch, slab.box, h):
+            continue
+        if (np.floor((spos[k] + h) / 1.5) != np.floor((spos[k] - h) / 1.5)).any():
+            continue
+        L0 = L_at(ps)
+        for d in range(3):
+            pp, pm = ps.clone(), ps.clone()
+            pp[k, d] += h
+            pm[k, d] -= h
+            fd = (L_at(pp) - L_at(pm)) / (2 * h)
+            floor = 20 * abs(L0) * 2.2e-16 / h
+            assert G64[k, d] == pytest.approx(fd, rel=2e-4, abs=floor)
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3
