@@ -880,3 +880,34 @@ def test_degenerate_pipelines(D, slab_1935, case):
     F = st.force.cpu().numpy()[:, :3]
     assert np.abs(F - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
     assert st.thermo[3].item() == ref.npairs
+
+
+def test_scale_1m_mixed_against_fp64_run():
+    """The 990,904-particle slab for 1,000 timesteps (cutoffs every 10) in
+    the mixed form and in the FP64 form on the GPU.  The trajectories part
+    ways (the dynamics is chaotic) but both integrate the same system: total
+    energy, kinetic energy and the number of accepted pairs must agree to the
+    level of the system's own statistical fluctuations."""
+    import paper_1701_05242_gb300.dcm as D
+    slab = synth.make_slab(synth.named("slab_1m"))
+    th = {}
+    for prec in (D.DCM_PREC_MIXED, D.DCM_PREC_FP64):
+        ctx = make_ctx(D, slab.box, slab.n, prec, recompute_every=10)
+        real = real_of(D, prec)
+        st = D.State(ctx, pos4_of(D, slab.pos, None, prec), D.to_real4(torch.from_numpy(slab.vel), None, real))
+        D.dcm_step_init(ctx, st)
+        e0 = st.thermo.cpu().numpy().copy()
+        for _ in range(10):
+            D.dcm_step(ctx, st, 0.005, 100)
+        assert D.dcm_status(ctx) == D.DCM_OK
+        th[prec] = (e0, st.thermo.cpu().numpy().copy())
+        del st, ctx
+        torch.cuda.empty_cache()
+    (a0, a1), (b0, b1) = th[D.DCM_PREC_MIXED], th[D.DCM_PREC_FP64]
+    assert a0[0] == pytest.approx(b0[0], rel=1e-7)                 # same start
+    # measured: total energy within 5e-5 at every 100 steps, kinetic energy
+    # and pair count within 9e-4 (the fluctuations of a million particles)
+    tot_a, tot_b = a1[0] + a1[2], b1[0] + b1[2]
+    assert tot_a == pytest.approx(tot_b, rel=1e-4)
+    assert a1[2] == pytest.approx(b1[2], rel=2e-3)                  # kinetic energy
+    assert a1[3] == pytest.approx(b1[3], rel=2e-3)                  # accepted pairs
