@@ -38,7 +38,10 @@
  *   "real4" below means float4 or double4 accordingly, "real" float or double.
  * - Positions are real4 {x, y, z, w}: w holds the particle type as a number
  *   (0, 1, ...; 0 for one-type systems).  Coordinates must lie in [0, L);
- *   values outside are clamped into the boundary cells by the binning.
+ *   finite values outside are clamped into the boundary cells by the binning
+ *   and take part in no pair farther than their cutoff (a NaN or infinite
+ *   coordinate turns the forces of its cell neighbours into NaN).  No value
+ *   makes a kernel read or write outside its arrays.
  * - Forces are real4 {fx, fy, fz, e_i}: e_i is the particle's energy (half of
  *   every accepted pair's U).
  * - Cell and box indices are linear: c = cx + nx * (cy + ny * cz).
@@ -66,15 +69,16 @@ enum dcm_status_code {
 };
 
 /* Cell-list force kernels (all walk the same culled cell rows and accept the
- * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2,
- * 3 and 4 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
+ * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2
+ * to 5 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
  * ntypes = 1) and fall back to kernel 1 otherwise. */
 enum {
   DCM_FORCE_AUTO = 0,        /* kernel 3 where it applies, else kernel 1 */
   DCM_FORCE_THREAD = 1,      /* one thread per particle i, one candidate per instruction */
   DCM_FORCE_TWO_PHASE = 2,   /* per-lane shared-memory buffers of accepted pairs */
   DCM_FORCE_PACKED = 3,      /* one thread per particle i, two candidates per FP32x2 instruction */
-  DCM_FORCE_TILE = 4         /* as 3, with each warp's row windows staged in shared memory */
+  DCM_FORCE_TILE = 4,        /* as 3, with each warp's row windows staged in shared memory */
+  DCM_FORCE_FLAT = 5         /* as 3, each lane running its row segments back to back in one loop */
 };
 
 enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
         int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
         ulo = max(ulo, cx - H);
         uhi = min(uhi, cx + H);
+        if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
         const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
         if (ulo < 0) {
           int a1 = min(uhi, -1);

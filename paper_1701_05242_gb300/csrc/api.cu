@@ -193,7 +193,7 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "iter_max must be in 1..100000");
   if (p->recompute_every < 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "recompute_every must be >= 1");
   if (p->min_component < 0) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "min_component must be >= 0");
-  if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_TILE)
+  if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_FLAT)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "precision must be DCM_PREC_FP64 or DCM_PREC_MIXED");

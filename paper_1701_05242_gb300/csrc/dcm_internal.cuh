@@ -42,10 +42,12 @@ __device__ __forceinline__ dvec4 ldg4(const dvec4* p) {
 
 // Exact floor(x / l) for an edge l with a short mantissa (k * l exact), clamped
 // to [0, n-1].  One correction step suffices because x * (1/l) is within one
-// unit of the true quotient.
+// unit of the true quotient.  The quotient is first clamped to [-1, n] (NaN
+// to -1), so that coordinates far outside the box stay clear of integer
+// overflow.
 template <typename R>
 __device__ __forceinline__ int cell_coord(R x, R l, R inv_l, int n) {
-  R q = floor(x * inv_l);
+  R q = fmin(fmax(floor(x * inv_l), (R)-1), (R)n);
   int k = (int)q;
   if ((R)k * l > x)
     --k;

@@ -188,6 +188,126 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_forces_tile(int64_t n, cons
 }
 
 // ----------------------------------------------------------------------------
+// Flattened kernel (one type, FP32): the same culled walk, split in two.  The
+// warp first walks its rows in lockstep (the rows are the same for all lanes
+// up to the cutoff), and each lane only records its non-empty in-grid
+// segments [j0, j1) in its own column of a shared-memory table.  The lanes
+// then run one packed pair loop each over the concatenation of their
+// segments, all for the same number of iterations (the largest lane's), so a
+// lane whose window in one row is short goes straight on to its next row
+// instead of idling until the longest window of that row ends.  Segments that
+// reach a periodic image are evaluated afterwards by the lanes that have them,
+// with the exact image shifts of the row walk.  When some lane's column could
+// overflow, the table is drained before the walk goes on.
+// ----------------------------------------------------------------------------
+constexpr int kFlatCap = 24;  // table entries per lane
+
+__global__ void __launch_bounds__(kForceBlock) k_forces_flat(int64_t n, const float4* __restrict__ pos,
+                                                             const float* __restrict__ rc,
+                                                             const int32_t* __restrict__ start,
+                                                             ForceArgs<float> a, float4* __restrict__ force,
+                                                             double* __restrict__ part, int64_t nwarp) {
+  __shared__ int2 table[kForceBlock / 32][kFlatCap][32];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int2 (*tab)[32] = table[threadIdx.x >> 5];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  const Grid<float>& g = a.g;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const float l = g.edge, il = g.inv_edge;
+  const float4 pi = valid ? __ldg(pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float rci = clamp_cutoff<float>(valid ? __ldg(rc + i) : 0.f, a.rc_max);
+  const float rc2 = rci * rci, rc2s = rc2 * 1.000004f;
+  const int cx = cell_coord<float>(pi.x, l, il, nx), cy = cell_coord<float>(pi.y, l, il, ny),
+            cz = cell_coord<float>(pi.z, l, il, nz);
+  const int H = valid ? (int)ceilf(rci * il) : -1;
+  int Hw = H;
+  for (int o = 16; o > 0; o >>= 1) Hw = max(Hw, __shfl_xor_sync(FULL, Hw, o));
+  const int self = (int)i;
+  Acc2 c2;
+  int cnt = 0, iters = 0;  // table entries, packed iterations they need
+  bool img = false;        // some segment reaches a periodic image
+  const int side = 2 * Hw + 1, nrows = side * side;
+  int dz = -Hw, dy = -Hw;
+  for (int r = 0; r <= nrows; ++r) {
+    if (r == nrows || __any_sync(FULL, cnt > kFlatCap - 2)) {
+      // drain: every lane runs the warp's largest iteration count
+      int T = iters;
+      for (int o = 16; o > 0; o >>= 1) T = max(T, __shfl_xor_sync(FULL, T, o));
+      int k = 0, j = 0, je = 0;
+      int2 nxt = cnt > 0 ? tab[0][lane] : make_int2(0, 0);
+      for (int it = 0; it < T; ++it) {
+        if (j >= je && k < cnt) {
+          j = nxt.x;
+          je = nxt.y;
+          if (++k < cnt) nxt = tab[k][lane];
+        }
+        const bool v0 = j < je, v1 = j + 1 < je;
+        const float4 p0 = __ldg(pos + (v0 ? j : 0)), p1 = __ldg(pos + (v1 ? j + 1 : 0));
+        pair_x2<false>(p0, p1, v0, v1, pi.x, pi.y, pi.z, 0.f, 0.f, 0.f, rc2, c2);
+        j += 2;
+      }
+      cnt = 0;
+      iters = 0;
+      if (r == nrows) break;
+    }
+    const int uz = cz + dz, uy = cy + dy;
+    const float gz = uz > cz ? (float)uz * l - pi.z : (uz < cz ? pi.z - (float)(uz + 1) * l : 0.f);
+    const float gy = uy > cy ? (float)uy * l - pi.y : (uy < cy ? pi.y - (float)(uy + 1) * l : 0.f);
+    const float gyz2 = gz * gz + gy * gy;
+    if (dz >= -H && dz <= H && dy >= -H && dy <= H && gyz2 < rc2s) {
+      const float wx = window_half_width(rc2s - gyz2);
+      const int ulo = max(ufloor<float>((pi.x - wx) * il - 5e-4f), cx - H);
+      const int uhi = min(ufloor<float>((pi.x + wx) * il + 5e-4f), cx + H);
+      const bool img_row = uy < 0 || uy >= ny || uz < 0 || uz >= nz;
+      img |= img_row || ulo < 0 || uhi >= nx;
+      const int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
+      if (!img_row && a0 <= a1) {
+        const int64_t row = (int64_t)nx * (uy + (int64_t)ny * uz);
+        const int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
+        auto push = [&](int s0, int s1) {
+          if (s0 < s1) {
+            tab[cnt][lane] = make_int2(s0, s1);
+            ++cnt;
+            iters += (s1 - s0 + 1) >> 1;
+          }
+        };
+        if (dz == 0 && dy == 0) {  // the particle's own row: cut it out
+          push(j0, min(j1, self));
+          push(max(j0, self + 1), j1);
+        } else {
+          push(j0, j1);
+        }
+      }
+    }
+    if (++dy > Hw) {
+      dy = -Hw;
+      ++dz;
+    }
+  }
+  if (img) {
+    Acc<float> c;
+    const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+    walk_rows<float, false, true, Walk::kImagesOnly>(pos, start, g, a, self, pi, rci, 0, zero, c, c2);
+  }
+  float e_out = 0.f, w_out = 0.f;
+  int np = c2.np;
+  if (valid) {
+    float ush = 0.f;
+    if (a.shift && rc2 > 0.f) {
+      const float s2 = 1.f / rc2, s6 = s2 * s2 * s2;
+      ush = 4.f * s6 * (s6 - 1.f);
+    }
+    e_out = 2.f * (c2.en.x + c2.en.y) - 0.5f * (float)np * ush;
+    w_out = 12.f * (c2.vir.x + c2.vir.y);
+    force[i] = make_float4(-24.f * (c2.fx.x + c2.fx.y), -24.f * (c2.fy.x + c2.fy.y), -24.f * (c2.fz.x + c2.fz.y),
+                           e_out);
+  }
+  if (part) warp_partials3<float>(e_out, w_out, np, part, nwarp);
+}
+
+// ----------------------------------------------------------------------------
 // Two-phase force kernel (one type, FP32, eps = sigma = 1): every lane first
 // filters its candidates row by row and appends the accepted ones (r_ij and
 // r^2) to its own shared-memory buffer; before a row whose window could
@@ -366,7 +486,7 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
   if (part) warp_partials3<float>(e_out, w_out, c.np, part, nwarp);
 }
 
-// Kernels 2, 3 and 4 serve one-type mixed-precision runs with eps = sigma = 1.
+// Kernels 2 to 5 serve one-type mixed-precision runs with eps = sigma = 1.
 int resolve_force_kernel(const dcm_ctx* ctx) {
   int k = force_kernel_choice(ctx->p);
   if (k == DCM_FORCE_THREAD) return k;
@@ -403,7 +523,11 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   if constexpr (sizeof(R) == 4) {
     const ForceArgs<float>& af = a;
     const int kind = resolve_force_kernel(ctx);
-    if (kind == DCM_FORCE_TILE) {
+    if (kind == DCM_FORCE_FLAT) {
+      DCM_LAUNCH(ctx, k_forces_flat, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part,
+                 nwarp);
+      done = true;
+    } else if (kind == DCM_FORCE_TILE) {
       static_assert(32 * kTileWarps == kForceBlock, "partials layout assumes equal blocks");
       DCM_LAUNCH(ctx, k_forces_tile, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part,
                  nwarp);

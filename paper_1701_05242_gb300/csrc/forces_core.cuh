@@ -127,44 +127,57 @@ struct Acc2 {
   int np = 0;
 };
 
+// One packed step on the differences d = r_j - r_i of two candidates (m0,
+// m1: whether each slot holds a real candidate).
+__device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, Acc2& c) {
+  const float2 two = make_float2(2.f, 2.f), m1f = make_float2(-1.f, -1.f);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  float y0, y1;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+  const float2 e = make_float2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
+  float2 y = make_float2(y0, y1);
+  y = __ffma2_rn(y, e, y);
+  const bool a0 = m0 && r2.x < rc2, a1 = m1 && r2.y < rc2;
+  y = make_float2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
+  const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+  const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1f));  // r.F / 24
+  const float2 q = __fmul2_rn(pv, y);
+  c.fx = __ffma2_rn(q, dx, c.fx);
+  c.fy = __ffma2_rn(q, dy, c.fy);
+  c.fz = __ffma2_rn(q, dz, c.fz);
+  c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1f), c.en);
+  c.vir = __fadd2_rn(c.vir, pv);
+  c.np += (int)a0 + (int)a1;
+}
+
+// One packed step: candidates p0 and p1 against particle i.
+template <bool SJ>
+__device__ __forceinline__ void pair_x2(const float4& p0, const float4& p1, bool m0, bool m1, float xi, float yi,
+                                        float zi, float shx, float shy, float shz, float rc2, Acc2& c) {
+  float2 dx, dy, dz;
+  if (SJ) {
+    dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
+    dy = make_float2((p0.y + shy) - yi, (p1.y + shy) - yi);
+    dz = make_float2((p0.z + shz) - zi, (p1.z + shz) - zi);
+  } else {
+    dx = make_float2(p0.x - xi, p1.x - xi);
+    dy = make_float2(p0.y - yi, p1.y - yi);
+    dz = make_float2(p0.z - zi, p1.z - zi);
+  }
+  pair_x2_d(dx, dy, dz, m0, m1, rc2, c);
+}
+
 // STAGED: pos points into a shared-memory tile (plain loads) instead of
 // global memory (read-only cached loads).
 template <bool SJ, bool STAGED = false>
 __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                               float zi, float shx, float shy, float shz, float rc2, Acc2& c) {
-  const float2 two = make_float2(2.f, 2.f), m1 = make_float2(-1.f, -1.f);
   for (int j = lo; j < hi; j += 2) {
     const bool has1 = j + 1 < hi;
     const int j1 = has1 ? j + 1 : j;
     const float4 p0 = STAGED ? pos[j] : __ldg(pos + j), p1 = STAGED ? pos[j1] : __ldg(pos + j1);
-    float2 dx, dy, dz;
-    if (SJ) {
-      dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
-      dy = make_float2((p0.y + shy) - yi, (p1.y + shy) - yi);
-      dz = make_float2((p0.z + shz) - zi, (p1.z + shz) - zi);
-    } else {
-      dx = make_float2(p0.x - xi, p1.x - xi);
-      dy = make_float2(p0.y - yi, p1.y - yi);
-      dz = make_float2(p0.z - zi, p1.z - zi);
-    }
-    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-    float y0, y1;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
-    const float2 e = make_float2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
-    float2 y = make_float2(y0, y1);
-    y = __ffma2_rn(y, e, y);
-    const bool a0 = r2.x < rc2, a1 = has1 && r2.y < rc2;
-    y = make_float2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
-    const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
-    const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1));  // r.F / 24
-    const float2 q = __fmul2_rn(pv, y);
-    c.fx = __ffma2_rn(q, dx, c.fx);
-    c.fy = __ffma2_rn(q, dy, c.fy);
-    c.fz = __ffma2_rn(q, dz, c.fz);
-    c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1), c.en);
-    c.vir = __fadd2_rn(c.vir, pv);
-    c.np += (int)a0 + (int)a1;
+    pair_x2<SJ>(p0, p1, true, has1, xi, yi, zi, shx, shy, shz, rc2, c);
   }
 }
 
@@ -181,37 +194,24 @@ __device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ p
   }
 }
 
-// Forces, energy and virial of particle `self` (position pi, cutoff rc_in)
-// over the cell grid g whose cell starts are start[0 .. ncell] (positions
-// pos, sorted by cell).  Returns the force and writes e_i, w_i, pairs.
-template <typename R, bool TYPED, bool X2 = false>
-__device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
-                                                        const int32_t* __restrict__ start, const Grid<R>& g,
-                                                        const ForceArgs<R>& a, int self,
-                                                        const typename RT<R>::R4& pi, R rc_in, R& e_out, R& w_out,
-                                                        int& np_out) {
-  static_assert(!X2 || (sizeof(R) == 4 && !TYPED), "the packed loop serves one-type FP32 only");
-  Acc<R> c;
-  Acc2 c2;
+// Which segments of the row walk are evaluated: all of them, or only those
+// that reach a periodic image (a row outside the grid in y or z, or the part
+// of a window beyond either x end).
+enum class Walk { kAll, kImagesOnly };
+
+// The culled cell-row walk of particle `self` (position pi, clamped cutoff
+// rci) over the cell grid g whose cell starts are start[0 .. ncell] (positions
+// pos sorted by cell), accumulating into c (scalar loop) or c2 (packed).
+template <typename R, bool TYPED, bool X2, Walk MODE = Walk::kAll>
+__device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__ pos,
+                                          const int32_t* __restrict__ start, const Grid<R>& g,
+                                          const ForceArgs<R>& a, int self, const typename RT<R>::R4& pi, R rci,
+                                          int ti, const R* ushift, Acc<R>& c, Acc2& c2) {
+  constexpr bool kImg = MODE == Walk::kImagesOnly;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const R l = g.edge, il = g.inv_edge;
-  // cutoffs outside [0, rc_max] (or NaN) are clamped: the stencil then never
-  // reaches past one periodic image, which keeps every cell index in range
-  R rci = rc_in;
-  if (!(rci <= a.rc_max)) rci = a.rc_max;
-  if (!(rci > (R)0)) rci = (R)0;
   const R rc2 = rci * rci;
   const R rc2s = rc2 * (R)1.000004;  // culling slack; the pair test is exact
-  const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
-  R ushift[4] = {0, 0, 0, 0};
-  if (a.shift && rc2 > (R)0) {  // no pairs at rc = 0: no shift either
-    for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
-      int tp = ti * a.ntypes + t;
-      R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
-      R s6 = s2 * s2 * s2;
-      ushift[t] = (TYPED ? a.eps4[tp] : (R)4) * s6 * (s6 - (R)1);
-    }
-  }
   const int cx = cell_coord<R>(pi.x, l, il, nx);
   const int cy = cell_coord<R>(pi.y, l, il, ny);
   const int cz = cell_coord<R>(pi.z, l, il, nz);
@@ -235,6 +235,9 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
       ulo = max(ulo, cx - H);
       uhi = min(uhi, cx + H);
+      // empty only for a coordinate outside [0, L) (its cell is clamped into
+      // the grid, its window is not): skipping keeps every index in range
+      if (ulo > uhi) continue;
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
       // segment u < 0: image -L (shift j)
       if (ulo < 0) {
@@ -243,11 +246,12 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
         segment<R, true, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2);
       }
       // segment 0 <= u < nx: no x shift; the particle itself is skipped
-      {
+      const bool img_row = uy < 0 || uy >= ny || uz < 0 || uz >= nz;
+      if (!kImg || img_row) {
         int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
         if (a0 <= a1) {
           int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
-          if (uy == cy && uz == cz) {  // the particle's own row: cut it out
+          if (!kImg && uy == cy && uz == cz) {  // the particle's own row: cut it out
             segment<R, false, TYPED, X2>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2);
             segment<R, false, TYPED, X2>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
                                          c2);
@@ -266,6 +270,43 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       }
     }
   }
+}
+
+// Cutoffs outside [0, rc_max] (or NaN) are clamped: the stencil then never
+// reaches past one periodic image, which keeps every cell index in range.
+template <typename R>
+__device__ __forceinline__ R clamp_cutoff(R rc_in, R rc_max) {
+  R rci = rc_in;
+  if (!(rci <= rc_max)) rci = rc_max;
+  if (!(rci > (R)0)) rci = (R)0;
+  return rci;
+}
+
+// Forces, energy and virial of particle `self` (position pi, cutoff rc_in)
+// over the cell grid g whose cell starts are start[0 .. ncell] (positions
+// pos, sorted by cell).  Returns the force and writes e_i, w_i, pairs.
+template <typename R, bool TYPED, bool X2 = false>
+__device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
+                                                        const int32_t* __restrict__ start, const Grid<R>& g,
+                                                        const ForceArgs<R>& a, int self,
+                                                        const typename RT<R>::R4& pi, R rc_in, R& e_out, R& w_out,
+                                                        int& np_out) {
+  static_assert(!X2 || (sizeof(R) == 4 && !TYPED), "the packed loop serves one-type FP32 only");
+  Acc<R> c;
+  Acc2 c2;
+  const R rci = clamp_cutoff<R>(rc_in, a.rc_max);
+  const R rc2 = rci * rci;
+  const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
+  R ushift[4] = {0, 0, 0, 0};
+  if (a.shift && rc2 > (R)0) {  // no pairs at rc = 0: no shift either
+    for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
+      int tp = ti * a.ntypes + t;
+      R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
+      R s6 = s2 * s2 * s2;
+      ushift[t] = (TYPED ? a.eps4[tp] : (R)4) * s6 * (s6 - (R)1);
+    }
+  }
+  walk_rows<R, TYPED, X2>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2);
   if constexpr (X2) {  // fold the two packed lanes (and the sign of d) into c
     c.fx = -(c2.fx.x + c2.fx.y);
     c.fy = -(c2.fy.x + c2.fy.y);

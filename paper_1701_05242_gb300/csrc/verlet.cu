@@ -63,6 +63,7 @@ __device__ __forceinline__ void walk_segments(const int32_t* __restrict__ start,
       R wx = window_half_width(rl2s - gyz2);
       int ulo = max(ufloor<R>((pi.x - wx) * il - (R)5e-4), cx - H);
       int uhi = min(ufloor<R>((pi.x + wx) * il + (R)5e-4), cx + H);
+      if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
       const uint32_t yzc = (yc << 2) | (zc << 4);
       if (ulo < 0) {  // image -L in x: shift j

@@ -33,6 +33,7 @@ DCM_FORCE_THREAD = 1
 DCM_FORCE_TWO_PHASE = 2
 DCM_FORCE_PACKED = 3
 DCM_FORCE_TILE = 4
+DCM_FORCE_FLAT = 5
 
 _ERRNAMES = {1: "INVALID_ARG", 2: "BOX", 3: "CUDA", 4: "NOT_CONVERGED", 5: "CAPACITY", 6: "NOMEM"}
 
@@ -334,7 +335,8 @@ def dcm_force_kernel(ctx: Context) -> int:
     return k.value
 
 
-FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_TWO_PHASE: "k_forces2", DCM_FORCE_PACKED: "k_forces_x2", DCM_FORCE_TILE: "k_forces_tile"}
+FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_TWO_PHASE: "k_forces2", DCM_FORCE_PACKED: "k_forces_x2", DCM_FORCE_TILE: "k_forces_tile",
+                      DCM_FORCE_FLAT: "k_forces_flat"}
 
 
 # ---------------------------------------------------------------- batched form

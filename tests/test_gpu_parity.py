@@ -319,7 +319,7 @@ def test_forces_two_types(D, prec):
         assert int(tot[2]) == ref.npairs
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("l", [1.5, 1.0])
 def test_forces_kernel_variants(D, slab_1935, kernel, l):
     """Every cell-list force kernel against the oracle (mixed, one type)."""
@@ -337,13 +337,112 @@ def test_forces_kernel_variants(D, slab_1935, kernel, l):
     assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
 
 
-@pytest.mark.parametrize("k", [-1, 5])
+@pytest.mark.parametrize("l", [1.5, 1.0])
+def test_flat_kernel_matches_packed_away_from_images(D, l):
+    """Kernel 5 evaluates each particle's in-grid row segments in the order
+    and pairing of kernel 3's row walk, only concatenated into one loop and
+    with the periodic-image segments deferred; so particles whose stencil
+    reaches no image get bit-identical forces and energies, every particle
+    accepts the same pairs, and the rest agree to rounding.  A 30^3 box at
+    rho = 0.8 with cutoffs spread over [3, 6] (several table drains per warp
+    at l = 1.0, where a cutoff of 6 visits up to 169 rows)."""
+    rng = np.random.default_rng(31)
+    L = 30.0
+    n = 21601  # a ragged last warp
+    pts = rng.uniform(0, L, size=(n, 3)).astype(np.float32)
+    rcv = rng.uniform(3.0, 6.0, n).astype(np.float32)
+    out = {}
+    for k in (3, 5):
+        ctx = make_ctx(D, (L, L, L), n, l=l, force_kernel=k)
+        assert D.dcm_force_kernel(ctx) == k
+        cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, pts, None, D.DCM_PREC_MIXED))
+        F = torch.empty_like(ps)
+        tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+        D.dcm_forces(ctx, n, ps, torch.from_numpy(rcv[perm]).cuda(), torch.from_numpy(start).cuda(), F, tot)
+        torch.cuda.synchronize()
+        out[k] = (F.cpu().numpy(), tot.cpu().numpy(), perm, ps.cpu().numpy())
+    (F3, t3, perm, ps), (F5, t5, _, _) = out[3], out[5]
+    nc = int(round(L / l))
+    c = np.clip(np.floor(ps[:, :3].astype(np.float64) / l).astype(int), 0, nc - 1)
+    H = np.ceil(rcv[perm].astype(np.float64) / l).astype(int) + 1  # one cell of margin
+    inner = ((c - H[:, None] >= 0) & (c + H[:, None] < nc)).all(axis=1)
+    assert 1000 < inner.sum() < n
+    assert np.array_equal(F5[inner], F3[inner])
+    assert t5[2] == t3[2]
+    assert rms_rel(F5[:, :3].astype(np.float64), F3[:, :3].astype(np.float64)) <= 4e-6
+    assert abs(t5[0] - t3[0]) <= 1e-6 * abs(t3[0]) and abs(t5[1] - t3[1]) <= 1e-6 * abs(t3[1])
+
+
+FAR = np.array([[1.0e4, 5.0, 5.0], [-1.0e4, 6.0, 20.0], [3.0, 5.0e3, 30.0], [7.0, -3.0e3, 10.0],
+                [2.0, 2.0, 1.0e5], [4.0, 9.0, -2.0e4], [1.0e30, 1.0, 1.0], [-1.0e30, -1.0e30, 40.0]], np.float32)
+
+
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
+def test_coordinates_outside_the_box(D, slab_1935, kernel):
+    """Finite coordinates far outside [0, L) are binned into the boundary
+    cells: every kernel keeps its indices in range, the far particles accept
+    no pair, and the others get the forces of the system without them."""
+    n0 = slab_1935.n
+    pos = np.concatenate([slab_1935.pos.astype(np.float32), FAR])
+    n = len(pos)
+    rc64 = O.assign_cutoffs(slab_1935.pos, O.Params(box=slab_1935.box))["rc"]
+    rc = np.concatenate([rc64, np.full(len(FAR), 6.0)]).astype(np.float32)
+    ctx = make_ctx(D, slab_1935.box, n, force_kernel=kernel)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, pos, None, D.DCM_PREC_MIXED))
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    rcs = torch.from_numpy(rc[perm]).cuda()
+    starts = torch.from_numpy(start).cuda()
+    D.dcm_forces(ctx, n, ps, rcs, starts, F, tot)
+    torch.cuda.synchronize()
+    Fg = np.empty((n, 4))
+    Fg[perm] = F.cpu().numpy()
+    rc_in = rc[:n0].astype(np.float64)
+    ref = O.forces_cells(slab_1935.pos, rc_in, slab_1935.box, 1.5)
+    assert np.all(Fg[n0:] == 0.0)
+    assert rms_rel(Fg[:n0, :3], ref.F) <= F_RMS_TOL
+    assert abs(int(tot[2].item()) - ref.npairs) <= near_cutoff_pairs(slab_1935.pos, rc_in, slab_1935.box)
+    if kernel == 1:  # the adjoint walks the same rows
+        A = torch.zeros_like(ps)
+        A[:, :3] = 2 * F[:, :3]
+        G = torch.empty_like(ps)
+        dpar = torch.zeros(4, dtype=torch.float64, device="cuda")
+        D.dcm_forces_backward(ctx, n, ps, rcs, starts, A, 1.0, G, dpar)
+        torch.cuda.synchronize()
+        assert np.isfinite(G.cpu().numpy()).all() and np.isfinite(dpar.cpu().numpy()).all()
+    assert D.dcm_status(ctx) == D.DCM_OK
+
+
+@pytest.mark.parametrize("skin", [0.0, 0.4])
+def test_step_with_coordinates_outside_the_box(D, slab_1935, skin):
+    """Steps (cell path, and Verlet lists whose build walks the same rows)
+    with particles far outside the box: no error, finite thermodynamics, and
+    the far particles feel no force."""
+    pos = np.concatenate([slab_1935.pos.astype(np.float32), FAR])
+    vel = np.concatenate([slab_1935.vel.astype(np.float32), np.zeros_like(FAR)])
+    n = len(pos)
+    ctx = make_ctx(D, slab_1935.box, n, recompute_every=5, skin=skin, rc_max=5.5)
+    st = D.State(ctx, pos4_of(D, pos, None, D.DCM_PREC_MIXED),
+                 D.to_real4(torch.from_numpy(vel), None, torch.float32))
+    D.dcm_step_init(ctx, st)
+    for _ in range(12):
+        D.dcm_step(ctx, st, 0.005, 1)
+    th = st.thermo.cpu().numpy()
+    assert D.dcm_status(ctx) == D.DCM_OK
+    assert np.isfinite(th).all()
+    p, v, _, ids = st.current()
+    far = ids.cpu().numpy() >= slab_1935.n
+    assert far.sum() == len(FAR)
+    assert np.all(v.cpu().numpy()[far, :3] == 0.0)
+
+
+@pytest.mark.parametrize("k", [-1, 6])
 def test_forces_kernel_rejects_unknown(D, k):
     with pytest.raises(D.DcmError):
         make_ctx(D, (12.0, 12.0, 48.0), 10, force_kernel=k)
 
 
-@pytest.mark.parametrize("kernel", [1, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 3, 4, 5])
 def test_forces_tiny_box_and_ragged_kernels(D, kernel):
     """rc_max = L/2 (rows reaching both periodic images), 97 particles,
     some cutoffs 0 (no pairs, no shift)."""
@@ -581,7 +680,7 @@ def test_full_size_sampled(D, slab_16m):
     spos = slab.pos[operm].astype(np.float64)
     Fo, eo, wo, po = O.forces_subset(spos, rcn, slab.box, 1.5, idx, nthreads=8)
     totals = []
-    for kernel in (0, 1, 2, 3, 4):  # every cell-list kernel on the same sorted input
+    for kernel in (0, 1, 2, 3, 4, 5):  # every cell-list kernel on the same sorted input
         kctx = make_ctx(D, slab.box, n, force_kernel=kernel)
         F = torch.empty_like(ps)
         tot = torch.zeros(3, dtype=torch.float64, device="cuda")
