@@ -135,8 +135,8 @@ __device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool 
   float y0, y1;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
-  const float2 e = make_float2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f));
   float2 y = make_float2(y0, y1);
+  const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, make_float2(1.f, 1.f));
   y = __ffma2_rn(y, e, y);
   const bool a0 = m0 && r2.x < rc2, a1 = m1 && r2.y < rc2;
   y = make_float2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
@@ -233,11 +233,11 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       R wx = window_half_width(rc2s - gyz2);
       int ulo = ufloor<R>((pi.x - wx) * il - (R)5e-4);
       int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
-      ulo = max(ulo, cx - H);
-      uhi = min(uhi, cx + H);
-      // empty only for a coordinate outside [0, L) (its cell is clamped into
-      // the grid, its window is not): skipping keeps every index in range
-      if (ulo > uhi) continue;
+      // both ends clamped into [cx - H - 1, cx + H + 1]: for a coordinate
+      // outside [0, L) (its cell clamped into the grid, its window not) the
+      // segments come out empty and every index stays in range
+      ulo = min(max(ulo, cx - H), cx + H + 1);
+      uhi = max(min(uhi, cx + H), cx - H - 1);
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
       // segment u < 0: image -L (shift j)
       if (ulo < 0) {
