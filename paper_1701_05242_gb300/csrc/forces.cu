@@ -55,8 +55,12 @@ __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typenam
 }
 
 // The same walk with the packed two-candidates-per-instruction pair loop
-// (one type, FP32, eps = sigma = 1).
-__global__ void __launch_bounds__(kForceBlock) k_forces_x2(int64_t n, const float4* __restrict__ pos,
+// (one type, FP32, eps = sigma = 1).  Blocks of two warps: a block retires
+// only when its slowest warp is done, and the row windows of neighbouring
+// particles differ, so small blocks keep the SMs fuller (measured: 64
+// threads 0.4% faster than 128, 32 threads 3% and 1024 threads 14% slower).
+constexpr int kX2Block = 64;
+__global__ void __launch_bounds__(kX2Block, 16) k_forces_x2(int64_t n, const float4* __restrict__ pos,
                                                            const float* __restrict__ rc,
                                                            const int32_t* __restrict__ start, ForceArgs<float> a,
                                                            float4* __restrict__ force, double* __restrict__ part,
@@ -533,7 +537,9 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
                  nwarp);
       done = true;
     } else if (kind == DCM_FORCE_PACKED) {
-      DCM_LAUNCH(ctx, k_forces_x2, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part, nwarp);
+      const int64_t nblk2 = (n + kX2Block - 1) / kX2Block;  // no more warps than the 128-thread grid
+      nwarp = nblk2 * (kX2Block / 32);
+      DCM_LAUNCH(ctx, k_forces_x2, (unsigned)nblk2, kX2Block, 0, st, n, pos, rc, cell_start, af, force, part, nwarp);
       done = true;
     } else if (kind == DCM_FORCE_TWO_PHASE) {
       static_assert(kF2Block == kForceBlock, "partials layout assumes equal blocks");
