@@ -133,6 +133,26 @@ struct FillVisitor {
     int k = kf;
     int j = j0;
     if constexpr (sizeof(R) == 4) {  // two candidates per packed r^2 (the same roundings as one at a time)
+      // four position loads in flight: the walk does little arithmetic per
+      // candidate, so without them it waits on the loads
+      for (; j + 3 < j1; j += 4) {
+        const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j + 1), p2 = __ldg(pos + j + 2), p3 = __ldg(pos + j + 3);
+        const float2 dx = make_float2(xi - p0.x, xi - p1.x), dy = make_float2(yi - p0.y, yi - p1.y),
+                     dz = make_float2(zi - p0.z, zi - p1.z);
+        const float2 ex = make_float2(xi - p2.x, xi - p3.x), ey = make_float2(yi - p2.y, yi - p3.y),
+                     ez = make_float2(zi - p2.z, zi - p3.z);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const float2 s2 = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, __fmul2_rn(ez, ez)));
+        const bool a0 = r2.x < rl2, a1 = r2.y < rl2, a2 = s2.x < rl2, a3 = s2.y < rl2;
+        store_if(a0 && k < lim, out + (int64_t)k * 32, (uint32_t)j);
+        k += a0 ? 1 : 0;
+        store_if(a1 && k < lim, out + (int64_t)k * 32, (uint32_t)(j + 1));
+        k += a1 ? 1 : 0;
+        store_if(a2 && k < lim, out + (int64_t)k * 32, (uint32_t)(j + 2));
+        k += a2 ? 1 : 0;
+        store_if(a3 && k < lim, out + (int64_t)k * 32, (uint32_t)(j + 3));
+        k += a3 ? 1 : 0;
+      }
       for (; j + 1 < j1; j += 2) {
         const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j + 1);
         const float2 dx = make_float2(xi - p0.x, xi - p1.x), dy = make_float2(yi - p0.y, yi - p1.y),

@@ -644,6 +644,60 @@ def test_skin_validation(D):
 
 
 # ----------------------------------------------------------- full-size sample
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_error_report_per_result(D, slab_1935, prec):
+    """The error of each result of the path against the FP64 oracle on the
+    1,935-particle slab, stage by stage on the same inputs (printed with an
+    ERR prefix, and held to the tolerances): distances, cutoffs, forces,
+    per-particle energies, total energy, virial and the accepted pairs."""
+    slab = slab_1935
+    n = slab.n
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    real = real_of(D, P)
+    ctx = make_ctx(D, slab.box, n, P)
+    pos4 = pos4_of(D, slab.pos, None, P)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4)
+    oc, ocount, ostart, operm = O.bin_particles(slab.pos, slab.box, 1.5)
+    assert np.array_equal(start, ostart) and np.array_equal(perm, operm)
+    bc, g, T, s_, iface = gpu_detect(D, ctx, pos4)
+    nh = O.grid_dims(slab.box, 1.5)
+    og, oT, os_, oif = O.detect_interface(ocount, nh, 2)
+    assert T == oT and np.array_equal(iface.cpu().numpy(), oif)
+    Dg = torch.empty(ctx.nbox, dtype=real, device="cuda")
+    D.dcm_distance(ctx, s_, iface, Dg)
+    Do, _ = O.cfsm(os_, oif, nh, 1.5, 6.0)
+    Dgn = Dg.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(Do)
+    d_err = float(np.max(np.abs(Dgn[fin] - Do[fin]) / np.maximum(np.abs(Do[fin]), 1.5)))
+    rc = torch.empty(n, dtype=real, device="cuda")
+    D.dcm_cutoffs(ctx, n, ps, Dg, rc)
+    spos = slab.pos[operm].astype(np.float64)
+    _, orc = O.cutoffs(spos, Do, nh, 1.5, 6.0, 3.0, 6.0, 3.0)
+    rcn = rc.cpu().numpy().astype(np.float64)
+    rc_err = float(np.abs(rcn - orc).max())
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    D.dcm_forces(ctx, n, ps, rc, torch.from_numpy(start).cuda(), F, tot)
+    torch.cuda.synchronize()
+    ref = O.forces_cells(spos, rcn, slab.box, 1.5)
+    Fg = F.cpu().numpy().astype(np.float64)
+    tot = tot.cpu().numpy()
+    f_err = rms_rel(Fg[:, :3], ref.F)
+    e_err = float(np.abs(Fg[:, 3] - ref.e).max() / np.abs(ref.e).max())
+    E_err = abs(tot[0] - ref.E) / abs(ref.E)
+    W_err = abs(tot[1] - ref.W) / abs(ref.W)
+    dp = int(tot[2]) - ref.npairs
+    print(f"ERR slab_1935 {prec}: distances {d_err:.3g} (of max(D, h)), cutoffs {rc_err:.3g} (abs), "
+          f"forces {f_err:.3g} (rms-rel), e_i {e_err:.3g} (of max |e_i|), E {E_err:.3g}, W {W_err:.3g} (rel), "
+          f"pairs {dp:+d} of {ref.npairs}")
+    if prec == "mixed":
+        assert d_err <= D_TOL and rc_err <= RC_TOL and f_err <= F_RMS_TOL and e_err <= 1e-5
+        assert E_err <= EW_TOL and W_err <= EW_TOL
+        assert abs(dp) <= near_cutoff_pairs(spos, rcn, slab.box)
+    else:
+        assert max(d_err, rc_err, f_err, e_err, E_err, W_err) <= FP64_TOL and dp == 0
+
+
 @pytest.fixture(scope="module")
 def slab_16m():
     return synth.make_slab(synth.named("slab_16m"))
@@ -672,6 +726,9 @@ def test_full_size_sampled(D, slab_16m):
     D.dcm_cutoffs(ctx, n, ps, Dg, rc)
     _, orc = O.cutoffs(slab.pos[operm], Do, nh, 1.5, 6.0, 3.0, 6.0, 3.0)
     rcn = rc.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(Do)
+    print(f"ERR slab_16m: distances max {np.max(np.abs(Dgn[fin] - Do[fin]) / np.maximum(np.abs(Do[fin]), 1.5)):.3g} "
+          f"(of max(D, h)), cutoffs max abs {np.abs(rcn - orc).max():.3g}")
     assert np.abs(rcn - orc).max() <= RC_TOL
     rng = np.random.default_rng(7)
     # sample: random particles plus all of a few interface-region cells
@@ -687,6 +744,8 @@ def test_full_size_sampled(D, slab_16m):
         D.dcm_forces(kctx, n, ps, rc, torch.from_numpy(start).cuda(), F, tot)
         torch.cuda.synchronize()
         Fs = F.cpu().numpy().astype(np.float64)[idx]
+        print(f"ERR slab_16m kernel {kernel}: forces rms-rel {rms_rel(Fs[:, :3], Fo):.3g} on {len(idx)} sampled "
+              f"particles, e_i max {np.abs(Fs[:, 3] - eo).max() / np.abs(eo).max():.3g} (of max |e_i|)")
         assert rms_rel(Fs[:, :3], Fo) <= F_RMS_TOL
         assert np.abs(Fs[:, 3] - eo).max() <= 1e-5 * np.abs(eo).max()
         tot = tot.cpu().numpy()
