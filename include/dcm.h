@@ -112,6 +112,10 @@ typedef struct dcm_params {
                              phase) of fewer boxes before the interface is taken (Section 2.1's
                              bubble filter); 0 (default): off.  Single-system contexts only */
   int32_t reserved2;
+  double lx;              /* force-cell edge along x, the direction in which a row of cells is one
+                             contiguous run of sorted particles; L_x / lx integer, short mantissa.
+                             0 (default): l.  Finer cells along the rows narrow each row's window
+                             without adding rows.  Single-system contexts only */
 } dcm_params;
 
 typedef struct dcm_ctx dcm_ctx;
@@ -181,8 +185,9 @@ int dcm_status(dcm_ctx* ctx, dcm_stream_t stream);
 
 /* ---- the hot path ------------------------------------------------------ */
 
-/* Binning, Sections 2.1 and 2.3.  Cell of particle i: cx = floor(x_i / l)
- * computed exactly (clamped to [0, nx-1]), same for y and z.  Stable counting
+/* Binning, Sections 2.1 and 2.3.  Cell of particle i: cx = floor(x_i / lx),
+ * cy = floor(y_i / l), cz = floor(z_i / l) (lx = l unless params.lx is set),
+ * computed exactly and clamped to [0, n-1] per axis.  Stable counting
  * sort: particles of one cell keep their input order.
  *   pos        real4[n]       input positions (any order)
  *   cell       int32[n]       out: cell of input particle i

@@ -108,12 +108,13 @@ def _vec3(v):
 
 
 def grid_dims(box, edge) -> np.ndarray:
-    """Number of boxes per dimension; the box must be an integer multiple of the edge."""
+    """Number of boxes per dimension; the box must be an integer multiple of the
+    edge (one edge for all three axes, or one per axis)."""
     n = []
-    for L in box:
-        k = int(round(L / edge))
-        if k < 1 or abs(k * edge - L) > 1e-9 * L:
-            raise ValueError(f"box length {L} is not a multiple of edge {edge}")
+    for L, e in zip(box, _vec3(edge)):
+        k = int(round(L / e))
+        if k < 1 or abs(k * e - L) > 1e-9 * L:
+            raise ValueError(f"box length {L} is not a multiple of edge {e}")
         n.append(k)
     return np.asarray(n, dtype=np.int64)
 
@@ -125,7 +126,8 @@ def bin_particles(pos, box, l):
     """Stable counting sort by cell (Sections 2.1, 2.3).
 
     Returns (cell[N], count[ncell], start[ncell+1], perm[N]) as int32, with the
-    cell of a particle c = cx + nx (cy + ny cz), cx = floor(x / l) exactly.
+    cell of a particle c = cx + nx (cy + ny cz), cx = floor(x / l_x) exactly
+    (l one edge for all axes or a per-axis triple).
     """
     pos = _f64(pos).reshape(-1, 3)
     n = pos.shape[0]

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
   if (i < n) {
     const Grid<R>& g = a.g;
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const R l = g.edge, il = g.inv_edge;
+    const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
     auto pi = ldg4(pos + i);
     auto ak = ldg4(A + i);
     R rck = rc[i];
@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
         ducsh[t] = (R)4 * e / sqrt(sig2) * ((R)12 * c12 - (R)6 * c6);
       }
     }
-    const int cx = cell_coord<R>(pi.x, l, il, nx);
+    const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
     const int cy = cell_coord<R>(pi.y, l, il, ny);
     const int cz = cell_coord<R>(pi.z, l, il, nz);
-    const int H = (int)ceil(reach * il);
+    const int H = (int)ceil(reach * il), Hx = (int)ceil(reach * ilx);
     for (int uz = cz - H; uz <= cz + H; ++uz) {
       R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
       R gz2 = gz * gz;
@@ -148,10 +148,10 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
         R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
         R ysh = uy < 0 ? -g.L[1] : (R)0;
         R wx = sqrt(reach2s - gyz2);
-        int ulo = ufloor<R>((pi.x - wx) * il - (R)5e-4);
-        int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
-        ulo = max(ulo, cx - H);
-        uhi = min(uhi, cx + H);
+        int ulo = ufloor<R>((pi.x - wx) * ilx - (R)5e-4);
+        int uhi = ufloor<R>((pi.x + wx) * ilx + (R)5e-4);
+        ulo = max(ulo, cx - Hx);
+        uhi = min(uhi, cx + Hx);
         if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
         const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
         if (ulo < 0) {

@@ -30,14 +30,16 @@ int check_launch(dcm_ctx* ctx, const char* what) {
 }
 
 template <typename R>
-static Grid<R> make_grid(const int64_t* n, double edge, const double* box) {
+static Grid<R> make_grid(const int64_t* n, double edge, double edge_x, const double* box) {
   Grid<R> g;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = (int)n[d];
-    g.L[d] = (R)((double)n[d] * edge);  // exact: short-mantissa edge times a small integer
+    g.L[d] = (R)((double)n[d] * (d == 0 ? edge_x : edge));  // exact: short-mantissa edge times a small integer
   }
   g.edge = (R)edge;
   g.inv_edge = (R)(1.0 / edge);
+  g.edge_x = (R)edge_x;
+  g.inv_edge_x = (R)(1.0 / edge_x);
   g.ncell = n[0] * n[1] * n[2];
   (void)box;
   return g;
@@ -45,11 +47,11 @@ static Grid<R> make_grid(const int64_t* n, double edge, const double* box) {
 
 template <typename R>
 Grid<R> cell_grid(const dcm_ctx* ctx) {
-  return make_grid<R>(ctx->nc, ctx->p.l, ctx->p.box);
+  return make_grid<R>(ctx->nc, ctx->p.l, ctx->p.lx, ctx->p.box);
 }
 template <typename R>
 Grid<R> box_grid(const dcm_ctx* ctx) {
-  return make_grid<R>(ctx->nh, ctx->p.h, ctx->p.box);
+  return make_grid<R>(ctx->nh, ctx->p.h, ctx->p.h, ctx->p.box);
 }
 template Grid<float> cell_grid<float>(const dcm_ctx*);
 template Grid<double> cell_grid<double>(const dcm_ctx*);
@@ -153,9 +155,13 @@ extern "C" int dcm_params_default(dcm_params* p) {
   return DCM_OK;
 }
 
+// Cell edge along axis d: lx along x when it is set, l otherwise.
+static double cell_edge(const dcm_params* p, int d) { return d == 0 && p->lx > 0.0 ? p->lx : p->l; }
+
 // Resolve the defaults that depend on other fields.
 static dcm_params resolved(const dcm_params* p) {
   dcm_params q = *p;
+  if (!(q.lx > 0.0)) q.lx = q.l;
   if (!(q.ramp > 0.0)) q.ramp = q.rc_max - q.rc_min;
   if (!(q.r_grid > 0.0)) q.r_grid = q.ramp + 2.0 * q.h;
   return q;
@@ -169,11 +175,15 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
       return msg_out(msg, len, DCM_ERR_BOX, "box[%d] = %g must be positive", d, p->box[d]);
   if (!short_mantissa(p->l)) return msg_out(msg, len, DCM_ERR_BOX, "cell edge l = %g needs a short mantissa", p->l);
   if (!short_mantissa(p->h)) return msg_out(msg, len, DCM_ERR_BOX, "box edge h = %g needs a short mantissa", p->h);
+  if (!(p->lx >= 0.0) || !std::isfinite(p->lx))
+    return msg_out(msg, len, DCM_ERR_INVALID_ARG, "lx = %g must be >= 0 (0: l)", p->lx);
+  if (p->lx > 0.0 && !short_mantissa(p->lx))
+    return msg_out(msg, len, DCM_ERR_BOX, "cell edge lx = %g needs a short mantissa", p->lx);
   int64_t n;
   for (int d = 0; d < 3; ++d) {
-    if (!grid_of(p->box[d], p->l, &n) || n >= 65536)
-      return msg_out(msg, len, DCM_ERR_BOX, "box[%d] = %g is not a multiple of l = %g (below 65536 cells)", d,
-                     p->box[d], p->l);
+    if (!grid_of(p->box[d], cell_edge(p, d), &n) || n >= 65536)
+      return msg_out(msg, len, DCM_ERR_BOX, "box[%d] = %g is not a multiple of the cell edge %g (below 65536 cells)",
+                     d, p->box[d], cell_edge(p, d));
     if (!grid_of(p->box[d], p->h, &n) || n >= 65536)
       return msg_out(msg, len, DCM_ERR_BOX, "box[%d] = %g is not a multiple of h = %g (below 65536 boxes)", d,
                      p->box[d], p->h);
@@ -200,7 +210,7 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
   if (p->n_max < 0 || p->n_max > 0x7fffffffLL) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "n_max out of range");
   int64_t nc[3], nh[3];
   for (int d = 0; d < 3; ++d) {
-    grid_of(p->box[d], p->l, nc + d);
+    grid_of(p->box[d], cell_edge(p, d), nc + d);
     grid_of(p->box[d], p->h, nh + d);
   }
   if (nc[0] * nc[1] * nc[2] >= 0x7fffffffLL || nh[0] * nh[1] * nh[2] >= 0x7fffffffLL)
@@ -220,7 +230,7 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
 extern "C" int dcm_grid_dims(const dcm_params* p, int64_t* cells3, int64_t* boxes3) {
   if (dcm_validate_params(p, nullptr, 0) != DCM_OK) return DCM_ERR_BOX;
   for (int d = 0; d < 3; ++d) {
-    if (cells3) grid_of(p->box[d], p->l, cells3 + d);
+    if (cells3) grid_of(p->box[d], cell_edge(p, d), cells3 + d);
     if (boxes3) grid_of(p->box[d], p->h, boxes3 + d);
   }
   return DCM_OK;
@@ -242,7 +252,7 @@ static ScratchPlan plan_of(const dcm_params* p) {
   ScratchPlan s;
   int64_t nc[3], nh[3];
   for (int d = 0; d < 3; ++d) {
-    grid_of(p->box[d], p->l, nc + d);
+    grid_of(p->box[d], cell_edge(p, d), nc + d);
     grid_of(p->box[d], p->h, nh + d);
   }
   s.n_max = p->n_max;
@@ -301,9 +311,9 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   ctx->p = resolved(p);
   ctx->precision = p->precision;
   for (int d = 0; d < 3; ++d) {
-    grid_of(p->box[d], p->l, ctx->nc + d);
+    grid_of(p->box[d], cell_edge(p, d), ctx->nc + d);
     grid_of(p->box[d], p->h, ctx->nh + d);
-    ctx->p.box[d] = (double)ctx->nc[d] * p->l;  // exact multiple of l
+    ctx->p.box[d] = (double)ctx->nc[d] * cell_edge(p, d);  // exact multiple of the cell edge
   }
   ctx->ncell = ctx->nc[0] * ctx->nc[1] * ctx->nc[2];
   ctx->nbox = ctx->nh[0] * ctx->nh[1] * ctx->nh[2];

@@ -97,6 +97,8 @@ __device__ __forceinline__ Grid<R> rep_cells(const RepGeom& G, R l, R il) {
   }
   g.edge = l;
   g.inv_edge = il;
+  g.edge_x = l;  // replicas use cubic cells
+  g.inv_edge_x = il;
   g.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
   return g;
 }
@@ -572,6 +574,8 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     ForceArgs<R> a;
     a.g.edge = (R)b->p.l;
     a.g.inv_edge = (R)(1.0 / b->p.l);
+    a.g.edge_x = a.g.edge;
+    a.g.inv_edge_x = a.g.inv_edge;
     LJTable t = lj_table(b->p);
     a.ntypes = t.ntypes;
     for (int k = 0; k < 16; ++k) {
@@ -695,6 +699,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   *out = nullptr;
   if (p->skin != 0.0) return DCM_ERR_INVALID_ARG;  // the batched form steps over cell lists only
   if (p->min_component != 0) return DCM_ERR_INVALID_ARG;  // no bubble filter in the batched form
+  if (p->lx != 0.0 && p->lx != p->l) return DCM_ERR_INVALID_ARG;  // replicas use cubic cells
   std::vector<RepGeom> geom((size_t)R);
   int64_t ntot = 0, nctot = 0, nbtot = 0;
   for (int r = 0; r < R; ++r) {

@@ -15,7 +15,7 @@ __global__ void k_count(int64_t n, const typename RT<R>::R4* __restrict__ pos, G
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   auto p = ldg4(pos + i);
-  int cx = cell_coord<R>(p.x, g.edge, g.inv_edge, g.n[0]);
+  int cx = cell_coord<R>(p.x, g.edge_x, g.inv_edge_x, g.n[0]);
   int cy = cell_coord<R>(p.y, g.edge, g.inv_edge, g.n[1]);
   int cz = cell_coord<R>(p.z, g.edge, g.inv_edge, g.n[2]);
   int c = cx + g.n[0] * (cy + g.n[1] * cz);

@@ -63,8 +63,10 @@ __device__ __forceinline__ int cell_coord(R x, R l, R inv_l, int n) {
 template <typename R>
 struct Grid {
   int n[3];      // cells per dimension
-  R edge;        // cell edge
+  R edge;        // cell edge along y and z
   R inv_edge;
+  R edge_x;      // cell edge along x, the direction of the contiguous cell rows
+  R inv_edge_x;
   R L[3];        // box lengths (= n * edge exactly)
   int64_t ncell;
 };

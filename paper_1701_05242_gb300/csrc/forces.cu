@@ -98,25 +98,26 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_forces_tile(int64_t n, cons
   const bool valid = i < n;
   const Grid<float>& g = a.g;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const float l = g.edge, il = g.inv_edge;
+  const float l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
   const float4 pi = valid ? __ldg(pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   const float rc_in = valid ? __ldg(rc + i) : 0.f;
   float rci = rc_in;
   if (!(rci <= a.rc_max)) rci = a.rc_max;
   if (!(rci > 0.f)) rci = 0.f;
-  const int cx = cell_coord<float>(pi.x, l, il, nx), cy = cell_coord<float>(pi.y, l, il, ny),
+  const int cx = cell_coord<float>(pi.x, g.edge_x, ilx, nx), cy = cell_coord<float>(pi.y, l, il, ny),
             cz = cell_coord<float>(pi.z, l, il, nz);
-  const int H = (int)ceilf(rci * il);
-  int Hm = H, cmin = cx, cmax = cx;
+  const int H = (int)ceilf(rci * il), Hx = (int)ceilf(rci * ilx);
+  int Hm = H, Hxm = Hx, cmin = cx, cmax = cx;
   for (int o = 16; o > 0; o >>= 1) {
     Hm = max(Hm, __shfl_xor_sync(FULL, Hm, o));
+    Hxm = max(Hxm, __shfl_xor_sync(FULL, Hxm, o));
     cmin = min(cmin, __shfl_xor_sync(FULL, cmin, o));
     cmax = max(cmax, __shfl_xor_sync(FULL, cmax, o));
   }
   const int cy0 = __shfl_sync(FULL, cy, 0), cz0 = __shfl_sync(FULL, cz, 0);
-  const bool tiled = __all_sync(FULL, valid && cy == cy0 && cz == cz0) && cmin - Hm >= 0 && cmax + Hm < nx &&
+  const bool tiled = __all_sync(FULL, valid && cy == cy0 && cz == cz0) && cmin - Hxm >= 0 && cmax + Hxm < nx &&
                      cy0 - Hm >= 0 && cy0 + Hm < ny && cz0 - Hm >= 0 && cz0 + Hm < nz &&
-                     (cmax - cmin) + 2 * Hm + 2 <= kTileCells;
+                     (cmax - cmin) + 2 * Hxm + 2 <= kTileCells;
   float e_out = 0.f, w_out = 0.f;
   int np = 0;
   if (!tiled) {
@@ -136,8 +137,8 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_forces_tile(int64_t n, cons
         int ulo = 0, uhi = -1;
         if (has) {
           const float wx = window_half_width(rc2s - gyz2);
-          ulo = max(ufloor<float>((pi.x - wx) * il - 5e-4f), cx - H);
-          uhi = min(ufloor<float>((pi.x + wx) * il + 5e-4f), cx + H);
+          ulo = max(ufloor<float>((pi.x - wx) * ilx - 5e-4f), cx - Hx);
+          uhi = min(ufloor<float>((pi.x + wx) * ilx + 5e-4f), cx + Hx);
           has = ulo <= uhi;
         }
         if (__ballot_sync(FULL, has) == 0) continue;
@@ -219,13 +220,13 @@ __global__ void __launch_bounds__(kForceBlock) k_forces_flat(int64_t n, const fl
   const bool valid = i < n;
   const Grid<float>& g = a.g;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const float l = g.edge, il = g.inv_edge;
+  const float l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
   const float4 pi = valid ? __ldg(pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   const float rci = clamp_cutoff<float>(valid ? __ldg(rc + i) : 0.f, a.rc_max);
   const float rc2 = rci * rci, rc2s = rc2 * 1.000004f;
-  const int cx = cell_coord<float>(pi.x, l, il, nx), cy = cell_coord<float>(pi.y, l, il, ny),
+  const int cx = cell_coord<float>(pi.x, g.edge_x, ilx, nx), cy = cell_coord<float>(pi.y, l, il, ny),
             cz = cell_coord<float>(pi.z, l, il, nz);
-  const int H = valid ? (int)ceilf(rci * il) : -1;
+  const int H = valid ? (int)ceilf(rci * il) : -1, Hx = valid ? (int)ceilf(rci * ilx) : -1;
   int Hw = H;
   for (int o = 16; o > 0; o >>= 1) Hw = max(Hw, __shfl_xor_sync(FULL, Hw, o));
   const int self = (int)i;
@@ -262,8 +263,8 @@ __global__ void __launch_bounds__(kForceBlock) k_forces_flat(int64_t n, const fl
     const float gyz2 = gz * gz + gy * gy;
     if (dz >= -H && dz <= H && dy >= -H && dy <= H && gyz2 < rc2s) {
       const float wx = window_half_width(rc2s - gyz2);
-      const int ulo = max(ufloor<float>((pi.x - wx) * il - 5e-4f), cx - H);
-      const int uhi = min(ufloor<float>((pi.x + wx) * il + 5e-4f), cx + H);
+      const int ulo = max(ufloor<float>((pi.x - wx) * ilx - 5e-4f), cx - Hx);
+      const int uhi = min(ufloor<float>((pi.x + wx) * ilx + 5e-4f), cx + Hx);
       const bool img_row = uy < 0 || uy >= ny || uz < 0 || uz >= nz;
       img |= img_row || ulo < 0 || uhi >= nx;
       const int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
@@ -376,17 +377,17 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
   float e_out = 0.f, w_out = 0.f;
   const Grid<float>& g = a.g;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const float l = g.edge, il = g.inv_edge;
+  const float l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
   float4 pi = live ? __ldg(pos + i) : make_float4(0.f, 0.f, 0.f, 0.f);
   float rci = live ? rc[i] : 0.f;
   if (!(rci <= a.rc_max)) rci = a.rc_max;
   if (!(rci > 0.f)) rci = 0.f;
   const float rc2 = rci * rci;
   const float rc2s = rc2 * 1.000004f;
-  const int cx = cell_coord<float>(pi.x, l, il, nx);
+  const int cx = cell_coord<float>(pi.x, g.edge_x, ilx, nx);
   const int cy = cell_coord<float>(pi.y, l, il, ny);
   const int cz = cell_coord<float>(pi.z, l, il, nz);
-  const int H = live ? (int)ceilf(rci * il) : -1;
+  const int H = live ? (int)ceilf(rci * il) : -1, Hx = live ? (int)ceilf(rci * ilx) : -1;
   // the warp walks the union of its lanes' (dz, dy) rows in lockstep
   int Hw = H;
   for (int o = 16; o > 0; o >>= 1) Hw = max(Hw, __shfl_xor_sync(0xffffffffu, Hw, o));
@@ -411,25 +412,20 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
         yi = uy >= ny ? pi.y - g.L[1] : pi.y;
         ysh = uy < 0 ? -g.L[1] : 0.f;
         float wx = window_half_width(rc2s - gyz2);
-        ulo = max((int)floorf((pi.x - wx) * il - 5e-4f), cx - H);
-        uhi = min((int)floorf((pi.x + wx) * il + 5e-4f), cx + H);
+        ulo = max((int)floorf((pi.x - wx) * ilx - 5e-4f), cx - Hx);
+        uhi = min((int)floorf((pi.x + wx) * ilx + 5e-4f), cx + Hx);
         row = (int64_t)nx * (wy + (int64_t)ny * wz);
       }
-      // the candidates this row can add: the whole window
-      int jlo = 0, jhi = 0;
+      // the candidates this row can add: the three pieces of the window (the
+      // part before x = 0, the in-grid part, the part past x = L), exactly
+      // the ranges filtered below
+      int wlen = 0;
       if (on && ulo <= uhi) {
-        int clo = ulo < 0 ? ulo + nx : ulo, chi = uhi >= nx ? uhi - nx : uhi;
-        if (ulo >= 0 && uhi < nx) {
-          jlo = __ldg(start + row + clo);
-          jhi = __ldg(start + row + chi + 1);
-        } else {  // wrapped window: count both pieces
-          int a0 = __ldg(start + row + clo), a1 = __ldg(start + row + nx);
-          int b0 = __ldg(start + row), b1 = __ldg(start + row + chi + 1);
-          jlo = 0;
-          jhi = (a1 - a0) + (b1 - b0);
-        }
+        if (ulo < 0) wlen += __ldg(start + row + min(uhi, -1) + nx + 1) - __ldg(start + row + ulo + nx);
+        const int m0 = max(ulo, 0), m1 = min(uhi, nx - 1);
+        if (m0 <= m1) wlen += __ldg(start + row + m1 + 1) - __ldg(start + row + m0);
+        if (uhi >= nx) wlen += __ldg(start + row + uhi - nx + 1) - __ldg(start + row + max(ulo, nx) - nx);
       }
-      int wlen = jhi - jlo;
       if (__any_sync(0xffffffffu, cnt + wlen > kBuf)) {
         drain(buf, cnt, c);
         cnt = 0;

@@ -209,13 +209,13 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
                                           int ti, const R* ushift, Acc<R>& c, Acc2& c2) {
   constexpr bool kImg = MODE == Walk::kImagesOnly;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const R l = g.edge, il = g.inv_edge;
+  const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
   const R rc2 = rci * rci;
   const R rc2s = rc2 * (R)1.000004;  // culling slack; the pair test is exact
-  const int cx = cell_coord<R>(pi.x, l, il, nx);
+  const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
   const int cy = cell_coord<R>(pi.y, l, il, ny);
   const int cz = cell_coord<R>(pi.z, l, il, nz);
-  const int H = (int)ceil(rci * il);
+  const int H = (int)ceil(rci * il), Hx = (int)ceil(rci * ilx);
   for (int uz = cz - H; uz <= cz + H; ++uz) {
     R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
     R gz2 = gz * gz;
@@ -231,13 +231,13 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
       R ysh = uy < 0 ? -g.L[1] : (R)0;
       R wx = window_half_width(rc2s - gyz2);
-      int ulo = ufloor<R>((pi.x - wx) * il - (R)5e-4);
-      int uhi = ufloor<R>((pi.x + wx) * il + (R)5e-4);
-      // both ends clamped into [cx - H - 1, cx + H + 1]: for a coordinate
+      int ulo = ufloor<R>((pi.x - wx) * ilx - (R)5e-4);
+      int uhi = ufloor<R>((pi.x + wx) * ilx + (R)5e-4);
+      // both ends clamped into [cx - Hx - 1, cx + Hx + 1]: for a coordinate
       // outside [0, L) (its cell clamped into the grid, its window not) the
       // segments come out empty and every index stays in range
-      ulo = min(max(ulo, cx - H), cx + H + 1);
-      uhi = max(min(uhi, cx + H), cx - H - 1);
+      ulo = min(max(ulo, cx - Hx), cx + Hx + 1);
+      uhi = max(min(uhi, cx + Hx), cx - Hx - 1);
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
       // segment u < 0: image -L (shift j)
       if (ulo < 0) {

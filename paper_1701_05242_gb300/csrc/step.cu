@@ -44,7 +44,7 @@ __global__ void k_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__ p
   p.z = wrap_coord<R>(p.z + dt * v.z, g.L[2]);
   pos[i] = p;
   vel[i] = v;
-  int cx = cell_coord<R>(p.x, g.edge, g.inv_edge, g.n[0]);
+  int cx = cell_coord<R>(p.x, g.edge_x, g.inv_edge_x, g.n[0]);
   int cy = cell_coord<R>(p.y, g.edge, g.inv_edge, g.n[1]);
   int cz = cell_coord<R>(p.z, g.edge, g.inv_edge, g.n[2]);
   int c = cx + g.n[0] * (cy + g.n[1] * cz);
@@ -100,7 +100,7 @@ template <typename R>
 static int recompute_cutoffs(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, R* rc, cudaStream_t st) {
   const int32_t* box_count;
   int r;
-  if (ctx->p.h == ctx->p.l) {
+  if (ctx->p.h == ctx->p.l && ctx->p.lx == ctx->p.l) {
     box_count = ctx->cell_count;  // the binning's counts are the gray-scale volume's input
   } else {
     r = histogram<R>(ctx, n, pos, box_grid<R>(ctx), ctx->box_count, st);

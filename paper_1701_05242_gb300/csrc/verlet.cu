@@ -38,12 +38,12 @@ template <typename R, typename V>
 __device__ __forceinline__ void walk_segments(const int32_t* __restrict__ start, const Grid<R>& g, int self,
                                               const typename RT<R>::R4& pi, R rl, V& v) {
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-  const R l = g.edge, il = g.inv_edge;
+  const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
   const R rl2s = rl * rl * (R)1.000004;  // culling slack; the pair test is exact
-  const int cx = cell_coord<R>(pi.x, l, il, nx);
+  const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
   const int cy = cell_coord<R>(pi.y, l, il, ny);
   const int cz = cell_coord<R>(pi.z, l, il, nz);
-  const int H = (int)ceil(rl * il);
+  const int H = (int)ceil(rl * il), Hx = (int)ceil(rl * ilx);
   for (int uz = cz - H; uz <= cz + H; ++uz) {
     R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
     R gz2 = gz * gz;
@@ -61,8 +61,8 @@ __device__ __forceinline__ void walk_segments(const int32_t* __restrict__ start,
       R yi = yc == 2 ? pi.y - g.L[1] : pi.y;
       R ysh = yc == 1 ? -g.L[1] : (R)0;
       R wx = window_half_width(rl2s - gyz2);
-      int ulo = max(ufloor<R>((pi.x - wx) * il - (R)5e-4), cx - H);
-      int uhi = min(ufloor<R>((pi.x + wx) * il + (R)5e-4), cx + H);
+      int ulo = max(ufloor<R>((pi.x - wx) * ilx - (R)5e-4), cx - Hx);
+      int uhi = min(ufloor<R>((pi.x + wx) * ilx + (R)5e-4), cx + Hx);
       if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
       const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
       const uint32_t yzc = (yc << 2) | (zc << 4);
@@ -558,7 +558,7 @@ __global__ void k_wrap_count(int64_t n, typename RT<R>::R4* __restrict__ pos, Gr
     *c3[d] = x;
   }
   pos[i] = p;
-  int cx = cell_coord<R>(p.x, g.edge, g.inv_edge, g.n[0]);
+  int cx = cell_coord<R>(p.x, g.edge_x, g.inv_edge_x, g.n[0]);
   int cy = cell_coord<R>(p.y, g.edge, g.inv_edge, g.n[1]);
   int cz = cell_coord<R>(p.z, g.edge, g.inv_edge, g.n[2]);
   int c = cx + g.n[0] * (cy + g.n[1] * cz);

@@ -51,7 +51,8 @@ class dcm_params(ctypes.Structure):
                 ("iter_max", ctypes.c_int32), ("ntypes", ctypes.c_int32), ("eps", ctypes.c_double * 4),
                 ("sigma", ctypes.c_double * 4), ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("force_kernel", ctypes.c_int32), ("n_max", ctypes.c_int64),
-                ("skin", ctypes.c_double), ("min_component", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("skin", ctypes.c_double), ("min_component", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("lx", ctypes.c_double)]
 
 
 class dcm_state(ctypes.Structure):

@@ -73,6 +73,9 @@ def test_params_default_and_validate(lib):
     (dict(skin=-0.1), 1),
     (dict(skin=0.5, rc_max=5.8), 2),             # rc_max + skin > L/2
     (dict(skin=0.3, rc_max=5.5, n_max=2 ** 26), 5),  # list entries keep 26 index bits
+    (dict(lx=-0.75), 1),
+    (dict(lx=1.3), 2),                          # long mantissa
+    (dict(lx=0.625), 2),                        # 12 / 0.625 is not an integer
 ])
 def test_params_rejected(lib, kw, code):
     D, p = _params(lib, **kw)
@@ -86,6 +89,9 @@ def test_grid_dims_and_scratch(lib):
     boxes = (ctypes.c_int64 * 3)()
     assert D.lib.dcm_grid_dims(ctypes.byref(p), cells, boxes) == 0
     assert tuple(cells) == (160, 160, 640) and tuple(boxes) == (160, 160, 640)
+    D, p = _params(lib, box=(240.0, 240.0, 960.0), n_max=15482880, lx=0.75)
+    assert D.lib.dcm_grid_dims(ctypes.byref(p), cells, boxes) == 0
+    assert tuple(cells) == (320, 160, 640) and tuple(boxes) == (160, 160, 640)
     b = ctypes.c_int64()
     assert D.lib.dcm_scratch_bytes(ctypes.byref(p), ctypes.byref(b)) == 0
     assert 0.2e9 < b.value < 2e9

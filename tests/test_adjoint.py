@@ -116,9 +116,10 @@ def test_oracle_adjoint_matches_dense_autograd(small2):
 
 
 # -------------------------------------------------------------------- GPU
-def gpu_setup(D, slab, rc64, prec, shift=False):
+def gpu_setup(D, slab, rc64, prec, shift=False, lx=0.0):
     real = torch.float32 if prec == D.DCM_PREC_MIXED else torch.float64
-    p = D.make_params(slab.box, n_max=slab.n, precision=prec, ntypes=2, eps=EPS, sigma=SIG, shift_energy=int(shift))
+    p = D.make_params(slab.box, n_max=slab.n, precision=prec, ntypes=2, eps=EPS, sigma=SIG, shift_energy=int(shift),
+                      lx=lx)
     ctx = D.Context(p)
     pos4 = D.to_real4(torch.from_numpy(slab.pos), torch.from_numpy(slab.types), real)
     n = slab.n
@@ -135,11 +136,12 @@ def gpu_setup(D, slab, rc64, prec, shift=False):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_gpu_adjoint_matches_oracle(small2, prec):
+@pytest.mark.parametrize("lx", [0.0, 0.75])
+def test_gpu_adjoint_matches_oracle(small2, prec, lx):
     import paper_1701_05242_gb300.dcm as D
     slab, rc = small2
     P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
-    ctx, ps, rcs, start, perm, rc_in = gpu_setup(D, slab, rc, P)
+    ctx, ps, rcs, start, perm, rc_in = gpu_setup(D, slab, rc, P, lx=lx)
     n = slab.n
     F = torch.empty_like(ps)
     D.dcm_forces(ctx, n, ps, rcs, start, F)

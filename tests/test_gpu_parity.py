@@ -337,6 +337,43 @@ def test_forces_kernel_variants(D, slab_1935, kernel, l):
     assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
 
 
+@pytest.mark.parametrize("lx", [0.75, 0.5])
+def test_binning_with_a_finer_row_edge(D, slab_1935, lx):
+    """Cells of lx x 1.5 x 1.5 (finer along the contiguous rows): binning
+    bit-exact against the oracle's per-axis floor and stable order."""
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, lx=lx)
+    assert ctx.ncell == int(np.prod(O.grid_dims(slab_1935.box, (lx, 1.5, 1.5))))
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED))
+    oc, ocount, ostart, operm = O.bin_particles(slab_1935.pos, slab_1935.box, (lx, 1.5, 1.5))
+    assert np.array_equal(cell, oc) and np.array_equal(start, ostart) and np.array_equal(perm, operm)
+
+
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("lx", [0.75, 0.5])
+def test_forces_with_a_finer_row_edge(D, slab_1935, kernel, lx):
+    """Every cell-list kernel on cells of lx x 1.5 x 1.5 against the oracle
+    (whose result does not depend on the cells)."""
+    p = O.Params(box=slab_1935.box)
+    rc64 = O.assign_cutoffs(slab_1935.pos, p)["rc"]
+    box = slab_1935.box
+    ctx = make_ctx(D, box, slab_1935.n, lx=lx, force_kernel=kernel)
+    rc_in = rc64.astype(np.float32).astype(np.float64)
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED))
+    F = torch.empty_like(ps)
+    tot = torch.zeros(3, dtype=torch.float64, device="cuda")
+    D.dcm_forces(ctx, slab_1935.n, ps, torch.from_numpy(rc_in[perm]).float().cuda(), torch.from_numpy(start).cuda(),
+                 F, tot)
+    torch.cuda.synchronize()
+    Fg = np.empty((slab_1935.n, 4))
+    Fg[perm] = F.cpu().numpy()
+    tot = tot.cpu().numpy()
+    ref = O.forces_cells(slab_1935.pos, rc_in, box, 1.5)
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
+    assert abs(tot[1] - ref.W) <= EW_TOL * abs(ref.W)
+    assert abs(int(tot[2]) - ref.npairs) <= near_cutoff_pairs(slab_1935.pos, rc_in, box)
+
+
 @pytest.mark.parametrize("l", [1.5, 1.0])
 def test_flat_kernel_matches_packed_away_from_images(D, l):
     """Kernel 5 evaluates each particle's in-grid row segments in the order
@@ -377,8 +414,8 @@ FAR = np.array([[1.0e4, 5.0, 5.0], [-1.0e4, 6.0, 20.0], [3.0, 5.0e3, 30.0], [7.0
                 [2.0, 2.0, 1.0e5], [4.0, 9.0, -2.0e4], [1.0e30, 1.0, 1.0], [-1.0e30, -1.0e30, 40.0]], np.float32)
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
-def test_coordinates_outside_the_box(D, slab_1935, kernel):
+@pytest.mark.parametrize("kernel,lx", [(1, 0.0), (2, 0.0), (3, 0.0), (4, 0.0), (5, 0.0), (3, 0.75), (5, 0.5)])
+def test_coordinates_outside_the_box(D, slab_1935, kernel, lx):
     """Finite coordinates far outside [0, L) are binned into the boundary
     cells: every kernel keeps its indices in range, the far particles accept
     no pair, and the others get the forces of the system without them."""
@@ -387,7 +424,7 @@ def test_coordinates_outside_the_box(D, slab_1935, kernel):
     n = len(pos)
     rc64 = O.assign_cutoffs(slab_1935.pos, O.Params(box=slab_1935.box))["rc"]
     rc = np.concatenate([rc64, np.full(len(FAR), 6.0)]).astype(np.float32)
-    ctx = make_ctx(D, slab_1935.box, n, force_kernel=kernel)
+    ctx = make_ctx(D, slab_1935.box, n, force_kernel=kernel, lx=lx)
     cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, pos, None, D.DCM_PREC_MIXED))
     F = torch.empty_like(ps)
     tot = torch.zeros(3, dtype=torch.float64, device="cuda")
@@ -484,8 +521,8 @@ def test_forces_tiny_box_and_ragged(D):
 
 
 # ------------------------------------------------------------------------ step
-def run_gpu_steps(D, slab, P, nsteps, dt=0.005, K=1, per_step=True):
-    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K)
+def run_gpu_steps(D, slab, P, nsteps, dt=0.005, K=1, per_step=True, lx=0.0):
+    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, lx=lx)
     real = real_of(D, P)
     pos4 = pos4_of(D, slab.pos, None, P)
     vel4 = D.to_real4(torch.from_numpy(slab.vel), None, real)
@@ -499,9 +536,12 @@ def run_gpu_steps(D, slab, P, nsteps, dt=0.005, K=1, per_step=True):
     return ctx, st, np.array(out)
 
 
-def test_step_fp64_matches_oracle_trajectory(D, slab_1935):
+@pytest.mark.parametrize("lx", [0.0, 0.75])
+def test_step_fp64_matches_oracle_trajectory(D, slab_1935, lx):
+    # lx = 0.75: force cells of 0.75 x 1.5 x 1.5 (binning, walk and the
+    # separate density histogram), the same trajectory
     nsteps = 30
-    ctx, st, th = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, nsteps, K=1)
+    ctx, st, th = run_gpu_steps(D, slab_1935, D.DCM_PREC_FP64, nsteps, K=1, lx=lx)
     p = O.Params(box=slab_1935.box, recompute_every=1)
     ost = O.init_state(slab_1935.pos, slab_1935.vel, p)
     assert th[0, 0] == pytest.approx(ost.E, rel=1e-9)
@@ -548,8 +588,8 @@ def test_step_batched_call_equals_single_calls(D, slab_1935, prec):
     assert torch.equal(st1.current()[1], st2.current()[1])
 
 
-def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5):
-    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, skin=skin, rc_max=rc_max)
+def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5, lx=0.0):
+    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, skin=skin, rc_max=rc_max, lx=lx)
     real = real_of(D, P)
     st = D.State(ctx, pos4_of(D, slab.pos, None, P), D.to_real4(torch.from_numpy(slab.vel), None, real))
     D.dcm_step_init(ctx, st)
@@ -561,11 +601,12 @@ def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5):
     return ctx, st, np.array(out)
 
 
-def test_step_verlet_lists_fp64_matches_oracle(D, slab_1935):
+@pytest.mark.parametrize("lx", [0.0, 0.75])
+def test_step_verlet_lists_fp64_matches_oracle(D, slab_1935, lx):
     # Verlet lists (Algorithm 2.2) with skin: same trajectory as the oracle's
     # cell-list steps (rebuilds on displacement and at every cutoff recomputation)
     nsteps = 24
-    ctx, st, th = run_gpu_steps_list(D, slab_1935, D.DCM_PREC_FP64, nsteps, skin=0.3, K=10)
+    ctx, st, th = run_gpu_steps_list(D, slab_1935, D.DCM_PREC_FP64, nsteps, skin=0.3, K=10, lx=lx)
     p = O.Params(box=slab_1935.box, recompute_every=10, rc_max=5.5)
     ost = O.init_state(slab_1935.pos, slab_1935.vel, p)
     for k in range(nsteps):

@@ -210,9 +210,10 @@ def test_dcm_net_force_nonzero_reported(slab_1935):
 # --------------------------------------------------------------- binning ---
 def test_binning_properties(slab_1935):
     pos, box = slab_1935.pos.astype(np.float64), np.array(slab_1935.box)
-    for l in (1.5, 1.0, 0.75):
+    for l in (1.5, 1.0, 0.75, (0.75, 1.5, 1.5), (0.5, 1.5, 1.5)):
         cell, count, start, perm = O.bin_particles(pos, box, l)
         nc = O.grid_dims(box, l)
+        l = np.broadcast_to(np.asarray(l, np.float64), (3,))
         assert count.sum() == len(pos)
         assert start[0] == 0 and start[-1] == len(pos)
         assert np.array_equal(np.diff(start), count)
