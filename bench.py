@@ -166,16 +166,20 @@ def force_source_sha():
     return h.hexdigest()
 
 
-def recorded_traffic(workload):
+def recorded_traffic(workload, cells):
     """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the current force kernel sources (else None)."""
+    taken on the current force kernel sources and the same cell edges (l, lx)
+    (else None)."""
     path = os.path.join(ROOT, "profiles", f"forces_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"forces_src_sha256:\s*([0-9a-f]{64})", txt)
+    c = re.search(r"cell_edges:\s*([0-9.]+)\s+([0-9.]+)", txt)
     if not m or not h or h.group(1) != force_source_sha():
+        return None
+    if not c or (float(c.group(1)), float(c.group(2))) != cells:
         return None
     return float(m.group(1))
 
@@ -353,7 +357,9 @@ def run_gb300(args):
     fkern = "k_forces_list" if args.skin > 0 else D.FORCE_KERNEL_NAMES[D.dcm_force_kernel(ctx)]
     roof = {"bound": "alu", "kernel": fkern, "achieved": achieved, "peak": peak_tinstr,
             "unit": "T FP32-instr/s", "frac": (achieved / peak_tinstr) if achieved else None,
-            "traffic": recorded_traffic(args.workload), "avg_launch_ms": f_ms / max(f_cnt, 1),
+            "traffic": recorded_traffic(args.workload, (args.cell_edge, args.cell_edge_x if args.cell_edge_x > 0
+                                                        else args.cell_edge)),
+            "avg_launch_ms": f_ms / max(f_cnt, 1),
             "pairs_per_launch": pairs, "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
     stage_ms = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
     # step roofline: the force kernel at the FP32-pipe peak plus every other
