@@ -51,8 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="slab_16m")
     ap.add_argument("--cell-edge", type=float, default=1.5, help="force-cell edge l (density grid h stays 1.5)")
-    ap.add_argument("--cell-edge-x", type=float, default=0.75,
-                    help="force-cell edge along x, the row direction (0: the cell edge); 0.75 measured fastest "
+    ap.add_argument("--cell-edge-x", type=float, default=0.5,
+                    help="force-cell edge along x, the row direction (0: the cell edge); 0.5 measured fastest "
                          "with the 1.5 cell edge")
     ap.add_argument("--skin", type=float, default=0.0, help="Verlet-list skin (0: forces from cell lists every step)")
     ap.add_argument("--force-kernel", type=int, default=0, help="cell-list force kernel (DCM_FORCE_*; 0: auto)")

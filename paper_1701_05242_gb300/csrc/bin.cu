@@ -107,6 +107,24 @@ __global__ void k_scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* 
   out[i] += part[i / kScanTile];
 }
 
+// The same, four items per thread with 16-byte accesses (out 16-byte
+// aligned; a tile holds a multiple of four items, so the four share a tile).
+__global__ void k_scan_add4(int32_t* __restrict__ out, int64_t n, const int32_t* __restrict__ part) {
+  const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const int32_t a = part[i / kScanTile];
+  if (i + 4 <= n) {
+    int4 v = *reinterpret_cast<const int4*>(out + i);
+    v.x += a;
+    v.y += a;
+    v.z += a;
+    v.w += a;
+    *reinterpret_cast<int4*>(out + i) = v;
+  } else {
+    for (int64_t k = i; k < n; ++k) out[k] += a;
+  }
+}
+
 int exclusive_scan(dcm_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
   int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles > ctx->scan_cap) return set_error(ctx, DCM_ERR_CAPACITY, "scan of %lld items exceeds scratch", (long long)n);
@@ -116,7 +134,11 @@ int exclusive_scan(dcm_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cud
   }
   DCM_LAUNCH(ctx, k_scan_tiles, (unsigned)tiles, kScanBlock, 0, st, in, out, n, ctx->scan_part);
   DCM_LAUNCH(ctx, k_scan_parts, 1, kScanBlock, 0, st, ctx->scan_part, tiles, out + n);
-  DCM_LAUNCH(ctx, k_scan_add, (unsigned)((n + 255) / 256), 256, 0, st, out, n, ctx->scan_part);
+  static_assert(kScanTile % 4 == 0, "four-item adds stay inside a tile");
+  if (((uintptr_t)out & 15) == 0)
+    DCM_LAUNCH(ctx, k_scan_add4, (unsigned)(((n + 3) / 4 + 255) / 256), 256, 0, st, out, n, ctx->scan_part);
+  else
+    DCM_LAUNCH(ctx, k_scan_add, (unsigned)((n + 255) / 256), 256, 0, st, out, n, ctx->scan_part);
   return check_launch(ctx, "exclusive_scan");
 }
 
@@ -127,11 +149,8 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ cell, const int
   perm[start[cell[i]] + slot[i]] = (int32_t)i;
 }
 
-// One thread per cell: insertion sort of the cell's entries by input index.
-__global__ void k_cell_sort(int64_t ncell, const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  int b = start[c], e = start[c + 1];
+// Insertion sort of one cell's entries perm[b .. e) by input index.
+__device__ __forceinline__ void sort_cell(int b, int e, int32_t* __restrict__ perm) {
   for (int k = b + 1; k < e; ++k) {
     int v = perm[k];
     int j = k - 1;
@@ -141,6 +160,41 @@ __global__ void k_cell_sort(int64_t ncell, const int32_t* __restrict__ start, in
     }
     perm[j + 1] = v;
   }
+}
+
+// One thread per cell.
+__global__ void k_cell_sort(int64_t ncell, const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  sort_cell(start[c], start[c + 1], perm);
+}
+
+// Four cells per thread, their five starts from one 16-byte load and one
+// more (start 16-byte aligned; most cells hold at most one particle, so the
+// pass is a read of the starts).
+__global__ void k_cell_sort4(int64_t ncell, const int32_t* __restrict__ start, int32_t* __restrict__ perm) {
+  const int64_t c = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (c >= ncell) return;
+  int s[5];
+  if (c + 4 <= ncell) {
+    const int4 v = *reinterpret_cast<const int4*>(start + c);
+    s[0] = v.x;
+    s[1] = v.y;
+    s[2] = v.z;
+    s[3] = v.w;
+    s[4] = start[c + 4];
+  } else {
+    for (int q = 0; q < 5; ++q) s[q] = start[min(c + q, ncell)];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sort_cell(s[q], s[q + 1], perm);
+}
+
+static void launch_cell_sort(dcm_ctx* ctx, int64_t ncell, const int32_t* start, int32_t* perm, cudaStream_t st) {
+  if (((uintptr_t)start & 15) == 0)
+    DCM_LAUNCH(ctx, k_cell_sort4, (unsigned)(((ncell + 3) / 4 + 255) / 256), 256, 0, st, ncell, start, perm);
+  else
+    DCM_LAUNCH(ctx, k_cell_sort, (unsigned)((ncell + 255) / 256), 256, 0, st, ncell, start, perm);
 }
 
 template <typename V>
@@ -163,7 +217,7 @@ int bin_particles(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const 
   if (n > 0) {
     unsigned nb = (unsigned)((n + 255) / 256);
     DCM_LAUNCH(ctx, k_scatter, nb, 256, 0, st, n, cell, ctx->slot, cell_start, perm);
-    DCM_LAUNCH(ctx, k_cell_sort, (unsigned)((grid.ncell + 255) / 256), 256, 0, st, grid.ncell, cell_start, perm);
+    launch_cell_sort(ctx, grid.ncell, cell_start, perm, st);
     if (pos_sorted) k_gather<typename RT<R>::R4><<<nb, 256, 0, st>>>(n, perm, pos, pos_sorted);
   }
   return check_launch(ctx, "bin_particles");
@@ -201,7 +255,7 @@ int scatter_sort(dcm_ctx* ctx, int64_t n, const int32_t* cell, const int32_t* sl
                  int64_t ncell, int32_t* perm, cudaStream_t st) {
   if (n > 0) {
     DCM_LAUNCH(ctx, k_scatter, (unsigned)((n + 255) / 256), 256, 0, st, n, cell, slot, cell_start, perm);
-    DCM_LAUNCH(ctx, k_cell_sort, (unsigned)((ncell + 255) / 256), 256, 0, st, ncell, cell_start, perm);
+    launch_cell_sort(ctx, ncell, cell_start, perm, st);
   }
   return check_launch(ctx, "scatter_sort");
 }
