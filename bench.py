@@ -256,8 +256,8 @@ def run_batch(args, D, dev):
     pos = np.concatenate([s.pos for s in slabs])
     vel = np.concatenate([s.vel for s in slabs])
     best, table = autotune.tune(boxes, counts, pos, vel, K=K_RECOMPUTE, dt=DT)
-    b, st = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_MIXED, K_RECOMPUTE, best[0])
-    D.dcm_batch_set_force_block(b, best[1])
+    b, st = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_MIXED, K_RECOMPUTE, best[0], best[1])
+    D.dcm_batch_set_force_block(b, best[2])
     D.dcm_batch_step_init(b, st)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
@@ -279,8 +279,8 @@ def run_batch(args, D, dev):
            "particles": int(sum(counts)), "n_min": int(min(counts)), "n_max": int(max(counts)),
            "timesteps": steps, "ms_per_timestep": ms / steps, "cuda_graph": True,
            "graph_timesteps": per, "launches_per_timestep": D.dcm_batch_launch_count(b) / steps,
-           "autotuned": {"cell_edge": best[0], "force_block": best[1],
-                         "candidates_ms": {f"l={k[0]},block={k[1]}": v for k, v in table.items()}},
+           "autotuned": {"cell_edge": best[0], "cell_edge_x": best[1], "force_block": best[2],
+                         "candidates_ms": {f"l={k[0]},lx={k[1]},block={k[2]}": v for k, v in table.items()}},
            "device_status": status}
     b.close()
     return out

@@ -113,9 +113,9 @@ typedef struct dcm_params {
                              bubble filter); 0 (default): off.  Single-system contexts only */
   int32_t reserved2;
   double lx;              /* force-cell edge along x, the direction in which a row of cells is one
-                             contiguous run of sorted particles; L_x / lx integer, short mantissa.
-                             0 (default): l.  Finer cells along the rows narrow each row's window
-                             without adding rows.  Single-system contexts only */
+                             contiguous run of sorted particles; L_x / lx integer, short mantissa
+                             (for a batch: every replica's L_x).  0 (default): l.  Finer cells
+                             along the rows narrow each row's window without adding rows */
 } dcm_params;
 
 typedef struct dcm_ctx dcm_ctx;

@@ -1,9 +1,10 @@
-"""Autotuner for the batched form: picks the force-cell edge l and the force
-kernel's block size by timing a few steps of every candidate on the actual
-replicas (CUDA events on the stepping stream).
+"""Autotuner for the batched form: picks the force-cell edges (l, and lx
+along the rows) and the force kernel's block size by timing a few steps of
+every candidate on the actual replicas (CUDA events on the stepping stream).
 
-Candidates: l in {1.5, 1.0, 0.75} where it divides every replica box (and
-h = 1.5 stays the density-grid edge), block sizes {64, 128, 256}.
+Candidates: (l, lx) in {(1.5, 1.5), (1.5, 0.75), (1.5, 0.5), (1.0, 1.0),
+(0.75, 0.75)} where both divide every replica box (h = 1.5 stays the
+density-grid edge), block sizes {64, 128, 256}.
 """
 from __future__ import annotations
 
@@ -12,7 +13,7 @@ import torch
 
 from . import dcm as D
 
-EDGES = (1.5, 1.0, 0.75)
+EDGES = ((1.5, 1.5), (1.5, 0.75), (1.5, 0.5), (1.0, 1.0), (0.75, 0.75))
 BLOCKS = (64, 128, 256)
 
 
@@ -20,8 +21,8 @@ def divides(box, edge):
     return all(abs(round(L / edge) * edge - L) <= 1e-9 * L for L in box)
 
 
-def make_batch(boxes, counts, pos, vel, precision, K, edge, **kw):
-    p = D.make_params((1, 1, 1), precision=precision, recompute_every=K, l=edge, **kw)
+def make_batch(boxes, counts, pos, vel, precision, K, edge, lx=0.0, **kw):
+    p = D.make_params((1, 1, 1), precision=precision, recompute_every=K, l=edge, lx=lx, **kw)
     b = D.Batch(p, boxes, counts)
     real = b.real
     st = D.BatchState(b, D.to_real4(torch.from_numpy(pos), None, real), D.to_real4(torch.from_numpy(vel), None, real))
@@ -29,13 +30,13 @@ def make_batch(boxes, counts, pos, vel, precision, K, edge, **kw):
 
 
 def tune(boxes, counts, pos, vel, precision=D.DCM_PREC_MIXED, K=10, dt=0.005, steps=3, **kw):
-    """Returns (best (edge, block), {(edge, block): ms per step})."""
+    """Returns (best (edge, lx, block), {(edge, lx, block): ms per step})."""
     results = {}
     stream = torch.cuda.current_stream()
-    for edge in EDGES:
-        if not all(divides(b, edge) for b in boxes):
+    for edge, lx in EDGES:
+        if not all(divides(b, edge) and divides(b, lx) for b in boxes):
             continue
-        b, st = make_batch(boxes, counts, pos, vel, precision, K, edge, **kw)
+        b, st = make_batch(boxes, counts, pos, vel, precision, K, edge, lx, **kw)
         D.dcm_batch_step_init(b, st)
         for bs in BLOCKS:
             D.dcm_batch_set_force_block(b, bs)
@@ -45,7 +46,7 @@ def tune(boxes, counts, pos, vel, precision=D.DCM_PREC_MIXED, K=10, dt=0.005, st
             D.dcm_batch_step(b, st, dt, steps)
             e1.record(stream)
             e1.synchronize()
-            results[(edge, bs)] = e0.elapsed_time(e1) / steps
+            results[(edge, lx, bs)] = e0.elapsed_time(e1) / steps
         b.close()
     best = min(results, key=results.get)
     return best, results

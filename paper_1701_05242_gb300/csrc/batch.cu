@@ -89,7 +89,7 @@ __device__ __forceinline__ R wrapL(R x, R L) {
 }
 
 template <typename R>
-__device__ __forceinline__ Grid<R> rep_cells(const RepGeom& G, R l, R il) {
+__device__ __forceinline__ Grid<R> rep_cells(const RepGeom& G, R l, R il, R lx, R ilx) {
   Grid<R> g;
   for (int d = 0; d < 3; ++d) {
     g.n[d] = G.nc[d];
@@ -97,8 +97,8 @@ __device__ __forceinline__ Grid<R> rep_cells(const RepGeom& G, R l, R il) {
   }
   g.edge = l;
   g.inv_edge = il;
-  g.edge_x = l;  // replicas use cubic cells
-  g.inv_edge_x = il;
+  g.edge_x = lx;
+  g.inv_edge_x = ilx;
   g.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
   return g;
 }
@@ -107,7 +107,7 @@ __device__ __forceinline__ Grid<R> rep_cells(const RepGeom& G, R l, R il) {
 template <typename R>
 __global__ void k_b_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__ pos, typename RT<R>::R4* __restrict__ vel,
                                      const typename RT<R>::R4* __restrict__ force, R half_dt, R dt, R l, R il,
-                                     const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep,
+                                     R lx, R ilx, const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep,
                                      int32_t* __restrict__ cell, int32_t* __restrict__ slot, int32_t* __restrict__ count,
                                      int drift) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,7 +126,7 @@ __global__ void k_b_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__
     pos[i] = p;
     vel[i] = v;
   }
-  int cx = cell_coord<R>(p.x, l, il, G.nc[0]);
+  int cx = cell_coord<R>(p.x, lx, ilx, G.nc[0]);
   int cy = cell_coord<R>(p.y, l, il, G.nc[1]);
   int cz = cell_coord<R>(p.z, l, il, G.nc[2]);
   int c = (int)G.c0 + cx + G.nc[0] * (cy + G.nc[1] * cz);
@@ -446,7 +446,7 @@ __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const RepGeom& G = geom[rep[i]];
-  Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge);
+  Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge, a.g.edge_x, a.g.inv_edge_x);
   R e = 0, w = 0;
   int np = 0;
   force[i] = force_one<R, TYPED, X2>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
@@ -522,7 +522,7 @@ static int b_recompute(dcm_batch* b, const typename RT<R>::R4* pos, R* rc, cudaS
   int64_t n = b->ntot, nb = b->nbox_tot;
   unsigned gp = (unsigned)((n + 255) / 256), gb = (unsigned)((nb + 255) / 256);
   const int32_t* counts = ctx->cell_count;
-  if (p.h != p.l) {
+  if (p.h != p.l || p.lx != p.l) {
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->box_count, 0, sizeof(int32_t) * nb, st));
     if (n > 0)
       DCM_LAUNCH(ctx, k_b_box_count<R>, gp, 256, 0, st, n, pos, (R)p.h, (R)(1.0 / p.h), b->geom, b->rep_of_particle,
@@ -574,8 +574,8 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     ForceArgs<R> a;
     a.g.edge = (R)b->p.l;
     a.g.inv_edge = (R)(1.0 / b->p.l);
-    a.g.edge_x = a.g.edge;
-    a.g.inv_edge_x = a.g.inv_edge;
+    a.g.edge_x = (R)b->p.lx;
+    a.g.inv_edge_x = (R)(1.0 / b->p.lx);
     LJTable t = lj_table(b->p);
     a.ntypes = t.ntypes;
     for (int k = 0; k < 16; ++k) {
@@ -616,7 +616,8 @@ static int b_bin_gather(dcm_batch* b, dcm_state* s, bool drift, R hdt, R dt, cud
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cell_count, 0, sizeof(int32_t) * b->ncell_tot, st));
   if (n > 0)
     DCM_LAUNCH(ctx, k_b_kick_drift_count<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, (R4*)s->pos[c],
-               (R4*)s->vel[c], (const R4*)s->force, hdt, dt, (R)b->p.l, (R)(1.0 / b->p.l), b->geom,
+               (R4*)s->vel[c], (const R4*)s->force, hdt, dt, (R)b->p.l, (R)(1.0 / b->p.l), (R)b->p.lx,
+               (R)(1.0 / b->p.lx), b->geom,
                b->rep_of_particle, ctx->cell, ctx->slot, ctx->cell_count, drift ? 1 : 0);
   stage_end(ctx, DCM_STAGE_KICK_DRIFT, st);
   stage_begin(ctx, DCM_STAGE_BIN, st);
@@ -699,7 +700,6 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   *out = nullptr;
   if (p->skin != 0.0) return DCM_ERR_INVALID_ARG;  // the batched form steps over cell lists only
   if (p->min_component != 0) return DCM_ERR_INVALID_ARG;  // no bubble filter in the batched form
-  if (p->lx != 0.0 && p->lx != p->l) return DCM_ERR_INVALID_ARG;  // replicas use cubic cells
   std::vector<RepGeom> geom((size_t)R);
   int64_t ntot = 0, nctot = 0, nbtot = 0;
   for (int r = 0; r < R; ++r) {
@@ -719,7 +719,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
     for (int d = 0; d < 3; ++d) {
       G.nc[d] = (int)nc[d];
       G.nb[d] = (int)nb[d];
-      G.L[d] = (double)nc[d] * p->l;
+      G.L[d] = (double)nc[d] * (d == 0 && p->lx > 0.0 ? p->lx : p->l);
     }
     ntot += counts[r];
     nctot += nc[0] * nc[1] * nc[2];
@@ -730,6 +730,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   if (!b) return DCM_ERR_NOMEM;
   memset(&b->base, 0, sizeof(b->base));
   b->p = *p;
+  if (!(b->p.lx > 0.0)) b->p.lx = b->p.l;
   if (!(b->p.ramp > 0.0)) b->p.ramp = b->p.rc_max - b->p.rc_min;
   if (!(b->p.r_grid > 0.0)) b->p.r_grid = b->p.ramp + 2.0 * b->p.h;
   b->R = R;

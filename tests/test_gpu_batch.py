@@ -33,9 +33,9 @@ def replicas():
     return out
 
 
-def batch_state(D, reps, prec):
+def batch_state(D, reps, prec, lx=0.0):
     real = torch.float32 if prec == D.DCM_PREC_MIXED else torch.float64
-    p = D.make_params((1, 1, 1), precision=prec, recompute_every=K)
+    p = D.make_params((1, 1, 1), precision=prec, recompute_every=K, lx=lx)
     b = D.Batch(p, [s.box for s in reps], [s.n for s in reps])
     pos = np.concatenate([s.pos for s in reps])
     vel = np.concatenate([s.vel for s in reps])
@@ -43,9 +43,9 @@ def batch_state(D, reps, prec):
     return b, st
 
 
-def single_run(D, slab, prec, nsteps):
+def single_run(D, slab, prec, nsteps, lx=0.0):
     real = torch.float32 if prec == D.DCM_PREC_MIXED else torch.float64
-    ctx = D.Context(D.make_params(slab.box, n_max=slab.n, precision=prec, recompute_every=K))
+    ctx = D.Context(D.make_params(slab.box, n_max=slab.n, precision=prec, recompute_every=K, lx=lx))
     st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real), D.to_real4(torch.from_numpy(slab.vel), None, real))
     D.dcm_step_init(ctx, st)
     D.dcm_step(ctx, st, DT, nsteps)
@@ -64,16 +64,17 @@ def by_id(st, b, r):
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batch_matches_single_systems(D, replicas, prec):
+@pytest.mark.parametrize("lx", [0.0, 0.75])
+def test_batch_matches_single_systems(D, replicas, prec, lx):
     P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
     nsteps = 2 * K + 2
-    b, st = batch_state(D, replicas, P)
+    b, st = batch_state(D, replicas, P, lx)
     D.dcm_batch_step_init(b, st)
     D.dcm_batch_step(b, st, DT, nsteps)
     assert D.dcm_batch_status(b) == D.DCM_OK
     th = st.thermo.cpu().numpy().reshape(-1, 4)
     for r, slab in enumerate(replicas):
-        pos1, th1 = single_run(D, slab, P, nsteps)
+        pos1, th1 = single_run(D, slab, P, nsteps, lx)
         pb = by_id(st, b, r)
         assert np.abs(pb - pos1).max() <= (1e-12 if prec == "fp64" else 1e-5)
         tol = 1e-10 if prec == "fp64" else 1e-6
@@ -102,8 +103,9 @@ def test_batch_graph_replay_equals_stepping(D, replicas):
     assert D.dcm_batch_status(b2) == D.DCM_OK
 
 
-def test_batch_fp64_tracks_oracle(D, replicas):
-    b, st = batch_state(D, replicas, D.DCM_PREC_FP64)
+@pytest.mark.parametrize("lx", [0.0, 0.5])
+def test_batch_fp64_tracks_oracle(D, replicas, lx):
+    b, st = batch_state(D, replicas, D.DCM_PREC_FP64, lx)
     D.dcm_batch_step_init(b, st)
     D.dcm_batch_step(b, st, DT, 3)
     th = st.thermo.cpu().numpy().reshape(-1, 4)
