@@ -61,6 +61,7 @@ def parse_args(argv=None):
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-lists", action="store_true")
+    ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args(argv)
 
@@ -286,6 +287,67 @@ def run_batch(args, D, dev):
     return out
 
 
+def run_adjoint(args, D, dev):
+    """Differentiation form on the two-type workload (260,522 particles,
+    per-type eps and sigma, Lorentz-Berthelot): cutoffs from the method's own
+    stages, then the force evaluation and the hand-written adjoint of
+    L = sum_i |F_i|^2 + E (cutoffs held fixed), each timed with CUDA events on
+    the launching stream, in both precision forms."""
+    import torch
+    from paper_1701_05242_gb300 import synth
+    slab = synth.make_slab(synth.named("slab_256k_2types"))
+    n = slab.n
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "slab_256k_2types", "particles": n, "unit": "particle-gradients/s",
+           "loss": "sum_i |F_i|^2 + E, cutoffs held fixed"}
+    for prec, key in ((D.DCM_PREC_MIXED, "mixed"), (D.DCM_PREC_FP64, "fp64")):
+        p = D.make_params(slab.box, n_max=n, precision=prec, ntypes=2, eps=(1.0, 0.8), sigma=(1.0, 1.1),
+                          l=args.cell_edge, lx=args.cell_edge_x)
+        ctx = D.Context(p)
+        real = ctx.real
+        pos4 = D.to_real4(torch.from_numpy(slab.pos), torch.from_numpy(slab.types), real, dev)
+        i32 = dict(dtype=torch.int32, device=dev)
+        cell, start, perm = torch.empty(n, **i32), torch.empty(ctx.ncell + 1, **i32), torch.empty(n, **i32)
+        ps = torch.empty_like(pos4)
+        D.dcm_bin(ctx, n, pos4, cell, start, perm, ps)
+        bc, g = torch.empty(ctx.nbox, **i32), torch.empty(ctx.nbox, **i32)
+        s = torch.empty(ctx.nbox, dtype=torch.uint8, device=dev)
+        iface = torch.empty_like(s)
+        thr = torch.empty(1, **i32)
+        D.dcm_box_counts(ctx, n, ps, bc)
+        D.dcm_detect_interface(ctx, bc, s, iface, thr, g)
+        dist = torch.empty(ctx.nbox, dtype=real, device=dev)
+        D.dcm_distance(ctx, s, iface, dist)
+        rc = torch.empty(n, dtype=real, device=dev)
+        D.dcm_cutoffs(ctx, n, ps, dist, rc)
+        F = torch.empty_like(ps)
+        tot = torch.zeros(3, dtype=torch.float64, device=dev)
+        A = torch.zeros_like(ps)
+        G = torch.empty_like(ps)
+        dpar = torch.zeros(4, dtype=torch.float64, device=dev)
+        reps = 10 if prec == D.DCM_PREC_MIXED else 3
+        fwd_ms = bwd_ms = 0.0
+        for it in range(3 + reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            D.dcm_forces(ctx, n, ps, rc, start, F, tot)
+            ev[1].record(stream)
+            A[:, :3] = 2.0 * F[:, :3]  # dL/dF
+            ev[2].record(stream)
+            D.dcm_forces_backward(ctx, n, ps, rc, start, A, 1.0, G, dpar)
+            ev[3].record(stream)
+            ev[3].synchronize()
+            if it >= 3:
+                fwd_ms += ev[0].elapsed_time(ev[1]) / reps
+                bwd_ms += ev[2].elapsed_time(ev[3]) / reps
+        out[key] = {"forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+                    "value": n / ((fwd_ms + bwd_ms) / 1000.0), "device_status": D.dcm_status(ctx)}
+        ctx.close()
+    out["value"] = out["mixed"]["value"]
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -467,12 +529,15 @@ def run_gb300(args):
         ctx, st = new_state(D.DCM_PREC_MIXED)
 
     # ---------------- batched form: 64 replicas, autotuned, graph-captured
-    batch = None
-    if not args.skip_batch:
+    batch = adjoint = None
+    if not args.skip_batch or not args.skip_adjoint:
         del st
         ctx.close()
         torch.cuda.empty_cache()
+    if not args.skip_batch:
         batch = run_batch(args, D, dev)
+    if not args.skip_adjoint and rank == 0:
+        adjoint = run_adjoint(args, D, dev)
 
     # ---------------- CPU oracle on the host cores (rank 0, N = 1)
     cpu = None
@@ -497,7 +562,8 @@ def run_gb300(args):
                           "precision": "fp32 pair math, fp64 totals", "l2": f"inputs larger than L2 (positions {16 * n / 1e6:.0f} MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "stage_ms_per_step": stage_ms, "step_roofline": step_roof, "fp64_form": fp64, "lists_form": lists, "batched_form": batch, "device_status": status,
+               "stage_ms_per_step": stage_ms, "step_roofline": step_roof, "fp64_form": fp64, "lists_form": lists, "batched_form": batch,
+               "adjoint_form": adjoint, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}
         print(json.dumps(out), flush=True)
