@@ -9,10 +9,14 @@
 // (symmetric) Jacobian, g = 24 eps [2 s12 - s6] / r^2 and
 // g'/r = 24 eps [-28 s12 + 8 s6] / r^4 with s6 = (sigma/r)^6, s12 = s6^2.
 // Because the cutoffs differ per particle the second (reverse) sum runs over
-// the j whose own cutoff reaches k: one thread per k walks the stencil of
-// radius rc_max, and every candidate is tested against both rc_k (forward
-// pair) and rc_j (reverse pair).  The forward force itself is not needed:
-// only A and dLdE enter.
+// the j whose own cutoff reaches k: one thread per k walks the stencil of a
+// radius that bounds every such rc_j, and every candidate is tested against
+// both rc_k (forward pair) and rc_j (reverse pair).  The bound is the largest
+// cutoff in the 27 blocks around k, blocks of edge at least 1.001 rc_max
+// (a j with |r_kj| < rc_j <= rc_max lies in one of them), so away from the
+// interfaces, where every cutoff is rc_min, the walk covers the rc_min
+// sphere instead of the rc_max one.  The forward force itself is not
+// needed: only A and dLdE enter.
 //
 // Parameter gradients per type pair p of every forward pair (k, j in N(k)):
 //   dL/deps_p   += A_k . phi_kj / eps_p + dLdE/2 (U - U(rc_k) if shifted) / eps_p
@@ -24,6 +28,36 @@
 #include "forces_core.cuh"
 
 namespace dcm {
+
+// Blocks of the reverse-pair bound: nb[d] per axis of edge L[d] / nb[d].
+struct BlockGrid {
+  int nb[3];
+  float inv_be[3];
+};
+
+__device__ __forceinline__ int block_coord(float x, float inv_be, int nb) {
+  return (int)fminf(fmaxf(floorf(x * inv_be), 0.f), (float)(nb - 1));  // NaN -> 0
+}
+
+__device__ __forceinline__ float up_float(float v) { return v; }
+__device__ __forceinline__ float up_float(double v) { return __double2float_ru(v); }
+
+// Largest cutoff of each block (float bits: the order of positive floats is
+// the order of their bit patterns), rounded up from FP64.
+template <typename R>
+__global__ void k_block_max(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
+                            R rc_max, BlockGrid bg, int32_t* __restrict__ bmax) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto p = ldg4(pos + i);
+  R v = rc[i];
+  if (!(v <= rc_max)) v = rc_max;
+  if (!(v > (R)0)) v = (R)0;
+  const int bx = block_coord((float)p.x, bg.inv_be[0], bg.nb[0]);
+  const int by = block_coord((float)p.y, bg.inv_be[1], bg.nb[1]);
+  const int bz = block_coord((float)p.z, bg.inv_be[2], bg.nb[2]);
+  atomicMax(bmax + bx + bg.nb[0] * (by + bg.nb[1] * bz), __float_as_int(up_float(v)));
+}
 
 template <typename R>
 struct AdjAcc {
@@ -100,7 +134,8 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
                                                  const R* __restrict__ rc, const int32_t* __restrict__ start,
                                                  ForceArgs<R> a, const typename RT<R>::R4* __restrict__ A,
                                                  R half_dlde, typename RT<R>::R4* __restrict__ G,
-                                                 double* __restrict__ part, int64_t nwarp) {
+                                                 double* __restrict__ part, int64_t nwarp, BlockGrid bg,
+                                                 const int32_t* __restrict__ bmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int np = a.ntypes * a.ntypes;
   AdjAcc<R> c;
@@ -115,7 +150,25 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
     if (!(rck <= a.rc_max)) rck = a.rc_max;
     if (!(rck > (R)0)) rck = (R)0;
     const R rck2 = rck * rck;
-    const R reach = a.rc_max;  // reverse pairs: any j's cutoff, at most rc_max
+    R reach = a.rc_max;  // reverse pairs: the largest cutoff around k
+    if (bmax) {
+      const int bx = block_coord((float)pi.x, bg.inv_be[0], bg.nb[0]);
+      const int by = block_coord((float)pi.y, bg.inv_be[1], bg.nb[1]);
+      const int bz = block_coord((float)pi.z, bg.inv_be[2], bg.nb[2]);
+      float m = 0.f;
+      for (int dz = -1; dz <= 1; ++dz) {
+        const int zz = (bz + dz + bg.nb[2]) % bg.nb[2];
+        for (int dy = -1; dy <= 1; ++dy) {
+          const int yy = (by + dy + bg.nb[1]) % bg.nb[1];
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int xx = (bx + dx + bg.nb[0]) % bg.nb[0];
+            m = fmaxf(m, __int_as_float(__ldg(bmax + xx + bg.nb[0] * (yy + bg.nb[1] * zz))));
+          }
+        }
+      }
+      reach = (R)m < reach ? (R)m : reach;
+      if (reach < rck) reach = rck;
+    }
     const R reach2s = reach * reach * (R)1.000004;
     const int tk = TYPED ? type_of(pi.w, a.ntypes) : 0;
     R ucsh[4] = {0, 0, 0, 0}, ducsh[4] = {0, 0, 0, 0};
@@ -240,8 +293,16 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   if (want && nwarp > ctx->red_cap)
     return set_error(ctx, DCM_ERR_CAPACITY, "adjoint reduction needs %lld partials", (long long)nwarp);
   double* part = want ? ctx->adj_part : nullptr;  // [32][nwarp]: de pairs 0..15, ds pairs 16..31
+  BlockGrid bg;
+  for (int d = 0; d < 3; ++d) {
+    bg.nb[d] = ctx->nblk3[d];
+    bg.inv_be[d] = (float)((double)ctx->nblk3[d] / ctx->p.box[d]);
+  }
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->blk_max, 0, sizeof(int32_t) * ctx->nblk, st));
+  DCM_LAUNCH(ctx, k_block_max<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, pos, rc, a.rc_max, bg, ctx->blk_max);
   auto kern = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
-  DCM_LAUNCH(ctx, kern, (unsigned)nblk, 128, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part, nwarp);
+  DCM_LAUNCH(ctx, kern, (unsigned)nblk, 128, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part, nwarp, bg,
+             (const int32_t*)ctx->blk_max);
   int r = check_launch(ctx, "lj_adjoint");
   if (r || !want) return r;
   int npair = nt * nt;

@@ -155,6 +155,14 @@ extern "C" int dcm_params_default(dcm_params* p) {
   return DCM_OK;
 }
 
+// Blocks of the adjoint's reverse-pair bound along axis d: edge at least
+// 1.001 rc_max, so that any particle within rc_max of another lies in one of
+// the 27 blocks around it even after the rounding of the block index.
+static int64_t adjoint_blocks(const dcm_params* p, int d) {
+  int64_t k = (int64_t)std::floor(p->box[d] / (1.001 * p->rc_max));
+  return k < 1 ? 1 : k;
+}
+
 // Cell edge along axis d: lx along x when it is set, l otherwise.
 static double cell_edge(const dcm_params* p, int d) { return d == 0 && p->lx > 0.0 ? p->lx : p->l; }
 
@@ -237,14 +245,14 @@ extern "C" int dcm_grid_dims(const dcm_params* p, int64_t* cells3, int64_t* boxe
 }
 
 struct ScratchPlan {
-  int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags;
+  int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags, nblk;
   double skin;
   int32_t min_component;
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
            8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
-           (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2);
+           (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2) + 4 * nblk;
   }
 };
 
@@ -265,6 +273,7 @@ static ScratchPlan plan_of(const dcm_params* p) {
   s.flags = p->iter_max + 2;
   s.skin = p->skin;
   s.min_component = p->min_component;
+  s.nblk = adjoint_blocks(p, 0) * adjoint_blocks(p, 1) * adjoint_blocks(p, 2);
   return s;
 }
 
@@ -288,7 +297,7 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
                  ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
                  ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0, ctx->dq[0], ctx->dq[1], ctx->dqlen,
-                 ctx->dstamp, ctx->dfixed};
+                 ctx->dstamp, ctx->dfixed, ctx->blk_max};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -370,6 +379,9 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
     alloc((void**)&ctx->cc_s0, s.nbox);
   }
   alloc((void**)&ctx->adj_pairs, 8 * 48);
+  for (int d = 0; d < 3; ++d) ctx->nblk3[d] = (int)adjoint_blocks(p, d);  // as counted in the plan
+  ctx->nblk = s.nblk;
+  alloc((void**)&ctx->blk_max, 4 * s.nblk);
   if (ok && cudaMallocHost((void**)&ctx->host_status, 16) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();

@@ -114,6 +114,9 @@ struct dcm_ctx {
   double* totals;           // [4]
   int32_t* host_status;     // pinned host mirror
   int64_t red_cap;          // number of partial slots in red (per quantity)
+  int32_t* blk_max;         // nblk: largest cutoff (float bits) per adjoint block
+  int nblk3[3];             // adjoint blocks per dimension (edge >= 1.001 rc_max)
+  int64_t nblk;
   int64_t scan_cap;
   int64_t launches;         // kernels launched through this context
   // Verlet lists (params.skin > 0)

@@ -134,12 +134,7 @@ def gpu_setup(D, slab, rc64, prec, shift=False, lx=0.0):
     return ctx, ps, rcs, start, permh, rc_in
 
 
-@pytest.mark.gpu
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-@pytest.mark.parametrize("lx", [0.0, 0.75])
-def test_gpu_adjoint_matches_oracle(small2, prec, lx):
-    import paper_1701_05242_gb300.dcm as D
-    slab, rc = small2
+def gpu_adjoint_against_oracle(D, slab, rc, prec, lx=0.0):
     P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
     ctx, ps, rcs, start, perm, rc_in = gpu_setup(D, slab, rc, P, lx=lx)
     n = slab.n
@@ -164,6 +159,31 @@ def test_gpu_adjoint_matches_oracle(small2, prec, lx):
     else:
         assert err <= 1e-10
         assert np.allclose(d[:2], de, rtol=1e-10) and np.allclose(d[2:], ds, rtol=1e-10)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("lx", [0.0, 0.75])
+def test_gpu_adjoint_matches_oracle(small2, prec, lx):
+    import paper_1701_05242_gb300.dcm as D
+    slab, rc = small2
+    gpu_adjoint_against_oracle(D, slab, rc, prec, lx)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_gpu_adjoint_with_the_method_cutoffs(prec):
+    """Cutoffs from the method itself on a slab thick enough for a bulk at
+    rc_min far from both interfaces: there the reverse-pair walk is bounded
+    by the blocks' largest cutoff instead of rc_max, and the gradients must
+    still match the oracle's all-pairs adjoint."""
+    import paper_1701_05242_gb300.dcm as D
+    spec = synth.named("slab_256k_2types")
+    spec.box = (13.5, 13.5, 108.0)
+    slab = synth.make_slab(spec)
+    rc = O.assign_cutoffs(slab.pos, O.Params(box=slab.box))["rc"]
+    assert (rc <= 3.0).mean() > 0.3  # a bulk at rc_min, beyond a block of the interfaces
+    gpu_adjoint_against_oracle(D, slab, rc, prec)
 
 
 @pytest.mark.gpu
