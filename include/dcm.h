@@ -269,7 +269,9 @@ int dcm_set_lj(dcm_ctx* ctx, int32_t ntypes, const double* eps, const double* si
  *              + sum_{j : k in N(j)} [-J(r_kj) A_j - dL_dE/2 phi_kj]
  * with N(i) = {j != i : |r_ij| < rc_i}, phi_ij the pair force on i and J its
  * Jacobian (the second sum runs over the particles whose own cutoff reaches
- * k, so the stencil has radius rc_max).  dL_dparams (device double[2 ntypes],
+ * k: the stencil's radius is the largest cutoff within the 27 blocks of edge
+ * >= 1.001 rc_max around k, found in the context's scratch, so concurrent
+ * calls on one context must not overlap).  dL_dparams (device double[2 ntypes],
  * nullable) receives dL/deps_a then dL/dsigma_a, chained through
  * Lorentz-Berthelot mixing.  Inputs as for dcm_forces (sorted order). */
 int dcm_forces_backward(dcm_ctx* ctx, int64_t n, const void* pos_sorted, const void* rc, const int32_t* cell_start,
