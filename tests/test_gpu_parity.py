@@ -588,6 +588,64 @@ def test_step_batched_call_equals_single_calls(D, slab_1935, prec):
     assert torch.equal(st1.current()[1], st2.current()[1])
 
 
+def test_jobs_on_two_states_and_a_copy_stream(D, slab_1935):
+    """A stream of jobs as an end-to-end user runs them: two States share one
+    context, each job copies its state in from pinned host memory on a copy
+    stream, runs dcm_step_init + 10 timesteps on the compute stream and copies
+    state and thermo back out; the copies of neighbouring jobs overlap the
+    compute.  Every job must give, bit for bit, what one State stepped alone
+    gives for the same input."""
+    P = D.DCM_PREC_MIXED
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n, P, recompute_every=10, lx=0.75)
+    pos_h = D.to_real4(torch.from_numpy(slab_1935.pos), None, torch.float32, "cpu").pin_memory()
+    vel_h = D.to_real4(torch.from_numpy(slab_1935.vel), None, torch.float32, "cpu").pin_memory()
+    ref = D.State(ctx, pos_h.cuda(), vel_h.cuda())
+    D.dcm_step_init(ctx, ref)
+    D.dcm_step(ctx, ref, 0.005, 10)
+    torch.cuda.synchronize()
+    rp, rv = ref.current()[0].cpu(), ref.current()[1].cpu()
+    rt = ref.thermo.cpu()
+    sts = [D.State(ctx, pos_h.cuda(), vel_h.cuda()) for _ in range(2)]
+    comp, cs = torch.cuda.current_stream(), torch.cuda.Stream()
+    h2d = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    outs = [(torch.empty_like(pos_h).pin_memory(), torch.empty_like(vel_h).pin_memory(),
+             torch.empty(4, dtype=torch.float64).pin_memory()) for _ in range(2)]
+    jobs, results = 5, []
+
+    def copy_in(j):
+        s = sts[j % 2]
+        with torch.cuda.stream(cs):
+            s.pos[s.c.cur].copy_(pos_h, non_blocking=True)
+            s.vel[s.c.cur].copy_(vel_h, non_blocking=True)
+            h2d[j % 2].record(cs)
+
+    copy_in(0)
+    for j in range(jobs):
+        if j + 1 < jobs:
+            copy_in(j + 1)
+        s = sts[j % 2]
+        comp.wait_event(h2d[j % 2])
+        D.dcm_step_init(ctx, s, comp)
+        D.dcm_step(ctx, s, 0.005, 10, comp)
+        done[j % 2].record(comp)
+        cs.wait_event(done[j % 2])
+        po, vo, to = outs[j % 2]
+        with torch.cuda.stream(cs):
+            po.copy_(s.pos[s.c.cur], non_blocking=True)
+            vo.copy_(s.vel[s.c.cur], non_blocking=True)
+            to.copy_(s.thermo, non_blocking=True)
+        if j >= 1:  # the previous job's copies out, read once they landed
+            cs.synchronize()
+            results.append(tuple(x.clone() for x in outs[(j - 1) % 2]))
+    torch.cuda.synchronize()
+    results.append(tuple(x.clone() for x in outs[(jobs - 1) % 2]))
+    assert D.dcm_status(ctx) == D.DCM_OK
+    assert len(results) == jobs
+    for po, vo, to in results:
+        assert torch.equal(po, rp) and torch.equal(vo, rv) and torch.equal(to, rt)
+
+
 def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5, lx=0.0):
     ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, skin=skin, rc_max=rc_max, lx=lx)
     real = real_of(D, P)
