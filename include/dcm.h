@@ -71,7 +71,8 @@ enum dcm_status_code {
 /* Cell-list force kernels (all walk the same culled cell rows and accept the
  * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2
  * to 5 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
- * ntypes = 1) and fall back to kernel 1 otherwise. */
+ * ntypes = 1); kernel 3 also serves FP32 runs of one or two types with their
+ * own eps and sigma; otherwise kernel 1 runs. */
 enum {
   DCM_FORCE_AUTO = 0,        /* kernel 3 where it applies, else kernel 1 */
   DCM_FORCE_THREAD = 1,      /* one thread per particle i, one candidate per instruction */

@@ -72,6 +72,19 @@ __global__ void __launch_bounds__(kX2Block, 16) k_forces_x2(int64_t n, const flo
   if (part) warp_partials3<float>(e_out, w_out, np, part, nwarp);
 }
 
+// The packed walk for one or two types with per-type eps and sigma (FP32).
+__global__ void __launch_bounds__(kX2Block, 16) k_forces_x2t(int64_t n, const float4* __restrict__ pos,
+                                                             const float* __restrict__ rc,
+                                                             const int32_t* __restrict__ start, ForceArgs<float> a,
+                                                             float4* __restrict__ force, double* __restrict__ part,
+                                                             int64_t nwarp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float e_out = 0, w_out = 0;
+  int np = 0;
+  if (i < n) force[i] = force_one<float, true, true>(pos, start, a.g, a, (int)i, __ldg(pos + i), rc[i], e_out, w_out, np);
+  if (part) warp_partials3<float>(e_out, w_out, np, part, nwarp);
+}
+
 // ----------------------------------------------------------------------------
 // Tile kernel (one type, FP32): the warp's 32 particles share one x-line of
 // cells, so for every row offset (dy, dz) their windows lie in one grid row;
@@ -486,11 +499,15 @@ __global__ void __launch_bounds__(kF2Block) k_forces2(int64_t n, const float4* _
   if (part) warp_partials3<float>(e_out, w_out, c.np, part, nwarp);
 }
 
-// Kernels 2 to 5 serve one-type mixed-precision runs with eps = sigma = 1.
+// Kernels 2 to 5 serve one-type mixed-precision runs with eps = sigma = 1;
+// kernel 3 also serves mixed runs of one or two types with their own eps and
+// sigma (its typed packed loop).
 int resolve_force_kernel(const dcm_ctx* ctx) {
   int k = force_kernel_choice(ctx->p);
   if (k == DCM_FORCE_THREAD) return k;
-  if (ctx->p.precision != DCM_PREC_MIXED || lj_general(lj_table(ctx->p))) return DCM_FORCE_THREAD;
+  if (ctx->p.precision != DCM_PREC_MIXED) return DCM_FORCE_THREAD;
+  const LJTable t = lj_table(ctx->p);
+  if (lj_general(t)) return k == DCM_FORCE_PACKED && t.ntypes <= 2 ? k : DCM_FORCE_THREAD;
   return k;
 }
 
@@ -531,6 +548,11 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
       static_assert(32 * kTileWarps == kForceBlock, "partials layout assumes equal blocks");
       DCM_LAUNCH(ctx, k_forces_tile, (unsigned)nblk, kForceBlock, 0, st, n, pos, rc, cell_start, af, force, part,
                  nwarp);
+      done = true;
+    } else if (kind == DCM_FORCE_PACKED && lj_general(t)) {
+      const int64_t nblk2 = (n + kX2Block - 1) / kX2Block;
+      nwarp = nblk2 * (kX2Block / 32);
+      DCM_LAUNCH(ctx, k_forces_x2t, (unsigned)nblk2, kX2Block, 0, st, n, pos, rc, cell_start, af, force, part, nwarp);
       done = true;
     } else if (kind == DCM_FORCE_PACKED) {
       const int64_t nblk2 = (n + kX2Block - 1) / kX2Block;  // no more warps than the 128-thread grid

@@ -168,6 +168,64 @@ __device__ __forceinline__ void pair_x2(const float4& p0, const float4& p1, bool
   pair_x2_d(dx, dy, dz, m0, m1, rc2, c);
 }
 
+// The packed step for up to two types: the constants of the pair type of
+// each slot (sigma^2, 24 eps, 4 eps and the energy shift) are picked from the
+// two of particle i's row by the slot's type; m0, m1 as in pair_x2_d.
+__device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, float2 sg,
+                                           float2 e24, float2 e4, float2 us, Acc2& c) {
+  const float2 two = make_float2(2.f, 2.f), m1f = make_float2(-1.f, -1.f);
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  float y0, y1;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+  float2 y = make_float2(y0, y1);
+  const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, make_float2(1.f, 1.f));
+  y = __ffma2_rn(y, e, y);
+  const bool a0 = m0 && r2.x < rc2, a1 = m1 && r2.y < rc2;
+  y = make_float2(a0 ? y.x : 0.f, a1 ? y.y : 0.f);
+  us = make_float2(a0 ? us.x : 0.f, a1 ? us.y : 0.f);
+  const float2 s2 = __fmul2_rn(sg, y);
+  const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+  const float2 pv = __fmul2_rn(e24, __fmul2_rn(s6, __ffma2_rn(s6, two, m1f)));  // r . F_ij
+  const float2 q = __fmul2_rn(pv, y);
+  c.fx = __ffma2_rn(q, dx, c.fx);
+  c.fy = __ffma2_rn(q, dy, c.fy);
+  c.fz = __ffma2_rn(q, dz, c.fz);
+  c.en = __fadd2_rn(c.en, __ffma2_rn(e4, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), make_float2(-us.x, -us.y)));
+  c.vir = __fadd2_rn(c.vir, pv);
+  c.np += (int)a0 + (int)a1;
+}
+
+// Typed form of pair_range_x2 for one or two types.  k8 holds particle i's
+// row: k8[t] the energy shift, k8[2 + t] sigma^2, k8[4 + t] 24 eps, k8[6 + t]
+// 4 eps of the pair type (type of i, t); a candidate's type is 1 if its w is
+// at least 1 (type_of clamped to two types), and with one type both columns
+// are equal.
+template <bool SJ>
+__device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
+                                               float zi, float shx, float shy, float shz, float rc2,
+                                               const float* k8, Acc2& c) {
+  for (int j = lo; j < hi; j += 2) {
+    const bool has1 = j + 1 < hi;
+    const int j1 = has1 ? j + 1 : j;
+    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j1);
+    float2 dx, dy, dz;
+    if (SJ) {
+      dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
+      dy = make_float2((p0.y + shy) - yi, (p1.y + shy) - yi);
+      dz = make_float2((p0.z + shz) - zi, (p1.z + shz) - zi);
+    } else {
+      dx = make_float2(p0.x - xi, p1.x - xi);
+      dy = make_float2(p0.y - yi, p1.y - yi);
+      dz = make_float2(p0.z - zi, p1.z - zi);
+    }
+    const bool t0 = p0.w >= 1.f, t1 = p1.w >= 1.f;
+    pair_x2_dt(dx, dy, dz, true, has1, rc2, make_float2(t0 ? k8[3] : k8[2], t1 ? k8[3] : k8[2]),
+               make_float2(t0 ? k8[5] : k8[4], t1 ? k8[5] : k8[4]), make_float2(t0 ? k8[7] : k8[6], t1 ? k8[7] : k8[6]),
+               make_float2(t0 ? k8[1] : k8[0], t1 ? k8[1] : k8[0]), c);
+  }
+}
+
 // STAGED: pos points into a shared-memory tile (plain loads) instead of
 // global memory (read-only cached loads).
 template <bool SJ, bool STAGED = false>
@@ -181,13 +239,15 @@ __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, in
   }
 }
 
-// Segment dispatch: the packed loop for one-type FP32, the scalar loop
-// otherwise.
+// Segment dispatch: the packed loop for FP32 (one type, or up to two types
+// with the row constants in ushift[0 .. 7]), the scalar loop otherwise.
 template <typename R, bool SJ, bool TYPED, bool X2>
 __device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi, R zi,
                                         R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a, const R* ushift,
                                         Acc<R>& c, Acc2& c2) {
-  if constexpr (X2) {
+  if constexpr (X2 && TYPED) {
+    pair_range_x2t<SJ>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2);
+  } else if constexpr (X2) {
     pair_range_x2<SJ>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2);
   } else {
     pair_range<R, SJ, TYPED>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
@@ -291,19 +351,29 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
                                                         const ForceArgs<R>& a, int self,
                                                         const typename RT<R>::R4& pi, R rc_in, R& e_out, R& w_out,
                                                         int& np_out) {
-  static_assert(!X2 || (sizeof(R) == 4 && !TYPED), "the packed loop serves one-type FP32 only");
+  static_assert(!X2 || sizeof(R) == 4, "the packed loop serves FP32 only (with types: at most two)");
   Acc<R> c;
   Acc2 c2;
   const R rci = clamp_cutoff<R>(rc_in, a.rc_max);
   const R rc2 = rci * rci;
   const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
-  R ushift[4] = {0, 0, 0, 0};
+  R ushift[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (a.shift && rc2 > (R)0) {  // no pairs at rc = 0: no shift either
     for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
       int tp = ti * a.ntypes + t;
       R s2 = (TYPED ? a.sig2[tp] : (R)1) / rc2;
       R s6 = s2 * s2 * s2;
       ushift[t] = (TYPED ? a.eps4[tp] : (R)4) * s6 * (s6 - (R)1);
+    }
+  }
+  if constexpr (X2 && TYPED) {  // particle i's row for the packed typed loop (one or two types)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int tc = t < a.ntypes ? t : a.ntypes - 1, tp = ti * a.ntypes + tc;
+      ushift[t] = ushift[tc];
+      ushift[2 + t] = a.sig2[tp];
+      ushift[4 + t] = a.eps24[tp];
+      ushift[6 + t] = a.eps4[tp];
     }
   }
   walk_rows<R, TYPED, X2>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2);

@@ -302,21 +302,50 @@ def test_forces_uniform_and_shift(D, slab_1935, prec):
     assert np.abs(Fg[:, :3].sum(0)).max() <= (1e-5 if prec == "mixed" else 1e-10) * np.abs(Fg[:, :3]).sum()
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_forces_two_types(D, prec):
+@pytest.mark.parametrize("prec,kernel,shift", [("mixed", 1, 0), ("mixed", 3, 0), ("mixed", 3, 1), ("fp64", 0, 0)])
+def test_forces_two_types(D, prec, kernel, shift):
+    """Two types with Lorentz-Berthelot mixing: the scalar loop (kernel 1),
+    the packed typed loop (kernel 3, also with the shifted energy) and FP64."""
     spec = synth.named("slab_256k_2types")
     spec.box = (18.0, 18.0, 72.0)
     slab = synth.make_slab(spec)
     rng = np.random.default_rng(3)
     rc64 = rng.uniform(3.0, 6.0, slab.n)
-    Fg, tot, ref, rc_in = forces_case(D, slab, prec, rc64, types=slab.types, eps=(1.0, 0.8), sigma=(1.0, 1.1))
+    Fg, tot, ref, rc_in = forces_case(D, slab, prec, rc64, types=slab.types, eps=(1.0, 0.8), sigma=(1.0, 1.1),
+                                      kernel=kernel, shift=shift)
     if prec == "mixed":
         assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
         assert abs(tot[0] - ref.E) <= EW_TOL * abs(ref.E)
         assert abs(tot[1] - ref.W) <= EW_TOL * abs(ref.W)
+        assert np.abs(Fg[:, 3] - ref.e).max() <= 1e-5 * np.abs(ref.e).max()
+        assert abs(int(tot[2]) - ref.npairs) <= near_cutoff_pairs(slab.pos, rc_in, slab.box)
     else:
         assert np.abs(Fg[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
         assert int(tot[2]) == ref.npairs
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_forces_one_type_scaled(D, slab_1935, kernel, shift):
+    """One type with eps and sigma other than 1: the scalar loop and the
+    packed typed loop (both columns of its row equal).  With sigma = 1.05 the
+    0.85 placement puts pairs at 0.81 sigma, deep in the repulsive wall, and
+    a few pair energies of ~30 dominate E; each carries the FP32 rounding of
+    (sigma^2 / r^2)^6 (a dozen roundings of 2^-24), which does not average
+    out over so few terms, so E and W are held to 32 u32 sum |e_i| (and the
+    same relative share for W) instead of the 1e-7 of the sigma = 1 slabs."""
+    p = O.Params(box=slab_1935.box)
+    rc64 = O.assign_cutoffs(slab_1935.pos, p)["rc"]
+    Fg, tot, ref, rc_in = forces_case(D, slab_1935, "mixed", rc64, eps=(0.9,), sigma=(1.05,), shift=shift,
+                                      kernel=kernel)
+    u32 = 2.0 ** -24
+    bound = 32 * u32 * np.abs(ref.e).sum()
+    print(f"ERR scaled one type kernel {kernel} shift {shift}: E {abs(tot[0] - ref.E) / abs(ref.E):.3g} "
+          f"W {abs(tot[1] - ref.W) / abs(ref.W):.3g} (rel), bound {bound / abs(ref.E):.3g}")
+    assert rms_rel(Fg[:, :3], ref.F) <= F_RMS_TOL
+    assert abs(tot[0] - ref.E) <= bound
+    assert abs(tot[1] - ref.W) <= bound / abs(ref.E) * abs(ref.W)
+    assert np.abs(Fg[:, 3] - ref.e).max() <= 1e-5 * np.abs(ref.e).max()
 
 
 @pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
