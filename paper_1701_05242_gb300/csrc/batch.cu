@@ -587,8 +587,10 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     a.rc_max = (R)b->p.rc_max;
     int bs = b->force_block;
     // one type in FP32: the packed two-candidates-per-instruction pair loop
-    auto kern = lj_general(t) ? k_b_forces<R, true, false>
-                              : (sizeof(R) == 4 ? k_b_forces<R, false, sizeof(R) == 4> : k_b_forces<R, false, false>);
+    // the packed loop in FP32 for one type, and for one or two types with
+    // their own eps and sigma; the scalar loop otherwise
+    auto kern = lj_general(t) ? (t.ntypes <= 2 ? k_b_forces<R, true, sizeof(R) == 4> : k_b_forces<R, true, false>)
+                              : k_b_forces<R, false, sizeof(R) == 4>;
     stage_begin(ctx, DCM_STAGE_FORCES, st);
     DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
                b->rep_of_particle, force, (R*)b->w_i, b->np_i);

@@ -83,6 +83,42 @@ def test_batch_matches_single_systems(D, replicas, prec, lx):
         assert th[r, 3] == th1[3]
 
 
+def test_batch_two_types_matches_single_systems(D):
+    """Replicas of two types (Lorentz-Berthelot mixing, the packed typed
+    loop in both paths) evolve as the same systems stepped alone."""
+    reps = []
+    for r, L in enumerate((12.0, 13.5)):
+        spec = synth.SlabSpec(box=(L, L, 4 * L), ntypes=2, seed=10 + r, name=f"typed{r}")
+        reps.append(synth.make_slab(spec))
+    kw = dict(precision=D.DCM_PREC_MIXED, recompute_every=K, ntypes=2, eps=(1.0, 0.8), sigma=(1.0, 1.1))
+    b = D.Batch(D.make_params((1, 1, 1), **kw), [s.box for s in reps], [s.n for s in reps])
+    pos = np.concatenate([s.pos for s in reps])
+    vel = np.concatenate([s.vel for s in reps])
+    typ = np.concatenate([s.types for s in reps])
+    st = D.BatchState(b, D.to_real4(torch.from_numpy(pos), torch.from_numpy(typ), torch.float32),
+                      D.to_real4(torch.from_numpy(vel), None, torch.float32))
+    nsteps = K + 2
+    D.dcm_batch_step_init(b, st)
+    D.dcm_batch_step(b, st, DT, nsteps)
+    assert D.dcm_batch_status(b) == D.DCM_OK
+    th = st.thermo.cpu().numpy().reshape(-1, 4)
+    for r, slab in enumerate(reps):
+        ctx = D.Context(D.make_params(slab.box, n_max=slab.n, **kw))
+        assert D.dcm_force_kernel(ctx) == D.DCM_FORCE_PACKED
+        s1 = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), torch.from_numpy(slab.types), torch.float32),
+                     D.to_real4(torch.from_numpy(slab.vel), None, torch.float32))
+        D.dcm_step_init(ctx, s1)
+        D.dcm_step(ctx, s1, DT, nsteps)
+        p1, _, _, ids = s1.current()
+        order = torch.argsort(ids.long())
+        pb = by_id(st, b, r)
+        assert np.abs(pb - p1[order].cpu().numpy()).max() <= 1e-5
+        t1 = s1.thermo.cpu().numpy()
+        for q in range(3):
+            assert th[r, q] == pytest.approx(t1[q], rel=1e-6)
+    b.close()
+
+
 def test_batch_graph_replay_equals_stepping(D, replicas):
     P = D.DCM_PREC_MIXED
     b1, s1 = batch_state(D, replicas, P)
