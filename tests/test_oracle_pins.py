@@ -167,6 +167,35 @@ def test_brute_force_equals_cells(slab_1935):
         assert b.W == pytest.approx(a.W, rel=1e-12)
 
 
+@pytest.mark.parametrize("l", [1.5, (0.5, 1.5, 1.5)])
+def test_forces_subset_equals_brute_rows(slab_1935, l):
+    # the sampled form used at full sizes: its rows and per-particle sums
+    # against the O(N^2) pair loop, two types and the shifted energy
+    pos, box = slab_1935.pos.astype(np.float64), slab_1935.box
+    rng = np.random.default_rng(11)
+    n = len(pos)
+    rc = rng.uniform(3.0, 6.0, n)
+    types = (np.arange(n) % 2).astype(np.int32)
+    kw = dict(types=types, eps=(1.0, 0.8), sigma=(1.0, 1.1), shift=True)
+    a = O.forces_brute(pos, rc, box, **kw)
+    every = np.arange(n)
+    F, e, w, npairs = O.forces_subset(pos, rc, box, l, every, **kw)
+    assert np.abs(F - a.F).max() < 1e-12 * np.abs(a.F).max()
+    assert np.abs(e - a.e).max() < 1e-12 * np.abs(a.e).max()
+    assert int(npairs.sum()) == a.npairs
+    assert w.sum() == pytest.approx(a.W, rel=1e-12)
+    idx = rng.choice(n, 37, replace=False)
+    F, e, w, npairs = O.forces_subset(pos, rc, box, l, idx, **kw)
+    assert np.abs(F - a.F[idx]).max() < 1e-12 * np.abs(a.F).max()
+    assert np.abs(e - a.e[idx]).max() < 1e-12 * np.abs(a.e).max()
+    # per-particle pair count by direct minimum-image distances
+    d = pos[idx, None, :] - pos[None, :, :]
+    d -= np.asarray(box) * np.round(d / np.asarray(box))
+    r2 = (d * d).sum(-1)
+    r2[np.arange(37), idx] = np.inf
+    assert np.array_equal(npairs, (r2 < rc[idx, None] ** 2).sum(1))
+
+
 def test_dcm_force_is_per_particle_uniform(slab_1935):
     # F_i under DCM equals the uniform-cutoff force at r_c = rc_i, evaluated at i
     pos, box = slab_1935.pos.astype(np.float64), slab_1935.box
