@@ -21,8 +21,15 @@
 // Parameter gradients per type pair p of every forward pair (k, j in N(k)):
 //   dL/deps_p   += A_k . phi_kj / eps_p + dLdE/2 (U - U(rc_k) if shifted) / eps_p
 //   dL/dsigma_p += A_k . (dg/dsigma) r_kj + dLdE/2 d(U - U(rc_k))/dsigma
-// summed per warp in the working precision, reduced in FP64, then chained to
-// per-type gradients through Lorentz-Berthelot mixing.
+// Both terms are eps_p (resp. eps_p / sigma_p) times a function of s6 alone:
+//   d/deps:   24 (2 s12 - s6) / r^2 (A_k . r_kj) + 2 dLdE [(s12 - s6) - (c12 - c6)]
+//   d/dsigma: 24 (24 s12 - 6 s6) / r^2 (A_k . r_kj) + 2 dLdE [(12 s12 - 6 s6) - (12 c12 - 6 c6)]
+//             times eps_p / sigma_p
+// with c6 = (sigma_p / rc_k)^6 when shifted (else the c terms are 0), so the
+// pair loop sums the brackets (no division or root per pair) and the factor
+// eps_p / sigma_p is applied once to each warp's sum.  The sums are taken per
+// warp in the working precision, reduced in FP64, then chained to per-type
+// gradients through Lorentz-Berthelot mixing.
 #include <algorithm>
 
 #include "forces_core.cuh"
@@ -70,7 +77,7 @@ __device__ __forceinline__ void adj_range(const typename RT<R>::R4* __restrict__
                                           const typename RT<R>::R4* __restrict__ A, int lo, int hi, int self, R xi,
                                           R yi, R zi, R shx, R shy, R shz, R rck2, int tk,
                                           const typename RT<R>::R4& ak, R half_dlde, const ForceArgs<R>& a,
-                                          const R* ucsh, const R* ducsh, AdjAcc<R>& c) {
+                                          const R* ku, const R* kd, AdjAcc<R>& c) {
   for (int j = lo; j < hi; ++j) {
     if (j == self) continue;
     auto pj = ldg4(pos + j);
@@ -85,13 +92,13 @@ __device__ __forceinline__ void adj_range(const typename RT<R>::R4* __restrict__
     if (!(fwd || rev)) continue;
     int tj = TYPED ? type_of(pj.w, a.ntypes) : 0;
     int p = TYPED ? tk * a.ntypes + tj : 0;
-    R e = TYPED ? a.eps4[p] * (R)0.25 : (R)1;
+    R e24 = TYPED ? a.eps24[p] : (R)24;
     R sig2 = TYPED ? a.sig2[p] : (R)1;
-    R inv = (R)1 / r2;
+    R inv = recip(r2);
     R s2 = sig2 * inv;
     R s6 = s2 * s2 * s2, s12 = s6 * s6;
-    R g = (R)24 * e * ((R)2 * s12 - s6) * inv;
-    R gpr = (R)24 * e * ((R)-28 * s12 + (R)8 * s6) * inv * inv;
+    R g = e24 * ((R)2 * s12 - s6) * inv;
+    R gpr = e24 * ((R)-28 * s12 + (R)8 * s6) * inv * inv;
     R ex = -half_dlde * g;  // -dLdE/2 phi / r_vec, both sums
     R tx = 0, ty = 0, tz = 0;
     if (fwd) {
@@ -102,16 +109,11 @@ __device__ __forceinline__ void adj_range(const typename RT<R>::R4* __restrict__
       tx += ex * dx;
       ty += ex * dy;
       tz += ex * dz;
-      R sg = sqrt(sig2);
-      R dg_ds = (R)24 * e / sg * ((R)24 * s12 - (R)6 * s6) * inv;
-      R du_ds = (R)4 * e / sg * ((R)12 * s12 - (R)6 * s6);
-      R u = (R)4 * e * (s12 - s6);
-      R tjsel = TYPED ? (R)tj : (R)0;
-      (void)tjsel;
-      R uc = TYPED ? (tj == 0 ? ucsh[0] : tj == 1 ? ucsh[1] : tj == 2 ? ucsh[2] : ucsh[3]) : ucsh[0];
-      R duc = TYPED ? (tj == 0 ? ducsh[0] : tj == 1 ? ducsh[1] : tj == 2 ? ducsh[2] : ducsh[3]) : ducsh[0];
-      c.de[p] += g * ra / e + half_dlde * (u - uc) / e;
-      c.ds[p] += dg_ds * ra + half_dlde * (du_ds - duc);
+      R cu = TYPED ? (tj == 0 ? ku[0] : tj == 1 ? ku[1] : tj == 2 ? ku[2] : ku[3]) : ku[0];
+      R cd = TYPED ? (tj == 0 ? kd[0] : tj == 1 ? kd[1] : tj == 2 ? kd[2] : kd[3]) : kd[0];
+      R hd2 = (R)4 * half_dlde;
+      c.de[p] += (R)24 * ((R)2 * s12 - s6) * inv * ra + hd2 * ((s12 - s6) - cu);
+      c.ds[p] += (R)24 * ((R)24 * s12 - (R)6 * s6) * inv * ra + hd2 * (((R)12 * s12 - (R)6 * s6) - cd);
     }
     if (rev) {
       auto aj = ldg4(A + j);
@@ -129,13 +131,18 @@ __device__ __forceinline__ void adj_range(const typename RT<R>::R4* __restrict__
   }
 }
 
+// Threads per block of the adjoint: the cost per particle varies several-fold
+// (rc_k and the reverse reach grow toward the interfaces), so small blocks
+// free their slots as soon as their own warps finish.
+constexpr int kAdjBlock = 64;
+
 template <typename R, bool TYPED>
-__global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>::R4* __restrict__ pos,
-                                                 const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                 ForceArgs<R> a, const typename RT<R>::R4* __restrict__ A,
-                                                 R half_dlde, typename RT<R>::R4* __restrict__ G,
-                                                 double* __restrict__ part, int64_t nwarp, BlockGrid bg,
-                                                 const int32_t* __restrict__ bmax) {
+__global__ void __launch_bounds__(kAdjBlock) k_adjoint(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                       const R* __restrict__ rc, const int32_t* __restrict__ start,
+                                                       ForceArgs<R> a, const typename RT<R>::R4* __restrict__ A,
+                                                       R half_dlde, typename RT<R>::R4* __restrict__ G,
+                                                       double* __restrict__ part, int64_t nwarp, BlockGrid bg,
+                                                       const int32_t* __restrict__ bmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int np = a.ntypes * a.ntypes;
   AdjAcc<R> c;
@@ -171,15 +178,14 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
     }
     const R reach2s = reach * reach * (R)1.000004;
     const int tk = TYPED ? type_of(pi.w, a.ntypes) : 0;
-    R ucsh[4] = {0, 0, 0, 0}, ducsh[4] = {0, 0, 0, 0};
+    // (sigma_p / rc_k)^6 terms of the shifted energy per partner type
+    R ku[4] = {0, 0, 0, 0}, kd[4] = {0, 0, 0, 0};
     if (a.shift) {
       for (int t = 0; t < (TYPED ? a.ntypes : 1); ++t) {
-        int p = tk * a.ntypes + t;
-        R e = TYPED ? a.eps4[p] * (R)0.25 : (R)1;
-        R sig2 = TYPED ? a.sig2[p] : (R)1;
+        R sig2 = TYPED ? a.sig2[tk * a.ntypes + t] : (R)1;
         R c2 = sig2 / rck2, c6 = c2 * c2 * c2, c12 = c6 * c6;
-        ucsh[t] = (R)4 * e * (c12 - c6);
-        ducsh[t] = (R)4 * e / sqrt(sig2) * ((R)12 * c12 - (R)6 * c6);
+        ku[t] = c12 - c6;
+        kd[t] = (R)12 * c12 - (R)6 * c6;
       }
     }
     const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
@@ -210,19 +216,19 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
         if (ulo < 0) {
           int a1 = min(uhi, -1);
           adj_range<R, TYPED>(pos, rc, A, __ldg(start + row + ulo + nx), __ldg(start + row + a1 + nx + 1), -1, pi.x,
-                              yi, zi, -g.L[0], ysh, zsh, rck2, tk, ak, half_dlde, a, ucsh, ducsh, c);
+                              yi, zi, -g.L[0], ysh, zsh, rck2, tk, ak, half_dlde, a, ku, kd, c);
         }
         {
           int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
           if (a0 <= a1)
             adj_range<R, TYPED>(pos, rc, A, __ldg(start + row + a0), __ldg(start + row + a1 + 1),
                                 (ysh == (R)0 && zsh == (R)0) ? (int)i : -1, pi.x, yi, zi, (R)0, ysh, zsh, rck2, tk, ak,
-                                half_dlde, a, ucsh, ducsh, c);
+                                half_dlde, a, ku, kd, c);
         }
         if (uhi >= nx) {
           int a0 = max(ulo, nx);
           adj_range<R, TYPED>(pos, rc, A, __ldg(start + row + a0 - nx), __ldg(start + row + uhi - nx + 1), -1,
-                              pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rck2, tk, ak, half_dlde, a, ucsh, ducsh, c);
+                              pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rck2, tk, ak, half_dlde, a, ku, kd, c);
         }
       }
     }
@@ -242,8 +248,10 @@ __global__ void __launch_bounds__(128) k_adjoint(int64_t n, const typename RT<R>
         ds += __shfl_xor_sync(0xffffffffu, ds, o);
       }
       if ((threadIdx.x & 31) == 0) {
+        // eps_p / sigma_p, the factor taken out of the d/dsigma terms
+        const double f = TYPED ? 0.25 * (double)a.eps4[p] / sqrt((double)a.sig2[p]) : 1.0;
         part[(int64_t)p * nwarp + w] = (double)de;
-        part[(int64_t)(16 + p) * nwarp + w] = (double)ds;
+        part[(int64_t)(16 + p) * nwarp + w] = (double)ds * f;
       }
     }
   }
@@ -288,7 +296,7 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   }
   a.shift = ctx->p.shift_energy;
   a.rc_max = (R)ctx->p.rc_max;
-  int64_t nblk = (n + 127) / 128, nwarp = nblk * 4;
+  int64_t nblk = (n + kAdjBlock - 1) / kAdjBlock, nwarp = nblk * (kAdjBlock / 32);
   bool want = dparams != nullptr;
   if (want && nwarp > ctx->red_cap)
     return set_error(ctx, DCM_ERR_CAPACITY, "adjoint reduction needs %lld partials", (long long)nwarp);
@@ -301,8 +309,8 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->blk_max, 0, sizeof(int32_t) * ctx->nblk, st));
   DCM_LAUNCH(ctx, k_block_max<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, pos, rc, a.rc_max, bg, ctx->blk_max);
   auto kern = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
-  DCM_LAUNCH(ctx, kern, (unsigned)nblk, 128, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part, nwarp, bg,
-             (const int32_t*)ctx->blk_max);
+  DCM_LAUNCH(ctx, kern, (unsigned)nblk, kAdjBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
+             nwarp, bg, (const int32_t*)ctx->blk_max);
   int r = check_launch(ctx, "lj_adjoint");
   if (r || !want) return r;
   int npair = nt * nt;
