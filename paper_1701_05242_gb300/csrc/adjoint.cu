@@ -133,16 +133,20 @@ __device__ __forceinline__ void adj_range(const typename RT<R>::R4* __restrict__
 
 // Threads per block of the adjoint: the cost per particle varies several-fold
 // (rc_k and the reverse reach grow toward the interfaces), so small blocks
-// free their slots as soon as their own warps finish.
-constexpr int kAdjBlock = 64;
+// free their slots as soon as their own warps finish (measured best: 64 for
+// FP32, 32 for FP64).
+template <typename R>
+constexpr int adj_block() {
+  return sizeof(R) == 4 ? 64 : 32;
+}
 
 template <typename R, bool TYPED>
-__global__ void __launch_bounds__(kAdjBlock) k_adjoint(int64_t n, const typename RT<R>::R4* __restrict__ pos,
-                                                       const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                       ForceArgs<R> a, const typename RT<R>::R4* __restrict__ A,
-                                                       R half_dlde, typename RT<R>::R4* __restrict__ G,
-                                                       double* __restrict__ part, int64_t nwarp, BlockGrid bg,
-                                                       const int32_t* __restrict__ bmax) {
+__global__ void __launch_bounds__(adj_block<R>()) k_adjoint(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                            const R* __restrict__ rc, const int32_t* __restrict__ start,
+                                                            ForceArgs<R> a, const typename RT<R>::R4* __restrict__ A,
+                                                            R half_dlde, typename RT<R>::R4* __restrict__ G,
+                                                            double* __restrict__ part, int64_t nwarp, BlockGrid bg,
+                                                            const int32_t* __restrict__ bmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int np = a.ntypes * a.ntypes;
   AdjAcc<R> c;
@@ -296,7 +300,8 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   }
   a.shift = ctx->p.shift_energy;
   a.rc_max = (R)ctx->p.rc_max;
-  int64_t nblk = (n + kAdjBlock - 1) / kAdjBlock, nwarp = nblk * (kAdjBlock / 32);
+  constexpr int kBlock = adj_block<R>();
+  int64_t nblk = (n + kBlock - 1) / kBlock, nwarp = nblk * (kBlock / 32);
   bool want = dparams != nullptr;
   if (want && nwarp > ctx->red_cap)
     return set_error(ctx, DCM_ERR_CAPACITY, "adjoint reduction needs %lld partials", (long long)nwarp);
@@ -309,7 +314,7 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->blk_max, 0, sizeof(int32_t) * ctx->nblk, st));
   DCM_LAUNCH(ctx, k_block_max<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, pos, rc, a.rc_max, bg, ctx->blk_max);
   auto kern = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
-  DCM_LAUNCH(ctx, kern, (unsigned)nblk, kAdjBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
+  DCM_LAUNCH(ctx, kern, (unsigned)nblk, kBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
              nwarp, bg, (const int32_t*)ctx->blk_max);
   int r = check_launch(ctx, "lj_adjoint");
   if (r || !want) return r;
