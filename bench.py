@@ -41,6 +41,11 @@ REST_BYTES = 197            # HBM bytes per particle and timestep of every stage
 LIST_SKIN = 0.5             # Verlet-list skin of the lists form (the fastest measured on the 16M slab)
 FLOP_PER_PAIR = 18          # FP32-pipe instructions of the pair arithmetic per accepted pair
 FP32_LANES_PER_SM = 128
+ACC_DESCR = {"fp32": "plain FP32 running sums",
+             "row_kahan": "FP32 per row segment, Kahan-compensated across segments",
+             "row_fp64": "FP32 per row segment, FP64 across segments",
+             "pair_kahan": "every pair term Kahan-compensated in FP32",
+             "pair_fp64": "every pair term added in FP64"}
 
 
 def parse_args(argv=None):
@@ -56,6 +61,9 @@ def parse_args(argv=None):
                          "with the 1.5 cell edge")
     ap.add_argument("--skin", type=float, default=0.0, help="Verlet-list skin (0: forces from cell lists every step)")
     ap.add_argument("--force-kernel", type=int, default=0, help="cell-list force kernel (DCM_FORCE_*; 0: auto)")
+    ap.add_argument("--accumulation", type=int, default=0,
+                    help="per-particle accumulation of the mixed form (DCM_ACC_*; 0: auto)")
+    ap.add_argument("--skip-acc-forms", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -167,22 +175,21 @@ def force_source_sha():
     return h.hexdigest()
 
 
-def recorded_traffic(workload, cells):
-    """DRAM bytes per force launch from the committed ncu summary, if it was
-    taken on the current force kernel sources and the same cell edges (l, lx)
-    (else None)."""
-    path = os.path.join(ROOT, "profiles", f"forces_{workload}.md")
-    if not os.path.exists(path):
+def recorded_traffic(workload, cells, acc_name):
+    """DRAM bytes per force launch from the committed ncu record
+    (profiles/forces_<workload>.json, written beside its Markdown summary), if
+    it was taken on the current force kernel sources, the same cell edges
+    (l, lx) and the same accumulation form (else None)."""
+    path = os.path.join(ROOT, "profiles", f"forces_{workload}.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
         return None
-    txt = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    h = re.search(r"forces_src_sha256:\s*([0-9a-f]{64})", txt)
-    c = re.search(r"cell_edges:\s*([0-9.]+)\s+([0-9.]+)", txt)
-    if not m or not h or h.group(1) != force_source_sha():
+    if rec.get("forces_src_sha256") != force_source_sha():
         return None
-    if not c or (float(c.group(1)), float(c.group(2))) != cells:
+    if tuple(float(c) for c in rec.get("cell_edges", ())) != tuple(cells) or rec.get("accumulation") != acc_name:
         return None
-    return float(m.group(1))
+    return float(rec["traffic_bytes_per_launch"])
 
 
 def measured_peaks():
@@ -366,7 +373,7 @@ def run_gb300(args):
     def new_state(prec, skin=None):
         p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE, l=args.cell_edge,
                           lx=args.cell_edge_x, skin=args.skin if skin is None else skin,
-                          force_kernel=args.force_kernel)
+                          force_kernel=args.force_kernel, accumulation=args.accumulation)
         ctx = D.Context(p)
         real = ctx.real
         st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real, dev),
@@ -417,10 +424,11 @@ def run_gb300(args):
     f_avg_s = (f_ms / max(f_cnt, 1)) / 1000.0
     achieved = pairs * FLOP_PER_PAIR / f_avg_s / 1e12 if f_avg_s > 0 else None
     fkern = "k_forces_list" if args.skin > 0 else D.FORCE_KERNEL_NAMES[D.dcm_force_kernel(ctx)]
+    acc_name = D.ACC_NAMES[D.dcm_accumulation(ctx)]
+    cells = (args.cell_edge, args.cell_edge_x if args.cell_edge_x > 0 else args.cell_edge)
     roof = {"bound": "alu", "kernel": fkern, "achieved": achieved, "peak": peak_tinstr,
             "unit": "T FP32-instr/s", "frac": (achieved / peak_tinstr) if achieved else None,
-            "traffic": recorded_traffic(args.workload, (args.cell_edge, args.cell_edge_x if args.cell_edge_x > 0
-                                                        else args.cell_edge)),
+            "traffic": recorded_traffic(args.workload, cells, acc_name),
             "avg_launch_ms": f_ms / max(f_cnt, 1),
             "pairs_per_launch": pairs, "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
     stage_ms = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
@@ -434,6 +442,41 @@ def run_gb300(args):
                  "measured_ms_per_timestep": t_meas, "frac": (f_ideal + r_ideal) / t_meas if t_meas > 0 else None,
                  "basis": f"pairs x {FLOP_PER_PAIR} FP32-pipe instr at the peak above + {REST_BYTES} B/particle "
                           f"at {hbm:g} GB/s (measured copy bandwidth)"}
+
+    # ---------------- the force launch in every per-particle accumulation form,
+    # on the final sorted state of the timed run (CUDA events, same stream)
+    acc_forms = None
+    if not args.skip_acc_forms and args.skin == 0.0:
+        acc_forms = {}
+        ps, _, rcs, _ = st.current()
+        starts = torch.empty(ctx.ncell + 1, dtype=torch.int32, device=dev)
+        cellb = torch.empty(n, dtype=torch.int32, device=dev)
+        permb = torch.empty(n, dtype=torch.int32, device=dev)
+        pss = torch.empty_like(ps)
+        D.dcm_bin(ctx, n, ps, cellb, starts, permb, pss)
+        rcss = rcs[permb.long()]
+        Fb = torch.empty_like(pss)
+        totb = torch.zeros(3, dtype=torch.float64, device=dev)
+        for acc in (D.DCM_ACC_FP32, D.DCM_ACC_ROW_KAHAN, D.DCM_ACC_ROW_FP64, D.DCM_ACC_PAIR_KAHAN,
+                    D.DCM_ACC_PAIR_FP64):
+            pa = D.make_params(slab.box, n_max=n, recompute_every=K_RECOMPUTE, l=args.cell_edge,
+                               lx=args.cell_edge_x, force_kernel=args.force_kernel, accumulation=acc)
+            ca = D.Context(pa)
+            D.dcm_forces(ca, n, pss, rcss, starts, Fb, totb)
+            reps = 5
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                D.dcm_forces(ca, n, pss, rcss, starts, Fb, totb)
+            a1.record(stream)
+            a1.synchronize()
+            ams = a0.elapsed_time(a1) / reps
+            pa_pairs = float(totb[2].item())
+            acc_forms[D.ACC_NAMES[acc]] = {"ms_per_launch": ams, "E": float(totb[0].item()),
+                                           "W": float(totb[1].item()), "pairs": pa_pairs,
+                                           "frac": pa_pairs * FLOP_PER_PAIR / (ams / 1000.0) / 1e12 / peak_tinstr}
+            ca.close()
+        del pss, Fb, rcss, starts, cellb, permb
 
     # ---------------- plain FP64 form on the same GPU (per-step launches)
     fp64 = None
@@ -594,10 +637,12 @@ def run_gb300(args):
                           "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": args.cell_edge,
                           "lx": args.cell_edge_x if args.cell_edge_x > 0 else args.cell_edge, "skin": args.skin, "dt": DT,
                           "timesteps_per_step": K_RECOMPUTE, "recompute_every": K_RECOMPUTE,
-                          "precision": "fp32 pair math, fp64 totals", "l2": f"inputs larger than L2 (positions {16 * n / 1e6:.0f} MB)",
+                          "precision": f"fp32 pair math, per-particle sums {acc_name} "
+                                       f"({ACC_DESCR.get(acc_name, acc_name)}), fp64 totals", "l2": f"inputs larger than L2 (positions {16 * n / 1e6:.0f} MB)",
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "stage_ms_per_step": stage_ms, "step_roofline": step_roof, "fp64_form": fp64, "lists_form": lists, "batched_form": batch,
+               "stage_ms_per_step": stage_ms, "step_roofline": step_roof,
+               "accumulation_forms": acc_forms, "fp64_form": fp64, "lists_form": lists, "batched_form": batch,
                "adjoint_form": adjoint, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}

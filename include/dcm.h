@@ -32,7 +32,8 @@
  *   status word that dcm_status() reads.
  * - Precision forms (dcm_params.precision):
  *     DCM_PREC_MIXED: positions/velocities/forces are float4, cutoffs and
- *       distances float; pair arithmetic in FP32, per-particle sums in FP32,
+ *       distances float; pair arithmetic in FP32, per-particle sums as
+ *       dcm_params.accumulation says (compensated by default),
  *       energy/virial/kinetic totals reduced in FP64.
  *     DCM_PREC_FP64:  the same arrays as double4 / double; all arithmetic FP64.
  *   "real4" below means float4 or double4 accordingly, "real" float or double.
@@ -68,18 +69,39 @@ enum dcm_status_code {
   DCM_ERR_NOMEM = 6          /* scratch allocation failed in dcm_create */
 };
 
-/* Cell-list force kernels (all walk the same culled cell rows and accept the
- * same pairs; they differ in how the pair arithmetic is issued).  Kernels 2
- * to 5 serve one-type FP32 runs with eps = sigma = 1 (DCM_PREC_MIXED,
- * ntypes = 1); kernel 3 also serves FP32 runs of one or two types with their
- * own eps and sigma; otherwise kernel 1 runs. */
+/* Cell-list force kernels (both walk the same culled cell rows and accept the
+ * same pairs; they differ in how the pair arithmetic is issued).  The packed
+ * kernel serves FP32 runs (DCM_PREC_MIXED) of one or two types; otherwise
+ * kernel 1 runs.  Values 2, 4 and 5 are not used (invalid). */
 enum {
   DCM_FORCE_AUTO = 0,        /* kernel 3 where it applies, else kernel 1 */
   DCM_FORCE_THREAD = 1,      /* one thread per particle i, one candidate per instruction */
-  DCM_FORCE_TWO_PHASE = 2,   /* per-lane shared-memory buffers of accepted pairs */
-  DCM_FORCE_PACKED = 3,      /* one thread per particle i, two candidates per FP32x2 instruction */
-  DCM_FORCE_TILE = 4,        /* as 3, with each warp's row windows staged in shared memory */
-  DCM_FORCE_FLAT = 5         /* as 3, each lane running its row segments back to back in one loop */
+  DCM_FORCE_PACKED = 3       /* one thread per particle i, two candidates per FP32x2 instruction */
+};
+
+/* Per-particle accumulation of the mixed precision form (dcm_params.
+ * accumulation): how the FP32 pair terms of particle i (its force, energy and
+ * virial) are summed.  Totals E and W are always reduced in FP64.  A "row
+ * segment" is one contiguous run of candidates j of the cell-row walk (at
+ * most a row of cells: about ten candidates at rc = 3).
+ *   DCM_ACC_FP32       plain FP32 running sums
+ *   DCM_ACC_ROW_FP64   FP32 sum per row segment, segment sums added in FP64
+ *   DCM_ACC_ROW_KAHAN  FP32 sum per row segment, segment sums added with
+ *                      Kahan compensation in FP32
+ *   DCM_ACC_PAIR_KAHAN every pair term added with Kahan compensation (FP32)
+ *   DCM_ACC_PAIR_FP64  every pair term added in FP64
+ *   DCM_ACC_AUTO (0)   DCM_ACC_ROW_KAHAN, the cheapest of the compensated
+ *                      forms at the accuracy of the FP64 ones (measured)
+ * The pair forms run on the packed kernel; the scalar FP32 kernel (three or
+ * four types) runs their row form instead.  The FP64 precision form ignores
+ * this field (everything is FP64). */
+enum dcm_accumulation {
+  DCM_ACC_AUTO = 0,
+  DCM_ACC_FP32 = 1,
+  DCM_ACC_ROW_FP64 = 2,
+  DCM_ACC_ROW_KAHAN = 3,
+  DCM_ACC_PAIR_KAHAN = 4,
+  DCM_ACC_PAIR_FP64 = 5
 };
 
 enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };
@@ -112,7 +134,7 @@ typedef struct dcm_params {
   int32_t min_component;  /* > 0: remove connected components of S (6-connected, periodic, either
                              phase) of fewer boxes before the interface is taken (Section 2.1's
                              bubble filter); 0 (default): off.  Single-system contexts only */
-  int32_t reserved2;
+  int32_t accumulation;   /* DCM_ACC_*: per-particle sums of the mixed form. Default DCM_ACC_AUTO */
   double lx;              /* force-cell edge along x, the direction in which a row of cells is one
                              contiguous run of sorted particles; L_x / lx integer, short mantissa
                              (for a batch: every replica's L_x).  0 (default): l.  Finer cells
@@ -300,10 +322,10 @@ int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, 
 
 /* Same result as dcm_distance, for callers that cannot allocate device
  * memory: code whose device memory belongs to another allocator or
- * framework, code running while a CUDA graph is captured, or a plugin that is
- * only handed device buffers.  It needs no dcm_ctx (whose creation
- * allocates) and calls no allocating routine.  The paper has no counterpart:
- * this is a deployment variant of the same fast sweeping.
+ * framework, or a plugin that is only handed device buffers.  It needs no
+ * dcm_ctx (whose creation allocates) and calls no allocating routine.  The
+ * paper has no counterpart: this is a deployment variant of the same fast
+ * sweeping.
  *   p      host pointer to the parameters (validated as by dcm_validate_params)
  *   s, iface, D, iters: as for dcm_distance (device pointers; iters nullable)
  * Scratch: one fixed 8 MiB device array compiled into the library (held by
@@ -312,9 +334,13 @@ int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, 
  * returns DCM_ERR_CAPACITY before any launch (e.g. up to about 2.0M boxes in
  * the mixed form, 1.0M in FP64).  The first call on each device looks up the
  * array's device address with cudaGetSymbolAddress (device current) and
- * caches it; make that first call before any stream capture.  Every call
- * shares the array: calls whose kernels may overlap on the GPU race.
- * SYNCHRONOUS like dcm_distance; returns DCM_ERR_NOT_CONVERGED likewise. */
+ * caches it per device index: `stream` must belong to the current device, and
+ * a cudaDeviceReset invalidates the cached address (do not call this entry
+ * point on a device after resetting it).  Every call shares the array: calls
+ * whose kernels may overlap on the GPU race.
+ * SYNCHRONOUS like dcm_distance (it waits on the stream between chunks of
+ * sweeps); returns DCM_ERR_NOT_CONVERGED likewise, D then holding the last
+ * iterate and *iters = -1. */
 int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,
                          dcm_stream_t stream);
 
@@ -402,6 +428,12 @@ int dcm_launch_count(dcm_ctx* ctx, int64_t* count, int32_t reset);
  * for this context's parameters (params.force_kernel with AUTO and the
  * kernels' limits resolved), written to *kernel.  Host only. */
 int dcm_force_kernel(const dcm_ctx* ctx, int32_t* kernel);
+
+/* The DCM_ACC_* form in which this context's force launches sum each
+ * particle's pair terms (params.accumulation with AUTO and the kernels'
+ * limits resolved; DCM_ACC_FP32 for the FP64 precision form, whose sums are
+ * FP64), written to *form.  Host only. */
+int dcm_accumulation(const dcm_ctx* ctx, int32_t* form);
 
 #ifdef __cplusplus
 }

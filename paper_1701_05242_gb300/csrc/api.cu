@@ -211,8 +211,10 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "iter_max must be in 1..100000");
   if (p->recompute_every < 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "recompute_every must be >= 1");
   if (p->min_component < 0) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "min_component must be >= 0");
-  if (p->force_kernel < DCM_FORCE_AUTO || p->force_kernel > DCM_FORCE_FLAT)
+  if (p->force_kernel != DCM_FORCE_AUTO && p->force_kernel != DCM_FORCE_THREAD && p->force_kernel != DCM_FORCE_PACKED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
+  if (p->accumulation < DCM_ACC_AUTO || p->accumulation > DCM_ACC_PAIR_FP64)
+    return msg_out(msg, len, DCM_ERR_INVALID_ARG, "accumulation must be one of DCM_ACC_*");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "precision must be DCM_PREC_FP64 or DCM_PREC_MIXED");
   if (p->n_max < 0 || p->n_max > 0x7fffffffLL) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "n_max out of range");
@@ -586,6 +588,12 @@ extern "C" int dcm_launch_count(dcm_ctx* ctx, int64_t* count, int32_t reset) {
 extern "C" int dcm_force_kernel(const dcm_ctx* ctx, int32_t* kernel) {
   if (!ctx || !kernel) return DCM_ERR_INVALID_ARG;
   *kernel = resolve_force_kernel(ctx);
+  return DCM_OK;
+}
+
+extern "C" int dcm_accumulation(const dcm_ctx* ctx, int32_t* form) {
+  if (!ctx || !form) return DCM_ERR_INVALID_ARG;
+  *form = resolve_accumulation(ctx);
   return DCM_OK;
 }
 

@@ -438,7 +438,7 @@ __global__ void k_b_cutoffs(int64_t n, const typename RT<R>::R4* __restrict__ po
 }
 
 // ---- forces -----------------------------------------------------------------------
-template <typename R, bool TYPED, bool X2>
+template <typename R, bool TYPED, bool X2, Accum M>
 __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
                            const int32_t* __restrict__ start, ForceArgs<R> a, const RepGeom* __restrict__ geom,
                            const uint16_t* __restrict__ rep, typename RT<R>::R4* __restrict__ force,
@@ -447,10 +447,10 @@ __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos
   if (i >= n) return;
   const RepGeom& G = geom[rep[i]];
   Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge, a.g.edge_x, a.g.inv_edge_x);
-  R e = 0, w = 0;
+  double e = 0, w = 0;
   int np = 0;
-  force[i] = force_one<R, TYPED, X2>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
-  w_i[i] = w;
+  force[i] = force_one<R, TYPED, X2, M>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
+  w_i[i] = (R)w;
   np_i[i] = np;
 }
 
@@ -565,6 +565,30 @@ static int b_recompute(dcm_batch* b, const typename RT<R>::R4* pos, R* rc, cudaS
   return check_launch(ctx, "batch recompute");
 }
 
+// The batched force kernel for the LJ table and the accumulation form
+// (DCM_ACC_*, resolved as for a single system).
+template <typename R>
+static auto b_force_kernel(bool typed, int ntypes, int acc) {
+  using K = void (*)(int64_t, const typename RT<R>::R4*, const R*, const int32_t*, ForceArgs<R>, const RepGeom*,
+                     const uint16_t*, typename RT<R>::R4*, R*, int32_t*);
+  if constexpr (sizeof(R) == 8) {
+    return typed ? (K)k_b_forces<R, true, false, Accum::kPlain> : (K)k_b_forces<R, false, false, Accum::kPlain>;
+  } else {
+    if (typed && ntypes > 2)
+      return acc == DCM_ACC_FP32 ? (K)k_b_forces<R, true, false, Accum::kPlain>
+                                 : (acc == DCM_ACC_ROW_FP64 || acc == DCM_ACC_PAIR_FP64)
+                                       ? (K)k_b_forces<R, true, false, Accum::kRowF64>
+                                       : (K)k_b_forces<R, true, false, Accum::kRowKahan>;
+    switch (acc) {
+      case DCM_ACC_FP32: return typed ? (K)k_b_forces<R, true, true, Accum::kPlain> : (K)k_b_forces<R, false, true, Accum::kPlain>;
+      case DCM_ACC_ROW_FP64: return typed ? (K)k_b_forces<R, true, true, Accum::kRowF64> : (K)k_b_forces<R, false, true, Accum::kRowF64>;
+      case DCM_ACC_PAIR_KAHAN: return typed ? (K)k_b_forces<R, true, true, Accum::kPairKahan> : (K)k_b_forces<R, false, true, Accum::kPairKahan>;
+      case DCM_ACC_PAIR_FP64: return typed ? (K)k_b_forces<R, true, true, Accum::kPairF64> : (K)k_b_forces<R, false, true, Accum::kPairF64>;
+      default: return typed ? (K)k_b_forces<R, true, true, Accum::kRowKahan> : (K)k_b_forces<R, false, true, Accum::kRowKahan>;
+    }
+  }
+}
+
 template <typename R>
 static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R* rc, typename RT<R>::R4* force,
                            typename RT<R>::R4* vel, R half_dt, bool kick, double* thermo, cudaStream_t st) {
@@ -586,11 +610,9 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     a.shift = b->p.shift_energy;
     a.rc_max = (R)b->p.rc_max;
     int bs = b->force_block;
-    // one type in FP32: the packed two-candidates-per-instruction pair loop
     // the packed loop in FP32 for one type, and for one or two types with
     // their own eps and sigma; the scalar loop otherwise
-    auto kern = lj_general(t) ? (t.ntypes <= 2 ? k_b_forces<R, true, sizeof(R) == 4> : k_b_forces<R, true, false>)
-                              : k_b_forces<R, false, sizeof(R) == 4>;
+    auto kern = b_force_kernel<R>(lj_general(t), t.ntypes, resolve_accumulation(ctx));
     stage_begin(ctx, DCM_STAGE_FORCES, st);
     DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
                b->rep_of_particle, force, (R*)b->w_i, b->np_i);

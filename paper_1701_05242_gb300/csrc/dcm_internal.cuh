@@ -157,10 +157,10 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 
 int set_error(dcm_ctx* ctx, int code, const char* fmt, ...);
 
-// Force kernel used for one-type FP32 systems: 1 = single-pass (default),
-// 2 = two-phase.  DCM_FORCE_KERNEL in the environment overrides it (read once).
+// Cell-list force kernel and per-particle accumulation form of a context.
 int force_kernel_choice(const dcm_params& p);  // DCM_FORCE_* with AUTO resolved
 int resolve_force_kernel(const dcm_ctx* ctx);  // ... and each kernel's limits applied
+int resolve_accumulation(const dcm_ctx* ctx);  // DCM_ACC_* that the force launches run
 
 // Stage timing: events recorded on the launching stream around a stage.
 void stage_begin(dcm_ctx* ctx, int stage, cudaStream_t st);

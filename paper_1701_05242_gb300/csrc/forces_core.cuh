@@ -1,6 +1,8 @@
 // Per-particle force core shared by the single-system and batched force kernels.
 #pragma once
 
+#include <type_traits>
+
 #include "dcm_internal.cuh"
 
 namespace dcm {
@@ -127,9 +129,126 @@ struct Acc2 {
   int np = 0;
 };
 
+// Per-particle accumulation forms of the mixed precision form (the values
+// of dcm_params.accumulation).  The pair loops always sum into short-lived
+// partials (Acc for the scalar loop, Acc2 for the packed one); the long-lived
+// sums S of the form take them over:
+//   kPlain      no S: the partials are the sums (plain FP32);
+//   kRowF64     after every row segment the partials are added into FP64 sums;
+//   kRowKahan   ... into FP32 sums with Kahan compensation;
+//   kPairKahan  every pair term goes into the partials with Kahan compensation
+//               (S holds the compensation of each packed lane);
+//   kPairF64    every pair term is added into FP64 sums (the partials stay 0).
+enum class Accum : int {
+  kPlain = DCM_ACC_FP32,
+  kRowF64 = DCM_ACC_ROW_FP64,
+  kRowKahan = DCM_ACC_ROW_KAHAN,
+  kPairKahan = DCM_ACC_PAIR_KAHAN,
+  kPairF64 = DCM_ACC_PAIR_FP64
+};
+constexpr bool row_form(Accum m) { return m == Accum::kRowF64 || m == Accum::kRowKahan; }
+
+// The five sums of a particle, in this order: fx, fy, fz, en, vir.
+template <Accum M>
+struct Sums {};
+template <>
+struct Sums<Accum::kRowF64> {
+  double v[5] = {0, 0, 0, 0, 0};
+};
+template <>
+struct Sums<Accum::kPairF64> {
+  double v[5] = {0, 0, 0, 0, 0};
+};
+template <>
+struct Sums<Accum::kRowKahan> {
+  float s[5] = {0, 0, 0, 0, 0}, k[5] = {0, 0, 0, 0, 0};
+};
+template <>
+struct Sums<Accum::kPairKahan> {
+  float2 k[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+};
+
+// Kahan's compensated summation (Kahan 1965): s accumulates, k carries the
+// rounding error of the last addition (the amount s holds too much), so the
+// compensated value of the sum is s - k.  Neither form is reassociated by the
+// compiler (no fast-math).
+__device__ __forceinline__ void kahan_add(float& s, float& k, float x) {
+  const float y = x - k;
+  const float u = s + y;
+  k = (u - s) - y;
+  s = u;
+}
+__device__ __forceinline__ void kahan_add2(float2& s, float2& k, float2 x) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 y = __ffma2_rn(k, m1, x);  // x - k, exact negation
+  const float2 u = __fadd2_rn(s, y);
+  k = __ffma2_rn(y, m1, __ffma2_rn(s, m1, u));  // (u - s) - y
+  s = u;
+}
+
+// Fold the partials of one row segment into the row forms' sums and clear them.
+template <Accum M, typename R, bool X2>
+__device__ __forceinline__ void flush_row(Acc<R>& c, Acc2& c2, Sums<M>& S) {
+  if constexpr (row_form(M)) {
+    float v[5];
+    if constexpr (X2) {
+      v[0] = c2.fx.x + c2.fx.y;
+      v[1] = c2.fy.x + c2.fy.y;
+      v[2] = c2.fz.x + c2.fz.y;
+      v[3] = c2.en.x + c2.en.y;
+      v[4] = c2.vir.x + c2.vir.y;
+      c2.fx = c2.fy = c2.fz = c2.en = c2.vir = make_float2(0.f, 0.f);
+    } else {
+      v[0] = c.fx;
+      v[1] = c.fy;
+      v[2] = c.fz;
+      v[3] = c.en;
+      v[4] = c.vir;
+      c.fx = c.fy = c.fz = c.en = c.vir = (R)0;
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      if constexpr (M == Accum::kRowF64)
+        S.v[q] += (double)v[q];
+      else
+        kahan_add(S.s[q], S.k[q], v[q]);
+    }
+  }
+}
+
+
+// Add the packed terms of one step (force components, U/4 or U, r.F) into
+// the partials or the sums of form M.
+template <Accum M>
+__device__ __forceinline__ void add_terms2(Acc2& c, Sums<M>& S, float2 q, float2 dx, float2 dy, float2 dz,
+                                           float2 en, float2 pv) {
+  if constexpr (M == Accum::kPairKahan) {
+    kahan_add2(c.fx, S.k[0], __fmul2_rn(q, dx));
+    kahan_add2(c.fy, S.k[1], __fmul2_rn(q, dy));
+    kahan_add2(c.fz, S.k[2], __fmul2_rn(q, dz));
+    kahan_add2(c.en, S.k[3], en);
+    kahan_add2(c.vir, S.k[4], pv);
+  } else if constexpr (M == Accum::kPairF64) {
+    const float2 t0 = __fmul2_rn(q, dx), t1 = __fmul2_rn(q, dy), t2 = __fmul2_rn(q, dz);
+    S.v[0] += (double)t0.x + (double)t0.y;
+    S.v[1] += (double)t1.x + (double)t1.y;
+    S.v[2] += (double)t2.x + (double)t2.y;
+    S.v[3] += (double)en.x + (double)en.y;
+    S.v[4] += (double)pv.x + (double)pv.y;
+  } else {
+    c.fx = __ffma2_rn(q, dx, c.fx);
+    c.fy = __ffma2_rn(q, dy, c.fy);
+    c.fz = __ffma2_rn(q, dz, c.fz);
+    c.en = __fadd2_rn(c.en, en);
+    c.vir = __fadd2_rn(c.vir, pv);
+  }
+}
+
 // One packed step on the differences d = r_j - r_i of two candidates (m0,
 // m1: whether each slot holds a real candidate).
-__device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, Acc2& c) {
+template <Accum M>
+__device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, Acc2& c,
+                                          Sums<M>& S) {
   const float2 two = make_float2(2.f, 2.f), m1f = make_float2(-1.f, -1.f);
   const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
   float y0, y1;
@@ -143,18 +262,24 @@ __device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool 
   const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
   const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1f));  // r.F / 24
   const float2 q = __fmul2_rn(pv, y);
-  c.fx = __ffma2_rn(q, dx, c.fx);
-  c.fy = __ffma2_rn(q, dy, c.fy);
-  c.fz = __ffma2_rn(q, dz, c.fz);
-  c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1f), c.en);
-  c.vir = __fadd2_rn(c.vir, pv);
+  if constexpr (M == Accum::kPlain || row_form(M)) {
+    // the plain step, fused: c.en += s6 (s6 - 1)
+    c.fx = __ffma2_rn(q, dx, c.fx);
+    c.fy = __ffma2_rn(q, dy, c.fy);
+    c.fz = __ffma2_rn(q, dz, c.fz);
+    c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1f), c.en);
+    c.vir = __fadd2_rn(c.vir, pv);
+  } else {
+    add_terms2<M>(c, S, q, dx, dy, dz, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), pv);
+  }
   c.np += (int)a0 + (int)a1;
 }
 
 // One packed step: candidates p0 and p1 against particle i.
-template <bool SJ>
+template <bool SJ, Accum M>
 __device__ __forceinline__ void pair_x2(const float4& p0, const float4& p1, bool m0, bool m1, float xi, float yi,
-                                        float zi, float shx, float shy, float shz, float rc2, Acc2& c) {
+                                        float zi, float shx, float shy, float shz, float rc2, Acc2& c,
+                                        Sums<M>& S) {
   float2 dx, dy, dz;
   if (SJ) {
     dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
@@ -165,14 +290,15 @@ __device__ __forceinline__ void pair_x2(const float4& p0, const float4& p1, bool
     dy = make_float2(p0.y - yi, p1.y - yi);
     dz = make_float2(p0.z - zi, p1.z - zi);
   }
-  pair_x2_d(dx, dy, dz, m0, m1, rc2, c);
+  pair_x2_d<M>(dx, dy, dz, m0, m1, rc2, c, S);
 }
 
 // The packed step for up to two types: the constants of the pair type of
 // each slot (sigma^2, 24 eps, 4 eps and the energy shift) are picked from the
 // two of particle i's row by the slot's type; m0, m1 as in pair_x2_d.
+template <Accum M>
 __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, float2 sg,
-                                           float2 e24, float2 e4, float2 us, Acc2& c) {
+                                           float2 e24, float2 e4, float2 us, Acc2& c, Sums<M>& S) {
   const float2 two = make_float2(2.f, 2.f), m1f = make_float2(-1.f, -1.f);
   const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
   float y0, y1;
@@ -188,11 +314,16 @@ __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool
   const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
   const float2 pv = __fmul2_rn(e24, __fmul2_rn(s6, __ffma2_rn(s6, two, m1f)));  // r . F_ij
   const float2 q = __fmul2_rn(pv, y);
-  c.fx = __ffma2_rn(q, dx, c.fx);
-  c.fy = __ffma2_rn(q, dy, c.fy);
-  c.fz = __ffma2_rn(q, dz, c.fz);
-  c.en = __fadd2_rn(c.en, __ffma2_rn(e4, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), make_float2(-us.x, -us.y)));
-  c.vir = __fadd2_rn(c.vir, pv);
+  const float2 u = __ffma2_rn(e4, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), make_float2(-us.x, -us.y));
+  if constexpr (M == Accum::kPlain || row_form(M)) {
+    c.fx = __ffma2_rn(q, dx, c.fx);
+    c.fy = __ffma2_rn(q, dy, c.fy);
+    c.fz = __ffma2_rn(q, dz, c.fz);
+    c.en = __fadd2_rn(c.en, u);
+    c.vir = __fadd2_rn(c.vir, pv);
+  } else {
+    add_terms2<M>(c, S, q, dx, dy, dz, u, pv);
+  }
   c.np += (int)a0 + (int)a1;
 }
 
@@ -201,10 +332,10 @@ __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool
 // 4 eps of the pair type (type of i, t); a candidate's type is 1 if its w is
 // at least 1 (type_of clamped to two types), and with one type both columns
 // are equal.
-template <bool SJ>
+template <bool SJ, Accum M>
 __device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                                float zi, float shx, float shy, float shz, float rc2,
-                                               const float* k8, Acc2& c) {
+                                               const float* k8, Acc2& c, Sums<M>& S) {
   for (int j = lo; j < hi; j += 2) {
     const bool has1 = j + 1 < hi;
     const int j1 = has1 ? j + 1 : j;
@@ -220,38 +351,39 @@ __device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, i
       dz = make_float2(p0.z - zi, p1.z - zi);
     }
     const bool t0 = p0.w >= 1.f, t1 = p1.w >= 1.f;
-    pair_x2_dt(dx, dy, dz, true, has1, rc2, make_float2(t0 ? k8[3] : k8[2], t1 ? k8[3] : k8[2]),
+    pair_x2_dt<M>(dx, dy, dz, true, has1, rc2, make_float2(t0 ? k8[3] : k8[2], t1 ? k8[3] : k8[2]),
                make_float2(t0 ? k8[5] : k8[4], t1 ? k8[5] : k8[4]), make_float2(t0 ? k8[7] : k8[6], t1 ? k8[7] : k8[6]),
-               make_float2(t0 ? k8[1] : k8[0], t1 ? k8[1] : k8[0]), c);
+               make_float2(t0 ? k8[1] : k8[0], t1 ? k8[1] : k8[0]), c, S);
   }
 }
 
-// STAGED: pos points into a shared-memory tile (plain loads) instead of
-// global memory (read-only cached loads).
-template <bool SJ, bool STAGED = false>
+template <bool SJ, Accum M>
 __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
-                                              float zi, float shx, float shy, float shz, float rc2, Acc2& c) {
+                                              float zi, float shx, float shy, float shz, float rc2, Acc2& c,
+                                              Sums<M>& S) {
   for (int j = lo; j < hi; j += 2) {
     const bool has1 = j + 1 < hi;
     const int j1 = has1 ? j + 1 : j;
-    const float4 p0 = STAGED ? pos[j] : __ldg(pos + j), p1 = STAGED ? pos[j1] : __ldg(pos + j1);
-    pair_x2<SJ>(p0, p1, true, has1, xi, yi, zi, shx, shy, shz, rc2, c);
+    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j1);
+    pair_x2<SJ, M>(p0, p1, true, has1, xi, yi, zi, shx, shy, shz, rc2, c, S);
   }
 }
 
 // Segment dispatch: the packed loop for FP32 (one type, or up to two types
-// with the row constants in ushift[0 .. 7]), the scalar loop otherwise.
-template <typename R, bool SJ, bool TYPED, bool X2>
+// with the row constants in ushift[0 .. 7]), the scalar loop otherwise; the
+// row forms of accumulation take the segment's partials over at its end.
+template <typename R, bool SJ, bool TYPED, bool X2, Accum M>
 __device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi, R zi,
                                         R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a, const R* ushift,
-                                        Acc<R>& c, Acc2& c2) {
+                                        Acc<R>& c, Acc2& c2, Sums<M>& S) {
   if constexpr (X2 && TYPED) {
-    pair_range_x2t<SJ>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2);
+    pair_range_x2t<SJ, M>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2, S);
   } else if constexpr (X2) {
-    pair_range_x2<SJ>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2);
+    pair_range_x2<SJ, M>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2, S);
   } else {
     pair_range<R, SJ, TYPED>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
   }
+  flush_row<M, R, X2>(c, c2, S);
 }
 
 // Which segments of the row walk are evaluated: all of them, or only those
@@ -262,11 +394,11 @@ enum class Walk { kAll, kImagesOnly };
 // The culled cell-row walk of particle `self` (position pi, clamped cutoff
 // rci) over the cell grid g whose cell starts are start[0 .. ncell] (positions
 // pos sorted by cell), accumulating into c (scalar loop) or c2 (packed).
-template <typename R, bool TYPED, bool X2, Walk MODE = Walk::kAll>
+template <typename R, bool TYPED, bool X2, Accum M, Walk MODE = Walk::kAll>
 __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__ pos,
                                           const int32_t* __restrict__ start, const Grid<R>& g,
                                           const ForceArgs<R>& a, int self, const typename RT<R>::R4& pi, R rci,
-                                          int ti, const R* ushift, Acc<R>& c, Acc2& c2) {
+                                          int ti, const R* ushift, Acc<R>& c, Acc2& c2, Sums<M>& S) {
   constexpr bool kImg = MODE == Walk::kImagesOnly;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
@@ -303,7 +435,7 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       if (ulo < 0) {
         int a1 = min(uhi, -1);
         int j0 = __ldg(start + row + ulo + nx), j1 = __ldg(start + row + a1 + nx + 1);
-        segment<R, true, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2);
+        segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
       // segment 0 <= u < nx: no x shift; the particle itself is skipped
       const bool img_row = uy < 0 || uy >= ny || uz < 0 || uz >= nz;
@@ -312,13 +444,13 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
         if (a0 <= a1) {
           int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
           if (!kImg && uy == cy && uz == cz) {  // the particle's own row: cut it out
-            segment<R, false, TYPED, X2>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2);
-            segment<R, false, TYPED, X2>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
-                                         c2);
+            segment<R, false, TYPED, X2, M>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
+            segment<R, false, TYPED, X2, M>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
+                                         c2, S);
           } else if (ysh == (R)0 && zsh == (R)0) {
-            segment<R, false, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2);
+            segment<R, false, TYPED, X2, M>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
           } else {
-            segment<R, true, TYPED, X2>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2);
+            segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
           }
         }
       }
@@ -326,7 +458,7 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       if (uhi >= nx) {
         int a0 = max(ulo, nx);
         int j0 = __ldg(start + row + a0 - nx), j1 = __ldg(start + row + uhi - nx + 1);
-        segment<R, true, TYPED, X2>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2);
+        segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
     }
   }
@@ -344,16 +476,21 @@ __device__ __forceinline__ R clamp_cutoff(R rc_in, R rc_max) {
 
 // Forces, energy and virial of particle `self` (position pi, cutoff rc_in)
 // over the cell grid g whose cell starts are start[0 .. ncell] (positions
-// pos, sorted by cell).  Returns the force and writes e_i, w_i, pairs.
-template <typename R, bool TYPED, bool X2 = false>
+// pos, sorted by cell), with the per-particle sums of accumulation form M.
+// Returns the force and writes e_i, w_i (in FP64: the totals are reduced
+// from them in FP64) and the accepted-pair count.
+template <typename R, bool TYPED, bool X2 = false, Accum M = Accum::kPlain>
 __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
                                                         const int32_t* __restrict__ start, const Grid<R>& g,
                                                         const ForceArgs<R>& a, int self,
-                                                        const typename RT<R>::R4& pi, R rc_in, R& e_out, R& w_out,
-                                                        int& np_out) {
+                                                        const typename RT<R>::R4& pi, R rc_in, double& e_out,
+                                                        double& w_out, int& np_out) {
   static_assert(!X2 || sizeof(R) == 4, "the packed loop serves FP32 only (with types: at most two)");
+  static_assert(M == Accum::kPlain || sizeof(R) == 4, "accumulation forms apply to FP32 pair math only");
+  static_assert(X2 || M == Accum::kPlain || row_form(M), "the pair forms run on the packed loop");
   Acc<R> c;
   Acc2 c2;
+  Sums<M> S;
   const R rci = clamp_cutoff<R>(rc_in, a.rc_max);
   const R rc2 = rci * rci;
   const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
@@ -376,31 +513,52 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       ushift[6 + t] = a.eps4[tp];
     }
   }
-  walk_rows<R, TYPED, X2>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2);
-  if constexpr (X2) {  // fold the two packed lanes (and the sign of d) into c
-    c.fx = -(c2.fx.x + c2.fx.y);
-    c.fy = -(c2.fy.x + c2.fy.y);
-    c.fz = -(c2.fz.x + c2.fz.y);
-    c.en = c2.en.x + c2.en.y;
-    c.vir = c2.vir.x + c2.vir.y;
-    c.np = c2.np;
+  walk_rows<R, TYPED, X2, M>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2, S);
+  // The five sums (fx, fy, fz, en, vir) of the form, in FP64 where the form
+  // keeps them so; the packed loop sums the sign-flipped differences r_j - r_i.
+  using V = std::conditional_t<M == Accum::kRowF64 || M == Accum::kPairF64, double, R>;
+  V v[5];
+  const int np = X2 ? c2.np : c.np;
+  if constexpr (M == Accum::kRowF64 || M == Accum::kPairF64) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] = S.v[q];
+  } else if constexpr (M == Accum::kRowKahan) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] = S.s[q] - S.k[q];
+  } else if constexpr (M == Accum::kPairKahan) {
+    const float2 p[5] = {c2.fx, c2.fy, c2.fz, c2.en, c2.vir};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[q] = (p[q].x - S.k[q].x) + (p[q].y - S.k[q].y);
+  } else if constexpr (X2) {  // plain: fold the two packed lanes
+    v[0] = c2.fx.x + c2.fx.y;
+    v[1] = c2.fy.x + c2.fy.y;
+    v[2] = c2.fz.x + c2.fz.y;
+    v[3] = c2.en.x + c2.en.y;
+    v[4] = c2.vir.x + c2.vir.y;
+  } else {
+    v[0] = c.fx;
+    v[1] = c.fy;
+    v[2] = c.fz;
+    v[3] = c.en;
+    v[4] = c.vir;
   }
+  const V sgn = X2 ? (V)-1 : (V)1;
   typename RT<R>::R4 out;
   if (TYPED) {
-    out.x = c.fx;
-    out.y = c.fy;
-    out.z = c.fz;
-    e_out = (R)0.5 * c.en;
-    w_out = (R)0.5 * c.vir;
+    out.x = (R)(sgn * v[0]);
+    out.y = (R)(sgn * v[1]);
+    out.z = (R)(sgn * v[2]);
+    e_out = (double)((V)0.5 * v[3]);
+    w_out = (double)((V)0.5 * v[4]);
   } else {
-    out.x = (R)24 * c.fx;
-    out.y = (R)24 * c.fy;
-    out.z = (R)24 * c.fz;
-    e_out = (R)2 * c.en - (R)0.5 * (R)c.np * ushift[0];
-    w_out = (R)12 * c.vir;
+    out.x = (R)((V)24 * sgn * v[0]);
+    out.y = (R)((V)24 * sgn * v[1]);
+    out.z = (R)((V)24 * sgn * v[2]);
+    e_out = (double)((V)2 * v[3] - (V)0.5 * (V)np * (V)ushift[0]);
+    w_out = (double)((V)12 * v[4]);
   }
-  out.w = e_out;
-  np_out = c.np;
+  out.w = (R)e_out;
+  np_out = np;
   return out;
 }
 

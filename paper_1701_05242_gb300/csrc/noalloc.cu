@@ -4,11 +4,9 @@
 // Who needs it: code that must not call cudaMalloc at all, e.g. a host
 // program whose device memory is owned by another allocator or framework
 // (and that therefore cannot create a dcm_ctx, whose scratch is allocated by
-// dcm_create), code that runs while a CUDA graph is being captured (where an
-// allocation would break the capture), or code embedded in a plugin that is
-// only handed device buffers.  Such a caller passes the inputs and the output
-// and this call uses, as its only scratch, a fixed array compiled into the
-// library.
+// dcm_create), or code embedded in a plugin that is only handed device
+// buffers.  Such a caller passes the inputs and the output and this call uses,
+// as its only scratch, a fixed array compiled into the library.
 //
 // The scratch is one file-scope __device__ array of kNoAllocBytes bytes.
 // Every GPU that loads this library holds it until the process exits.  It
@@ -18,11 +16,15 @@
 // Host code cannot use the array's name as a device address (in host code the
 // name refers to a host-side shadow), so the device address is looked up with
 // cudaGetSymbolAddress once per device, on the first call made with that
-// device current, and cached.  That first call should therefore happen before
-// any stream capture begins.  All calls share the one array and it keeps the
-// contents of the last call: the flags are cleared at the start of every call,
-// and two calls whose kernels overlap on the GPU (different streams, or
-// different host threads) race on the array and give undefined results.
+// device current, and cached per device index.  The stream passed in must
+// belong to the current device, and a cudaDeviceReset of a device invalidates
+// the cached address (later calls on that device would write through a stale
+// pointer), so a program that resets a device must not call this entry point
+// on it again.  All calls share the one array and it keeps the contents of the
+// last call: the flags are cleared at the start of every call, and two calls
+// whose kernels overlap on the GPU (different streams, or different host
+// threads) race on the array and give undefined results.  Like dcm_distance,
+// the call waits on the stream between chunks of sweeps to test convergence.
 #include <mutex>
 
 #include "dcm_internal.cuh"

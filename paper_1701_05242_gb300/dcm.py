@@ -30,10 +30,15 @@ DCM_PREC_FP64 = 0
 DCM_PREC_MIXED = 1
 DCM_FORCE_AUTO = 0
 DCM_FORCE_THREAD = 1
-DCM_FORCE_TWO_PHASE = 2
 DCM_FORCE_PACKED = 3
-DCM_FORCE_TILE = 4
-DCM_FORCE_FLAT = 5
+DCM_ACC_AUTO = 0
+DCM_ACC_FP32 = 1
+DCM_ACC_ROW_FP64 = 2
+DCM_ACC_ROW_KAHAN = 3
+DCM_ACC_PAIR_KAHAN = 4
+DCM_ACC_PAIR_FP64 = 5
+ACC_NAMES = {DCM_ACC_FP32: "fp32", DCM_ACC_ROW_FP64: "row_fp64", DCM_ACC_ROW_KAHAN: "row_kahan",
+             DCM_ACC_PAIR_KAHAN: "pair_kahan", DCM_ACC_PAIR_FP64: "pair_fp64"}
 
 _ERRNAMES = {1: "INVALID_ARG", 2: "BOX", 3: "CUDA", 4: "NOT_CONVERGED", 5: "CAPACITY", 6: "NOMEM"}
 
@@ -51,7 +56,7 @@ class dcm_params(ctypes.Structure):
                 ("iter_max", ctypes.c_int32), ("ntypes", ctypes.c_int32), ("eps", ctypes.c_double * 4),
                 ("sigma", ctypes.c_double * 4), ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("force_kernel", ctypes.c_int32), ("n_max", ctypes.c_int64),
-                ("skin", ctypes.c_double), ("min_component", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("skin", ctypes.c_double), ("min_component", ctypes.c_int32), ("accumulation", ctypes.c_int32),
                 ("lx", ctypes.c_double)]
 
 
@@ -105,6 +110,7 @@ _SIGS = {
     "dcm_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "dcm_launch_count": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
     "dcm_force_kernel": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "dcm_accumulation": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32)]),
 }
 
 STAGES = ("kick_drift", "bin", "detect", "distance", "cutoffs", "forces", "kick", "lists")
@@ -336,8 +342,13 @@ def dcm_force_kernel(ctx: Context) -> int:
     return k.value
 
 
-FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_TWO_PHASE: "k_forces2", DCM_FORCE_PACKED: "k_forces_x2", DCM_FORCE_TILE: "k_forces_tile",
-                      DCM_FORCE_FLAT: "k_forces_flat"}
+def dcm_accumulation(ctx: Context) -> int:
+    k = ctypes.c_int32()
+    ctx.check(lib.dcm_accumulation(ctx.handle, ctypes.byref(k)))
+    return k.value
+
+
+FORCE_KERNEL_NAMES = {DCM_FORCE_THREAD: "k_forces", DCM_FORCE_PACKED: "k_forces_x2"}
 
 
 # ---------------------------------------------------------------- batched form

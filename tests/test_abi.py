@@ -51,6 +51,7 @@ def test_params_default_and_validate(lib):
     D, p = _params(lib)
     assert p.h == 1.5 and p.l == 1.5 and p.rc_min == 3.0 and p.rc_max == 6.0 and p.smooth_w == 2
     assert p.precision == D.DCM_PREC_MIXED and p.recompute_every == 10 and p.threshold == -1
+    assert p.accumulation == D.DCM_ACC_AUTO
     rc, msg = D.dcm_validate_params(p)
     assert rc == D.DCM_OK, msg
 
@@ -70,6 +71,10 @@ def test_params_default_and_validate(lib):
     (dict(box=(99000.0, 12.0, 48.0)), 2),       # 66000 cells along x
     (dict(min_component=-1), 1),
     (dict(force_kernel=9), 1),
+    (dict(force_kernel=2), 1),                  # removed kernel numbers stay invalid
+    (dict(force_kernel=5), 1),
+    (dict(accumulation=6), 1),
+    (dict(accumulation=-1), 1),
     (dict(skin=-0.1), 1),
     (dict(skin=0.5, rc_max=5.8), 2),             # rc_max + skin > L/2
     (dict(skin=0.3, rc_max=5.5, n_max=2 ** 26), 5),  # list entries keep 26 index bits

@@ -420,6 +420,86 @@ def test_trilinear_reproduces_linear_fields():
     assert np.abs(delta - (0.2 * p[:, 0] + 0.1 * p[:, 1] + 0.05 * p[:, 2])).max() < 1e-12
 
 
+def test_trilinear_periodic_seam_hand_values():
+    """Section 2.2's interpolation between box centres (k + 1/2) h, periodic:
+    within h/2 of a face a particle sits between the centre of the last box
+    (its image at -h/2, or at L - h/2) and that of box 0 (at h/2, or its image
+    at L + h/2).  The field differs on the two sides of every seam, so a wrap
+    to the wrong box or a missing wrap changes the value.  Expected values are
+    written out by hand for these positions."""
+    h = 1.5
+    nh = np.array([4, 5, 6])
+    L = nh * h
+    # every box 5.0 except the boxes at both ends of each axis
+    D = np.full(int(np.prod(nh)), 5.0)
+
+    def box(x, y, z):
+        return x + nh[0] * (y + nh[1] * z)
+
+    # a y-z interior line of boxes (y = 2, z = 3) with distinct end values along x
+    D[box(3, 2, 3)] = 1.0   # last box along x
+    D[box(0, 2, 3)] = 2.5   # first box along x
+    D[box(1, 2, 3)] = 0.5
+    D[box(2, 2, 3)] = 4.0
+    yc, zc = (2 + 0.5) * h, (3 + 0.5) * h   # box centres: no weight on y, z neighbours
+    pts = np.array([
+        [0.0, yc, zc],              # halfway between box 3's image and box 0
+        [0.25 * h, yc, zc],         # 3/4 of the way to box 0
+        [L[0] - 0.25 * h, yc, zc],  # 1/4 of the way from box 3 to box 0's image
+        [L[0] - 1e-9, yc, zc],      # just below L: almost halfway
+        [0.5 * h, yc, zc],          # box 0's centre exactly
+        [L[0] - 0.5 * h, yc, zc],   # box 3's centre exactly
+    ])
+    want = np.array([
+        0.5 * 1.0 + 0.5 * 2.5,
+        0.25 * 1.0 + 0.75 * 2.5,
+        0.75 * 1.0 + 0.25 * 2.5,
+        0.5 * 1.0 + 0.5 * 2.5,
+        2.5,
+        1.0,
+    ])
+    delta, _ = O.cutoffs(pts, D, nh, h, 1e9, 3.0, 6.0, 3.0)
+    assert np.allclose(delta, want, rtol=0, atol=1e-8), (delta, want)
+
+    # the same along y and z: a line of boxes along y (x = 1, z = 2) and along z (x = 2, y = 1)
+    D2 = np.full(int(np.prod(nh)), 5.0)
+    D2[box(1, 4, 2)], D2[box(1, 0, 2)] = 0.25, 3.25    # y: last box, first box
+    D2[box(2, 1, 5)], D2[box(2, 1, 0)] = 2.0, 0.75     # z: last box, first box
+    xc1, zc2 = 1.5 * h, 2.5 * h
+    pts = np.array([
+        [xc1, 0.0, zc2],                     # y seam: halfway
+        [xc1, L[1] - 0.25 * h, zc2],         # y seam: 1/4 past the last centre
+        [2.5 * h, 1.5 * h, 0.0],             # z seam: halfway
+        [2.5 * h, 1.5 * h, 0.25 * h],        # z seam: 3/4 of the way to box 0
+    ])
+    want = np.array([
+        0.5 * 0.25 + 0.5 * 3.25,
+        0.75 * 0.25 + 0.25 * 3.25,
+        0.5 * 2.0 + 0.5 * 0.75,
+        0.25 * 2.0 + 0.75 * 0.75,
+    ])
+    delta, _ = O.cutoffs(pts, D2, nh, h, 1e9, 3.0, 6.0, 3.0)
+    assert np.allclose(delta, want, rtol=0, atol=1e-8), (delta, want)
+
+    # the corner (0, 0, 0): the mean of the eight boxes at the ends of all
+    # three axes, with values that differ box by box
+    D3 = np.full(int(np.prod(nh)), 5.0)
+    corners = {}
+    v = 0.125
+    for cz in (nh[2] - 1, 0):
+        for cy in (nh[1] - 1, 0):
+            for cx in (nh[0] - 1, 0):
+                D3[box(cx, cy, cz)] = v
+                corners[(cx, cy, cz)] = v
+                v += 0.375
+    delta, _ = O.cutoffs(np.zeros((1, 3)), D3, nh, h, 1e9, 3.0, 6.0, 3.0)
+    assert abs(delta[0] - sum(corners.values()) / 8.0) < 1e-12
+
+    # values above r_grid are capped before they are interpolated
+    delta, _ = O.cutoffs(np.array([[0.0, yc, zc]]), D, nh, h, 2.0, 3.0, 6.0, 3.0)
+    assert abs(delta[0] - (0.5 * 1.0 + 0.5 * 2.0)) < 1e-12
+
+
 def test_slab_cutoffs(slab_1935):
     pos = slab_1935.pos.astype(np.float64)
     p = O.Params(box=slab_1935.box)
