@@ -42,6 +42,8 @@ LIST_SKIN = 0.5             # Verlet-list skin of the lists form (the fastest me
 FLOP_PER_PAIR = 18          # FP32-pipe instructions of the pair arithmetic per accepted pair
 FP32_LANES_PER_SM = 128
 ACC_DESCR = {"fp32": "plain FP32 running sums",
+             "plane_kahan": "FP32 per z-plane of the stencil, Kahan-compensated across planes",
+             "plane_fp64": "FP32 per z-plane of the stencil, FP64 across planes",
              "row_kahan": "FP32 per row segment, Kahan-compensated across segments",
              "row_fp64": "FP32 per row segment, FP64 across segments",
              "pair_kahan": "every pair term Kahan-compensated in FP32",
@@ -252,8 +254,11 @@ def run_reference(args):
 
 def run_batch(args, D, dev):
     """64 independent replicas (N log-uniform in [2K, 200K]) stepped together:
-    autotuned cell edge and force block, one CUDA graph per recomputation
-    period, args.batch_steps timesteps timed."""
+    autotuned cell edges and launch plan (persistent, one cooperative launch
+    per timestep with a (replica, tile) force queue, or one launch per stage),
+    one CUDA graph per recomputation period, args.batch_steps timesteps timed.
+    Beside it, on the same replicas: the plain FP64 form (FP64 arrays and
+    arithmetic, one launch per stage, no graph)."""
     import numpy as np
     import torch
     from paper_1701_05242_gb300 import autotune, synth
@@ -265,7 +270,7 @@ def run_batch(args, D, dev):
     vel = np.concatenate([s.vel for s in slabs])
     best, table = autotune.tune(boxes, counts, pos, vel, K=K_RECOMPUTE, dt=DT)
     b, st = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_MIXED, K_RECOMPUTE, best[0], best[1])
-    D.dcm_batch_set_force_block(b, best[2])
+    autotune.apply_plan(b, best[2], best[3])
     D.dcm_batch_step_init(b, st)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
@@ -282,15 +287,38 @@ def run_batch(args, D, dev):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     steps = ngraphs * per
+    launches = D.dcm_batch_launch_count(b)
     status = D.dcm_batch_status(b, stream)
-    out = {"value": sum(counts) * steps / (ms / 1000.0), "unit": UNIT, "replicas": len(counts),
+    pairs = float(st.thermo.view(-1, 4)[:, 3].sum().item())
+    acc = D.ACC_NAMES[D.dcm_batch_accumulation(b)]
+    b.close()
+    # the plain FP64 form on the same replicas: per-stage launches, no graph
+    b64, s64 = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_FP64, K_RECOMPUTE, 1.5, 0.0)
+    D.dcm_batch_set_persistent(b64, False)
+    D.dcm_batch_step_init(b64, s64)
+    D.dcm_batch_step(b64, s64, DT, 1)
+    n64 = K_RECOMPUTE
+    torch.cuda.synchronize()
+    e0.record()
+    D.dcm_batch_step(b64, s64, DT, n64)
+    e1.record()
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    status64 = D.dcm_batch_status(b64)
+    b64.close()
+    value = sum(counts) * steps / (ms / 1000.0)
+    value64 = sum(counts) * n64 / (ms64 / 1000.0)
+    out = {"value": value, "unit": UNIT, "replicas": len(counts),
            "particles": int(sum(counts)), "n_min": int(min(counts)), "n_max": int(max(counts)),
            "timesteps": steps, "ms_per_timestep": ms / steps, "cuda_graph": True,
-           "graph_timesteps": per, "launches_per_timestep": D.dcm_batch_launch_count(b) / steps,
-           "autotuned": {"cell_edge": best[0], "cell_edge_x": best[1], "force_block": best[2],
-                         "candidates_ms": {f"l={k[0]},lx={k[1]},block={k[2]}": v for k, v in table.items()}},
+           "graph_timesteps": per, "launches_per_timestep": launches / steps,
+           "plan": best[2], "tile_or_block": best[3], "accumulation": acc, "pairs_per_timestep": pairs,
+           "autotuned": {"cell_edge": best[0], "cell_edge_x": best[1], "plan": best[2], "size": best[3],
+                         "candidates_ms": {f"l={k[0]},lx={k[1]},{k[2]}={k[3]}": v for k, v in table.items()}},
+           "plain_fp64_form": {"value": value64, "unit": UNIT, "timesteps": n64, "ms_per_timestep": ms64 / n64,
+                               "plan": "stages", "cuda_graph": False, "device_status": status64},
+           "speedup_over_plain_fp64": value / value64,
            "device_status": status}
-    b.close()
     return out
 
 
@@ -457,8 +485,8 @@ def run_gb300(args):
         rcss = rcs[permb.long()]
         Fb = torch.empty_like(pss)
         totb = torch.zeros(3, dtype=torch.float64, device=dev)
-        for acc in (D.DCM_ACC_FP32, D.DCM_ACC_ROW_KAHAN, D.DCM_ACC_ROW_FP64, D.DCM_ACC_PAIR_KAHAN,
-                    D.DCM_ACC_PAIR_FP64):
+        for acc in (D.DCM_ACC_FP32, D.DCM_ACC_PLANE_KAHAN, D.DCM_ACC_PLANE_FP64, D.DCM_ACC_ROW_KAHAN,
+                    D.DCM_ACC_ROW_FP64, D.DCM_ACC_PAIR_KAHAN, D.DCM_ACC_PAIR_FP64):
             pa = D.make_params(slab.box, n_max=n, recompute_every=K_RECOMPUTE, l=args.cell_edge,
                                lx=args.cell_edge_x, force_kernel=args.force_kernel, accumulation=acc)
             ca = D.Context(pa)

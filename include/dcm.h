@@ -66,7 +66,8 @@ enum dcm_status_code {
   DCM_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
   DCM_ERR_NOT_CONVERGED = 4, /* fast sweeping did not converge within iter_max */
   DCM_ERR_CAPACITY = 5,      /* n > n_max, or a density value range beyond the histogram */
-  DCM_ERR_NOMEM = 6          /* scratch allocation failed in dcm_create */
+  DCM_ERR_NOMEM = 6,         /* scratch allocation failed in dcm_create */
+  DCM_ERR_TIMEOUT = 7        /* a device-side wait ran past its time budget (batched persistent step) */
 };
 
 /* Cell-list force kernels (both walk the same culled cell rows and accept the
@@ -90,7 +91,10 @@ enum {
  *                      Kahan compensation in FP32
  *   DCM_ACC_PAIR_KAHAN every pair term added with Kahan compensation (FP32)
  *   DCM_ACC_PAIR_FP64  every pair term added in FP64
- *   DCM_ACC_AUTO (0)   DCM_ACC_ROW_KAHAN, the cheapest of the compensated
+ *   DCM_ACC_PLANE_FP64 FP32 sum per z-plane of the stencil (its rows: up to
+ *                      five at rc = 3), plane sums added in FP64
+ *   DCM_ACC_PLANE_KAHAN the same, plane sums Kahan-compensated in FP32
+ *   DCM_ACC_AUTO (0)   DCM_ACC_PLANE_KAHAN, the cheapest of the compensated
  *                      forms at the accuracy of the FP64 ones (measured)
  * The pair forms run on the packed kernel; the scalar FP32 kernel (three or
  * four types) runs their row form instead.  The FP64 precision form ignores
@@ -101,7 +105,9 @@ enum dcm_accumulation {
   DCM_ACC_ROW_FP64 = 2,
   DCM_ACC_ROW_KAHAN = 3,
   DCM_ACC_PAIR_KAHAN = 4,
-  DCM_ACC_PAIR_FP64 = 5
+  DCM_ACC_PAIR_FP64 = 5,
+  DCM_ACC_PLANE_FP64 = 6,
+  DCM_ACC_PLANE_KAHAN = 7
 };
 
 enum dcm_precision { DCM_PREC_FP64 = 0, DCM_PREC_MIXED = 1 };
@@ -344,7 +350,7 @@ int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, 
 int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,
                          dcm_stream_t stream);
 
-/* ---- batched form: many independent systems in one launch per stage ---- */
+/* ---- batched form: many independent systems, one launch per timestep ---- */
 
 /* R independent replicas (the batching form) that share every
  * parameter in *p except the box and the particle count: replica r has box
@@ -352,9 +358,14 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
  * validated as a single system (dcm_validate_params).  The state arrays of
  * dcm_state are the concatenation of the replicas: replica r owns slots
  * [offset[r], offset[r+1]) (dcm_batch_offsets) and its particles stay there;
- * thermo is double[4 R] = {E, W, KE, pairs} per replica.  Every stage of a
- * step is one launch over all replicas (per-replica boxes, grids, thresholds
- * and reductions are read from a device table).  The batched form steps over
+ * thermo is double[4 R] = {E, W, KE, pairs} per replica.  By default a whole
+ * timestep of all replicas is ONE persistent cooperative launch (the
+ * persistent plan): its stages are separated by grid-wide barriers, and the
+ * force stage pulls (replica, tile) work items of 32 particles from a device
+ * queue (Section 2.4's dynamic tasks).  dcm_batch_set_persistent(b, 0)
+ * selects the per-stage plan instead (each stage one launch over all
+ * replicas).  Per-replica boxes, grids, thresholds and reductions are read
+ * from a device table in both plans.  The batched form steps over
  * cell lists: p->skin must be 0, and p->min_component 0 (no bubble filter).
  * Synchronous; allocates. */
 typedef struct dcm_batch dcm_batch;
@@ -371,7 +382,10 @@ int dcm_batch_set_force_block(dcm_batch* b, int32_t threads);
 
 /* As dcm_step_init / dcm_step for all replicas at once (asynchronous; the
  * distance sweeps run a fixed budget and report non-convergence through
- * dcm_batch_status). */
+ * dcm_batch_status).  In the persistent plan a barrier wait that runs past
+ * the wait budget (dcm_batch_set_wait_budget) ends the launch and records
+ * DCM_ERR_TIMEOUT in the batch's device status; the step's results are then
+ * undefined. */
 int dcm_batch_step_init(dcm_batch* b, dcm_state* st, dcm_stream_t stream);
 int dcm_batch_step(dcm_batch* b, dcm_state* st, double dt, int32_t nsteps, dcm_stream_t stream);
 
@@ -380,6 +394,37 @@ int dcm_batch_step(dcm_batch* b, dcm_state* st, double dt, int32_t nsteps, dcm_s
  * on `stream` (must not be the legacy default stream); st->t must be a
  * multiple of K.  The graph is bound to st's buffers.  Nothing is executed. */
 int dcm_batch_capture(dcm_batch* b, dcm_state* st, double dt, dcm_stream_t stream);
+
+/* 1 (default): the persistent plan, one cooperative launch per timestep;
+ * 0: the per-stage plan.  Both give the same results (bit for bit, except
+ * for the order of floating-point atomics, which neither plan uses).
+ * Invalidates a captured graph. */
+int dcm_batch_set_persistent(dcm_batch* b, int32_t on);
+
+/* The DCM_ACC_* form of the batched force stage, written to *form: the
+ * context rule of dcm_accumulation, then DCM_ACC_PLANE_FP64 for every FP64
+ * form and DCM_ACC_PLANE_KAHAN for every other compensated one (the batched
+ * form runs the plain and the plane forms).  Host only. */
+int dcm_batch_accumulation(const dcm_batch* b, int32_t* form);
+
+/* Particles per work item of the persistent plan's force queue: a multiple
+ * of 32 in 32 .. 4096 (default 32; set by the autotuner).  Each item lies in
+ * one replica; a warp takes one item at a time.  Invalidates a captured
+ * graph. */
+int dcm_batch_set_tile(dcm_batch* b, int32_t particles);
+
+/* Longest time, in nanoseconds (>= 1000), that a block of the persistent
+ * plan waits at a grid barrier before it gives up with DCM_ERR_TIMEOUT.
+ * Default 2 s.  Invalidates a captured graph. */
+int dcm_batch_set_wait_budget(dcm_batch* b, int64_t ns);
+
+/* Self-test of the persistent plan's failure path: launches the persistent
+ * grid with one barrier that waits for `phantom` (> 0) blocks that do not
+ * exist, so every wait must run out after budget_ns (1000 .. 1e10)
+ * nanoseconds and every block must return.  Synchronises `stream` and returns
+ * the device status it read and cleared: DCM_ERR_TIMEOUT when the waits ran
+ * out as they must (phantom = 0: DCM_OK). */
+int dcm_batch_barrier_selftest(dcm_batch* b, int32_t phantom, int64_t budget_ns, dcm_stream_t stream);
 
 /* Launch the captured graph ngraphs times (st->t advances by
  * ngraphs * dcm_batch_graph_steps).  st must hold the captured buffers. */

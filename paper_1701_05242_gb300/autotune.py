@@ -1,20 +1,23 @@
 """Autotuner for the batched form: picks the force-cell edges (l, and lx
-along the rows) and the force kernel's block size by timing a few steps of
-every candidate on the actual replicas (CUDA events on the stepping stream).
+along the rows) and the launch plan with its work size by timing a few steps
+of every candidate on the actual replicas (CUDA events on the stepping
+stream).
 
 Candidates: (l, lx) in {(1.5, 1.5), (1.5, 0.75), (1.5, 0.5), (1.0, 1.0),
 (0.75, 0.75)} where both divide every replica box (h = 1.5 stays the
-density-grid edge), block sizes {64, 128, 256}.
+density-grid edge), crossed with the persistent plan at force-queue tiles of
+{32, 64, 128} particles and the per-stage plan at force blocks of {64, 128,
+256} threads.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import dcm as D
 
 EDGES = ((1.5, 1.5), (1.5, 0.75), (1.5, 0.5), (1.0, 1.0), (0.75, 0.75))
-BLOCKS = (64, 128, 256)
+PLANS = (("persistent", 32), ("persistent", 64), ("persistent", 128),
+         ("stages", 64), ("stages", 128), ("stages", 256))
 
 
 def divides(box, edge):
@@ -29,8 +32,17 @@ def make_batch(boxes, counts, pos, vel, precision, K, edge, lx=0.0, **kw):
     return b, st
 
 
-def tune(boxes, counts, pos, vel, precision=D.DCM_PREC_MIXED, K=10, dt=0.005, steps=3, **kw):
-    """Returns (best (edge, lx, block), {(edge, lx, block): ms per step})."""
+def apply_plan(b, plan, size):
+    """Select the launch plan and its work size on batch b."""
+    D.dcm_batch_set_persistent(b, plan == "persistent")
+    if plan == "persistent":
+        D.dcm_batch_set_tile(b, size)
+    else:
+        D.dcm_batch_set_force_block(b, size)
+
+
+def tune(boxes, counts, pos, vel, precision=D.DCM_PREC_MIXED, K=10, dt=0.005, steps=3, plans=PLANS, **kw):
+    """Returns (best (edge, lx, plan, size), {(edge, lx, plan, size): ms per step})."""
     results = {}
     stream = torch.cuda.current_stream()
     for edge, lx in EDGES:
@@ -38,15 +50,15 @@ def tune(boxes, counts, pos, vel, precision=D.DCM_PREC_MIXED, K=10, dt=0.005, st
             continue
         b, st = make_batch(boxes, counts, pos, vel, precision, K, edge, lx, **kw)
         D.dcm_batch_step_init(b, st)
-        for bs in BLOCKS:
-            D.dcm_batch_set_force_block(b, bs)
+        for plan, size in plans:
+            apply_plan(b, plan, size)
             D.dcm_batch_step(b, st, dt, 1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             D.dcm_batch_step(b, st, dt, steps)
             e1.record(stream)
             e1.synchronize()
-            results[(edge, lx, bs)] = e0.elapsed_time(e1) / steps
+            results[(edge, lx, plan, size)] = e0.elapsed_time(e1) / steps
         b.close()
     best = min(results, key=results.get)
     return best, results

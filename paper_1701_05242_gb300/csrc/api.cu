@@ -213,7 +213,7 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
   if (p->min_component < 0) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "min_component must be >= 0");
   if (p->force_kernel != DCM_FORCE_AUTO && p->force_kernel != DCM_FORCE_THREAD && p->force_kernel != DCM_FORCE_PACKED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
-  if (p->accumulation < DCM_ACC_AUTO || p->accumulation > DCM_ACC_PAIR_FP64)
+  if (p->accumulation < DCM_ACC_AUTO || p->accumulation > DCM_ACC_PLANE_KAHAN)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "accumulation must be one of DCM_ACC_*");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "precision must be DCM_PREC_FP64 or DCM_PREC_MIXED");

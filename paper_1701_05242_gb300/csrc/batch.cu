@@ -1,16 +1,12 @@
 // Batched form: R independent systems (replicas) of different sizes stepped
-// together, each stage one launch over the concatenation of all replicas.
-//
-// Layout: the replicas' particles are concatenated (replica r owns sorted
-// slots [p0_r, p1_r)), their force cells are concatenated (replica r's cells
-// start at c0_r) and so are their density boxes (b0_r).  A particle never
-// leaves its replica, so its replica index is fixed (rep_of_particle); a box's
-// replica index is fixed too (rep_of_box).  Because cells are concatenated in
-// replica order, one exclusive scan over all cell counts gives every
-// replica's cell starts as global slot indices, and the single-system scan,
-// scatter and per-cell sort work unchanged on the concatenation.  The kernels
-// that depend on the box geometry read it from a per-replica table.
-//
+// together.  Two launch plans share the per-element device code of
+// batch_core.cuh:
+//   - the persistent plan (default): one cooperative launch per timestep that
+//     runs every stage, with bounded grid-wide barriers between them and the
+//     force stage pulling (replica, tile) work items from a device queue
+//     (batch_persist.cu);
+//   - the per-stage plan: each stage one launch over the concatenation of all
+//     replicas (this file).
 // The whole K-step recomputation period can be captured once in a CUDA graph
 // and replayed (dcm_batch_capture / dcm_batch_replay): every size is fixed,
 // the distance sweeps run a fixed budget with device-side early exit, and no
@@ -22,49 +18,7 @@
 #include <new>
 #include <vector>
 
-#include "forces_core.cuh"
-
-namespace dcm {
-
-struct RepGeom {
-  int64_t p0, p1;  // particle slots
-  int64_t c0;      // first force cell
-  int64_t b0;      // first density box
-  int nc[3];       // force cells per dimension
-  int nb[3];       // density boxes per dimension
-  double L[3];     // box lengths
-};
-
-constexpr int kBatchHistBins = 4096;  // per-replica histogram of box sums
-constexpr int64_t kThermoChunk = 4096;  // particles per block of the per-replica sums
-
-}  // namespace dcm
-
-struct dcm_batch {
-  dcm_params p;
-  int R;
-  int precision;
-  int64_t ntot, ncell_tot, nbox_tot;
-  dcm_ctx base;  // scratch sized for the concatenation (shared launchers use it)
-  std::vector<dcm::RepGeom> geom_h;
-  dcm::RepGeom* geom;
-  uint16_t* rep_of_particle;
-  uint16_t* rep_of_box;
-  int32_t* thr;       // [R][4]: gmin, gmax, T, unused
-  int32_t* hist;      // [R][kBatchHistBins]
-  void* w_i;          // per-particle virial (real)
-  void* ke_i;         // per-particle kinetic energy (real)
-  int32_t* np_i;      // per-particle accepted pairs
-  int32_t nchunk;     // thermo reduction: chunks of at most kThermoChunk particles of one replica
-  int64_t* chunk;     // [nchunk][2]: first, end particle
-  int32_t* chunk0;    // [R + 1]: first chunk of each replica
-  double* tpart;      // [4][nchunk]: per-chunk E, W, KE, pairs
-  int force_block;    // threads per block of the force kernel
-  cudaGraphExec_t graph;
-  int graph_steps;
-  int64_t graph_launches;  // kernels per replay
-  void* graph_key[8];
-};
+#include "batch_core.cuh"
 
 namespace dcm {
 
@@ -78,32 +32,7 @@ static int berr(dcm_batch* b, int code, const char* fmt, ...) {
   return code;
 }
 
-template <typename R>
-__device__ __forceinline__ R wrapL(R x, R L) {
-  if (x >= L) x -= L;
-  if (x < (R)0) {
-    x += L;
-    if (x >= L) x = (R)0;
-  }
-  return x;
-}
-
-template <typename R>
-__device__ __forceinline__ Grid<R> rep_cells(const RepGeom& G, R l, R il, R lx, R ilx) {
-  Grid<R> g;
-  for (int d = 0; d < 3; ++d) {
-    g.n[d] = G.nc[d];
-    g.L[d] = (R)G.L[d];
-  }
-  g.edge = l;
-  g.inv_edge = il;
-  g.edge_x = lx;
-  g.inv_edge_x = ilx;
-  g.ncell = (int64_t)G.nc[0] * G.nc[1] * G.nc[2];
-  return g;
-}
-
-// ---- integrate + bin ---------------------------------------------------------
+// ---- per-stage kernels (one thread per element) ----------------------------------
 template <typename R>
 __global__ void k_b_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__ pos, typename RT<R>::R4* __restrict__ vel,
                                      const typename RT<R>::R4* __restrict__ force, R half_dt, R dt, R l, R il,
@@ -111,27 +40,7 @@ __global__ void k_b_kick_drift_count(int64_t n, typename RT<R>::R4* __restrict__
                                      int32_t* __restrict__ cell, int32_t* __restrict__ slot, int32_t* __restrict__ count,
                                      int drift) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const RepGeom& G = geom[rep[i]];
-  auto p = pos[i];
-  if (drift) {
-    auto v = vel[i];
-    auto f = force[i];
-    v.x += half_dt * f.x;
-    v.y += half_dt * f.y;
-    v.z += half_dt * f.z;
-    p.x = wrapL<R>(p.x + dt * v.x, (R)G.L[0]);
-    p.y = wrapL<R>(p.y + dt * v.y, (R)G.L[1]);
-    p.z = wrapL<R>(p.z + dt * v.z, (R)G.L[2]);
-    pos[i] = p;
-    vel[i] = v;
-  }
-  int cx = cell_coord<R>(p.x, lx, ilx, G.nc[0]);
-  int cy = cell_coord<R>(p.y, l, il, G.nc[1]);
-  int cz = cell_coord<R>(p.z, l, il, G.nc[2]);
-  int c = (int)G.c0 + cx + G.nc[0] * (cy + G.nc[1] * cz);
-  cell[i] = c;
-  slot[i] = atomicAdd(count + c, 1);
+  if (i < n) b_kick_drift_count<R>(i, pos, vel, force, half_dt, dt, l, il, lx, ilx, geom, rep, cell, slot, count, drift);
 }
 
 template <typename R>
@@ -140,12 +49,7 @@ __global__ void k_b_gather(int64_t n, const int32_t* __restrict__ perm, const ty
                            typename RT<R>::R4* __restrict__ v1, const R* __restrict__ r0, R* __restrict__ r1,
                            const int32_t* __restrict__ id0, int32_t* __restrict__ id1) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  int src = perm[k];
-  p1[k] = p0[src];
-  v1[k] = v0[src];
-  r1[k] = r0[src];
-  if (id0) id1[k] = id0[src];
+  if (k < n) b_gather<R>(k, perm, p0, p1, v0, v1, r0, r1, id0, id1);
 }
 
 template <typename R>
@@ -153,198 +57,48 @@ __global__ void k_b_box_count(int64_t n, const typename RT<R>::R4* __restrict__ 
                               const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep,
                               int32_t* __restrict__ count) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const RepGeom& G = geom[rep[i]];
-  auto p = pos[i];
-  int cx = cell_coord<R>(p.x, h, ih, G.nb[0]);
-  int cy = cell_coord<R>(p.y, h, ih, G.nb[1]);
-  int cz = cell_coord<R>(p.z, h, ih, G.nb[2]);
-  atomicAdd(count + G.b0 + cx + G.nb[0] * (cy + G.nb[1] * cz), 1);
+  if (i < n) b_box_count<R>(i, pos, h, ih, geom, rep, count);
 }
 
-// ---- interface detection (per replica) -----------------------------------------
 template <int AXIS>
 __global__ void k_b_box_sum(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t nbox,
                             const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep, int w) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbox) return;
-  const RepGeom& G = geom[rep[b]];
-  int64_t lb = b - G.b0;
-  int nx = G.nb[0], ny = G.nb[1], nz = G.nb[2];
-  int x = (int)(lb % nx), y = (int)((lb / nx) % ny), z = (int)(lb / ((int64_t)nx * ny));
-  int n = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);
-  int c = AXIS == 0 ? x : (AXIS == 1 ? y : z);
-  int64_t stride = AXIS == 0 ? 1 : (AXIS == 1 ? nx : (int64_t)nx * ny);
-  int64_t base = b - (int64_t)c * stride;
-  int s = 0;
-  for (int a = -w; a <= w; ++a) {
-    int k = (c + a) % n;
-    if (k < 0) k += n;
-    s += in[base + (int64_t)k * stride];
-  }
-  out[b] = s;
+  if (b < nbox) b_box_sum<AXIS>(b, in, out, geom, rep, w);
 }
 
 __global__ void k_b_thr_init(int32_t* thr, int R, int fixed) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  thr[4 * r + 0] = INT_MAX;
-  thr[4 * r + 1] = INT_MIN;
-  thr[4 * r + 2] = fixed;
+  if (r < R) b_thr_init(r, thr, fixed);
 }
 
 __global__ void k_b_minmax(const int32_t* __restrict__ g, int64_t nbox, const uint16_t* __restrict__ rep, int32_t* thr) {
-  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int r = b < nbox ? rep[b] : -1;
-  int v = b < nbox ? g[b] : 0;
-  int r0 = __shfl_sync(0xffffffffu, r, 0);
-  bool uniform = __all_sync(0xffffffffu, r == r0);
-  if (uniform) {
-    if (r0 < 0) return;
-    int lo = v, hi = v;
-    for (int o = 16; o > 0; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicMin(thr + 4 * r0, lo);
-      atomicMax(thr + 4 * r0 + 1, hi);
-    }
-  } else if (r >= 0) {
-    atomicMin(thr + 4 * r, v);
-    atomicMax(thr + 4 * r + 1, v);
-  }
+  b_minmax((int64_t)blockIdx.x * blockDim.x + threadIdx.x, g, nbox, rep, thr);
 }
 
 __global__ void k_b_value_hist(const int32_t* __restrict__ g, int64_t nbox, const uint16_t* __restrict__ rep,
                                const int32_t* thr, int32_t* hist, int32_t* status) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbox) return;
-  int r = rep[b];
-  int gmin = thr[4 * r], gmax = thr[4 * r + 1];
-  if ((int64_t)gmax - gmin >= kBatchHistBins) {
-    raise_status(status, DCM_ERR_CAPACITY);
-    return;
-  }
-  atomicAdd(hist + (int64_t)r * kBatchHistBins + (g[b] - gmin), 1);
+  if (b < nbox) b_value_hist(b, g, rep, thr, hist, status);
 }
 
-__device__ long long bsum_ll(long long v, long long* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  long long t = 0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
-  return t;
-}
-
-// one block per replica: integer 2-means on the replica's histogram (same
-// iteration as the single-system detection)
+// one block per replica
 __global__ void k_b_two_means(const int32_t* __restrict__ hist, int32_t* thr, int max_iter) {
-  __shared__ long long sh[32];
-  __shared__ int T_sh;
-  int r = blockIdx.x;
-  if (thr[4 * r + 2] >= 0) return;  // fixed threshold
-  int gmin = thr[4 * r], gmax = thr[4 * r + 1];
-  if ((int64_t)gmax - gmin >= kBatchHistBins) return;
-  const int32_t* h = hist + (int64_t)r * kBatchHistBins;
-  int Rn = gmax - gmin + 1;
-  if (threadIdx.x == 0) T_sh = (int)(((long long)gmin + gmax) / 2);
-  __syncthreads();
-  for (int it = 0; it < max_iter; ++it) {
-    int T = T_sh;
-    long long n0 = 0, n1 = 0, s0 = 0, s1 = 0;
-    for (int k = threadIdx.x; k < Rn; k += blockDim.x) {
-      long long c = h[k], v = (long long)(gmin + k);
-      if (gmin + k < T) {
-        n0 += c;
-        s0 += c * v;
-      } else {
-        n1 += c;
-        s1 += c * v;
-      }
-    }
-    n0 = bsum_ll(n0, sh);
-    n1 = bsum_ll(n1, sh);
-    s0 = bsum_ll(s0, sh);
-    s1 = bsum_ll(s1, sh);
-    __syncthreads();
-    int stop = 0;
-    if (n0 == 0 || n1 == 0) {
-      if (threadIdx.x == 0) T_sh = gmax + 1;
-      stop = 1;
-    } else {
-      int Tn = (int)((s0 * n1 + s1 * n0) / (2 * n0 * n1) + 1);
-      if (Tn == T) stop = 1;
-      if (threadIdx.x == 0) T_sh = Tn;
-    }
-    __syncthreads();
-    if (stop) break;
-  }
-  if (threadIdx.x == 0) thr[4 * r + 2] = T_sh;
+  b_two_means(blockIdx.x, hist, thr, max_iter);
 }
 
 __global__ void k_b_segment(const int32_t* __restrict__ g, int64_t nbox, const RepGeom* __restrict__ geom,
                             const uint16_t* __restrict__ rep, const int32_t* thr, uint8_t* __restrict__ s,
                             uint8_t* __restrict__ iface) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbox) return;
-  int r = rep[b];
-  const RepGeom& G = geom[r];
-  int T = thr[4 * r + 2];
-  int64_t lb = b - G.b0;
-  int nx = G.nb[0], ny = G.nb[1], nz = G.nb[2];
-  int x = (int)(lb % nx), y = (int)((lb / nx) % ny), z = (int)(lb / ((int64_t)nx * ny));
-  int me = g[b] >= T;
-  int f = 0;
-  if (me) {
-    const int32_t* gb = g + G.b0;
-    int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
-    f |= gb[row + xm] < T;
-    f |= gb[row + xp] < T;
-    f |= gb[x + nx * (ym + (int64_t)ny * z)] < T;
-    f |= gb[x + nx * (yp + (int64_t)ny * z)] < T;
-    f |= gb[x + nx * (y + (int64_t)ny * zm)] < T;
-    f |= gb[x + nx * (y + (int64_t)ny * zp)] < T;
-  }
-  s[b] = (uint8_t)me;
-  iface[b] = (uint8_t)f;
+  if (b < nbox) b_segment(b, g, geom, rep, thr, s, iface);
 }
 
-// ---- distances (per replica grids, one convergence flag for all) ----------------
 template <typename R>
 __global__ void k_b_dist_init(const uint8_t* __restrict__ s, const uint8_t* __restrict__ iface, int64_t nbox,
                               R* __restrict__ D0, R* __restrict__ D1) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbox) return;
-  R v = (!s[b] || iface[b]) ? (R)0 : RT<R>::inf();
-  D0[b] = v;
-  D1[b] = v;
-}
-
-template <typename R>
-__device__ __forceinline__ R b_godunov3(R a0, R a1, R a2, R h) {
-  R t;
-  if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
-  if (a1 > a2) { t = a1; a1 = a2; a2 = t; }
-  if (a0 > a1) { t = a0; a0 = a1; a1 = t; }
-  R d = a0 + h;
-  if (d > a1) {
-    R df = a0 - a1;
-    d = (R)0.5 * (a0 + a1 + sqrt((R)2 * h * h - df * df));
-    if (d > a2) {
-      R sa = a0 + a1 + a2;
-      R sq = a0 * a0 + a1 * a1 + a2 * a2;
-      R disc = sa * sa - (R)3 * (sq - h * h);
-      d = (sa + sqrt(disc > (R)0 ? disc : (R)0)) / (R)3;
-    }
-  }
-  return d;
+  if (b < nbox) b_dist_init<R>(b, s, iface, D0, D1);
 }
 
 template <typename R>
@@ -353,29 +107,8 @@ __global__ void k_b_dist_sweep(const R* __restrict__ Din, R* __restrict__ Dout, 
                                int32_t* __restrict__ flags, int it) {
   if (it > 0 && flags[it - 1] == 0) return;
   bool changed = false;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += (int64_t)gridDim.x * blockDim.x) {
-    R cur = Din[b];
-    if (cur == (R)0) continue;
-    const RepGeom& G = geom[rep[b]];
-    int64_t lb = b - G.b0;
-    int nx = G.nb[0], ny = G.nb[1], nz = G.nb[2];
-    int x = (int)(lb % nx), y = (int)((lb / nx) % ny), z = (int)(lb / ((int64_t)nx * ny));
-    const R* D = Din + G.b0;
-    int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
-    R a0 = fmin(D[row + xm], D[row + xp]);
-    R a1 = fmin(D[x + nx * (ym + (int64_t)ny * z)], D[x + nx * (yp + (int64_t)ny * z)]);
-    R a2 = fmin(D[x + nx * (y + (int64_t)ny * zm)], D[x + nx * (y + (int64_t)ny * zp)]);
-    R d = b_godunov3<R>(a0, a1, a2, h);
-    R out = cur;
-    if (d < cur && d <= r_grid) {
-      out = d;
-      changed = true;
-    }
-    Dout[b] = out;
-  }
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += (int64_t)gridDim.x * blockDim.x)
+    changed |= b_dist_update<R>(b, Din, Dout, geom, rep, h, r_grid);
   if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
 }
 
@@ -389,86 +122,28 @@ __global__ void k_b_dist_finish(const int32_t* flags, int sweeps, int32_t* statu
   if (first < 0) raise_status(status, DCM_ERR_NOT_CONVERGED);
 }
 
-// ---- cutoffs ----------------------------------------------------------------------
 template <typename R>
 __global__ void k_b_cutoffs(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ D,
                             const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep, R h, R r_grid,
                             R rc_min, R rc_max, R ramp, R* __restrict__ rc) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const RepGeom& G = geom[rep[i]];
-  auto p = ldg4(pos + i);
-  int k[3];
-  R t[3];
-  R x[3] = {p.x, p.y, p.z};
-  for (int d = 0; d < 3; ++d) {
-    R q = floor(x[d] / h - (R)0.5);
-    int kk = (int)q;
-    if (((R)kk + (R)0.5) * h > x[d])
-      --kk;
-    else if (((R)kk + (R)1.5) * h <= x[d])
-      ++kk;
-    k[d] = kk;
-    t[d] = (x[d] - ((R)kk + (R)0.5) * h) / h;
-  }
-  auto wrapk = [](int kk, int nn) { kk %= nn; return kk < 0 ? kk + nn : kk; };
-  int nx = G.nb[0], ny = G.nb[1], nz = G.nb[2];
-  int x0 = wrapk(k[0], nx), x1 = wrapk(k[0] + 1, nx);
-  int y0 = wrapk(k[1], ny), y1 = wrapk(k[1] + 1, ny);
-  int z0 = wrapk(k[2], nz), z1 = wrapk(k[2] + 1, nz);
-  const R* Dr = D + G.b0;
-  auto at = [&](int a, int b, int c) {
-    R v = Dr[a + (int64_t)nx * (b + (int64_t)ny * c)];
-    return v < r_grid ? v : r_grid;
-  };
-  auto lerp = [](R a, R b, R tt) { return fma(tt, b - a, a); };
-  R c00 = lerp(at(x0, y0, z0), at(x1, y0, z0), t[0]);
-  R c10 = lerp(at(x0, y1, z0), at(x1, y1, z0), t[0]);
-  R c01 = lerp(at(x0, y0, z1), at(x1, y0, z1), t[0]);
-  R c11 = lerp(at(x0, y1, z1), at(x1, y1, z1), t[0]);
-  R delta = lerp(lerp(c00, c10, t[1]), lerp(c01, c11, t[1]), t[2]);
-  R r;
-  if (ramp > (R)0) {
-    r = rc_max - (rc_max - rc_min) * delta / ramp;
-    r = r < rc_min ? rc_min : (r > rc_max ? rc_max : r);
-  } else {
-    r = delta > (R)0 ? rc_min : rc_max;
-  }
-  rc[i] = r;
+  if (i < n) b_cutoffs<R>(i, pos, D, geom, rep, h, r_grid, rc_min, rc_max, ramp, rc);
 }
 
-// ---- forces -----------------------------------------------------------------------
 template <typename R, bool TYPED, bool X2, Accum M>
 __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
                            const int32_t* __restrict__ start, ForceArgs<R> a, const RepGeom* __restrict__ geom,
                            const uint16_t* __restrict__ rep, typename RT<R>::R4* __restrict__ force,
                            R* __restrict__ w_i, int32_t* __restrict__ np_i) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const RepGeom& G = geom[rep[i]];
-  Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge, a.g.edge_x, a.g.inv_edge_x);
-  double e = 0, w = 0;
-  int np = 0;
-  force[i] = force_one<R, TYPED, X2, M>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
-  w_i[i] = (R)w;
-  np_i[i] = np;
+  if (i < n) b_force<R, TYPED, X2, M>(i, pos, rc, start, a, geom, rep, force, w_i, np_i);
 }
 
-// ---- kick + per-replica thermo ----------------------------------------------------
 template <typename R>
 __global__ void k_b_kick(int64_t n, typename RT<R>::R4* __restrict__ vel, const typename RT<R>::R4* __restrict__ force,
                          R half_dt, R* __restrict__ ke_i) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  auto v = vel[i];
-  if (force) {
-    auto f = force[i];
-    v.x += half_dt * f.x;
-    v.y += half_dt * f.y;
-    v.z += half_dt * f.z;
-    vel[i] = v;
-  }
-  ke_i[i] = (R)0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+  if (i < n) b_kick<R>(i, vel, force, half_dt, ke_i);
 }
 
 // Per-replica thermo in two fixed-order levels: one block per chunk of at
@@ -479,39 +154,13 @@ __global__ void k_b_thermo_chunks(const int64_t* __restrict__ chunk, int32_t nch
                                   const typename RT<R>::R4* __restrict__ force, const R* __restrict__ w_i,
                                   const R* __restrict__ ke_i, const int32_t* __restrict__ np_i,
                                   double* __restrict__ tpart) {
-  __shared__ double sh[4][8];
-  const int64_t p0 = chunk[2 * blockIdx.x], p1 = chunk[2 * blockIdx.x + 1];
-  double v[4] = {0, 0, 0, 0};
-  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
-    v[0] += (double)force[i].w;
-    v[1] += (double)w_i[i];
-    v[2] += (double)ke_i[i];
-    v[3] += (double)np_i[i];
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = 0; q < 4; ++q)
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-  if (lane == 0)
-    for (int q = 0; q < 4; ++q) sh[q][wid] = v[q];
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[threadIdx.x][k];
-    tpart[(int64_t)threadIdx.x * nchunk + blockIdx.x] = t;
-  }
+  b_thermo_chunk<R>(blockIdx.x, chunk, nchunk, force, w_i, ke_i, np_i, tpart);
 }
 
 __global__ void k_b_thermo_sum(const int32_t* __restrict__ chunk0, int R, int32_t nchunk,
                                const double* __restrict__ tpart, double* __restrict__ thermo) {
-  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (r >= R) return;
-  const int c0 = chunk0[r], c1 = chunk0[r + 1];
-  for (int q = 0; q < 4; ++q) {
-    double t = 0;
-    for (int c = c0 + lane; c < c1; c += 32) t += tpart[(int64_t)q * nchunk + c];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) thermo[4 * r + q] = t;
-  }
+  const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (r < R) b_thermo_sum(r, chunk0, nchunk, tpart, thermo);
 }
 
 // ---- orchestration ------------------------------------------------------------------
@@ -565,8 +214,37 @@ static int b_recompute(dcm_batch* b, const typename RT<R>::R4* pos, R* rc, cudaS
   return check_launch(ctx, "batch recompute");
 }
 
+template <typename R>
+ForceArgs<R> batch_force_args(const dcm_batch* b) {
+  ForceArgs<R> a;
+  a.g.edge = (R)b->p.l;
+  a.g.inv_edge = (R)(1.0 / b->p.l);
+  a.g.edge_x = (R)b->p.lx;
+  a.g.inv_edge_x = (R)(1.0 / b->p.lx);
+  LJTable t = lj_table(b->p);
+  a.ntypes = t.ntypes;
+  for (int k = 0; k < 16; ++k) {
+    a.eps24[k] = (R)t.deps24[k];
+    a.eps4[k] = (R)t.deps4[k];
+    a.sig2[k] = (R)t.dsig2[k];
+  }
+  a.shift = b->p.shift_energy;
+  a.rc_max = (R)b->p.rc_max;
+  return a;
+}
+template ForceArgs<float> batch_force_args<float>(const dcm_batch*);
+template ForceArgs<double> batch_force_args<double>(const dcm_batch*);
+
 // The batched force kernel for the LJ table and the accumulation form
-// (DCM_ACC_*, resolved as for a single system).
+// (DCM_ACC_*, resolved as for a single system; the batched form runs the
+// plain and plane forms, and the plane form of the other compensated ones).
+int batch_accumulation(const dcm_batch* b) {
+  const int m = resolve_accumulation(&b->base);
+  if (m == DCM_ACC_FP32) return m;
+  return (m == DCM_ACC_ROW_FP64 || m == DCM_ACC_PAIR_FP64 || m == DCM_ACC_PLANE_FP64) ? DCM_ACC_PLANE_FP64
+                                                                                      : DCM_ACC_PLANE_KAHAN;
+}
+
 template <typename R>
 static auto b_force_kernel(bool typed, int ntypes, int acc) {
   using K = void (*)(int64_t, const typename RT<R>::R4*, const R*, const int32_t*, ForceArgs<R>, const RepGeom*,
@@ -574,18 +252,15 @@ static auto b_force_kernel(bool typed, int ntypes, int acc) {
   if constexpr (sizeof(R) == 8) {
     return typed ? (K)k_b_forces<R, true, false, Accum::kPlain> : (K)k_b_forces<R, false, false, Accum::kPlain>;
   } else {
-    if (typed && ntypes > 2)
-      return acc == DCM_ACC_FP32 ? (K)k_b_forces<R, true, false, Accum::kPlain>
-                                 : (acc == DCM_ACC_ROW_FP64 || acc == DCM_ACC_PAIR_FP64)
-                                       ? (K)k_b_forces<R, true, false, Accum::kRowF64>
-                                       : (K)k_b_forces<R, true, false, Accum::kRowKahan>;
-    switch (acc) {
-      case DCM_ACC_FP32: return typed ? (K)k_b_forces<R, true, true, Accum::kPlain> : (K)k_b_forces<R, false, true, Accum::kPlain>;
-      case DCM_ACC_ROW_FP64: return typed ? (K)k_b_forces<R, true, true, Accum::kRowF64> : (K)k_b_forces<R, false, true, Accum::kRowF64>;
-      case DCM_ACC_PAIR_KAHAN: return typed ? (K)k_b_forces<R, true, true, Accum::kPairKahan> : (K)k_b_forces<R, false, true, Accum::kPairKahan>;
-      case DCM_ACC_PAIR_FP64: return typed ? (K)k_b_forces<R, true, true, Accum::kPairF64> : (K)k_b_forces<R, false, true, Accum::kPairF64>;
-      default: return typed ? (K)k_b_forces<R, true, true, Accum::kRowKahan> : (K)k_b_forces<R, false, true, Accum::kRowKahan>;
-    }
+    const bool x2 = !(typed && ntypes > 2);
+    auto pick = [&](auto tag) -> K {
+      constexpr Accum M = decltype(tag)::value;
+      if (!x2) return (K)k_b_forces<R, true, false, M>;
+      return typed ? (K)k_b_forces<R, true, true, M> : (K)k_b_forces<R, false, true, M>;
+    };
+    if (acc == DCM_ACC_FP32) return pick(AccumTag<Accum::kPlain>{});
+    if (acc == DCM_ACC_PLANE_FP64) return pick(AccumTag<Accum::kPlaneF64>{});
+    return pick(AccumTag<Accum::kPlaneKahan>{});
   }
 }
 
@@ -595,24 +270,12 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
   dcm_ctx* ctx = &b->base;
   int64_t n = b->ntot;
   if (n > 0) {
-    ForceArgs<R> a;
-    a.g.edge = (R)b->p.l;
-    a.g.inv_edge = (R)(1.0 / b->p.l);
-    a.g.edge_x = (R)b->p.lx;
-    a.g.inv_edge_x = (R)(1.0 / b->p.lx);
-    LJTable t = lj_table(b->p);
-    a.ntypes = t.ntypes;
-    for (int k = 0; k < 16; ++k) {
-      a.eps24[k] = (R)t.deps24[k];
-      a.eps4[k] = (R)t.deps4[k];
-      a.sig2[k] = (R)t.dsig2[k];
-    }
-    a.shift = b->p.shift_energy;
-    a.rc_max = (R)b->p.rc_max;
+    const ForceArgs<R> a = batch_force_args<R>(b);
+    const LJTable t = lj_table(b->p);
     int bs = b->force_block;
     // the packed loop in FP32 for one type, and for one or two types with
     // their own eps and sigma; the scalar loop otherwise
-    auto kern = b_force_kernel<R>(lj_general(t), t.ntypes, resolve_accumulation(ctx));
+    auto kern = b_force_kernel<R>(lj_general(t), t.ntypes, batch_accumulation(b));
     stage_begin(ctx, DCM_STAGE_FORCES, st);
     DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
                b->rep_of_particle, force, (R*)b->w_i, b->np_i);
@@ -660,6 +323,13 @@ static int b_bin_gather(dcm_batch* b, dcm_state* s, bool drift, R hdt, R dt, cud
 template <typename R>
 static int b_init(dcm_batch* b, dcm_state* s, cudaStream_t st) {
   using R4 = typename RT<R>::R4;
+  if (b->persistent) {
+    int r = b_persistent_step<R>(b, s, (R)0, (R)0, false, true, false, st);
+    if (r) return r;
+    s->cur = 1 - s->cur;
+    s->t = 0;
+    return DCM_OK;
+  }
   int r = b_bin_gather<R>(b, s, false, (R)0, (R)0, st);
   if (r) return r;
   int o = 1 - s->cur;
@@ -678,6 +348,13 @@ static int b_steps(dcm_batch* b, dcm_state* s, double dt, int nsteps, cudaStream
   R hdt = (R)(0.5 * dt), rdt = (R)dt;
   int K = b->p.recompute_every;
   for (int k = 0; k < nsteps; ++k) {
+    if (b->persistent) {
+      s->t += 1;
+      int r = b_persistent_step<R>(b, s, hdt, rdt, true, s->t % K == 0, true, st);
+      if (r) return r;
+      s->cur = 1 - s->cur;
+      continue;
+    }
     int r = b_bin_gather<R>(b, s, true, hdt, rdt, st);
     if (r) return r;
     int o = 1 - s->cur;
@@ -706,7 +383,8 @@ extern "C" void dcm_batch_destroy(dcm_batch* b) {
   void* dev[] = {c->status, c->slot,  c->cell,  c->perm,   c->cell_start, c->cell_count, c->scan_part,
                  c->box_count, c->g,   c->g_tmp, c->s,      c->iface,      c->D[0],       c->D[1],
                  c->flags,  c->red,   c->red_tmp, c->totals, b->geom,       b->rep_of_particle, b->rep_of_box,
-                 b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart};
+                 b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart,
+                 b->tiles,  b->sync,  b->scan_blk};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (c->host_status) cudaFreeHost(c->host_status);
@@ -775,6 +453,14 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   b->chunk0 = nullptr;
   b->tpart = nullptr;
   b->force_block = 128;
+  b->persistent = 1;
+  b->tiles = nullptr;
+  b->ntiles = 0;
+  b->tile = 0;
+  b->sync = nullptr;
+  b->scan_blk = nullptr;
+  b->pgrid = 0;
+  b->wait_budget = (int64_t)2000000000;  // 2 s
   b->graph = nullptr;
   b->graph_steps = 0;
   b->graph_launches = 0;
@@ -856,6 +542,12 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
     cudaGetLastError();
     dcm_batch_destroy(b);
     return DCM_ERR_CUDA;
+  }
+  int ps = b_persistent_setup(b);
+  if (ps) {
+    cudaGetLastError();
+    dcm_batch_destroy(b);
+    return ps;
   }
   *out = b;
   return DCM_OK;
@@ -966,6 +658,48 @@ extern "C" int dcm_batch_replay(dcm_batch* b, dcm_state* s, int32_t ngraphs, dcm
 }
 
 extern "C" int dcm_batch_graph_steps(const dcm_batch* b) { return b ? b->graph_steps : 0; }
+
+extern "C" int dcm_batch_set_persistent(dcm_batch* b, int32_t on) {
+  if (!b || (on != 0 && on != 1)) return DCM_ERR_INVALID_ARG;
+  b->persistent = on;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return DCM_OK;
+}
+
+extern "C" int dcm_batch_accumulation(const dcm_batch* b, int32_t* form) {
+  if (!b || !form) return DCM_ERR_INVALID_ARG;
+  *form = b->precision == DCM_PREC_MIXED ? batch_accumulation(b) : DCM_ACC_FP32;
+  return DCM_OK;
+}
+
+extern "C" int dcm_batch_set_tile(dcm_batch* b, int32_t particles) {
+  if (!b) return DCM_ERR_INVALID_ARG;
+  int r = b_persistent_set_tile(b, particles);
+  if (r) return r;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return DCM_OK;
+}
+
+extern "C" int dcm_batch_set_wait_budget(dcm_batch* b, int64_t ns) {
+  if (!b || ns < 1000) return DCM_ERR_INVALID_ARG;
+  b->wait_budget = ns;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return DCM_OK;
+}
+
+extern "C" int dcm_batch_barrier_selftest(dcm_batch* b, int32_t phantom, int64_t budget_ns, dcm_stream_t stream) {
+  if (!b || phantom < 0 || budget_ns < 1000 || budget_ns > (int64_t)10000000000) return DCM_ERR_INVALID_ARG;
+  return b_persistent_wait_selftest(b, phantom, budget_ns, (cudaStream_t)stream);
+}
 
 extern "C" int dcm_batch_status(dcm_batch* b, dcm_stream_t stream) {
   if (!b) return DCM_ERR_INVALID_ARG;

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typenam
 // more sums per thread and get 80 (12 blocks).
 constexpr int kX2Block = 64;
 template <Accum M>
-constexpr int x2_min_blocks() { return M == Accum::kPlain ? 16 : 12; }
+constexpr int x2_min_blocks() { return (M == Accum::kPlain || plane_form(M)) ? 16 : 12; }
 
 template <bool TYPED, Accum M>
 __global__ void __launch_bounds__(kX2Block, x2_min_blocks<M>()) k_forces_x2(int64_t n, const float4* __restrict__ pos,
@@ -97,11 +97,12 @@ int resolve_force_kernel(const dcm_ctx* ctx) {
 }
 
 // The accumulation form a force launch of this context runs (DCM_ACC_*,
-// AUTO resolved; the FP64 form is plain FP64; the scalar FP32 kernel runs the
-// row form of a pair form).
+// AUTO resolved to the plane-Kahan form, measured the cheapest compensated
+// form at the accuracy of the FP64 ones; the FP64 precision form is plain
+// FP64; the scalar FP32 kernel runs the row form of a pair form).
 int resolve_accumulation(const dcm_ctx* ctx) {
   if (ctx->p.precision != DCM_PREC_MIXED) return DCM_ACC_FP32;
-  int m = ctx->p.accumulation == DCM_ACC_AUTO ? DCM_ACC_ROW_KAHAN : ctx->p.accumulation;
+  int m = ctx->p.accumulation == DCM_ACC_AUTO ? DCM_ACC_PLANE_KAHAN : ctx->p.accumulation;
   if (resolve_force_kernel(ctx) != DCM_FORCE_PACKED) {
     if (m == DCM_ACC_PAIR_KAHAN) m = DCM_ACC_ROW_KAHAN;
     if (m == DCM_ACC_PAIR_FP64) m = DCM_ACC_ROW_FP64;
@@ -163,21 +164,16 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   stage_begin(ctx, DCM_STAGE_FORCES, st);
   if constexpr (sizeof(R) == 4) {
     const int m = resolve_accumulation(ctx);
-    if (kind == DCM_FORCE_PACKED) {
-      switch (m) {
-        case DCM_ACC_FP32: launch_x2<Accum::kPlain>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-        case DCM_ACC_ROW_FP64: launch_x2<Accum::kRowF64>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-        case DCM_ACC_PAIR_KAHAN: launch_x2<Accum::kPairKahan>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-        case DCM_ACC_PAIR_FP64: launch_x2<Accum::kPairF64>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-        default: launch_x2<Accum::kRowKahan>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-      }
-    } else {
-      switch (m) {
-        case DCM_ACC_FP32: launch_scalar<float, Accum::kPlain>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-        case DCM_ACC_ROW_FP64: launch_scalar<float, Accum::kRowF64>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-        default: launch_scalar<float, Accum::kRowKahan>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st); break;
-      }
-    }
+    if (kind == DCM_FORCE_PACKED)
+      with_accum<true>(m, [&](auto tag) {
+        launch_x2<decltype(tag)::value>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st);
+        return 0;
+      });
+    else
+      with_accum<false>(m, [&](auto tag) {
+        launch_scalar<float, decltype(tag)::value>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st);
+        return 0;
+      });
   } else {
     launch_scalar<R, Accum::kPlain>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st);
   }

@@ -136,6 +136,8 @@ struct Acc2 {
 //   kPlain      no S: the partials are the sums (plain FP32);
 //   kRowF64     after every row segment the partials are added into FP64 sums;
 //   kRowKahan   ... into FP32 sums with Kahan compensation;
+//   kPlaneF64, kPlaneKahan  the same once per z-plane of the stencil (the
+//               partials then span the plane's rows: up to five at rc = 3);
 //   kPairKahan  every pair term goes into the partials with Kahan compensation
 //               (S holds the compensation of each packed lane);
 //   kPairF64    every pair term is added into FP64 sums (the partials stay 0).
@@ -144,9 +146,38 @@ enum class Accum : int {
   kRowF64 = DCM_ACC_ROW_FP64,
   kRowKahan = DCM_ACC_ROW_KAHAN,
   kPairKahan = DCM_ACC_PAIR_KAHAN,
-  kPairF64 = DCM_ACC_PAIR_FP64
+  kPairF64 = DCM_ACC_PAIR_FP64,
+  kPlaneF64 = DCM_ACC_PLANE_FP64,
+  kPlaneKahan = DCM_ACC_PLANE_KAHAN
 };
 constexpr bool row_form(Accum m) { return m == Accum::kRowF64 || m == Accum::kRowKahan; }
+constexpr bool plane_form(Accum m) { return m == Accum::kPlaneF64 || m == Accum::kPlaneKahan; }
+// forms whose pair loop is the plain one (the partials are taken over later or never)
+constexpr bool plain_loop(Accum m) { return m == Accum::kPlain || row_form(m) || plane_form(m); }
+constexpr bool f64_form(Accum m) { return m == Accum::kRowF64 || m == Accum::kPairF64 || m == Accum::kPlaneF64; }
+
+template <Accum M>
+using AccumTag = std::integral_constant<Accum, M>;
+
+// Call f(AccumTag<M>{}) for the form acc (a DCM_ACC_* value, AUTO resolved).
+// The scalar loop (X2 false) runs no pair form: its callers resolve those to
+// the row forms first.
+template <bool X2, typename F>
+__host__ auto with_accum(int acc, F&& f) {
+  switch (acc) {
+    case DCM_ACC_FP32: return f(AccumTag<Accum::kPlain>{});
+    case DCM_ACC_ROW_FP64: return f(AccumTag<Accum::kRowF64>{});
+    case DCM_ACC_ROW_KAHAN: return f(AccumTag<Accum::kRowKahan>{});
+    case DCM_ACC_PLANE_FP64: return f(AccumTag<Accum::kPlaneF64>{});
+    case DCM_ACC_PAIR_KAHAN:
+      if constexpr (X2) return f(AccumTag<Accum::kPairKahan>{});
+      else return f(AccumTag<Accum::kRowKahan>{});
+    case DCM_ACC_PAIR_FP64:
+      if constexpr (X2) return f(AccumTag<Accum::kPairF64>{});
+      else return f(AccumTag<Accum::kRowF64>{});
+    default: return f(AccumTag<Accum::kPlaneKahan>{});
+  }
+}
 
 // The five sums of a particle, in this order: fx, fy, fz, en, vir.
 template <Accum M>
@@ -160,7 +191,15 @@ struct Sums<Accum::kPairF64> {
   double v[5] = {0, 0, 0, 0, 0};
 };
 template <>
+struct Sums<Accum::kPlaneF64> {
+  double v[5] = {0, 0, 0, 0, 0};
+};
+template <>
 struct Sums<Accum::kRowKahan> {
+  float s[5] = {0, 0, 0, 0, 0}, k[5] = {0, 0, 0, 0, 0};
+};
+template <>
+struct Sums<Accum::kPlaneKahan> {
   float s[5] = {0, 0, 0, 0, 0}, k[5] = {0, 0, 0, 0, 0};
 };
 template <>
@@ -186,10 +225,10 @@ __device__ __forceinline__ void kahan_add2(float2& s, float2& k, float2 x) {
   s = u;
 }
 
-// Fold the partials of one row segment into the row forms' sums and clear them.
+// Fold the partials into the sums of a row or plane form and clear them.
 template <Accum M, typename R, bool X2>
-__device__ __forceinline__ void flush_row(Acc<R>& c, Acc2& c2, Sums<M>& S) {
-  if constexpr (row_form(M)) {
+__device__ __forceinline__ void flush_partials(Acc<R>& c, Acc2& c2, Sums<M>& S) {
+  if constexpr (row_form(M) || plane_form(M)) {
     float v[5];
     if constexpr (X2) {
       v[0] = c2.fx.x + c2.fx.y;
@@ -208,7 +247,7 @@ __device__ __forceinline__ void flush_row(Acc<R>& c, Acc2& c2, Sums<M>& S) {
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      if constexpr (M == Accum::kRowF64)
+      if constexpr (f64_form(M))
         S.v[q] += (double)v[q];
       else
         kahan_add(S.s[q], S.k[q], v[q]);
@@ -262,7 +301,7 @@ __device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool 
   const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
   const float2 pv = __fmul2_rn(s6, __ffma2_rn(s6, two, m1f));  // r.F / 24
   const float2 q = __fmul2_rn(pv, y);
-  if constexpr (M == Accum::kPlain || row_form(M)) {
+  if constexpr (plain_loop(M)) {
     // the plain step, fused: c.en += s6 (s6 - 1)
     c.fx = __ffma2_rn(q, dx, c.fx);
     c.fy = __ffma2_rn(q, dy, c.fy);
@@ -315,7 +354,7 @@ __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool
   const float2 pv = __fmul2_rn(e24, __fmul2_rn(s6, __ffma2_rn(s6, two, m1f)));  // r . F_ij
   const float2 q = __fmul2_rn(pv, y);
   const float2 u = __ffma2_rn(e4, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), make_float2(-us.x, -us.y));
-  if constexpr (M == Accum::kPlain || row_form(M)) {
+  if constexpr (plain_loop(M)) {
     c.fx = __ffma2_rn(q, dx, c.fx);
     c.fy = __ffma2_rn(q, dy, c.fy);
     c.fz = __ffma2_rn(q, dz, c.fz);
@@ -383,7 +422,7 @@ __device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ p
   } else {
     pair_range<R, SJ, TYPED>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
   }
-  flush_row<M, R, X2>(c, c2, S);
+  if constexpr (row_form(M)) flush_partials<M, R, X2>(c, c2, S);
 }
 
 // Which segments of the row walk are evaluated: all of them, or only those
@@ -461,6 +500,7 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
         segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
     }
+    if constexpr (plane_form(M)) flush_partials<M, R, X2>(c, c2, S);
   }
 }
 
@@ -487,7 +527,7 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
                                                         double& w_out, int& np_out) {
   static_assert(!X2 || sizeof(R) == 4, "the packed loop serves FP32 only (with types: at most two)");
   static_assert(M == Accum::kPlain || sizeof(R) == 4, "accumulation forms apply to FP32 pair math only");
-  static_assert(X2 || M == Accum::kPlain || row_form(M), "the pair forms run on the packed loop");
+  static_assert(X2 || plain_loop(M), "the pair forms run on the packed loop");
   Acc<R> c;
   Acc2 c2;
   Sums<M> S;
@@ -516,13 +556,13 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
   walk_rows<R, TYPED, X2, M>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2, S);
   // The five sums (fx, fy, fz, en, vir) of the form, in FP64 where the form
   // keeps them so; the packed loop sums the sign-flipped differences r_j - r_i.
-  using V = std::conditional_t<M == Accum::kRowF64 || M == Accum::kPairF64, double, R>;
+  using V = std::conditional_t<f64_form(M), double, R>;
   V v[5];
   const int np = X2 ? c2.np : c.np;
-  if constexpr (M == Accum::kRowF64 || M == Accum::kPairF64) {
+  if constexpr (f64_form(M)) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) v[q] = S.v[q];
-  } else if constexpr (M == Accum::kRowKahan) {
+  } else if constexpr (M == Accum::kRowKahan || M == Accum::kPlaneKahan) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) v[q] = S.s[q] - S.k[q];
   } else if constexpr (M == Accum::kPairKahan) {

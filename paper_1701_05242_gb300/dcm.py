@@ -26,6 +26,7 @@ DCM_ERR_CUDA = 3
 DCM_ERR_NOT_CONVERGED = 4
 DCM_ERR_CAPACITY = 5
 DCM_ERR_NOMEM = 6
+DCM_ERR_TIMEOUT = 7
 DCM_PREC_FP64 = 0
 DCM_PREC_MIXED = 1
 DCM_FORCE_AUTO = 0
@@ -37,10 +38,13 @@ DCM_ACC_ROW_FP64 = 2
 DCM_ACC_ROW_KAHAN = 3
 DCM_ACC_PAIR_KAHAN = 4
 DCM_ACC_PAIR_FP64 = 5
+DCM_ACC_PLANE_FP64 = 6
+DCM_ACC_PLANE_KAHAN = 7
 ACC_NAMES = {DCM_ACC_FP32: "fp32", DCM_ACC_ROW_FP64: "row_fp64", DCM_ACC_ROW_KAHAN: "row_kahan",
-             DCM_ACC_PAIR_KAHAN: "pair_kahan", DCM_ACC_PAIR_FP64: "pair_fp64"}
+             DCM_ACC_PAIR_KAHAN: "pair_kahan", DCM_ACC_PAIR_FP64: "pair_fp64", DCM_ACC_PLANE_FP64: "plane_fp64",
+             DCM_ACC_PLANE_KAHAN: "plane_kahan"}
 
-_ERRNAMES = {1: "INVALID_ARG", 2: "BOX", 3: "CUDA", 4: "NOT_CONVERGED", 5: "CAPACITY", 6: "NOMEM"}
+_ERRNAMES = {1: "INVALID_ARG", 2: "BOX", 3: "CUDA", 4: "NOT_CONVERGED", 5: "CAPACITY", 6: "NOMEM", 7: "TIMEOUT"}
 
 
 class DcmError(RuntimeError):
@@ -100,6 +104,11 @@ _SIGS = {
     "dcm_batch_capture": (_i32, [_vp, ctypes.POINTER(dcm_state), ctypes.c_double, _vp]),
     "dcm_batch_replay": (_i32, [_vp, ctypes.POINTER(dcm_state), _i32, _vp]),
     "dcm_batch_graph_steps": (_i32, [_vp]),
+    "dcm_batch_set_persistent": (_i32, [_vp, _i32]),
+    "dcm_batch_set_wait_budget": (_i32, [_vp, _i64]),
+    "dcm_batch_set_tile": (_i32, [_vp, _i32]),
+    "dcm_batch_accumulation": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "dcm_batch_barrier_selftest": (_i32, [_vp, _i32, _i64, _vp]),
     "dcm_batch_status": (_i32, [_vp, _vp]),
     "dcm_batch_set_timing": (_i32, [_vp, _i32]),
     "dcm_batch_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
@@ -414,6 +423,30 @@ def dcm_batch_capture(b: Batch, st: BatchState, dt: float, stream):
 
 def dcm_batch_replay(b: Batch, st: BatchState, ngraphs: int, stream):
     b.check(lib.dcm_batch_replay(b.handle, ctypes.byref(st.c), int(ngraphs), _stream(stream)))
+
+
+def dcm_batch_set_persistent(b: Batch, on: bool):
+    b.check(lib.dcm_batch_set_persistent(b.handle, 1 if on else 0))
+
+
+def dcm_batch_accumulation(b: Batch) -> int:
+    k = ctypes.c_int32()
+    b.check(lib.dcm_batch_accumulation(b.handle, ctypes.byref(k)))
+    return k.value
+
+
+def dcm_batch_set_tile(b: Batch, particles: int):
+    b.check(lib.dcm_batch_set_tile(b.handle, int(particles)))
+
+
+def dcm_batch_set_wait_budget(b: Batch, ns: int):
+    b.check(lib.dcm_batch_set_wait_budget(b.handle, int(ns)))
+
+
+def dcm_batch_barrier_selftest(b: Batch, phantom: int, budget_ns: int, stream=None) -> int:
+    """Runs the persistent grid's barrier against `phantom` missing blocks;
+    returns the device status (DCM_ERR_TIMEOUT when the bounded waits ran out)."""
+    return lib.dcm_batch_barrier_selftest(b.handle, int(phantom), int(budget_ns), _stream(stream))
 
 
 def dcm_batch_graph_steps(b: Batch) -> int:

@@ -1,4 +1,5 @@
-"""Batched form: independent replicas stepped in one launch per stage.
+"""Batched form: independent replicas stepped together, one persistent launch
+per timestep by default (or one launch per stage).
 
 Each replica of a batch must evolve exactly as the same system stepped alone
 through dcm_step (the per-particle arithmetic is the same; only the order of
@@ -179,3 +180,130 @@ def test_batch_rejects_bad_replica(D):
     p = D.make_params((1, 1, 1))
     with pytest.raises(D.DcmError):
         D.Batch(p, [(12.0, 12.0, 48.0), (12.0, 12.0, 47.0)], [10, 10])
+
+
+# ------------------------------------------------ persistent plan (default)
+def _run_plan(D, reps, P, persistent, nsteps, lx=0.0):
+    b, st = batch_state(D, reps, P, lx)
+    D.dcm_batch_set_persistent(b, persistent)
+    D.dcm_batch_step_init(b, st)
+    D.dcm_batch_launch_count(b, reset=True)
+    D.dcm_batch_step(b, st, DT, nsteps)
+    launches = D.dcm_batch_launch_count(b)
+    assert D.dcm_batch_status(b) == D.DCM_OK
+    pos, vel, rc, ids = st.current()
+    out = [t.cpu().numpy() for t in (pos, vel, rc, ids, st.force)]
+    return out, st.thermo.cpu().numpy().reshape(-1, 4), launches, b
+
+
+@pytest.mark.parametrize("prec,lx", [("mixed", 0.0), ("mixed", 0.5), ("fp64", 0.0)])
+def test_persistent_plan_equals_per_stage_plan(D, replicas, prec, lx):
+    """One cooperative launch per timestep (grid barriers between the
+    stages, forces from the (replica, tile) queue) steps the same trajectory
+    as one launch per stage: positions, velocities, cutoffs, ids and forces
+    bit for bit (the same per-element code, the binning's order fixed by the
+    stable sort), per-replica totals to rounding (their block sums differ in
+    width).  The persistent plan launches exactly one kernel per timestep."""
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    nsteps = 2 * K + 3   # two recomputations, an odd step count (buffers end on the other side)
+    a, tha, la, _ = _run_plan(D, replicas, P, True, nsteps, lx)
+    s, ths, ls, _ = _run_plan(D, replicas, P, False, nsteps, lx)
+    for x, y in zip(a, s):
+        assert np.array_equal(x, y)
+    assert np.allclose(tha, ths, rtol=1e-12, atol=1e-9)
+    assert la == nsteps
+    assert ls > 10 * nsteps
+
+
+def test_persistent_plan_two_types_and_accumulation_forms(D):
+    """Two types on the packed typed loop, each batched accumulation form."""
+    reps = []
+    for r, L in enumerate((12.0, 13.5)):
+        reps.append(synth.make_slab(synth.SlabSpec(box=(L, L, 4 * L), ntypes=2, seed=20 + r, name=f"pt{r}")))
+    pos = np.concatenate([s.pos for s in reps])
+    vel = np.concatenate([s.vel for s in reps])
+    typ = np.concatenate([s.types for s in reps])
+    res = {}
+    for acc in (D.DCM_ACC_FP32, D.DCM_ACC_PLANE_KAHAN, D.DCM_ACC_PLANE_FP64):
+        for persistent in (True, False):
+            kw = dict(precision=D.DCM_PREC_MIXED, recompute_every=K, ntypes=2, eps=(1.0, 0.8), sigma=(1.0, 1.1),
+                      accumulation=acc)
+            b = D.Batch(D.make_params((1, 1, 1), **kw), [s.box for s in reps], [s.n for s in reps])
+            D.dcm_batch_set_persistent(b, persistent)
+            st = D.BatchState(b, D.to_real4(torch.from_numpy(pos), torch.from_numpy(typ), torch.float32),
+                              D.to_real4(torch.from_numpy(vel), None, torch.float32))
+            D.dcm_batch_step_init(b, st)
+            D.dcm_batch_step(b, st, DT, K + 1)
+            assert D.dcm_batch_status(b) == D.DCM_OK
+            res[acc, persistent] = (st.current()[0].cpu().numpy(), st.thermo.cpu().numpy())
+            b.close()
+        assert np.array_equal(res[acc, True][0], res[acc, False][0])
+        assert np.allclose(res[acc, True][1], res[acc, False][1], rtol=1e-12)
+    # the forms differ only in how the same pair terms are summed
+    e = [res[acc, True][1].reshape(-1, 4)[:, 0] for acc in (1, 7, 6)]
+    assert np.allclose(e[0], e[1], rtol=1e-6) and np.allclose(e[1], e[2], rtol=1e-6)
+
+
+def test_persistent_plan_graph_replay(D, replicas):
+    """The persistent step captured in a CUDA graph (one kernel per timestep
+    in the graph) replays the trajectory of direct stepping bit for bit."""
+    P = D.DCM_PREC_MIXED
+    b1, s1 = batch_state(D, replicas, P)
+    D.dcm_batch_step_init(b1, s1)
+    D.dcm_batch_step(b1, s1, DT, 2 * K)
+    b2, s2 = batch_state(D, replicas, P)
+    D.dcm_batch_step_init(b2, s2)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    D.dcm_batch_capture(b2, s2, DT, stream)
+    per = D.dcm_batch_graph_steps(b2)
+    D.dcm_batch_launch_count(b2, reset=True)
+    D.dcm_batch_replay(b2, s2, (2 * K) // per, stream)
+    stream.synchronize()
+    assert D.dcm_batch_launch_count(b2) == 2 * K
+    assert torch.equal(s1.current()[0], s2.current()[0])
+    assert torch.equal(s1.thermo, s2.thermo)
+    assert D.dcm_batch_status(b2) == D.DCM_OK
+
+
+def test_persistent_barrier_wait_runs_out(D, replicas):
+    """The bounded grid barrier: waiting for a block that does not exist, every
+    block gives up after the budget (50 ms) with DCM_ERR_TIMEOUT and returns;
+    with nothing missing it passes.  The batch steps normally afterwards."""
+    import time
+    b, st = batch_state(D, replicas, D.DCM_PREC_MIXED)
+    t0 = time.perf_counter()
+    assert D.dcm_batch_barrier_selftest(b, 1, 50_000_000) == D.DCM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 20.0
+    assert D.dcm_batch_barrier_selftest(b, 0, 50_000_000) == D.DCM_OK
+    D.dcm_batch_step_init(b, st)
+    D.dcm_batch_step(b, st, DT, 2)
+    assert D.dcm_batch_status(b) == D.DCM_OK
+    assert np.isfinite(st.thermo.cpu().numpy()).all()
+
+
+def test_persistent_step_with_an_exhausted_wait_budget(D, replicas):
+    """A wait budget of 1 microsecond, far below a stage's duration: the
+    launch's barriers run out, every block leaves, and the status reports
+    DCM_ERR_TIMEOUT instead of a hang; with the budget restored the batch
+    steps again and matches a fresh run."""
+    P = D.DCM_PREC_MIXED
+    b, st = batch_state(D, replicas, P)
+    D.dcm_batch_step_init(b, st)
+    assert D.dcm_batch_status(b) == D.DCM_OK
+    D.dcm_batch_set_wait_budget(b, 1000)
+    D.dcm_batch_step(b, st, DT, 1)
+    assert D.dcm_batch_status(b) == D.DCM_ERR_TIMEOUT
+    D.dcm_batch_set_wait_budget(b, 2_000_000_000)
+    b2, s2 = batch_state(D, replicas, P)
+    for bb, ss in ((b, st), (b2, s2)):
+        fresh = batch_state(D, replicas, P)[1]
+        for k in range(2):
+            ss.pos[k].copy_(fresh.pos[k])
+            ss.vel[k].copy_(fresh.vel[k])
+            ss.id[k].copy_(fresh.id[k])
+        ss.c.cur = 0
+        D.dcm_batch_step_init(bb, ss)
+        D.dcm_batch_step(bb, ss, DT, 3)
+        assert D.dcm_batch_status(bb) == D.DCM_OK
+    assert torch.equal(st.current()[0], s2.current()[0])

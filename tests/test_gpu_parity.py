@@ -304,8 +304,9 @@ def test_forces_uniform_and_shift(D, slab_1935, prec):
 
 
 @pytest.mark.parametrize("prec,kernel,shift,acc", [("mixed", 1, 0, 0), ("mixed", 3, 0, 0), ("mixed", 3, 1, 0),
-                                                   ("mixed", 3, 0, 1), ("mixed", 3, 1, 2), ("mixed", 3, 0, 4),
-                                                   ("mixed", 3, 1, 5), ("mixed", 1, 1, 2), ("fp64", 0, 0, 0)])
+                                                   ("mixed", 3, 0, 1), ("mixed", 3, 1, 2), ("mixed", 3, 0, 3),
+                                                   ("mixed", 3, 0, 4), ("mixed", 3, 1, 5), ("mixed", 3, 1, 6),
+                                                   ("mixed", 1, 1, 2), ("mixed", 1, 0, 7), ("fp64", 0, 0, 0)])
 def test_forces_two_types(D, prec, kernel, shift, acc):
     """Two types with Lorentz-Berthelot mixing: the scalar loop (kernel 1),
     the packed typed loop (kernel 3, also with the shifted energy), each
@@ -352,7 +353,7 @@ def test_forces_one_type_scaled(D, slab_1935, kernel, shift):
     assert np.abs(Fg[:, 3] - ref.e).max() <= 1e-5 * np.abs(ref.e).max()
 
 
-@pytest.mark.parametrize("acc", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("acc", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("kernel", [1, 3])
 @pytest.mark.parametrize("l", [1.5, 1.0])
 def test_forces_kernel_variants(D, slab_1935, kernel, l, acc):
@@ -479,17 +480,17 @@ def test_forces_kernel_rejects_unknown(D, k):
         make_ctx(D, (12.0, 12.0, 48.0), 10, force_kernel=k)
 
 
-@pytest.mark.parametrize("a", [-1, 6])
+@pytest.mark.parametrize("a", [-1, 8])
 def test_accumulation_rejects_unknown(D, a):
     with pytest.raises(D.DcmError):
         make_ctx(D, (12.0, 12.0, 48.0), 10, accumulation=a)
 
 
 def test_accumulation_resolution(D):
-    """AUTO runs the row-segment Kahan form; the FP64 form ignores the field;
+    """AUTO runs the plane Kahan form; the FP64 form ignores the field;
     the scalar kernel runs the row form of a pair form."""
     box = (12.0, 12.0, 48.0)
-    assert D.dcm_accumulation(make_ctx(D, box, 10)) == D.DCM_ACC_ROW_KAHAN
+    assert D.dcm_accumulation(make_ctx(D, box, 10)) == D.DCM_ACC_PLANE_KAHAN
     assert D.dcm_accumulation(make_ctx(D, box, 10, accumulation=D.DCM_ACC_PAIR_FP64)) == D.DCM_ACC_PAIR_FP64
     assert D.dcm_accumulation(make_ctx(D, box, 10, D.DCM_PREC_FP64, accumulation=4)) == D.DCM_ACC_FP32
     assert D.dcm_accumulation(make_ctx(D, box, 10, force_kernel=1, accumulation=4)) == D.DCM_ACC_ROW_KAHAN
@@ -853,7 +854,7 @@ def test_full_size_sampled(D, slab_16m):
     spos = slab.pos[operm].astype(np.float64)
     Fo, eo, wo, po = O.forces_subset(spos, rcn, slab.box, 1.5, idx, nthreads=8)
     totals = []
-    for kernel, acc in ((0, 0), (1, 1), (1, 3), (3, 1), (3, 2), (3, 4), (3, 5)):
+    for kernel, acc in ((0, 0), (1, 1), (1, 3), (1, 6), (3, 1), (3, 2), (3, 3), (3, 4), (3, 5), (3, 6)):
         # both cell-list kernels and the accumulation forms on the same sorted input
         kctx = make_ctx(D, slab.box, n, force_kernel=kernel, accumulation=acc)
         F = torch.empty_like(ps)
@@ -902,7 +903,7 @@ def test_full_size_energy_virial(D, slab_16m):
     rcn = rc.cpu().numpy().astype(np.float64)
     ref = O.forces_cells(spos, rcn, slab.box, 1.5, nthreads=os.cpu_count() or 1)
     worst = 0.0
-    for acc in (0, 1, 2, 3, 4, 5):
+    for acc in (0, 1, 2, 3, 4, 5, 6, 7):
         kctx = make_ctx(D, slab.box, n, lx=0.5, accumulation=acc)
         F = torch.empty_like(ps)
         tot = torch.zeros(3, dtype=torch.float64, device="cuda")
