@@ -380,13 +380,13 @@ __device__ __forceinline__ bool b_dist_update(int64_t b, const R* __restrict__ D
 }
 
 // ---- cutoffs ----------------------------------------------------------------------
-template <typename R>
+template <typename R, bool NC = true>
 __device__ __forceinline__ void b_cutoffs(int64_t i, const typename RT<R>::R4* __restrict__ pos,
                                           const R* __restrict__ D, const RepGeom* __restrict__ geom,
                                           const uint16_t* __restrict__ rep, R h, R r_grid, R rc_min, R rc_max, R ramp,
                                           R* __restrict__ rc) {
   const RepGeom& G = geom[rep[i]];
-  auto p = ldg4(pos + i);
+  auto p = ld_pos<NC>(pos + i);
   int k[3];
   R t[3];
   R x[3] = {p.x, p.y, p.z};
@@ -427,7 +427,10 @@ __device__ __forceinline__ void b_cutoffs(int64_t i, const typename RT<R>::R4* _
 }
 
 // ---- forces, kick, per-replica thermo -------------------------------------------------
-template <typename R, bool TYPED, bool X2, Accum M>
+// NC: positions and cell starts through the read-only path (the per-stage
+// kernel); the persistent kernel wrote them earlier in its launch and reads
+// them with ordinary loads.
+template <typename R, bool TYPED, bool X2, Accum M, bool NC = true>
 __device__ __forceinline__ void b_force(int64_t i, const typename RT<R>::R4* __restrict__ pos,
                                         const R* __restrict__ rc, const int32_t* __restrict__ start,
                                         const ForceArgs<R>& a, const RepGeom* __restrict__ geom,
@@ -437,7 +440,7 @@ __device__ __forceinline__ void b_force(int64_t i, const typename RT<R>::R4* __r
   Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge, a.g.edge_x, a.g.inv_edge_x);
   double e = 0, w = 0;
   int np = 0;
-  force[i] = force_one<R, TYPED, X2, M>(pos, start + G.c0, g, a, (int)i, ldg4(pos + i), rc[i], e, w, np);
+  force[i] = force_one<R, TYPED, X2, M, NC>(pos, start + G.c0, g, a, (int)i, ld_pos<NC>(pos + i), rc[i], e, w, np);
   w_i[i] = (R)w;
   np_i[i] = np;
 }

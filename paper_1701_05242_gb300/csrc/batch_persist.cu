@@ -118,13 +118,18 @@ __device__ bool grid_sync(uint32_t* sync, uint32_t expected, int64_t budget_ns, 
         __threadfence();
         atomicAdd(sync + 1, 1u);
       } else {
+        // bounded twice: by the global nanosecond timer, and by a poll count
+        // that a poll (an L2 round trip of well over 64 ns) cannot exhaust
+        // before the time budget, in case the timer does not advance
         const uint64_t t0 = global_ns();
+        const int64_t max_polls = budget_ns / 64 + 1024;
+        int64_t polls = 0;
         while (vs[1] == gen) {
           if (vs[2] != 0) {
             good = 0;
             break;
           }
-          if ((int64_t)(global_ns() - t0) > budget_ns) {
+          if ((int64_t)(global_ns() - t0) > budget_ns || ++polls > max_polls) {
             good = 0;
             atomicExch(sync + 2, 1u);
             raise_status(status, DCM_ERR_TIMEOUT);
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
       if (first < 0) raise_status(a.status, DCM_ERR_NOT_CONVERGED);
     }
     for (int64_t i = gt; i < a.n; i += gs)
-      b_cutoffs<R>(i, a.pos_o, a.D0, a.geom, a.rep_p, a.h, a.r_grid, a.rc_min, a.rc_max, a.ramp, a.rc_o);
+      b_cutoffs<R, false>(i, a.pos_o, a.D0, a.geom, a.rep_p, a.h, a.r_grid, a.rc_min, a.rc_max, a.ramp, a.rc_o);
     PSYNC();
   }
   // ---- forces over the (replica, tile) queue (Section 2.4, Alg. 2.3)
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
       const int2 item = a.tiles[t];
       const int64_t end = min((int64_t)item.y + a.tile, a.geom[item.x].p1);
       for (int64_t i = (int64_t)item.y + lane; i < end; i += 32)
-        b_force<R, TYPED, X2, M>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i, a.np_i);
+        b_force<R, TYPED, X2, M, false>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i, a.np_i);
     }
   }
   PSYNC();

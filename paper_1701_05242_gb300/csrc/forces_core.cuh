@@ -27,6 +27,31 @@ __device__ __forceinline__ float recip(float x) {
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Loads of positions and cell starts in the pair walk.  NC: through the
+// read-only (non-coherent) path, for kernels in which the arrays are never
+// written; otherwise ordinary cached loads (ld.global.ca), for a kernel that
+// wrote them earlier in the same launch behind a grid barrier.
+template <bool NC>
+__device__ __forceinline__ float4 ld_pos(const float4* p) {
+  if constexpr (NC) return __ldg(p);
+  else return __ldca(p);
+}
+template <bool NC>
+__device__ __forceinline__ dvec4 ld_pos(const dvec4* p) {
+  if constexpr (NC) {
+    return ldg4(p);
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldca(q), b = __ldca(q + 1);
+    return dvec4{a.x, a.y, b.x, b.y};
+  }
+}
+template <bool NC>
+__device__ __forceinline__ int32_t ld_start(const int32_t* p) {
+  if constexpr (NC) return __ldg(p);
+  else return __ldca(p);
+}
+
 // particle type stored as a number in w, clamped to [0, ntypes)
 template <typename R>
 __device__ __forceinline__ int type_of(R w, int ntypes) {
@@ -66,13 +91,13 @@ struct Acc {
 // Pairs of particle i (coordinates xi, yi, zi in the image frame of the
 // segment) with sorted particles [lo, hi).  SJ: the segment's j coordinates
 // need the exact -L image shift (sh); otherwise they are used as loaded.
-template <typename R, bool SJ, bool TYPED>
+template <typename R, bool SJ, bool TYPED, bool NC = true>
 __device__ __forceinline__ void pair_range(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi,
                                            R zi, R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a,
                                            const R* ushift, Acc<R>& c) {
 #pragma unroll 2
   for (int j = lo; j < hi; ++j) {
-    auto pj = ldg4(pos + j);
+    auto pj = ld_pos<NC>(pos + j);
     R dx, dy, dz;
     if (SJ) {
       dx = xi - (pj.x + shx);
@@ -371,14 +396,14 @@ __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool
 // 4 eps of the pair type (type of i, t); a candidate's type is 1 if its w is
 // at least 1 (type_of clamped to two types), and with one type both columns
 // are equal.
-template <bool SJ, Accum M>
+template <bool SJ, Accum M, bool NC = true>
 __device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                                float zi, float shx, float shy, float shz, float rc2,
                                                const float* k8, Acc2& c, Sums<M>& S) {
   for (int j = lo; j < hi; j += 2) {
     const bool has1 = j + 1 < hi;
     const int j1 = has1 ? j + 1 : j;
-    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j1);
+    const float4 p0 = ld_pos<NC>(pos + j), p1 = ld_pos<NC>(pos + j1);
     float2 dx, dy, dz;
     if (SJ) {
       dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
@@ -396,14 +421,14 @@ __device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, i
   }
 }
 
-template <bool SJ, Accum M>
+template <bool SJ, Accum M, bool NC = true>
 __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                               float zi, float shx, float shy, float shz, float rc2, Acc2& c,
                                               Sums<M>& S) {
   for (int j = lo; j < hi; j += 2) {
     const bool has1 = j + 1 < hi;
     const int j1 = has1 ? j + 1 : j;
-    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j1);
+    const float4 p0 = ld_pos<NC>(pos + j), p1 = ld_pos<NC>(pos + j1);
     pair_x2<SJ, M>(p0, p1, true, has1, xi, yi, zi, shx, shy, shz, rc2, c, S);
   }
 }
@@ -411,16 +436,16 @@ __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, in
 // Segment dispatch: the packed loop for FP32 (one type, or up to two types
 // with the row constants in ushift[0 .. 7]), the scalar loop otherwise; the
 // row forms of accumulation take the segment's partials over at its end.
-template <typename R, bool SJ, bool TYPED, bool X2, Accum M>
+template <typename R, bool SJ, bool TYPED, bool X2, Accum M, bool NC = true>
 __device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi, R zi,
                                         R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a, const R* ushift,
                                         Acc<R>& c, Acc2& c2, Sums<M>& S) {
   if constexpr (X2 && TYPED) {
-    pair_range_x2t<SJ, M>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2, S);
+    pair_range_x2t<SJ, M, NC>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2, S);
   } else if constexpr (X2) {
-    pair_range_x2<SJ, M>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2, S);
+    pair_range_x2<SJ, M, NC>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2, S);
   } else {
-    pair_range<R, SJ, TYPED>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
+    pair_range<R, SJ, TYPED, NC>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
   }
   if constexpr (row_form(M)) flush_partials<M, R, X2>(c, c2, S);
 }
@@ -433,7 +458,7 @@ enum class Walk { kAll, kImagesOnly };
 // The culled cell-row walk of particle `self` (position pi, clamped cutoff
 // rci) over the cell grid g whose cell starts are start[0 .. ncell] (positions
 // pos sorted by cell), accumulating into c (scalar loop) or c2 (packed).
-template <typename R, bool TYPED, bool X2, Accum M, Walk MODE = Walk::kAll>
+template <typename R, bool TYPED, bool X2, Accum M, bool NC = true, Walk MODE = Walk::kAll>
 __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__ pos,
                                           const int32_t* __restrict__ start, const Grid<R>& g,
                                           const ForceArgs<R>& a, int self, const typename RT<R>::R4& pi, R rci,
@@ -473,31 +498,31 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       // segment u < 0: image -L (shift j)
       if (ulo < 0) {
         int a1 = min(uhi, -1);
-        int j0 = __ldg(start + row + ulo + nx), j1 = __ldg(start + row + a1 + nx + 1);
-        segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2, S);
+        int j0 = ld_start<NC>(start + row + ulo + nx), j1 = ld_start<NC>(start + row + a1 + nx + 1);
+        segment<R, true, TYPED, X2, M, NC>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
       // segment 0 <= u < nx: no x shift; the particle itself is skipped
       const bool img_row = uy < 0 || uy >= ny || uz < 0 || uz >= nz;
       if (!kImg || img_row) {
         int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
         if (a0 <= a1) {
-          int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
+          int j0 = ld_start<NC>(start + row + a0), j1 = ld_start<NC>(start + row + a1 + 1);
           if (!kImg && uy == cy && uz == cz) {  // the particle's own row: cut it out
-            segment<R, false, TYPED, X2, M>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
-            segment<R, false, TYPED, X2, M>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
+            segment<R, false, TYPED, X2, M, NC>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
+            segment<R, false, TYPED, X2, M, NC>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
                                          c2, S);
           } else if (ysh == (R)0 && zsh == (R)0) {
-            segment<R, false, TYPED, X2, M>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
+            segment<R, false, TYPED, X2, M, NC>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
           } else {
-            segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
+            segment<R, true, TYPED, X2, M, NC>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
           }
         }
       }
       // segment u >= nx: image +L (shift i)
       if (uhi >= nx) {
         int a0 = max(ulo, nx);
-        int j0 = __ldg(start + row + a0 - nx), j1 = __ldg(start + row + uhi - nx + 1);
-        segment<R, true, TYPED, X2, M>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
+        int j0 = ld_start<NC>(start + row + a0 - nx), j1 = ld_start<NC>(start + row + uhi - nx + 1);
+        segment<R, true, TYPED, X2, M, NC>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
     }
     if constexpr (plane_form(M)) flush_partials<M, R, X2>(c, c2, S);
@@ -519,7 +544,7 @@ __device__ __forceinline__ R clamp_cutoff(R rc_in, R rc_max) {
 // pos, sorted by cell), with the per-particle sums of accumulation form M.
 // Returns the force and writes e_i, w_i (in FP64: the totals are reduced
 // from them in FP64) and the accepted-pair count.
-template <typename R, bool TYPED, bool X2 = false, Accum M = Accum::kPlain>
+template <typename R, bool TYPED, bool X2 = false, Accum M = Accum::kPlain, bool NC = true>
 __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
                                                         const int32_t* __restrict__ start, const Grid<R>& g,
                                                         const ForceArgs<R>& a, int self,
@@ -553,7 +578,7 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       ushift[6 + t] = a.eps4[tp];
     }
   }
-  walk_rows<R, TYPED, X2, M>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2, S);
+  walk_rows<R, TYPED, X2, M, NC>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2, S);
   // The five sums (fx, fy, fz, en, vir) of the form, in FP64 where the form
   // keeps them so; the packed loop sums the sign-flipped differences r_j - r_i.
   using V = std::conditional_t<f64_form(M), double, R>;
