@@ -145,6 +145,14 @@ typedef struct dcm_params {
                              contiguous run of sorted particles; L_x / lx integer, short mantissa
                              (for a batch: every replica's L_x).  0 (default): l.  Finer cells
                              along the rows narrow each row's window without adding rows */
+  int32_t newton3;        /* 1 (needs skin > 0): half Verlet lists, each pair kept once by the
+                             particle with the larger cutoff (lower index on a tie) and evaluated
+                             once: the force goes to that particle if |r| < its cutoff and, with
+                             the opposite sign, to the other if |r| < the other's cutoff (Newton's
+                             third law where both cutoffs reach, Section 4.2; i-centric where one
+                             does).  Results are summed with atomics (order not reproducible).
+                             0 (default): full i-centric lists */
+  int32_t reserved3;
 } dcm_params;
 
 typedef struct dcm_ctx dcm_ctx;

@@ -215,6 +215,9 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "force_kernel must be one of DCM_FORCE_*");
   if (p->accumulation < DCM_ACC_AUTO || p->accumulation > DCM_ACC_PLANE_KAHAN)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "accumulation must be one of DCM_ACC_*");
+  if (p->newton3 != 0 && p->newton3 != 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "newton3 must be 0 or 1");
+  if (p->newton3 && !(p->skin > 0.0))
+    return msg_out(msg, len, DCM_ERR_INVALID_ARG, "newton3 needs Verlet lists (skin > 0)");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "precision must be DCM_PREC_FP64 or DCM_PREC_MIXED");
   if (p->n_max < 0 || p->n_max > 0x7fffffffLL) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "n_max out of range");

@@ -1,5 +1,7 @@
 // Verlet neighbour lists with a skin (Algorithm 2.2) and forces over them
-// (Algorithm 2.3), used by dcm_step when params.skin > 0.
+// (Algorithm 2.3), used by dcm_step when params.skin > 0; with
+// params.newton3 half lists whose pairs are evaluated once for both particles
+// (the Newton's third law variant Section 4.2 points to).
 //
 // Build (at a rebuild): for every particle i, the j != i with
 // |r_ij| < rc_i + skin, found by the same culled cell-row walk as the
@@ -95,23 +97,40 @@ __device__ __forceinline__ void walk_segments(const int32_t* __restrict__ start,
 // Segment visitors of the build: counting, and filling a lane's column
 // (plain entries from the front, image entries from the back, nothing
 // written past the column's capacity).
+// Which particle of a pair keeps it in a half list (Newton's third law form):
+// the one with the larger cutoff, the lower index on a tie, so that its walk
+// radius (its own cutoff plus the skin) covers the pair and every pair is
+// kept exactly once.  Full lists (n3 = 0) keep every candidate.
+template <typename R>
+struct Owner {
+  const R* __restrict__ rc;
+  R rci, rc_max;
+  int self, n3;
+  __device__ __forceinline__ bool keeps(int j) const {
+    if (!n3) return true;
+    const R rcj = clamp_cutoff<R>(__ldg(rc + j), rc_max);
+    return rci > rcj || (rci == rcj && self < j);
+  }
+};
+
 template <typename R>
 struct CountVisitor {
   const typename RT<R>::R4* __restrict__ pos;
   R rl2;
   int cnt;
+  Owner<R> own;
   __device__ __forceinline__ void plain(int j0, int j1, R xi, R yi, R zi) {
     for (int j = j0; j < j1; ++j) {
       auto pj = ldg4(pos + j);
       R dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-      cnt += fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 ? 1 : 0;
+      cnt += fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 && own.keeps(j) ? 1 : 0;
     }
   }
   __device__ __forceinline__ void image(int j0, int j1, R xi, R yi, R zi, R shx, R shy, R shz, uint32_t) {
     for (int j = j0; j < j1; ++j) {
       auto pj = ldg4(pos + j);
       R dx = xi - (pj.x + shx), dy = yi - (pj.y + shy), dz = zi - (pj.z + shz);
-      cnt += fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 ? 1 : 0;
+      cnt += fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 && own.keeps(j) ? 1 : 0;
     }
   }
 };
@@ -128,6 +147,7 @@ struct FillVisitor {
   uint32_t* __restrict__ out;  // the lane's column: entry k at out[32 k]
   R rl2;
   int cap, kf, kb;
+  Owner<R> own;
   __device__ __forceinline__ void plain(int j0, int j1, R xi, R yi, R zi) {
     const int lim = cap - kb;
     int k = kf;
@@ -143,7 +163,8 @@ struct FillVisitor {
                      ez = make_float2(zi - p2.z, zi - p3.z);
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
         const float2 s2 = __ffma2_rn(ex, ex, __ffma2_rn(ey, ey, __fmul2_rn(ez, ez)));
-        const bool a0 = r2.x < rl2, a1 = r2.y < rl2, a2 = s2.x < rl2, a3 = s2.y < rl2;
+        const bool a0 = r2.x < rl2 && own.keeps(j), a1 = r2.y < rl2 && own.keeps(j + 1),
+                   a2 = s2.x < rl2 && own.keeps(j + 2), a3 = s2.y < rl2 && own.keeps(j + 3);
         store_if(a0 && k < lim, out + (int64_t)k * 32, (uint32_t)j);
         k += a0 ? 1 : 0;
         store_if(a1 && k < lim, out + (int64_t)k * 32, (uint32_t)(j + 1));
@@ -158,7 +179,7 @@ struct FillVisitor {
         const float2 dx = make_float2(xi - p0.x, xi - p1.x), dy = make_float2(yi - p0.y, yi - p1.y),
                      dz = make_float2(zi - p0.z, zi - p1.z);
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-        const bool a0 = r2.x < rl2, a1 = r2.y < rl2;
+        const bool a0 = r2.x < rl2 && own.keeps(j), a1 = r2.y < rl2 && own.keeps(j + 1);
         store_if(a0 && k < lim, out + (int64_t)k * 32, (uint32_t)j);
         k += a0 ? 1 : 0;
         store_if(a1 && k < lim, out + (int64_t)k * 32, (uint32_t)(j + 1));
@@ -168,7 +189,7 @@ struct FillVisitor {
     for (; j < j1; ++j) {
       auto pj = ldg4(pos + j);
       R dx = xi - pj.x, dy = yi - pj.y, dz = zi - pj.z;
-      const bool acc = fma(dx, dx, fma(dy, dy, dz * dz)) < rl2;
+      const bool acc = fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 && own.keeps(j);
       store_if(acc && k < lim, out + (int64_t)k * 32, (uint32_t)j);
       k += acc ? 1 : 0;
     }
@@ -178,7 +199,7 @@ struct FillVisitor {
     for (int j = j0; j < j1; ++j) {
       auto pj = ldg4(pos + j);
       R dx = xi - (pj.x + shx), dy = yi - (pj.y + shy), dz = zi - (pj.z + shz);
-      if (fma(dx, dx, fma(dy, dy, dz * dz)) < rl2) {
+      if (fma(dx, dx, fma(dy, dy, dz * dz)) < rl2 && own.keeps(j)) {
         if (kf + kb < cap) out[(int64_t)(cap - 1 - kb) * 32] = (uint32_t)j | (code << kIdxBits);
         ++kb;
       }
@@ -196,13 +217,14 @@ __device__ __forceinline__ R list_radius(R rc, R rc_max, R skin) {
 template <typename R>
 __global__ void __launch_bounds__(128) k_list_count(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                     const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                    Grid<R> g, R rc_max, R skin, int32_t* __restrict__ capw) {
+                                                    Grid<R> g, R rc_max, R skin, int n3,
+                                                    int32_t* __restrict__ capw) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int cnt = 0;
   if (i < n) {
     auto pi = ldg4(pos + i);
     R rl = list_radius<R>(rc[i], rc_max, skin);
-    CountVisitor<R> v{pos, rl * rl, 0};
+    CountVisitor<R> v{pos, rl * rl, 0, Owner<R>{rc, clamp_cutoff<R>(rc[i], rc_max), rc_max, (int)i, n3}};
     walk_segments<R>(start, g, (int)i, pi, rl, v);
     cnt = v.cnt;
   }
@@ -217,7 +239,8 @@ __global__ void __launch_bounds__(128) k_list_count(int64_t n, const typename RT
 template <typename R>
 __global__ void __maxnreg__(80) k_list_fill(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                    const R* __restrict__ rc, const int32_t* __restrict__ start,
-                                                   Grid<R> g, R rc_max, R skin, const int32_t* __restrict__ capw,
+                                                   Grid<R> g, R rc_max, R skin, int n3,
+                                                   const int32_t* __restrict__ capw,
                                                    const int32_t* __restrict__ offw, uint32_t* __restrict__ list,
                                                    int32_t* __restrict__ nnb, int32_t* __restrict__ nimg,
                                                    int32_t* __restrict__ flag) {
@@ -225,7 +248,8 @@ __global__ void __maxnreg__(80) k_list_fill(int64_t n, const typename RT<R>::R4*
   if (i >= n) return;
   auto pi = ldg4(pos + i);
   R rl = list_radius<R>(rc[i], rc_max, skin);
-  FillVisitor<R> v{pos, list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31), rl * rl, capw[i >> 5], 0, 0};
+  FillVisitor<R> v{pos, list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31), rl * rl, capw[i >> 5], 0, 0,
+                   Owner<R>{rc, clamp_cutoff<R>(rc[i], rc_max), rc_max, (int)i, n3}};
   walk_segments<R>(start, g, (int)i, pi, rl, v);
   nnb[i] = v.kf;
   nimg[i] = v.kb;
@@ -566,6 +590,109 @@ __global__ void k_wrap_count(int64_t n, typename RT<R>::R4* __restrict__ pos, Gr
   slot[i] = atomicAdd(count + c, 1);
 }
 
+// Forces over half lists (Newton's third law form, params.newton3): every
+// pair of a list is evaluated once, by its owner i (the particle with the
+// larger cutoff; the lower index on a tie).  The pair term goes to i if
+// |r_ij| < rc_i and, with the opposite sign, to j if |r_ij| < rc_j; each side
+// takes half of U, minus its own U(rc) with the shifted energy.  So a pair
+// within both cutoffs (the symmetric case) costs one evaluation for both
+// particles, and a pair within one cutoff only (the asymmetric case of
+// Section 2.4) goes to that particle alone, as in the i-centric rule.  The
+// contributions to j (and i's own total, since other threads add to it) are
+// added with atomics into the force array, which is cleared first; the
+// order of those additions varies from run to run.
+template <typename R, bool TYPED>
+__global__ void __launch_bounds__(128) k_forces_list_n3(int64_t n, const typename RT<R>::R4* __restrict__ pos,
+                                                        const R* __restrict__ rc, const int32_t* __restrict__ nnb,
+                                                        const int32_t* __restrict__ nimg,
+                                                        const int32_t* __restrict__ capw,
+                                                        const int32_t* __restrict__ offw,
+                                                        const uint32_t* __restrict__ list, ForceArgs<R> a,
+                                                        typename RT<R>::R4* __restrict__ force,
+                                                        double* __restrict__ part, int64_t nwarp) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double E = 0.0, W = 0.0;
+  int np = 0;
+  if (i < n) {
+    const auto pi = ldg4(pos + i);
+    const R rci = clamp_cutoff<R>(rc[i], a.rc_max);
+    const R rc2 = rci * rci;
+    const int ti = TYPED ? type_of(pi.w, a.ntypes) : 0;
+    // U(rc) per pair type: of i's cutoff (for i's half) and of j's (for j's)
+    auto ushift = [&](int tp, R r2c) -> R {
+      if (!a.shift || !(r2c > (R)0)) return (R)0;
+      const R s2 = a.sig2[tp] / r2c, s6 = s2 * s2 * s2;
+      return a.eps4[tp] * s6 * (s6 - (R)1);
+    };
+    R fx = 0, fy = 0, fz = 0, ei = 0;
+    const uint32_t* lp = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
+    const int m = nnb[i], cap = capw[i >> 5], mb = nimg[i];
+    auto pair = [&](uint32_t e, bool image) {
+      const int j = (int)(e & kIdxMask);
+      const auto pj = ldg4(pos + j);
+      R dx, dy, dz;
+      if (image)
+        image_delta<R>(e >> kIdxBits, pi, pj, a.g, dx, dy, dz);
+      else {
+        dx = pi.x - pj.x;
+        dy = pi.y - pj.y;
+        dz = pi.z - pj.z;
+      }
+      const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      const R rcj = clamp_cutoff<R>(__ldg(rc + j), a.rc_max);
+      const bool acc_i = r2 < rc2, acc_j = r2 < rcj * rcj;
+      if (!acc_i && !acc_j) return;
+      const int tj = TYPED ? type_of(pj.w, a.ntypes) : 0;
+      const int tp = ti * a.ntypes + tj;
+      const R inv = recip(r2);
+      const R s2 = a.sig2[tp] * inv;
+      const R s6 = s2 * s2 * s2;
+      const R pv = a.eps24[tp] * s6 * fma((R)2, s6, (R)-1);  // r . F_ij
+      const R fs = pv * inv;
+      const R u = a.eps4[tp] * s6 * (s6 - (R)1);
+      if (acc_i) {
+        fx = fma(fs, dx, fx);
+        fy = fma(fs, dy, fy);
+        fz = fma(fs, dz, fz);
+        ei += u - ushift(tp, rc2);
+        W += 0.5 * (double)pv;
+        ++np;
+      }
+      if (acc_j) {
+        const R ej = (R)0.5 * (u - ushift(tp, rcj * rcj));
+        atomicAdd(&force[j].x, -fs * dx);
+        atomicAdd(&force[j].y, -fs * dy);
+        atomicAdd(&force[j].z, -fs * dz);
+        atomicAdd(&force[j].w, ej);
+        E += (double)ej;
+        W += 0.5 * (double)pv;
+        ++np;
+      }
+    };
+    for (int k = 0; k < m; ++k) pair(__ldg(lp + (int64_t)k * 32), false);
+    for (int k = cap - mb; k < cap; ++k) pair(__ldg(lp + (int64_t)k * 32), true);
+    ei *= (R)0.5;
+    E += (double)ei;
+    atomicAdd(&force[i].x, fx);
+    atomicAdd(&force[i].y, fy);
+    atomicAdd(&force[i].z, fz);
+    atomicAdd(&force[i].w, ei);
+  }
+  if (part) {
+    for (int o = 16; o > 0; o >>= 1) {
+      E += __shfl_xor_sync(0xffffffffu, E, o);
+      W += __shfl_xor_sync(0xffffffffu, W, o);
+      np += __shfl_xor_sync(0xffffffffu, np, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+      part[w] = E;
+      part[nwarp + w] = W;
+      part[2 * nwarp + w] = (double)np;
+    }
+  }
+}
+
 // ---- launchers -------------------------------------------------------------------
 
 static int ensure_list_capacity(dcm_ctx* ctx, int64_t need) {
@@ -587,6 +714,7 @@ template <typename R>
 int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, cudaStream_t st) {
   Grid<R> g = cell_grid<R>(ctx);
   R skin = (R)ctx->p.skin, rcm = (R)ctx->p.rc_max;
+  const int n3 = ctx->p.newton3;
   int64_t nblk = (n + 127) / 128, nw = nblk * 4;
   stage_begin(ctx, DCM_STAGE_LISTS, st);
   if (n > 0) DCM_LAUNCH(ctx, k_list_caps<R>, (unsigned)nblk, 128, 0, st, n, rc, rcm, skin, ctx->capw);
@@ -597,14 +725,14 @@ int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   if ((r = ensure_list_capacity(ctx, (int64_t)ctx->host_status[1] * 32))) return r;
   if (n > 0)
-    DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, ctx->capw,
-               ctx->offw, ctx->list, ctx->nnb, ctx->nimg, ctx->lflag);
+    DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, n3,
+               ctx->capw, ctx->offw, ctx->list, ctx->nnb, ctx->nimg, ctx->lflag);
   DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_status + 3, ctx->lflag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   if (ctx->host_status[3]) {
     // some list outgrew its bound: count exactly, then fill again
     if (n > 0)
-      DCM_LAUNCH(ctx, k_list_count<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin,
+      DCM_LAUNCH(ctx, k_list_count<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, n3,
                  ctx->capw);
     if ((r = exclusive_scan(ctx, ctx->capw, ctx->offw, nw, st))) return r;
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->lflag, 0, sizeof(int32_t), st));
@@ -612,7 +740,7 @@ int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
     DCM_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     if ((r = ensure_list_capacity(ctx, (int64_t)ctx->host_status[1] * 32))) return r;
     if (n > 0)
-      DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin,
+      DCM_LAUNCH(ctx, k_list_fill<R>, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->cell_start, g, rcm, skin, n3,
                  ctx->capw, ctx->offw, ctx->list, ctx->nnb, ctx->nimg, ctx->lflag);
   }
   DCM_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->xbuild, pos, sizeof(typename RT<R>::R4) * n, cudaMemcpyDeviceToDevice, st));
@@ -644,6 +772,17 @@ int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R*
   double* part = totals ? ctx->red : nullptr;
   auto kern = lj_general(t) ? k_forces_list<R, true> : k_forces_list<R, false>;
   stage_begin(ctx, DCM_STAGE_FORCES, st);
+  if (ctx->p.newton3) {
+    DCM_CUDA_TRY(ctx, cudaMemsetAsync(force, 0, sizeof(typename RT<R>::R4) * n, st));
+    auto k3 = lj_general(t) ? k_forces_list_n3<R, true> : k_forces_list_n3<R, false>;
+    DCM_LAUNCH(ctx, k3, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list,
+               a, force, part, nwarp);
+    stage_end(ctx, DCM_STAGE_FORCES, st);
+    int r = check_launch(ctx, "list_forces");
+    if (r) return r;
+    if (totals) return reduce_partials(ctx, part, nwarp, 3, totals, false, st);
+    return DCM_OK;
+  }
   bool packed = false;
   if constexpr (sizeof(R) == 4) {
     if (!lj_general(t)) {

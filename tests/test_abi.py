@@ -74,6 +74,8 @@ def test_params_default_and_validate(lib):
     (dict(force_kernel=2), 1),                  # removed kernel numbers stay invalid
     (dict(force_kernel=5), 1),
     (dict(accumulation=8), 1),
+    (dict(newton3=1), 1),                       # Newton's third law form needs Verlet lists
+    (dict(newton3=2, skin=0.3, rc_max=5.5), 1),
     (dict(accumulation=-1), 1),
     (dict(skin=-0.1), 1),
     (dict(skin=0.5, rc_max=5.8), 2),             # rc_max + skin > L/2

@@ -223,7 +223,7 @@ def test_persistent_plan_two_types_and_accumulation_forms(D):
     pos = np.concatenate([s.pos for s in reps])
     vel = np.concatenate([s.vel for s in reps])
     typ = np.concatenate([s.types for s in reps])
-    res = {}
+    res, init = {}, {}
     for acc in (D.DCM_ACC_FP32, D.DCM_ACC_PLANE_KAHAN, D.DCM_ACC_PLANE_FP64):
         for persistent in (True, False):
             kw = dict(precision=D.DCM_PREC_MIXED, recompute_every=K, ntypes=2, eps=(1.0, 0.8), sigma=(1.0, 1.1),
@@ -233,15 +233,20 @@ def test_persistent_plan_two_types_and_accumulation_forms(D):
             st = D.BatchState(b, D.to_real4(torch.from_numpy(pos), torch.from_numpy(typ), torch.float32),
                               D.to_real4(torch.from_numpy(vel), None, torch.float32))
             D.dcm_batch_step_init(b, st)
+            init[acc, persistent] = st.thermo.cpu().numpy().copy()
             D.dcm_batch_step(b, st, DT, K + 1)
             assert D.dcm_batch_status(b) == D.DCM_OK
             res[acc, persistent] = (st.current()[0].cpu().numpy(), st.thermo.cpu().numpy())
             b.close()
         assert np.array_equal(res[acc, True][0], res[acc, False][0])
         assert np.allclose(res[acc, True][1], res[acc, False][1], rtol=1e-12)
-    # the forms differ only in how the same pair terms are summed
-    e = [res[acc, True][1].reshape(-1, 4)[:, 0] for acc in (1, 7, 6)]
-    assert np.allclose(e[0], e[1], rtol=1e-6) and np.allclose(e[1], e[2], rtol=1e-6)
+    # on the same positions the forms differ only in how the same pair terms
+    # are summed (the trajectories of the steps part ways: the dynamics from
+    # the random placement are chaotic)
+    e = [init[acc, True].reshape(-1, 4) for acc in (1, 7, 6)]
+    for q in (0, 1):
+        assert np.allclose(e[0][:, q], e[1][:, q], rtol=1e-7) and np.allclose(e[1][:, q], e[2][:, q], rtol=1e-7)
+    assert np.array_equal(e[0][:, 3], e[1][:, 3]) and np.array_equal(e[1][:, 3], e[2][:, 3])
 
 
 def test_persistent_plan_graph_replay(D, replicas):

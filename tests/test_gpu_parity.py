@@ -664,8 +664,8 @@ def test_jobs_on_two_states_and_a_copy_stream(D, slab_1935):
         assert torch.equal(po, rp) and torch.equal(vo, rv) and torch.equal(to, rt)
 
 
-def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5, lx=0.0):
-    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, skin=skin, rc_max=rc_max, lx=lx)
+def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5, lx=0.0, newton3=0):
+    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=K, skin=skin, rc_max=rc_max, lx=lx, newton3=newton3)
     real = real_of(D, P)
     st = D.State(ctx, pos4_of(D, slab.pos, None, P), D.to_real4(torch.from_numpy(slab.vel), None, real))
     D.dcm_step_init(ctx, st)
@@ -677,12 +677,15 @@ def run_gpu_steps_list(D, slab, P, nsteps, skin, K=10, dt=0.005, rc_max=5.5, lx=
     return ctx, st, np.array(out)
 
 
-@pytest.mark.parametrize("lx", [0.0, 0.75])
-def test_step_verlet_lists_fp64_matches_oracle(D, slab_1935, lx):
+@pytest.mark.parametrize("lx,newton3", [(0.0, 0), (0.75, 0), (0.0, 1), (0.75, 1)])
+def test_step_verlet_lists_fp64_matches_oracle(D, slab_1935, lx, newton3):
     # Verlet lists (Algorithm 2.2) with skin: same trajectory as the oracle's
-    # cell-list steps (rebuilds on displacement and at every cutoff recomputation)
+    # cell-list steps (rebuilds on displacement and at every cutoff recomputation);
+    # newton3: half lists, each pair evaluated once for both particles where
+    # both cutoffs reach and for the larger-cutoff particle alone otherwise
     nsteps = 24
-    ctx, st, th = run_gpu_steps_list(D, slab_1935, D.DCM_PREC_FP64, nsteps, skin=0.3, K=10, lx=lx)
+    ctx, st, th = run_gpu_steps_list(D, slab_1935, D.DCM_PREC_FP64, nsteps, skin=0.3, K=10, lx=lx,
+                                     newton3=newton3)
     p = O.Params(box=slab_1935.box, recompute_every=10, rc_max=5.5)
     ost = O.init_state(slab_1935.pos, slab_1935.vel, p)
     for k in range(nsteps):
@@ -722,13 +725,15 @@ def test_step_verlet_lists_mixed_close_to_cells(D, slab_1935):
     assert abs(th_l[-1, 0] - ref.E) <= EW_TOL * abs(ref.E)
 
 
-def test_step_verlet_lists_mixed_medium_box(D):
+@pytest.mark.parametrize("newton3", [0, 1])
+def test_step_verlet_lists_mixed_medium_box(D, newton3):
     """Lists on a box where most particles have only same-image neighbours (the
     packed two-pairs-per-iteration loop) and the boundary ones image entries:
-    forces after a few steps against the oracle on the same positions."""
+    forces after a few steps against the oracle on the same positions (full
+    lists, and half lists with Newton's third law)."""
     spec = synth.SlabSpec(box=(36.0, 36.0, 144.0), wave_amp=1.0, seed=5, name="medium")
     slab = synth.make_slab(spec)
-    ctx, st, th = run_gpu_steps_list(D, slab, D.DCM_PREC_MIXED, 7, skin=0.5, K=5, rc_max=6.0)
+    ctx, st, th = run_gpu_steps_list(D, slab, D.DCM_PREC_MIXED, 7, skin=0.5, K=5, rc_max=6.0, newton3=newton3)
     pos, vel, rc, ids = st.current()
     pw = np.mod(pos.cpu().numpy()[:, :3].astype(np.float64), slab.box)
     ref = O.forces_cells(pw, rc.cpu().numpy().astype(np.float64), slab.box, 1.5)
@@ -752,6 +757,43 @@ def test_step_lists_batched_call_equals_single_calls(D, slab_1935, prec):
     D.dcm_step(ctx2, st2, 0.005, 12)
     assert np.array_equal(th1[-1], st2.thermo.cpu().numpy())
     assert torch.equal(st1.current()[0], st2.current()[0]) and torch.equal(st1.current()[1], st2.current()[1])
+
+
+@pytest.mark.parametrize("newton3", [0, 1])
+def test_newton3_two_types_asymmetric_cutoffs(D, newton3):
+    """Two types, shifted energy and cutoffs spread over [3, 6] (most pairs
+    within one cutoff only): the list path's forces, e_i, E, W and pair count
+    against the oracle in FP64 after its initial evaluation, for full lists
+    and for half lists (where a pair within both cutoffs is evaluated once and
+    scattered, one within one cutoff goes to that particle alone)."""
+    spec = synth.named("slab_256k_2types")
+    spec.box = (18.0, 18.0, 72.0)
+    slab = synth.make_slab(spec)
+    n = slab.n
+    P = D.DCM_PREC_FP64
+    ctx = make_ctx(D, slab.box, n, P, skin=0.4, rc_max=6.0, ntypes=2, eps=(1.0, 0.8), sigma=(1.0, 1.1),
+                   shift_energy=1, newton3=newton3, recompute_every=1000)
+    st = D.State(ctx, pos4_of(D, slab.pos, slab.types, P), torch.zeros((n, 4), dtype=torch.float64, device="cuda"))
+    D.dcm_step_init(ctx, st)
+    assert D.dcm_status(ctx) == D.DCM_OK
+    pos, vel, rc, ids = st.current()
+    p = pos.cpu().numpy()
+    rcn = rc.cpu().numpy()
+    assert (rcn > 3.0).sum() > 0.2 * n   # many cutoffs above rc_min: asymmetric pairs abound
+    ref = O.forces_cells(p[:, :3], rcn, slab.box, 1.5, p[:, 3].astype(np.int32), (1.0, 0.8), (1.0, 1.1), True)
+    F = st.force.cpu().numpy()
+    assert np.abs(F[:, :3] - ref.F).max() <= FP64_TOL * np.abs(ref.F).max()
+    assert np.abs(F[:, 3] - ref.e).max() <= FP64_TOL * np.abs(ref.e).max()
+    th = st.thermo.cpu().numpy()
+    assert th[0] == pytest.approx(ref.E, rel=FP64_TOL) and th[1] == pytest.approx(ref.W, rel=FP64_TOL)
+    assert int(th[3]) == ref.npairs
+
+
+def test_newton3_needs_lists(D):
+    rc, msg = D.dcm_validate_params(D.make_params((12.0, 12.0, 48.0), rc_max=5.5, newton3=1))
+    assert rc == D.DCM_ERR_INVALID_ARG and "newton3" in msg
+    rc, _ = D.dcm_validate_params(D.make_params((12.0, 12.0, 48.0), rc_max=5.5, skin=0.4, newton3=1))
+    assert rc == D.DCM_OK
 
 
 def test_skin_validation(D):
@@ -1104,7 +1146,8 @@ def test_full_size_detection_with_filter(D, slab_16m):
     assert D.dcm_status(ctx) == D.DCM_OK
 
 
-def test_verlet_list_overflow_falls_back_to_exact_lists(D):
+@pytest.mark.parametrize("newton3", [0, 1])
+def test_verlet_list_overflow_falls_back_to_exact_lists(D, newton3):
     """A blob at density 2.4 holds more neighbours within rc + skin than the
     list capacity bound (density 1.3): the build must detect the overflow,
     count exactly and fill again; forces then match the oracle."""
@@ -1117,7 +1160,8 @@ def test_verlet_list_overflow_falls_back_to_exact_lists(D):
     box = (18.0, 18.0, 18.0)
     n = len(pts)
     # uniform cutoff 3: bound = 1.3 x (4/3) pi 3.5^3 + 24 = 257 < ~360 neighbours in the blob
-    ctx = make_ctx(D, box, n, D.DCM_PREC_FP64, skin=0.5, rc_min=3.0, rc_max=3.0, recompute_every=1000)
+    ctx = make_ctx(D, box, n, D.DCM_PREC_FP64, skin=0.5, rc_min=3.0, rc_max=3.0, recompute_every=1000,
+                   newton3=newton3)
     st = D.State(ctx, pos4_of(D, pts, None, D.DCM_PREC_FP64), torch.zeros((n, 4), dtype=torch.float64, device="cuda"))
     D.dcm_step_init(ctx, st)
     assert D.dcm_status(ctx) == D.DCM_OK
