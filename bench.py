@@ -398,10 +398,10 @@ def run_gb300(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    def new_state(prec, skin=None):
+    def new_state(prec, skin=None, newton3=0):
         p = D.make_params(slab.box, n_max=n, precision=prec, recompute_every=K_RECOMPUTE, l=args.cell_edge,
                           lx=args.cell_edge_x, skin=args.skin if skin is None else skin,
-                          force_kernel=args.force_kernel, accumulation=args.accumulation)
+                          force_kernel=args.force_kernel, accumulation=args.accumulation, newton3=newton3)
         ctx = D.Context(p)
         real = ctx.real
         st = D.State(ctx, D.to_real4(torch.from_numpy(slab.pos), None, real, dev),
@@ -599,39 +599,49 @@ def run_gb300(args):
                        "stream during a job's compute"}
         del sts
 
-    # ---------------- Verlet-list form (Alg. 2.2/2.3 with skin) on the same system
-    lists = None
+    # ---------------- Verlet-list forms (Alg. 2.2/2.3 with skin) on the same system:
+    # full i-centric lists, and half lists with Newton's third law
+    lists = lists_n3 = None
     if not args.skip_lists and args.skin == 0.0:
         del st
         ctx.close()
         torch.cuda.empty_cache()
-        cl, sl = new_state(D.DCM_PREC_MIXED, skin=LIST_SKIN)
-        for _ in range(args.warmup):
-            D.dcm_step(cl, sl, DT, K_RECOMPUTE)
-        kl = max(1, min(10, args.steps))
-        barrier()
-        D.dcm_set_timing(cl, kl * K_RECOMPUTE * 2 + 8)
-        e0.record(stream)
-        for _ in range(kl):
-            D.dcm_step(cl, sl, DT, K_RECOMPUTE)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msl = e0.elapsed_time(e1)
-        lst = D.dcm_stage_times(cl)
-        pl = float(sl.thermo[3].item())
-        ul, tl = aggregate(dist, float(n) * kl * K_RECOMPUTE, msl / 1000.0)
-        lf_ms, lf_cnt = lst["forces"]
-        lf_avg = lf_ms / max(lf_cnt, 1)
-        lists = {"value": ul / tl, "unit": UNIT, "steps": kl, "ms_per_step": msl / kl, "skin": LIST_SKIN,
-                 "force_kernel": "k_forces_list_x2", "force_avg_launch_ms": lf_avg,
-                 "force_frac_fp32": pl * FLOP_PER_PAIR / (lf_avg / 1000.0) / 1e12 / peak_tinstr if lf_avg > 0 else None,
-                 "list_builds": int(lst["lists"][1]), "build_avg_ms": lst["lists"][0] / max(lst["lists"][1], 1),
-                 "stage_ms_per_step": {k: v[0] / kl for k, v in lst.items()}, "pairs_last": pl,
-                 "note": "neighbour lists of radius rc_i + skin, rebuilt (with rebinning) when a particle moved "
-                         "more than skin/2 or the cutoffs were recomputed"}
-        del sl
-        cl.close()
-        torch.cuda.empty_cache()
+        for newton3 in (0, 1):
+            cl, sl = new_state(D.DCM_PREC_MIXED, skin=LIST_SKIN, newton3=newton3)
+            for _ in range(args.warmup):
+                D.dcm_step(cl, sl, DT, K_RECOMPUTE)
+            kl = max(1, min(10, args.steps))
+            barrier()
+            D.dcm_set_timing(cl, kl * K_RECOMPUTE * 2 + 8)
+            e0.record(stream)
+            for _ in range(kl):
+                D.dcm_step(cl, sl, DT, K_RECOMPUTE)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msl = e0.elapsed_time(e1)
+            lst = D.dcm_stage_times(cl)
+            pl = float(sl.thermo[3].item())
+            ul, tl = aggregate(dist, float(n) * kl * K_RECOMPUTE, msl / 1000.0)
+            lf_ms, lf_cnt = lst["forces"]
+            lf_avg = lf_ms / max(lf_cnt, 1)
+            rec = {"value": ul / tl, "unit": UNIT, "steps": kl, "ms_per_step": msl / kl, "skin": LIST_SKIN,
+                   "force_kernel": "k_forces_list_n3" if newton3 else "k_forces_list_x2",
+                   "force_avg_launch_ms": lf_avg,
+                   "force_frac_fp32": pl * FLOP_PER_PAIR / (lf_avg / 1000.0) / 1e12 / peak_tinstr if lf_avg > 0 else None,
+                   "list_builds": int(lst["lists"][1]), "build_avg_ms": lst["lists"][0] / max(lst["lists"][1], 1),
+                   "stage_ms_per_step": {k: v[0] / kl for k, v in lst.items()}, "pairs_last": pl,
+                   "note": ("half lists kept by the larger-cutoff particle, each pair evaluated once and scattered "
+                            "(atomics) to the other particle where its cutoff reaches" if newton3 else
+                            "neighbour lists of radius rc_i + skin") +
+                           ", rebuilt (with rebinning) when a particle moved more than skin/2 or the cutoffs were "
+                           "recomputed"}
+            if newton3:
+                lists_n3 = rec
+            else:
+                lists = rec
+            del sl
+            cl.close()
+            torch.cuda.empty_cache()
         ctx, st = new_state(D.DCM_PREC_MIXED)
 
     # ---------------- batched form: 64 replicas, autotuned, graph-captured
@@ -670,7 +680,7 @@ def run_gb300(args):
                           "parallelism": f"replicas x{world}"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "stage_ms_per_step": stage_ms, "step_roofline": step_roof,
-               "accumulation_forms": acc_forms, "fp64_form": fp64, "lists_form": lists, "batched_form": batch,
+               "accumulation_forms": acc_forms, "fp64_form": fp64, "lists_form": lists, "lists_newton3_form": lists_n3, "batched_form": batch,
                "adjoint_form": adjoint, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}
