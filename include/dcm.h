@@ -152,7 +152,17 @@ typedef struct dcm_params {
                              third law where both cutoffs reach, Section 4.2; i-centric where one
                              does).  Results are summed with atomics (order not reproducible).
                              0 (default): full i-centric lists */
-  int32_t reserved3;
+  int32_t segmentation;   /* 0 (default): S = threshold of the box sums (2-means or fixed);
+                             1: then refined by the regularised two-phase Mumford-Shah
+                             segmentation of the unsmoothed box counts (Section 2.1): phase
+                             values c0, c1 = the phase means, s minimising
+                             sum (g - c_s)^2 + ms_nu x (faces between the phases), by a
+                             primal-dual iteration on the convex relaxation thresholded at 1/2.
+                             Single-system contexts only */
+  int32_t ms_inner;       /* primal-dual iterations per outer iteration (1..100000). Default 200 */
+  int32_t ms_outer;       /* outer iterations (phase values, then s) at most (1..64). Default 4 */
+  int32_t reserved4;
+  double ms_nu;           /* weight of the length term, in (box count)^2 (>= 0). Default 4 */
 } dcm_params;
 
 typedef struct dcm_ctx dcm_ctx;
@@ -241,9 +251,10 @@ int dcm_box_counts(dcm_ctx* ctx, int64_t n, const void* pos, int32_t* box_count,
 
 /* Interface detection, Section 2.1 and Eq. 4.  g = box sum of box_count over
  * the (2w+1)^3 periodic neighbourhood; T = integer 2-means threshold of g (or
- * the fixed params.threshold); s = (g >= T), then (params.min_component > 0)
- * without its small components (dcm_remove_small_components); iface = s AND
- * some face neighbour has s = 0.  If one phase is empty, T = max(g) + 1 (no
+ * the fixed params.threshold); s = (g >= T), then (params.segmentation = 1)
+ * refined by the regularised two-phase segmentation of box_count, then
+ * (params.min_component > 0) without its small components
+ * (dcm_remove_small_components); iface = s AND some face neighbour has s = 0.  If one phase is empty, T = max(g) + 1 (no
  * interface).
  *   box_count int32[nboxes] in;  s, iface uint8[nboxes] out;
  *   threshold int32[1] out (device);  g int32[nboxes] out (nullable). */
@@ -439,7 +450,10 @@ int dcm_batch_barrier_selftest(dcm_batch* b, int32_t phantom, int64_t budget_ns,
 int dcm_batch_replay(dcm_batch* b, dcm_state* st, int32_t ngraphs, dcm_stream_t stream);
 int dcm_batch_graph_steps(const dcm_batch* b);
 
-/* As dcm_status, dcm_set_timing, dcm_stage_times, dcm_launch_count. */
+/* As dcm_status, dcm_set_timing, dcm_stage_times, dcm_launch_count.  In the
+ * persistent plan the stage times come from a clock inside the launch: block
+ * 0 reads the GPU's global timer as it leaves each grid barrier and charges
+ * the interval to the stage that just ended. */
 int dcm_batch_status(dcm_batch* b, dcm_stream_t stream);
 int dcm_batch_set_timing(dcm_batch* b, int32_t capacity);
 int dcm_batch_stage_times(dcm_batch* b, double* ms, int64_t* count);

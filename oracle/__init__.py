@@ -70,6 +70,7 @@ def _load():
                 "orc_segment": (None, [_i32p, _i64p, I64, _u8p, _u8p]),
                 "orc_interface": (None, [_u8p, _i64p, _u8p]),
                 "orc_remove_small_components": (I64, [_u8p, _i64p, I64, _u8p]),
+                "orc_ms_segment": (I32, [_i32p, _i64p, D, I32, I32, _u8p, _f64p, _f64p]),
                 "orc_cfsm": (I32, [_u8p, _u8p, _i64p, D, D, I32, _f64p]),
                 "orc_distance_jacobi": (I32, [_u8p, _u8p, _i64p, D, D, I32, _f64p]),
                 "orc_distance_sweep8": (I32, [_u8p, _u8p, _i64p, D, D, I32, _f64p]),
@@ -196,13 +197,43 @@ def remove_small_components(s, nh, min_boxes: int):
     return out, int(k)
 
 
-def detect_interface(count, nh, w: int = 2, threshold=None, min_component: int = 0):
+def ms_segment(count, nh, s0, nu: float, inner: int, outer: int):
+    """Section 2.1's regularised two-phase Mumford-Shah segmentation of the
+    box counts (reading and iteration in dcm_oracle.c), from the volume s0.
+    Returns (s, u, (c0, c1), outer iterations run)."""
+    nh = np.asarray(nh, dtype=np.int64)
+    g = np.ascontiguousarray(count, dtype=np.int32)
+    s = np.array(s0, dtype=np.uint8, copy=True)
+    u = np.zeros(g.size, dtype=np.float64)
+    c = np.zeros(2, dtype=np.float64)
+    k = _load().orc_ms_segment(_p(g, _i32p), _p(nh, _i64p), float(nu), int(inner), int(outer), _p(s, _u8p),
+                               _p(u, _f64p), _p(c, _f64p))
+    return s, u, (float(c[0]), float(c[1])), int(k)
+
+
+def ms_energy(count, nh, s, c0, c1, nu):
+    """The functional E(s; c0, c1) of the segmentation reading: squared
+    deviations from the phase values plus nu times the faces between phases."""
+    nh = np.asarray(nh, dtype=np.int64)
+    g = np.asarray(count, dtype=np.float64).reshape(nh[2], nh[1], nh[0])
+    sv = np.asarray(s, dtype=np.float64).reshape(nh[2], nh[1], nh[0])
+    data = (sv * (g - c1) ** 2 + (1.0 - sv) * (g - c0) ** 2).sum()
+    faces = sum(np.abs(np.roll(sv, -1, axis=a) - sv).sum() for a in range(3))
+    return float(data + nu * faces)
+
+
+def detect_interface(count, nh, w: int = 2, threshold=None, min_component: int = 0, ms=None):
     """count -> (g, T, s, iface).  ``threshold`` fixes T instead of 2-means;
+    ``ms = (nu, inner, outer)`` refines S by the regularised Mumford-Shah
+    segmentation of the unsmoothed counts, starting from the threshold's S;
     ``min_component > 0`` removes smaller components of either phase from S
     before the interface boxes are taken."""
     g = smooth(count, nh, w)
     T = two_means(g) if threshold is None else int(threshold)
     s, iface = segment(g, nh, T)
+    if ms is not None:
+        s, _, _, _ = ms_segment(count, nh, s, *ms)
+        iface = interface(s, nh)
     if min_component > 0:
         s, _ = remove_small_components(s, nh, min_component)
         iface = interface(s, nh)

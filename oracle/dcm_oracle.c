@@ -175,6 +175,112 @@ void orc_interface(const uint8_t* s, const int64_t* nh, uint8_t* iface) {
       }
 }
 
+/* Regularised two-phase segmentation (Section 2.1: the piecewise constant
+ * Mumford-Shah functional for two-phase segmentation, refs. [1, 18]).
+ * Reading: on the periodic grid of box counts g the functional of a binary
+ * volume s with phase values c0 (low density) and c1 (high density) is
+ *   E(s; c0, c1) = sum_b [ s_b (g_b - c1)^2 + (1 - s_b) (g_b - c0)^2 ]
+ *                + nu sum over box faces |s_b - s_b'|
+ * (the length term counts the faces between the phases).  It is minimised by
+ * alternating the phase values (the means of g over each phase) with the
+ * minimisation over s for fixed values.  For fixed values E is, up to a
+ * constant, sum_b w_b s_b + nu sum |D s| with w_b = (g_b - c1)^2 - (g_b - c0)^2;
+ * its convex relaxation over u in [0, 1]^n (the face sum is a total variation
+ * on the grid graph) has binary minimisers given by thresholding any
+ * minimiser at 1/2, and is solved by the first-order primal-dual iteration of
+ * Chambolle and Pock (2011), a stencil on the grid:
+ *   p_f  <- clip(p_f + sigma (D ubar)_f, -nu, nu)         (one p per face)
+ *   u'_b <- clip(u_b - tau ((D^T p)_b + w_b), 0, 1)
+ *   ubar <- 2 u' - u,  u <- u'
+ * with (D u)_f = u_{b+e} - u_b for the face f between b and b + e, and
+ * (D^T p)_b = sum_e (p_{b-e, e} - p_{b, e}); tau = sigma = 0.28 (tau sigma
+ * ||D||^2 < 1, ||D||^2 <= 12 on the 3D grid).  Each outer iteration starts
+ * from u = s, p = 0, runs `inner` iterations and sets s_b = (u_b >= 1/2); the
+ * loop stops after `outer` iterations, when s no longer changes, or when a
+ * phase is empty (s then stays as it is).  s is the initial volume on input
+ * and the result on output; u (nullable) receives the last relaxed solution
+ * and c[0..1] the phase values of the last outer iteration.  Returns the
+ * number of outer iterations run. */
+int orc_ms_segment(const int32_t* g, const int64_t* nh, double nu, int inner, int outer, uint8_t* s, double* u_out,
+                   double* c) {
+  const int64_t nx = nh[0], ny = nh[1], nz = nh[2], nbox = nx * ny * nz;
+  const double tau = 0.28, sigma = 0.28;
+  double* w = (double*)malloc(sizeof(double) * (size_t)nbox);
+  double* u = (double*)malloc(sizeof(double) * (size_t)nbox);
+  double* ub = (double*)malloc(sizeof(double) * (size_t)nbox);
+  double* p = (double*)malloc(sizeof(double) * 3 * (size_t)nbox); /* p[3 b + e]: face between b and b + e */
+  int done = 0;
+  for (int o = 0; o < outer; ++o) {
+    /* phase values: the means of g over each phase */
+    double s0 = 0.0, s1 = 0.0;
+    int64_t n0 = 0, n1 = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+      if (s[b]) {
+        s1 += g[b];
+        ++n1;
+      } else {
+        s0 += g[b];
+        ++n0;
+      }
+    }
+    if (n0 == 0 || n1 == 0) break;
+    const double c0 = s0 / (double)n0, c1 = s1 / (double)n1;
+    if (c) {
+      c[0] = c0;
+      c[1] = c1;
+    }
+    for (int64_t b = 0; b < nbox; ++b) {
+      w[b] = (g[b] - c1) * (g[b] - c1) - (g[b] - c0) * (g[b] - c0);
+      u[b] = s[b] ? 1.0 : 0.0;
+      ub[b] = u[b];
+      p[3 * b] = p[3 * b + 1] = p[3 * b + 2] = 0.0;
+    }
+    for (int it = 0; it < inner; ++it) {
+      /* dual step on every face (b, b + e) */
+      for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+          for (int64_t x = 0; x < nx; ++x) {
+            const int64_t b = x + nx * (y + ny * z);
+            const int64_t nb[3] = {wrap(x + 1, nx) + nx * (y + ny * z), x + nx * (wrap(y + 1, ny) + ny * z),
+                                   x + nx * (y + ny * wrap(z + 1, nz))};
+            for (int e = 0; e < 3; ++e) {
+              double q = p[3 * b + e] + sigma * (ub[nb[e]] - ub[b]);
+              p[3 * b + e] = q < -nu ? -nu : (q > nu ? nu : q);
+            }
+          }
+      /* primal step on every box */
+      for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+          for (int64_t x = 0; x < nx; ++x) {
+            const int64_t b = x + nx * (y + ny * z);
+            const int64_t pb[3] = {wrap(x - 1, nx) + nx * (y + ny * z), x + nx * (wrap(y - 1, ny) + ny * z),
+                                   x + nx * (y + ny * wrap(z - 1, nz))};
+            double dtp = 0.0;
+            for (int e = 0; e < 3; ++e) dtp += p[3 * pb[e] + e] - p[3 * b + e];
+            double v = u[b] - tau * (dtp + w[b]);
+            v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+            ub[b] = 2.0 * v - u[b];
+            u[b] = v;
+          }
+    }
+    ++done;
+    int changed = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+      const uint8_t t = u[b] >= 0.5 ? 1 : 0;
+      changed |= t != s[b];
+      s[b] = t;
+    }
+    if (u_out)
+      for (int64_t b = 0; b < nbox; ++b) u_out[b] = u[b];
+    if (!changed) break;
+  }
+  free(w);
+  free(u);
+  free(ub);
+  free(p);
+  return done;
+}
+
 /* Removal of small connected components (Section 2.1: "bubbles" of either
  * phase inside the other are filtered out by volume; the filter itself is in
  * the paper's reference [25], not available).  Reading: components are sets

@@ -152,6 +152,9 @@ extern "C" int dcm_params_default(dcm_params* p) {
   p->precision = DCM_PREC_MIXED;
   p->recompute_every = 10;
   p->n_max = 0;
+  p->ms_inner = 200;
+  p->ms_outer = 4;
+  p->ms_nu = 4.0;
   return DCM_OK;
 }
 
@@ -216,6 +219,14 @@ extern "C" int dcm_validate_params(const dcm_params* p, char* msg, int32_t len) 
   if (p->accumulation < DCM_ACC_AUTO || p->accumulation > DCM_ACC_PLANE_KAHAN)
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "accumulation must be one of DCM_ACC_*");
   if (p->newton3 != 0 && p->newton3 != 1) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "newton3 must be 0 or 1");
+  if (p->segmentation != 0 && p->segmentation != 1)
+    return msg_out(msg, len, DCM_ERR_INVALID_ARG, "segmentation must be 0 or 1");
+  if (p->segmentation) {
+    if (!(p->ms_nu >= 0.0) || !std::isfinite(p->ms_nu))
+      return msg_out(msg, len, DCM_ERR_INVALID_ARG, "ms_nu must be finite and >= 0");
+    if (p->ms_inner < 1 || p->ms_inner > 100000) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "ms_inner in 1..100000");
+    if (p->ms_outer < 1 || p->ms_outer > 64) return msg_out(msg, len, DCM_ERR_INVALID_ARG, "ms_outer in 1..64");
+  }
   if (p->newton3 && !(p->skin > 0.0))
     return msg_out(msg, len, DCM_ERR_INVALID_ARG, "newton3 needs Verlet lists (skin > 0)");
   if (p->precision != DCM_PREC_FP64 && p->precision != DCM_PREC_MIXED)
@@ -252,12 +263,13 @@ extern "C" int dcm_grid_dims(const dcm_params* p, int64_t* cells3, int64_t* boxe
 struct ScratchPlan {
   int64_t n_max, ncell, nbox, scan_cap, red_cap, rsize, flags, nblk;
   double skin;
-  int32_t min_component;
+  int32_t min_component, segmentation, ms_outer;
   int64_t total() const {
     return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
            8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
-           (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2) + 4 * nblk;
+           (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2) + 4 * nblk +
+           (segmentation ? 6 * rsize * nbox + 32 * ms_outer + 16 + 4 * (ms_outer + 2) : 0);
   }
 };
 
@@ -278,6 +290,8 @@ static ScratchPlan plan_of(const dcm_params* p) {
   s.flags = p->iter_max + 2;
   s.skin = p->skin;
   s.min_component = p->min_component;
+  s.segmentation = p->segmentation;
+  s.ms_outer = p->ms_outer;
   s.nblk = adjoint_blocks(p, 0) * adjoint_blocks(p, 1) * adjoint_blocks(p, 2);
   return s;
 }
@@ -302,7 +316,8 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
                  ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
                  ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0, ctx->dq[0], ctx->dq[1], ctx->dqlen,
-                 ctx->dstamp, ctx->dfixed, ctx->blk_max};
+                 ctx->dstamp, ctx->dfixed, ctx->blk_max, ctx->ms_u, ctx->ms_ub, ctx->ms_p, ctx->ms_w,
+                 ctx->ms_sums, ctx->ms_c, ctx->ms_flags};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -382,6 +397,15 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
     alloc((void**)&ctx->cc_cnt, 4 * s.nbox);
     alloc((void**)&ctx->cc_flags, 4 * 80);
     alloc((void**)&ctx->cc_s0, s.nbox);
+  }
+  if (p->segmentation) {
+    alloc(&ctx->ms_u, s.rsize * s.nbox);
+    alloc(&ctx->ms_ub, s.rsize * s.nbox);
+    alloc(&ctx->ms_p, 3 * s.rsize * s.nbox);
+    alloc(&ctx->ms_w, s.rsize * s.nbox);
+    alloc((void**)&ctx->ms_sums, 32 * (int64_t)p->ms_outer);
+    alloc((void**)&ctx->ms_c, 16);
+    alloc((void**)&ctx->ms_flags, 4 * (int64_t)(p->ms_outer + 2));
   }
   alloc((void**)&ctx->adj_pairs, 8 * 48);
   for (int d = 0; d < 3; ++d) ctx->nblk3[d] = (int)adjoint_blocks(p, d);  // as counted in the plan

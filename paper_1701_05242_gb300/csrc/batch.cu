@@ -384,7 +384,7 @@ extern "C" void dcm_batch_destroy(dcm_batch* b) {
                  c->box_count, c->g,   c->g_tmp, c->s,      c->iface,      c->D[0],       c->D[1],
                  c->flags,  c->red,   c->red_tmp, c->totals, b->geom,       b->rep_of_particle, b->rep_of_box,
                  b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart,
-                 b->tiles,  b->sync,  b->scan_blk};
+                 b->tiles,  b->sync,  b->scan_blk, b->pacc};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (c->host_status) cudaFreeHost(c->host_status);
@@ -402,6 +402,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   *out = nullptr;
   if (p->skin != 0.0) return DCM_ERR_INVALID_ARG;  // the batched form steps over cell lists only
   if (p->min_component != 0) return DCM_ERR_INVALID_ARG;  // no bubble filter in the batched form
+  if (p->segmentation != 0) return DCM_ERR_INVALID_ARG;   // nor the regularised segmentation
   std::vector<RepGeom> geom((size_t)R);
   int64_t ntot = 0, nctot = 0, nbtot = 0;
   for (int r = 0; r < R; ++r) {
@@ -459,6 +460,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   b->tile = 0;
   b->sync = nullptr;
   b->scan_blk = nullptr;
+  b->pacc = nullptr;
   b->pgrid = 0;
   b->wait_budget = (int64_t)2000000000;  // 2 s
   b->graph = nullptr;
@@ -711,7 +713,23 @@ extern "C" int dcm_batch_set_timing(dcm_batch* b, int32_t capacity) {
 }
 
 extern "C" int dcm_batch_stage_times(dcm_batch* b, double* ms, int64_t* count) {
-  return b ? dcm_stage_times(&b->base, ms, count) : DCM_ERR_INVALID_ARG;
+  if (!b) return DCM_ERR_INVALID_ARG;
+  double ev_ms[DCM_NSTAGES];
+  int64_t ev_n[DCM_NSTAGES];
+  int r = dcm_stage_times(&b->base, ev_ms, ev_n);
+  // the persistent plan's stage clock (nanoseconds and runs), read and cleared
+  unsigned long long acc[2 * DCM_NSTAGES + 1] = {0};
+  if (b->pacc) {
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(acc, b->pacc, sizeof(acc), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(b->pacc, 0, sizeof(acc)) != cudaSuccess)
+      return berr(b, DCM_ERR_CUDA, "persistent stage clock");
+  }
+  for (int s = 0; s < DCM_NSTAGES; ++s) {
+    if (ms) ms[s] = ev_ms[s] + 1e-6 * (double)acc[s];
+    if (count) count[s] = ev_n[s] + (int64_t)acc[DCM_NSTAGES + s];
+  }
+  return r;
 }
 
 extern "C" int dcm_batch_launch_count(dcm_batch* b, int64_t* count, int32_t reset) {

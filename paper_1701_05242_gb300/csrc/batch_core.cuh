@@ -66,6 +66,7 @@ struct dcm_batch {
   int32_t* scan_blk;       // [grid]: per-block totals of the persistent scan
   int32_t pgrid;           // blocks of the persistent launch (co-resident), 0 until sized
   int64_t wait_budget;     // nanoseconds a barrier wait may take before it reports DCM_ERR_TIMEOUT
+  unsigned long long* pacc;  // stage timing of the persistent plan: ns and runs per stage, last stamp
 };
 
 namespace dcm {

@@ -93,12 +93,30 @@ struct PArgs {
   int32_t* status;
   int64_t budget_ns;     // longest barrier wait
   uint32_t phantom;      // blocks the barrier waits for beyond the grid (the self-test only)
+  unsigned long long* pacc;  // nullable: [DCM_NSTAGES] nanoseconds per stage, [DCM_NSTAGES] runs, last stamp
 };
+
+
 
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Stage timing of the persistent plan (dcm_batch_set_timing): block 0 reads
+// the global timer whenever it leaves a barrier and charges the time since
+// its previous reading to the stage that just ended (so a stage's time is
+// the time until the grid's slowest block finished it).
+__device__ __forceinline__ void stage_mark(unsigned long long* pacc, int stage) {
+  if (pacc && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long t = global_ns();
+    if (stage >= 0) {
+      pacc[stage] += t - pacc[2 * DCM_NSTAGES];
+      pacc[DCM_NSTAGES + stage] += 1;
+    }
+    pacc[2 * DCM_NSTAGES] = t;
+  }
 }
 
 // Grid-wide barrier (arrival counter + generation).  Returns false, for the
@@ -187,7 +205,9 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
   do {                                                             \
     if (!grid_sync(a.sync, expected, a.budget_ns, a.status)) return; \
   } while (0)
+#define PSTAGE(stage) stage_mark(a.pacc, stage)
 
+  PSTAGE(-1);
   // ---- clear the counters of this step
   for (int64_t c = gt; c < a.ncell; c += gs) a.count[c] = 0;
   if (a.recompute) {
@@ -204,6 +224,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
     b_kick_drift_count<R>(i, a.pos_c, a.vel_c, a.force, a.hdt, a.dt, a.l, a.il, a.lx, a.ilx, a.geom, a.rep_p,
                           a.cell, a.slot, a.count, a.drift);
   PSYNC();
+  PSTAGE(DCM_STAGE_KICK_DRIFT);
   // ---- exclusive scan of the cell counts: each block owns one chunk
   const int64_t chunk = (a.ncell + gridDim.x - 1) / gridDim.x;
   const int64_t lo = min((int64_t)blockIdx.x * chunk, a.ncell), hi = min(lo + chunk, a.ncell);
@@ -237,6 +258,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
   for (int64_t k = gt; k < a.n; k += gs)
     b_gather<R>(k, a.perm, a.pos_c, a.pos_o, a.vel_c, a.vel_o, a.rc_c, a.rc_o, a.id_c, a.id_o);
   PSYNC();
+  PSTAGE(DCM_STAGE_BIN);
   // ---- every K steps: interface, distances, cutoffs (Sections 2.1, 2.2)
   if (a.recompute) {
     const int32_t* counts = a.count;
@@ -262,6 +284,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
     }
     for (int64_t k = gt; k < a.nbox; k += gs) b_segment(k, a.g, a.geom, a.rep_b, a.thr, a.s, a.iface);
     PSYNC();
+    PSTAGE(DCM_STAGE_DETECT);
     for (int64_t k = gt; k < a.nbox; k += gs) b_dist_init<R>(k, a.s, a.iface, a.D0, a.D1);
     PSYNC();
     // Jacobi sweeps until one changes nothing (both buffers then agree) or
@@ -287,9 +310,11 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
         }
       if (first < 0) raise_status(a.status, DCM_ERR_NOT_CONVERGED);
     }
+    PSTAGE(DCM_STAGE_DISTANCE);
     for (int64_t i = gt; i < a.n; i += gs)
       b_cutoffs<R, false>(i, a.pos_o, a.D0, a.geom, a.rep_p, a.h, a.r_grid, a.rc_min, a.rc_max, a.ramp, a.rc_o);
     PSYNC();
+    PSTAGE(DCM_STAGE_CUTOFFS);
   }
   // ---- forces over the (replica, tile) queue (Section 2.4, Alg. 2.3)
   {
@@ -306,6 +331,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
     }
   }
   PSYNC();
+  PSTAGE(DCM_STAGE_FORCES);
   // ---- second half kick, kinetic energy, per-replica thermo
   for (int64_t i = gt; i < a.n; i += gs) b_kick<R>(i, a.vel_o, a.kick ? a.force : nullptr, a.hdt, a.ke_i);
   PSYNC();
@@ -316,6 +342,10 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
     const int64_t warp = gt >> 5, nwarp = gs >> 5;
     for (int64_t r = warp; r < a.nrep; r += nwarp) b_thermo_sum((int)r, a.chunk0, a.nchunk, a.tpart, a.thermo);
   }
+  // the kick's time: up to the last barrier (the thermo sums of the last
+  // warps are not waited for)
+  PSTAGE(DCM_STAGE_KICK);
+#undef PSTAGE
 #undef PSYNC
 }
 
@@ -405,9 +435,12 @@ int b_persistent_setup(dcm_batch* b) {
     return DCM_ERR_CUDA;
   b->pgrid = sms * kPMaxBlocksPerSM;
   if (cudaMalloc((void**)&b->sync, 4 * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc((void**)&b->scan_blk, sizeof(int32_t) * (size_t)b->pgrid) != cudaSuccess)
+      cudaMalloc((void**)&b->scan_blk, sizeof(int32_t) * (size_t)b->pgrid) != cudaSuccess ||
+      cudaMalloc((void**)&b->pacc, sizeof(unsigned long long) * (2 * DCM_NSTAGES + 1)) != cudaSuccess)
     return DCM_ERR_NOMEM;
-  if (cudaMemset(b->sync, 0, 4 * sizeof(uint32_t)) != cudaSuccess) return DCM_ERR_CUDA;
+  if (cudaMemset(b->sync, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(b->pacc, 0, sizeof(unsigned long long) * (2 * DCM_NSTAGES + 1)) != cudaSuccess)
+    return DCM_ERR_CUDA;
   return build_tiles(b, kQueueTile);
 }
 
@@ -494,6 +527,7 @@ int b_persistent_step(dcm_batch* b, dcm_state* s, R hdt, R dt, bool drift, bool 
   a.status = ctx->status;
   a.budget_ns = b->wait_budget;
   a.phantom = 0;
+  a.pacc = b->base.timing ? b->pacc : nullptr;
   if (b->ntot == 0) return DCM_OK;
   int r = dispatch_persistent<R>(b, a, st);
   return r ? r : check_launch(ctx, "persistent step");

@@ -106,6 +106,11 @@ __global__ void k_interface_of(const uint8_t* __restrict__ s, int nx, int ny, in
   iface[b] = (uint8_t)f;
 }
 
+void interface_of(dcm_ctx* ctx, const uint8_t* s, uint8_t* iface, cudaStream_t st) {
+  const int nx = (int)ctx->nh[0], ny = (int)ctx->nh[1], nz = (int)ctx->nh[2];
+  DCM_LAUNCH(ctx, k_interface_of, (unsigned)((ctx->nbox + 255) / 256), 256, 0, st, s, nx, ny, nz, iface);
+}
+
 int remove_small_components(dcm_ctx* ctx, const uint8_t* s_in, uint8_t* s_out, uint8_t* iface, cudaStream_t st) {
   if (ctx->p.min_component <= 0 || !ctx->cc_lab)
     return set_error(ctx, DCM_ERR_INVALID_ARG, "the context was created with min_component = 0");

@@ -141,6 +141,14 @@ struct dcm_ctx {
   int32_t* dmax;            // largest squared displacement (float bits)
   int32_t* lflag;           // list overflow flag of the single-walk build
   int list_valid;
+  // regularised segmentation (params.segmentation = 1)
+  void* ms_u;               // nbox reals: relaxed volume u
+  void* ms_ub;              // nbox reals: extrapolated u
+  void* ms_p;               // 3 nbox reals: dual value per face
+  void* ms_w;               // nbox reals: data weights
+  unsigned long long* ms_sums;  // [ms_outer][4]: n0, S0, n1, S1
+  double* ms_c;             // [2]: phase values of the last outer iteration
+  int32_t* ms_flags;        // [ms_outer + 2]: stop mark, then "changed" per outer iteration
   // optional per-stage CUDA-event timing (dcm_set_timing)
   int timing;
   int ev_n[DCM_NSTAGES];
@@ -200,6 +208,11 @@ int scatter_sort(dcm_ctx* ctx, int64_t n, const int32_t* cell, const int32_t* sl
 int remove_small_components(dcm_ctx* ctx, const uint8_t* s_in, uint8_t* s_out, uint8_t* iface, cudaStream_t st);
 int detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t* iface,
                      int32_t* threshold, int32_t* g_out, cudaStream_t st);
+// segment_ms.cu: the regularised two-phase segmentation of the box counts,
+// refining s in place (params.segmentation = 1).
+int ms_segment(dcm_ctx* ctx, const int32_t* count, uint8_t* s, cudaStream_t st);
+// components.cu: interface boxes of a segmented volume.
+void interface_of(dcm_ctx* ctx, const uint8_t* s, uint8_t* iface, cudaStream_t st);
 
 // distance.cu
 template <typename R>

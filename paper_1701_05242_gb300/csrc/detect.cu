@@ -1,5 +1,7 @@
 // Interface detection (Section 2.1, Eq. 4): gray-scale volume from box counts,
-// two-phase segmentation by an integer 2-means threshold, interface boxes.
+// two-phase segmentation by an integer 2-means threshold (refined, with
+// params.segmentation = 1, by the regularised segmentation of segment_ms.cu),
+// interface boxes.
 //
 // All integer arithmetic, so the result is bit-identical to any correct
 // evaluation: the (2w+1)^3 box sum is computed as three separable 1-D periodic
@@ -198,13 +200,20 @@ int detect_interface(dcm_ctx* ctx, const int32_t* box_count, uint8_t* s, uint8_t
   }
   DCM_LAUNCH(ctx, k_two_means, 1, 1024, 0, st, ctx->hist, ctx->thr, 64, ctx->p.threshold, threshold);
   if (ctx->p.min_component > 0) {
-    // segment into scratch, then the filtered S and its interface into s, iface
+    // segment (and refine) into scratch, then the filtered S and its interface into s, iface
     DCM_LAUNCH(ctx, k_segment, nb, 256, 0, st, g, nx, ny, nz, ctx->thr, ctx->cc_s0, iface);
     int r = check_launch(ctx, "detect_interface");
     if (r) return r;
+    if (ctx->p.segmentation && (r = ms_segment(ctx, box_count, ctx->cc_s0, st))) return r;
     return remove_small_components(ctx, ctx->cc_s0, s, iface, st);
   }
   DCM_LAUNCH(ctx, k_segment, nb, 256, 0, st, g, nx, ny, nz, ctx->thr, s, iface);
+  if (ctx->p.segmentation) {
+    // the regularised segmentation of the counts refines the threshold's S
+    int r = ms_segment(ctx, box_count, s, st);
+    if (r) return r;
+    interface_of(ctx, s, iface, st);
+  }
   return check_launch(ctx, "detect_interface");
 }
 

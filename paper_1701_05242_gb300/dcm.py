@@ -61,7 +61,9 @@ class dcm_params(ctypes.Structure):
                 ("sigma", ctypes.c_double * 4), ("shift_energy", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("recompute_every", ctypes.c_int32), ("force_kernel", ctypes.c_int32), ("n_max", ctypes.c_int64),
                 ("skin", ctypes.c_double), ("min_component", ctypes.c_int32), ("accumulation", ctypes.c_int32),
-                ("lx", ctypes.c_double), ("newton3", ctypes.c_int32), ("reserved3", ctypes.c_int32)]
+                ("lx", ctypes.c_double), ("newton3", ctypes.c_int32),
+                ("segmentation", ctypes.c_int32), ("ms_inner", ctypes.c_int32), ("ms_outer", ctypes.c_int32),
+                ("reserved4", ctypes.c_int32), ("ms_nu", ctypes.c_double)]
 
 
 class dcm_state(ctypes.Structure):
