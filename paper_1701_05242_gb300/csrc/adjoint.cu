@@ -131,6 +131,88 @@ __device__ __forceinline__ void adj_range(const typename RT<R>::R4* __restrict__
   }
 }
 
+// The culled row walk of the adjoint (radius `reach`, the reverse pairs'
+// bound) around the particle `self` at pi, handing each row segment to
+// range(lo, hi, self_or_-1, xi, yi, zi, shx, shy, shz) as the force walk does
+// (image segments with the exact shifts; self is passed only for the
+// particle's own image, where it must be skipped).
+template <typename R, typename F>
+__device__ __forceinline__ void adj_walk(const int32_t* __restrict__ start, const Grid<R>& g,
+                                         const typename RT<R>::R4& pi, R reach2s, R reach, int self, F&& range) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
+  const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
+  const int cy = cell_coord<R>(pi.y, l, il, ny);
+  const int cz = cell_coord<R>(pi.z, l, il, nz);
+  const int H = (int)ceil(reach * il), Hx = (int)ceil(reach * ilx);
+  for (int uz = cz - H; uz <= cz + H; ++uz) {
+    R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
+    R gz2 = gz * gz;
+    if (gz2 >= reach2s) continue;
+    int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
+    R zi = uz >= nz ? pi.z - g.L[2] : pi.z;
+    R zsh = uz < 0 ? -g.L[2] : (R)0;
+    for (int uy = cy - H; uy <= cy + H; ++uy) {
+      R gy = uy > cy ? (R)uy * l - pi.y : (uy < cy ? pi.y - (R)(uy + 1) * l : (R)0);
+      R gyz2 = gz2 + gy * gy;
+      if (gyz2 >= reach2s) continue;
+      int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+      R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
+      R ysh = uy < 0 ? -g.L[1] : (R)0;
+      R wx = sqrt(reach2s - gyz2);
+      int ulo = ufloor<R>((pi.x - wx) * ilx - (R)5e-4);
+      int uhi = ufloor<R>((pi.x + wx) * ilx + (R)5e-4);
+      ulo = max(ulo, cx - Hx);
+      uhi = min(uhi, cx + Hx);
+      if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
+      const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
+      if (ulo < 0) {
+        int a1 = min(uhi, -1);
+        range(__ldg(start + row + ulo + nx), __ldg(start + row + a1 + nx + 1), -1, pi.x, yi, zi, -g.L[0], ysh, zsh);
+      }
+      {
+        int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
+        if (a0 <= a1)
+          range(__ldg(start + row + a0), __ldg(start + row + a1 + 1), (ysh == (R)0 && zsh == (R)0) ? self : -1, pi.x,
+                yi, zi, (R)0, ysh, zsh);
+      }
+      if (uhi >= nx) {
+        int a0 = max(ulo, nx);
+        range(__ldg(start + row + a0 - nx), __ldg(start + row + uhi - nx + 1), -1, pi.x - g.L[0], yi, zi, (R)0, ysh,
+              zsh);
+      }
+    }
+  }
+}
+
+// Radius of the adjoint walk of particle k: the largest cutoff in the 27
+// blocks around it (every j whose own cutoff reaches k lies in one of them),
+// at least rc_k; rc_max without the block table.
+template <typename R>
+__device__ __forceinline__ R reverse_reach(const typename RT<R>::R4& pi, R rck, R rc_max, const BlockGrid& bg,
+                                           const int32_t* __restrict__ bmax) {
+  R reach = rc_max;
+  if (bmax) {
+    const int bx = block_coord((float)pi.x, bg.inv_be[0], bg.nb[0]);
+    const int by = block_coord((float)pi.y, bg.inv_be[1], bg.nb[1]);
+    const int bz = block_coord((float)pi.z, bg.inv_be[2], bg.nb[2]);
+    float m = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (bz + dz + bg.nb[2]) % bg.nb[2];
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = (by + dy + bg.nb[1]) % bg.nb[1];
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = (bx + dx + bg.nb[0]) % bg.nb[0];
+          m = fmaxf(m, __int_as_float(__ldg(bmax + xx + bg.nb[0] * (yy + bg.nb[1] * zz))));
+        }
+      }
+    }
+    reach = (R)m < reach ? (R)m : reach;
+    if (reach < rck) reach = rck;
+  }
+  return reach;
+}
+
 // Threads per block of the adjoint: the cost per particle varies several-fold
 // (rc_k and the reverse reach grow toward the interfaces), so small blocks
 // free their slots as soon as their own warps finish (measured best: 64 for
@@ -153,33 +235,13 @@ __global__ void __launch_bounds__(adj_block<R>()) k_adjoint(int64_t n, const typ
   for (int p = 0; p < 16; ++p) c.de[p] = c.ds[p] = (R)0;
   if (i < n) {
     const Grid<R>& g = a.g;
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
     auto pi = ldg4(pos + i);
     auto ak = ldg4(A + i);
     R rck = rc[i];
     if (!(rck <= a.rc_max)) rck = a.rc_max;
     if (!(rck > (R)0)) rck = (R)0;
     const R rck2 = rck * rck;
-    R reach = a.rc_max;  // reverse pairs: the largest cutoff around k
-    if (bmax) {
-      const int bx = block_coord((float)pi.x, bg.inv_be[0], bg.nb[0]);
-      const int by = block_coord((float)pi.y, bg.inv_be[1], bg.nb[1]);
-      const int bz = block_coord((float)pi.z, bg.inv_be[2], bg.nb[2]);
-      float m = 0.f;
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int zz = (bz + dz + bg.nb[2]) % bg.nb[2];
-        for (int dy = -1; dy <= 1; ++dy) {
-          const int yy = (by + dy + bg.nb[1]) % bg.nb[1];
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int xx = (bx + dx + bg.nb[0]) % bg.nb[0];
-            m = fmaxf(m, __int_as_float(__ldg(bmax + xx + bg.nb[0] * (yy + bg.nb[1] * zz))));
-          }
-        }
-      }
-      reach = (R)m < reach ? (R)m : reach;
-      if (reach < rck) reach = rck;
-    }
+    const R reach = reverse_reach<R>(pi, rck, a.rc_max, bg, bmax);
     const R reach2s = reach * reach * (R)1.000004;
     const int tk = TYPED ? type_of(pi.w, a.ntypes) : 0;
     // (sigma_p / rc_k)^6 terms of the shifted energy per partner type
@@ -192,50 +254,11 @@ __global__ void __launch_bounds__(adj_block<R>()) k_adjoint(int64_t n, const typ
         kd[t] = (R)12 * c12 - (R)6 * c6;
       }
     }
-    const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
-    const int cy = cell_coord<R>(pi.y, l, il, ny);
-    const int cz = cell_coord<R>(pi.z, l, il, nz);
-    const int H = (int)ceil(reach * il), Hx = (int)ceil(reach * ilx);
-    for (int uz = cz - H; uz <= cz + H; ++uz) {
-      R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
-      R gz2 = gz * gz;
-      if (gz2 >= reach2s) continue;
-      int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
-      R zi = uz >= nz ? pi.z - g.L[2] : pi.z;
-      R zsh = uz < 0 ? -g.L[2] : (R)0;
-      for (int uy = cy - H; uy <= cy + H; ++uy) {
-        R gy = uy > cy ? (R)uy * l - pi.y : (uy < cy ? pi.y - (R)(uy + 1) * l : (R)0);
-        R gyz2 = gz2 + gy * gy;
-        if (gyz2 >= reach2s) continue;
-        int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
-        R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
-        R ysh = uy < 0 ? -g.L[1] : (R)0;
-        R wx = sqrt(reach2s - gyz2);
-        int ulo = ufloor<R>((pi.x - wx) * ilx - (R)5e-4);
-        int uhi = ufloor<R>((pi.x + wx) * ilx + (R)5e-4);
-        ulo = max(ulo, cx - Hx);
-        uhi = min(uhi, cx + Hx);
-        if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
-        const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
-        if (ulo < 0) {
-          int a1 = min(uhi, -1);
-          adj_range<R, TYPED>(pos, rc, A, __ldg(start + row + ulo + nx), __ldg(start + row + a1 + nx + 1), -1, pi.x,
-                              yi, zi, -g.L[0], ysh, zsh, rck2, tk, ak, half_dlde, a, ku, kd, c);
-        }
-        {
-          int a0 = max(ulo, 0), a1 = min(uhi, nx - 1);
-          if (a0 <= a1)
-            adj_range<R, TYPED>(pos, rc, A, __ldg(start + row + a0), __ldg(start + row + a1 + 1),
-                                (ysh == (R)0 && zsh == (R)0) ? (int)i : -1, pi.x, yi, zi, (R)0, ysh, zsh, rck2, tk, ak,
-                                half_dlde, a, ku, kd, c);
-        }
-        if (uhi >= nx) {
-          int a0 = max(ulo, nx);
-          adj_range<R, TYPED>(pos, rc, A, __ldg(start + row + a0 - nx), __ldg(start + row + uhi - nx + 1), -1,
-                              pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rck2, tk, ak, half_dlde, a, ku, kd, c);
-        }
-      }
-    }
+    adj_walk<R>(start, g, pi, reach2s, reach, (int)i,
+                [&](int lo, int hi, int self, R xi, R yi, R zi, R shx, R shy, R shz) {
+                  adj_range<R, TYPED>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, tk, ak, half_dlde, a,
+                                      ku, kd, c);
+                });
     typename RT<R>::R4 out;
     out.x = c.gx;
     out.y = c.gy;
@@ -254,6 +277,164 @@ __global__ void __launch_bounds__(adj_block<R>()) k_adjoint(int64_t n, const typ
       if ((threadIdx.x & 31) == 0) {
         // eps_p / sigma_p, the factor taken out of the d/dsigma terms
         const double f = TYPED ? 0.25 * (double)a.eps4[p] / sqrt((double)a.sig2[p]) : 1.0;
+        part[(int64_t)p * nwarp + w] = (double)de;
+        part[(int64_t)(16 + p) * nwarp + w] = (double)ds * f;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Packed form (FP32, one or two types): candidates j and j + 1 of a segment in
+// one FP32x2 step, branch-free (a slot that is neither a forward nor a reverse
+// pair gets 1/r^2 = 0, which zeroes its terms), the parameter sums per partner
+// type in registers.  With d = r_j - r_k = -r_kj the terms read
+//   G_k += fwd [g A_k + g'/r (d.A_k) d] - rev [g A_j + g'/r (d.A_j) d]
+//          + (fwd + rev) dLdE/2 g d,
+//   de_t += fwd [24 (2 s12 - s6) y (-d.A_k) + 2 dLdE ((s12 - s6) - cu_t)],
+//   ds_t += fwd [24 (24 s12 - 6 s6) y (-d.A_k) + 2 dLdE ((12 s12 - 6 s6) - cd_t)],
+// y = 1/r^2 (refined as in the force loop), t the partner's type.
+// ----------------------------------------------------------------------------
+struct AdjAcc2 {
+  float2 gx = {0.f, 0.f}, gy = {0.f, 0.f}, gz = {0.f, 0.f};
+  float2 de[2] = {{0.f, 0.f}, {0.f, 0.f}}, ds[2] = {{0.f, 0.f}, {0.f, 0.f}};
+};
+
+// Particle k's constants for partner type t in {0, 1}: sigma^2, 24 eps of the
+// pair type, and the shifted-energy terms cu, cd.
+struct AdjRow {
+  float sg[2], e24[2], cu[2], cd[2];
+};
+
+template <bool SJ>
+__device__ __forceinline__ void adj_range_x2(const float4* __restrict__ pos, const float* __restrict__ rc,
+                                             const float4* __restrict__ A, int lo, int hi, int self, float xi,
+                                             float yi, float zi, float shx, float shy, float shz, float rck2,
+                                             float rc_max, const float4& ak, float half_dlde, const AdjRow& k,
+                                             AdjAcc2& c) {
+  const float2 two = make_float2(2.f, 2.f), m1 = make_float2(-1.f, -1.f), one = make_float2(1.f, 1.f);
+  const float2 akx = make_float2(ak.x, ak.x), aky = make_float2(ak.y, ak.y), akz = make_float2(ak.z, ak.z);
+  const float hd2 = 4.f * half_dlde;
+  for (int j = lo; j < hi; j += 2) {
+    const bool has1 = j + 1 < hi;
+    const int j1 = has1 ? j + 1 : j;
+    const float4 p0 = __ldg(pos + j), p1 = __ldg(pos + j1);
+    const float4 a0 = __ldg(A + j), a1 = __ldg(A + j1);
+    const float rc0 = clamp_cutoff<float>(__ldg(rc + j), rc_max), rc1 = clamp_cutoff<float>(__ldg(rc + j1), rc_max);
+    float2 dx, dy, dz;
+    if (SJ) {
+      dx = make_float2((p0.x + shx) - xi, (p1.x + shx) - xi);
+      dy = make_float2((p0.y + shy) - yi, (p1.y + shy) - yi);
+      dz = make_float2((p0.z + shz) - zi, (p1.z + shz) - zi);
+    } else {
+      dx = make_float2(p0.x - xi, p1.x - xi);
+      dy = make_float2(p0.y - yi, p1.y - yi);
+      dz = make_float2(p0.z - zi, p1.z - zi);
+    }
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const bool v0 = j != self, v1 = has1 && j1 != self;
+    const bool f0 = v0 && r2.x < rck2, f1 = v1 && r2.y < rck2;
+    const bool b0 = v0 && r2.x < rc0 * rc0, b1 = v1 && r2.y < rc1 * rc1;
+    float y0, y1;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+    float2 y = make_float2(y0, y1);
+    const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, one);
+    y = __ffma2_rn(y, e, y);
+    y = make_float2(f0 || b0 ? y.x : 0.f, f1 || b1 ? y.y : 0.f);
+    const bool t0 = p0.w >= 1.f, t1 = p1.w >= 1.f;
+    const float2 sg = make_float2(k.sg[t0], k.sg[t1]), e24 = make_float2(k.e24[t0], k.e24[t1]);
+    const float2 s2 = __fmul2_rn(sg, y);
+    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2), s12 = __fmul2_rn(s6, s6);
+    const float2 ey = __fmul2_rn(e24, y);
+    const float2 g = __fmul2_rn(ey, __ffma2_rn(two, s12, make_float2(-s6.x, -s6.y)));        // 24 eps (2 s12 - s6) / r^2
+    const float2 gp = __fmul2_rn(__fmul2_rn(ey, y),
+                                 __ffma2_rn(make_float2(-28.f, -28.f), s12, __fmul2_rn(make_float2(8.f, 8.f), s6)));
+    const float2 fw = make_float2(f0 ? 1.f : 0.f, f1 ? 1.f : 0.f), rv = make_float2(b0 ? 1.f : 0.f, b1 ? 1.f : 0.f);
+    const float2 dak = __ffma2_rn(dx, akx, __ffma2_rn(dy, aky, __fmul2_rn(dz, akz)));
+    const float2 ajx = make_float2(a0.x, a1.x), ajy = make_float2(a0.y, a1.y), ajz = make_float2(a0.z, a1.z);
+    const float2 daj = __ffma2_rn(dx, ajx, __ffma2_rn(dy, ajy, __fmul2_rn(dz, ajz)));
+    const float2 gf = __fmul2_rn(g, fw), gr = __fmul2_rn(g, rv);
+    // coefficient of d: g'/r (fwd d.A_k - rev d.A_j) + (fwd + rev) dLdE/2 g
+    const float2 cd = __ffma2_rn(gp, __ffma2_rn(fw, dak, __fmul2_rn(make_float2(-rv.x, -rv.y), daj)),
+                                 __fmul2_rn(__fadd2_rn(fw, rv), __fmul2_rn(make_float2(half_dlde, half_dlde), g)));
+    c.gx = __fadd2_rn(c.gx, __ffma2_rn(cd, dx, __ffma2_rn(gf, akx, __fmul2_rn(make_float2(-gr.x, -gr.y), ajx))));
+    c.gy = __fadd2_rn(c.gy, __ffma2_rn(cd, dy, __ffma2_rn(gf, aky, __fmul2_rn(make_float2(-gr.x, -gr.y), ajy))));
+    c.gz = __fadd2_rn(c.gz, __ffma2_rn(cd, dz, __ffma2_rn(gf, akz, __fmul2_rn(make_float2(-gr.x, -gr.y), ajz))));
+    // parameter sums of the forward pairs, by partner type
+    const float2 rfa = __fmul2_rn(__fmul2_rn(y, make_float2(-dak.x, -dak.y)), make_float2(24.f, 24.f));  // 24 y (r.A_k)
+    const float2 ue = __fadd2_rn(s12, make_float2(-s6.x, -s6.y));                                      // s12 - s6
+    const float2 us = __ffma2_rn(make_float2(12.f, 12.f), s12, __fmul2_rn(make_float2(-6.f, -6.f), s6));
+    const float2 cu = make_float2(k.cu[t0], k.cu[t1]), cdd = make_float2(k.cd[t0], k.cd[t1]);
+    const float2 hd = make_float2(hd2, hd2);
+    const float2 te = __fmul2_rn(fw, __ffma2_rn(rfa, __ffma2_rn(two, s12, make_float2(-s6.x, -s6.y)),
+                                                __fmul2_rn(hd, __fadd2_rn(ue, make_float2(-cu.x, -cu.y)))));
+    const float2 u24 = __ffma2_rn(make_float2(24.f, 24.f), s12, __fmul2_rn(make_float2(-6.f, -6.f), s6));
+    const float2 ts = __fmul2_rn(fw, __ffma2_rn(rfa, u24, __fmul2_rn(hd, __fadd2_rn(us, make_float2(-cdd.x, -cdd.y)))));
+    // slot a of the packed pair belongs to partner type t_a
+    c.de[0] = __fadd2_rn(c.de[0], make_float2(t0 ? 0.f : te.x, t1 ? 0.f : te.y));
+    c.de[1] = __fadd2_rn(c.de[1], make_float2(t0 ? te.x : 0.f, t1 ? te.y : 0.f));
+    c.ds[0] = __fadd2_rn(c.ds[0], make_float2(t0 ? 0.f : ts.x, t1 ? 0.f : ts.y));
+    c.ds[1] = __fadd2_rn(c.ds[1], make_float2(t0 ? ts.x : 0.f, t1 ? ts.y : 0.f));
+  }
+}
+
+constexpr int kAdjX2Block = 64;
+
+__global__ void __launch_bounds__(kAdjX2Block) k_adjoint_x2(int64_t n, const float4* __restrict__ pos,
+                                                            const float* __restrict__ rc,
+                                                            const int32_t* __restrict__ start, ForceArgs<float> a,
+                                                            const float4* __restrict__ A, float half_dlde,
+                                                            float4* __restrict__ G, double* __restrict__ part,
+                                                            int64_t nwarp, BlockGrid bg,
+                                                            const int32_t* __restrict__ bmax) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nt = a.ntypes;
+  AdjAcc2 c;
+  int tk = 0;
+  if (i < n) {
+    const float4 pi = __ldg(pos + i);
+    const float4 ak = __ldg(A + i);
+    const float rck = clamp_cutoff<float>(__ldg(rc + i), a.rc_max), rck2 = rck * rck;
+    const float reach = reverse_reach<float>(pi, rck, a.rc_max, bg, bmax);
+    const float reach2s = reach * reach * 1.000004f;
+    tk = type_of(pi.w, nt);
+    AdjRow k;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int tc = t < nt ? t : nt - 1, p = tk * nt + tc;
+      k.sg[t] = a.sig2[p];
+      k.e24[t] = a.eps24[p];
+      k.cu[t] = k.cd[t] = 0.f;
+      if (a.shift && rck2 > 0.f) {
+        const float c2 = a.sig2[p] / rck2, c6 = c2 * c2 * c2, c12 = c6 * c6;
+        k.cu[t] = c12 - c6;
+        k.cd[t] = 12.f * c12 - 6.f * c6;
+      }
+    }
+    adj_walk<float>(start, a.g, pi, reach2s, reach, (int)i,
+                    [&](int lo, int hi, int self, float xi, float yi, float zi, float shx, float shy, float shz) {
+                      if (shx == 0.f && shy == 0.f && shz == 0.f)
+                        adj_range_x2<false>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak,
+                                            half_dlde, k, c);
+                      else
+                        adj_range_x2<true>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak,
+                                           half_dlde, k, c);
+                    });
+    G[i] = make_float4(c.gx.x + c.gx.y, c.gy.x + c.gy.y, c.gz.x + c.gz.y, 0.f);
+  }
+  if (part) {
+    const int64_t w = i >> 5;
+    for (int p = 0; p < nt * nt; ++p) {
+      const bool mine = i < n && tk == p / nt, t1 = p % nt == 1;
+      const float2 de2 = t1 ? c.de[1] : c.de[0], ds2 = t1 ? c.ds[1] : c.ds[0];
+      float de = mine ? de2.x + de2.y : 0.f, ds = mine ? ds2.x + ds2.y : 0.f;
+      for (int o = 16; o > 0; o >>= 1) {
+        de += __shfl_xor_sync(0xffffffffu, de, o);
+        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        const double f = 0.25 * (double)a.eps4[p] / sqrt((double)a.sig2[p]);  // eps_p / sigma_p
         part[(int64_t)p * nwarp + w] = (double)de;
         part[(int64_t)(16 + p) * nwarp + w] = (double)ds * f;
       }
@@ -313,9 +494,21 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   }
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->blk_max, 0, sizeof(int32_t) * ctx->nblk, st));
   DCM_LAUNCH(ctx, k_block_max<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, pos, rc, a.rc_max, bg, ctx->blk_max);
-  auto kern = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
-  DCM_LAUNCH(ctx, kern, (unsigned)nblk, kBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
-             nwarp, bg, (const int32_t*)ctx->blk_max);
+  bool packed = false;
+  if constexpr (sizeof(R) == 4) {
+    if (nt <= 2) {  // the packed loop (FP32, one or two types)
+      const int64_t nb2 = (n + kAdjX2Block - 1) / kAdjX2Block;
+      static_assert(kAdjX2Block == adj_block<float>(), "the partials layout assumes equal blocks");
+      DCM_LAUNCH(ctx, k_adjoint_x2, (unsigned)nb2, kAdjX2Block, 0, st, n, pos, rc, cell_start, a, A,
+                 (float)(0.5 * dlde), G, part, nwarp, bg, (const int32_t*)ctx->blk_max);
+      packed = true;
+    }
+  }
+  if (!packed) {
+    auto kern = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
+    DCM_LAUNCH(ctx, kern, (unsigned)nblk, kBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
+               nwarp, bg, (const int32_t*)ctx->blk_max);
+  }
   int r = check_launch(ctx, "lj_adjoint");
   if (r || !want) return r;
   int npair = nt * nt;
