@@ -292,7 +292,7 @@ def run_reference(args):
 
 def run_batch(args, D, dev):
     """64 independent replicas (N log-uniform in [2K, 200K]) stepped together:
-    autotuned cell edges and launch plan (persistent, one cooperative launch
+    autotuned cell edges and launch plan (persistent, two cooperative launches
     per timestep with a (replica, tile) force queue, or one launch per stage),
     one CUDA graph per recomputation period, args.batch_steps timesteps timed.
     Beside it, on the same replicas: the plain FP64 form (FP64 arrays and

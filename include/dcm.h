@@ -369,7 +369,7 @@ int dcm_step(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int32_t nsteps, 
 int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* iface, void* D, int32_t* iters,
                          dcm_stream_t stream);
 
-/* ---- batched form: many independent systems, one launch per timestep ---- */
+/* ---- batched form: many independent systems, two launches per timestep ---- */
 
 /* R independent replicas (the batching form) that share every
  * parameter in *p except the box and the particle count: replica r has box
@@ -378,10 +378,11 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
  * dcm_state are the concatenation of the replicas: replica r owns slots
  * [offset[r], offset[r+1]) (dcm_batch_offsets) and its particles stay there;
  * thermo is double[4 R] = {E, W, KE, pairs} per replica.  By default a whole
- * timestep of all replicas is ONE persistent cooperative launch (the
- * persistent plan): its stages are separated by grid-wide barriers, and the
- * force stage pulls (replica, tile) work items of 32 particles from a device
- * queue (Section 2.4's dynamic tasks).  dcm_batch_set_persistent(b, 0)
+ * timestep of all replicas is two persistent cooperative launches (the
+ * persistent plan): binning and recomputation, then forces, kick and thermo;
+ * the stages inside each are separated by grid-wide barriers, and the force
+ * stage pulls (replica, tile) work items of 32 particles from a device queue
+ * (Section 2.4's dynamic tasks).  dcm_batch_set_persistent(b, 0)
  * selects the per-stage plan instead (each stage one launch over all
  * replicas).  Per-replica boxes, grids, thresholds and reductions are read
  * from a device table in both plans.  The batched form steps over
@@ -414,7 +415,7 @@ int dcm_batch_step(dcm_batch* b, dcm_state* st, double dt, int32_t nsteps, dcm_s
  * multiple of K.  The graph is bound to st's buffers.  Nothing is executed. */
 int dcm_batch_capture(dcm_batch* b, dcm_state* st, double dt, dcm_stream_t stream);
 
-/* 1 (default): the persistent plan, one cooperative launch per timestep;
+/* 1 (default): the persistent plan, two cooperative launches per timestep;
  * 0: the per-stage plan.  Both give the same results (bit for bit, except
  * for the order of floating-point atomics, which neither plan uses).
  * Invalidates a captured graph. */

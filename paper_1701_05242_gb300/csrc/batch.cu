@@ -1,9 +1,9 @@
 // Batched form: R independent systems (replicas) of different sizes stepped
 // together.  Two launch plans share the per-element device code of
 // batch_core.cuh:
-//   - the persistent plan (default): one cooperative launch per timestep that
-//     runs every stage, with bounded grid-wide barriers between them and the
-//     force stage pulling (replica, tile) work items from a device queue
+//   - the persistent plan (default): two cooperative launches per timestep
+//     that run every stage, with bounded grid-wide barriers between them and
+//     the force stage pulling (replica, tile) work items from a device queue
 //     (batch_persist.cu);
 //   - the per-stage plan: each stage one launch over the concatenation of all
 //     replicas (this file).

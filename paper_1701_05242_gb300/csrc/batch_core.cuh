@@ -1,6 +1,6 @@
 // Batched form: shared declarations and the per-element device code of its
 // stages, used both by the per-stage kernels (batch.cu) and by the persistent
-// one-launch-per-timestep kernel (batch_persist.cu).
+// kernel (batch_persist.cu, two launches per timestep).
 //
 // Layout: the replicas' particles are concatenated (replica r owns sorted
 // slots [p0_r, p1_r)), their force cells are concatenated (replica r's cells
@@ -57,7 +57,7 @@ struct dcm_batch {
   int graph_steps;
   int64_t graph_launches;  // kernels per replay
   void* graph_key[8];
-  // persistent form (one cooperative launch per timestep)
+  // persistent form (two cooperative launches per timestep)
   int persistent;          // 1: dcm_batch_step runs the persistent kernel (default)
   int2* tiles;             // [ntiles]: (replica, first particle) of each work item of the force phase
   int32_t ntiles;

@@ -1,6 +1,12 @@
-// Batched form, persistent plan: one cooperative launch per timestep runs
+// Batched form, persistent plan: two cooperative launches per timestep run
 // every stage of the step for all replicas (Fig. 3's boxes 1-5 inside
-// velocity Verlet), with grid-wide barriers between the stages.
+// velocity Verlet), with grid-wide barriers between the stages: part 0 the
+// half kick, drift, binning and (every K steps) interface, distances and
+// cutoffs; part 1 the forces, the second half kick and the per-replica
+// thermo.  The split lets part 1 read the positions, cutoffs and cell starts
+// that part 0 wrote through the read-only data path (legal only for data no
+// thread of the same launch writes); reading them with coherent loads inside
+// one launch made the force stage twice as slow.
 //
 // The grid holds exactly as many blocks as can be resident at once (a
 // cooperative launch, which the driver refuses rather than oversubscribe), so
@@ -61,6 +67,7 @@ struct PArgs {
   // integration
   R hdt, dt;
   int drift, kick, recompute;
+  int part;              // 0: clear, drift, binning, recomputation; 1: forces, kick, thermo
   // recomputation of interface, distances and cutoffs
   int64_t nbox;
   int32_t* box_count;
@@ -208,115 +215,120 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
 #define PSTAGE(stage) stage_mark(a.pacc, stage)
 
   PSTAGE(-1);
-  // ---- clear the counters of this step
-  for (int64_t c = gt; c < a.ncell; c += gs) a.count[c] = 0;
-  if (a.recompute) {
-    if (a.own_boxes)
-      for (int64_t k = gt; k < a.nbox; k += gs) a.box_count[k] = 0;
-    for (int64_t k = gt; k < (int64_t)a.nrep * kBatchHistBins; k += gs) a.hist[k] = 0;
-    for (int64_t k = gt; k < a.sweeps + 2; k += gs) a.flags[k] = 0;
-    for (int64_t r = gt; r < a.nrep; r += gs) b_thr_init((int)r, a.thr, a.fixed_thr);
-  }
-  if (gt == 0) a.sync[3] = 0;
-  PSYNC();
-  // ---- half kick, drift, cell counts
-  for (int64_t i = gt; i < a.n; i += gs)
-    b_kick_drift_count<R>(i, a.pos_c, a.vel_c, a.force, a.hdt, a.dt, a.l, a.il, a.lx, a.ilx, a.geom, a.rep_p,
-                          a.cell, a.slot, a.count, a.drift);
-  PSYNC();
-  PSTAGE(DCM_STAGE_KICK_DRIFT);
-  // ---- exclusive scan of the cell counts: each block owns one chunk
-  const int64_t chunk = (a.ncell + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = min((int64_t)blockIdx.x * chunk, a.ncell), hi = min(lo + chunk, a.ncell);
-  {
-    int part = 0;
-    for (int64_t c = lo + threadIdx.x; c < hi; c += blockDim.x) part += a.count[c];
-    part = block_sum_int(part);
-    if (threadIdx.x == 0) a.scan_blk[blockIdx.x] = part;
-  }
-  PSYNC();
-  {
-    int off = 0;
-    for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) off += a.scan_blk[k];
-    int run = block_sum_int(off);
-    for (int64_t c0 = lo; c0 < hi; c0 += blockDim.x) {
-      const int64_t c = c0 + threadIdx.x;
-      const int v = c < hi ? a.count[c] : 0;
-      int tot;
-      const int ex = block_scan_excl(v, &tot);
-      if (c < hi) a.start[c] = run + ex;
-      run += tot;
+  if (a.part == 0) {
+    // ---- clear the counters of this step
+    for (int64_t c = gt; c < a.ncell; c += gs) a.count[c] = 0;
+    if (a.recompute) {
+      if (a.own_boxes)
+        for (int64_t k = gt; k < a.nbox; k += gs) a.box_count[k] = 0;
+      for (int64_t k = gt; k < (int64_t)a.nrep * kBatchHistBins; k += gs) a.hist[k] = 0;
+      for (int64_t k = gt; k < a.sweeps + 2; k += gs) a.flags[k] = 0;
+      for (int64_t r = gt; r < a.nrep; r += gs) b_thr_init((int)r, a.thr, a.fixed_thr);
     }
-    if (hi == a.ncell && threadIdx.x == 0) a.start[a.ncell] = run;
-  }
-  PSYNC();
-  // ---- stable counting sort: scatter, then order each cell by input index
-  for (int64_t i = gt; i < a.n; i += gs) a.perm[a.start[a.cell[i]] + a.slot[i]] = (int32_t)i;
-  PSYNC();
-  for (int64_t c = gt; c < a.ncell; c += gs) b_sort_cell(a.start[c], a.start[c + 1], a.perm);
-  PSYNC();
-  for (int64_t k = gt; k < a.n; k += gs)
-    b_gather<R>(k, a.perm, a.pos_c, a.pos_o, a.vel_c, a.vel_o, a.rc_c, a.rc_o, a.id_c, a.id_o);
-  PSYNC();
-  PSTAGE(DCM_STAGE_BIN);
-  // ---- every K steps: interface, distances, cutoffs (Sections 2.1, 2.2)
-  if (a.recompute) {
-    const int32_t* counts = a.count;
-    if (a.own_boxes) {
-      for (int64_t i = gt; i < a.n; i += gs) b_box_count<R>(i, a.pos_o, a.h, a.ih, a.geom, a.rep_p, a.box_count);
-      counts = a.box_count;
-      PSYNC();
-    }
-    for (int64_t k = gt; k < a.nbox; k += gs) b_box_sum<0>(k, counts, a.g, a.geom, a.rep_b, a.w);
+    if (gt == 0) a.sync[3] = 0;
     PSYNC();
-    for (int64_t k = gt; k < a.nbox; k += gs) b_box_sum<1>(k, a.g, a.g_tmp, a.geom, a.rep_b, a.w);
-    PSYNC();
-    for (int64_t k = gt; k < a.nbox; k += gs) b_box_sum<2>(k, a.g_tmp, a.g, a.geom, a.rep_b, a.w);
-    PSYNC();
-    if (a.fixed_thr < 0) {
-      for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < a.nbox; k0 += gs)
-        b_minmax(k0 + threadIdx.x, a.g, a.nbox, a.rep_b, a.thr);
-      PSYNC();
-      for (int64_t k = gt; k < a.nbox; k += gs) b_value_hist(k, a.g, a.rep_b, a.thr, a.hist, a.status);
-      PSYNC();
-      for (int r = blockIdx.x; r < a.nrep; r += gridDim.x) b_two_means(r, a.hist, a.thr, 64);
-      PSYNC();
-    }
-    for (int64_t k = gt; k < a.nbox; k += gs) b_segment(k, a.g, a.geom, a.rep_b, a.thr, a.s, a.iface);
-    PSYNC();
-    PSTAGE(DCM_STAGE_DETECT);
-    for (int64_t k = gt; k < a.nbox; k += gs) b_dist_init<R>(k, a.s, a.iface, a.D0, a.D1);
-    PSYNC();
-    // Jacobi sweeps until one changes nothing (both buffers then agree) or
-    // the even budget ends (the last iterate is then in D0)
-    for (int it = 0; it < a.sweeps; ++it) {
-      if (it > 0 && ((volatile int32_t*)a.flags)[it - 1] == 0) break;
-      const R* Din = (it & 1) ? a.D1 : a.D0;
-      R* Dout = (it & 1) ? a.D0 : a.D1;
-      bool changed = false;
-      for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < a.nbox; k0 += gs) {
-        const int64_t k = k0 + threadIdx.x;
-        if (k < a.nbox) changed |= b_dist_update<R>(k, Din, Dout, a.geom, a.rep_b, a.h, a.r_grid);
-      }
-      if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) a.flags[it] = 1;
-      PSYNC();
-    }
-    if (gt == 0) {
-      int first = -1;
-      for (int k = 0; k < a.sweeps; ++k)
-        if (a.flags[k] == 0) {
-          first = k;
-          break;
-        }
-      if (first < 0) raise_status(a.status, DCM_ERR_NOT_CONVERGED);
-    }
-    PSTAGE(DCM_STAGE_DISTANCE);
+    // ---- half kick, drift, cell counts
     for (int64_t i = gt; i < a.n; i += gs)
-      b_cutoffs<R, false>(i, a.pos_o, a.D0, a.geom, a.rep_p, a.h, a.r_grid, a.rc_min, a.rc_max, a.ramp, a.rc_o);
+      b_kick_drift_count<R>(i, a.pos_c, a.vel_c, a.force, a.hdt, a.dt, a.l, a.il, a.lx, a.ilx, a.geom, a.rep_p,
+                            a.cell, a.slot, a.count, a.drift);
     PSYNC();
-    PSTAGE(DCM_STAGE_CUTOFFS);
+    PSTAGE(DCM_STAGE_KICK_DRIFT);
+    // ---- exclusive scan of the cell counts: each block owns one chunk
+    const int64_t chunk = (a.ncell + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = min((int64_t)blockIdx.x * chunk, a.ncell), hi = min(lo + chunk, a.ncell);
+    {
+      int part = 0;
+      for (int64_t c = lo + threadIdx.x; c < hi; c += blockDim.x) part += a.count[c];
+      part = block_sum_int(part);
+      if (threadIdx.x == 0) a.scan_blk[blockIdx.x] = part;
+    }
+    PSYNC();
+    {
+      int off = 0;
+      for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) off += a.scan_blk[k];
+      int run = block_sum_int(off);
+      for (int64_t c0 = lo; c0 < hi; c0 += blockDim.x) {
+        const int64_t c = c0 + threadIdx.x;
+        const int v = c < hi ? a.count[c] : 0;
+        int tot;
+        const int ex = block_scan_excl(v, &tot);
+        if (c < hi) a.start[c] = run + ex;
+        run += tot;
+      }
+      if (hi == a.ncell && threadIdx.x == 0) a.start[a.ncell] = run;
+    }
+    PSYNC();
+    // ---- stable counting sort: scatter, then order each cell by input index
+    for (int64_t i = gt; i < a.n; i += gs) a.perm[a.start[a.cell[i]] + a.slot[i]] = (int32_t)i;
+    PSYNC();
+    for (int64_t c = gt; c < a.ncell; c += gs) b_sort_cell(a.start[c], a.start[c + 1], a.perm);
+    PSYNC();
+    for (int64_t k = gt; k < a.n; k += gs)
+      b_gather<R>(k, a.perm, a.pos_c, a.pos_o, a.vel_c, a.vel_o, a.rc_c, a.rc_o, a.id_c, a.id_o);
+    PSYNC();
+    PSTAGE(DCM_STAGE_BIN);
+    // ---- every K steps: interface, distances, cutoffs (Sections 2.1, 2.2)
+    if (a.recompute) {
+      const int32_t* counts = a.count;
+      if (a.own_boxes) {
+        for (int64_t i = gt; i < a.n; i += gs) b_box_count<R>(i, a.pos_o, a.h, a.ih, a.geom, a.rep_p, a.box_count);
+        counts = a.box_count;
+        PSYNC();
+      }
+      for (int64_t k = gt; k < a.nbox; k += gs) b_box_sum<0>(k, counts, a.g, a.geom, a.rep_b, a.w);
+      PSYNC();
+      for (int64_t k = gt; k < a.nbox; k += gs) b_box_sum<1>(k, a.g, a.g_tmp, a.geom, a.rep_b, a.w);
+      PSYNC();
+      for (int64_t k = gt; k < a.nbox; k += gs) b_box_sum<2>(k, a.g_tmp, a.g, a.geom, a.rep_b, a.w);
+      PSYNC();
+      if (a.fixed_thr < 0) {
+        for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < a.nbox; k0 += gs)
+          b_minmax(k0 + threadIdx.x, a.g, a.nbox, a.rep_b, a.thr);
+        PSYNC();
+        for (int64_t k = gt; k < a.nbox; k += gs) b_value_hist(k, a.g, a.rep_b, a.thr, a.hist, a.status);
+        PSYNC();
+        for (int r = blockIdx.x; r < a.nrep; r += gridDim.x) b_two_means(r, a.hist, a.thr, 64);
+        PSYNC();
+      }
+      for (int64_t k = gt; k < a.nbox; k += gs) b_segment(k, a.g, a.geom, a.rep_b, a.thr, a.s, a.iface);
+      PSYNC();
+      PSTAGE(DCM_STAGE_DETECT);
+      for (int64_t k = gt; k < a.nbox; k += gs) b_dist_init<R>(k, a.s, a.iface, a.D0, a.D1);
+      PSYNC();
+      // Jacobi sweeps until one changes nothing (both buffers then agree) or
+      // the even budget ends (the last iterate is then in D0)
+      for (int it = 0; it < a.sweeps; ++it) {
+        if (it > 0 && ((volatile int32_t*)a.flags)[it - 1] == 0) break;
+        const R* Din = (it & 1) ? a.D1 : a.D0;
+        R* Dout = (it & 1) ? a.D0 : a.D1;
+        bool changed = false;
+        for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < a.nbox; k0 += gs) {
+          const int64_t k = k0 + threadIdx.x;
+          if (k < a.nbox) changed |= b_dist_update<R>(k, Din, Dout, a.geom, a.rep_b, a.h, a.r_grid);
+        }
+        if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) a.flags[it] = 1;
+        PSYNC();
+      }
+      if (gt == 0) {
+        int first = -1;
+        for (int k = 0; k < a.sweeps; ++k)
+          if (a.flags[k] == 0) {
+            first = k;
+            break;
+          }
+        if (first < 0) raise_status(a.status, DCM_ERR_NOT_CONVERGED);
+      }
+      PSTAGE(DCM_STAGE_DISTANCE);
+      for (int64_t i = gt; i < a.n; i += gs)
+        b_cutoffs<R, false>(i, a.pos_o, a.D0, a.geom, a.rep_p, a.h, a.r_grid, a.rc_min, a.rc_max, a.ramp, a.rc_o);
+      PSYNC();
+      PSTAGE(DCM_STAGE_CUTOFFS);
+    }
+    return;
   }
-  // ---- forces over the (replica, tile) queue (Section 2.4, Alg. 2.3)
+  // ---- part 1: forces over the (replica, tile) queue (Section 2.4, Alg. 2.3).
+  // Positions, cutoffs and cell starts were written by part 0, an earlier
+  // launch, so they are read through the read-only path here.
   {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -327,7 +339,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
       const int2 item = a.tiles[t];
       const int64_t end = min((int64_t)item.y + a.tile, a.geom[item.x].p1);
       for (int64_t i = (int64_t)item.y + lane; i < end; i += 32)
-        b_force<R, TYPED, X2, M, false>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i, a.np_i);
+        b_force<R, TYPED, X2, M, true>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i, a.np_i);
     }
   }
   PSYNC();
@@ -367,8 +379,6 @@ int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
     return set_error(&b->base, DCM_ERR_CUDA, "persistent step: occupancy query failed");
   const int grid = std::min(per_sm, kPMaxBlocksPerSM) * sms;
   if (grid > b->pgrid) return set_error(&b->base, DCM_ERR_CAPACITY, "persistent grid %d exceeds its scratch", grid);
-  if (cudaMemsetAsync(b->sync, 0, 4 * sizeof(uint32_t), st) != cudaSuccess)
-    return set_error(&b->base, DCM_ERR_CUDA, "persistent step: memset failed");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kPBlock);
@@ -379,9 +389,17 @@ int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  ++b->base.launches;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
-  if (e != cudaSuccess) return set_error(&b->base, DCM_ERR_CUDA, "persistent step: %s", cudaGetErrorString(e));
+  // part 0 (binning, recomputation), then part 1 (forces, kick, thermo); the
+  // barrier words start cleared in each
+  for (int part = 0; part < 2; ++part) {
+    if (cudaMemsetAsync(b->sync, 0, 4 * sizeof(uint32_t), st) != cudaSuccess)
+      return set_error(&b->base, DCM_ERR_CUDA, "persistent step: memset failed");
+    PArgs<R> ap = a;
+    ap.part = part;
+    ++b->base.launches;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ap);
+    if (e != cudaSuccess) return set_error(&b->base, DCM_ERR_CUDA, "persistent step: %s", cudaGetErrorString(e));
+  }
   return DCM_OK;
 }
 

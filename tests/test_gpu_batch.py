@@ -1,4 +1,4 @@
-"""Batched form: independent replicas stepped together, one persistent launch
+"""Batched form: independent replicas stepped together, two persistent launches
 per timestep by default (or one launch per stage).
 
 Each replica of a batch must evolve exactly as the same system stepped alone
@@ -203,7 +203,7 @@ def test_persistent_plan_equals_per_stage_plan(D, replicas, prec, lx):
     as one launch per stage: positions, velocities, cutoffs, ids and forces
     bit for bit (the same per-element code, the binning's order fixed by the
     stable sort), per-replica totals to rounding (their block sums differ in
-    width).  The persistent plan launches exactly one kernel per timestep."""
+    width).  The persistent plan launches exactly two kernels per timestep."""
     P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
     nsteps = 2 * K + 3   # two recomputations, an odd step count (buffers end on the other side)
     a, tha, la, _ = _run_plan(D, replicas, P, True, nsteps, lx)
@@ -211,7 +211,7 @@ def test_persistent_plan_equals_per_stage_plan(D, replicas, prec, lx):
     for x, y in zip(a, s):
         assert np.array_equal(x, y)
     assert np.allclose(tha, ths, rtol=1e-12, atol=1e-9)
-    assert la == nsteps
+    assert la == 2 * nsteps
     assert ls > 10 * nsteps
 
 
@@ -250,7 +250,7 @@ def test_persistent_plan_two_types_and_accumulation_forms(D):
 
 
 def test_persistent_plan_graph_replay(D, replicas):
-    """The persistent step captured in a CUDA graph (one kernel per timestep
+    """The persistent step captured in a CUDA graph (two kernels per timestep
     in the graph) replays the trajectory of direct stepping bit for bit."""
     P = D.DCM_PREC_MIXED
     b1, s1 = batch_state(D, replicas, P)
@@ -265,7 +265,7 @@ def test_persistent_plan_graph_replay(D, replicas):
     D.dcm_batch_launch_count(b2, reset=True)
     D.dcm_batch_replay(b2, s2, (2 * K) // per, stream)
     stream.synchronize()
-    assert D.dcm_batch_launch_count(b2) == 2 * K
+    assert D.dcm_batch_launch_count(b2) == 4 * K
     assert torch.equal(s1.current()[0], s2.current()[0])
     assert torch.equal(s1.thermo, s2.thermo)
     assert D.dcm_batch_status(b2) == D.DCM_OK
