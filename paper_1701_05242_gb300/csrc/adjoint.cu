@@ -185,6 +185,78 @@ __device__ __forceinline__ void adj_walk(const int32_t* __restrict__ start, cons
   }
 }
 
+// The same walk split in two for the packed adjoint: in every row the cells
+// within the particle's own cutoff rk (the inner window: forward and reverse
+// pairs) go to full(lo, hi, self, xi, yi, zi, shx, shy, shz) and the rest of
+// the window of radius `reach` (the shell: only pairs with rc_j > r >= rk,
+// rare away from the interfaces) to shell(...).  Pieces are split at the
+// periodic x boundary as in adj_walk.
+template <typename R, typename F, typename S>
+__device__ __forceinline__ void adj_walk2(const int32_t* __restrict__ start, const Grid<R>& g,
+                                          const typename RT<R>::R4& pi, R rk, R reach, int self, F&& full,
+                                          S&& shell) {
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const R l = g.edge, il = g.inv_edge, ilx = g.inv_edge_x;
+  const R reach2s = reach * reach * (R)1.000004, rk2s = rk * rk * (R)1.000004;
+  const int cx = cell_coord<R>(pi.x, g.edge_x, ilx, nx);
+  const int cy = cell_coord<R>(pi.y, l, il, ny);
+  const int cz = cell_coord<R>(pi.z, l, il, nz);
+  const int H = (int)ceil(reach * il), Hx = (int)ceil(reach * ilx);
+  for (int uz = cz - H; uz <= cz + H; ++uz) {
+    R gz = uz > cz ? (R)uz * l - pi.z : (uz < cz ? pi.z - (R)(uz + 1) * l : (R)0);
+    R gz2 = gz * gz;
+    if (gz2 >= reach2s) continue;
+    int wz = uz < 0 ? uz + nz : (uz >= nz ? uz - nz : uz);
+    R zi = uz >= nz ? pi.z - g.L[2] : pi.z;
+    R zsh = uz < 0 ? -g.L[2] : (R)0;
+    for (int uy = cy - H; uy <= cy + H; ++uy) {
+      R gy = uy > cy ? (R)uy * l - pi.y : (uy < cy ? pi.y - (R)(uy + 1) * l : (R)0);
+      R gyz2 = gz2 + gy * gy;
+      if (gyz2 >= reach2s) continue;
+      int wy = uy < 0 ? uy + ny : (uy >= ny ? uy - ny : uy);
+      R yi = uy >= ny ? pi.y - g.L[1] : pi.y;
+      R ysh = uy < 0 ? -g.L[1] : (R)0;
+      R wx = sqrt(reach2s - gyz2);
+      int ulo = max(ufloor<R>((pi.x - wx) * ilx - (R)5e-4), cx - Hx);
+      int uhi = min(ufloor<R>((pi.x + wx) * ilx + (R)5e-4), cx + Hx);
+      if (ulo > uhi) continue;  // a coordinate outside [0, L): no window
+      int ilo = uhi + 1, ihi = uhi;  // inner window (empty unless the row meets the rk sphere)
+      if (gyz2 < rk2s) {
+        R wi = sqrt(rk2s - gyz2);
+        ilo = min(max(ufloor<R>((pi.x - wi) * ilx - (R)5e-4), ulo), uhi + 1);
+        ihi = max(min(ufloor<R>((pi.x + wi) * ilx + (R)5e-4), uhi), ilo - 1);
+      }
+      const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
+      const bool same = ysh == (R)0 && zsh == (R)0;
+      // cells [u0, u1] of the unwrapped row, split at the x boundary
+      auto emit = [&](int u0, int u1, bool inner) {
+        if (u0 > u1) return;
+        if (u0 < 0) {
+          const int a1 = min(u1, -1);
+          const int j0 = __ldg(start + row + u0 + nx), j1 = __ldg(start + row + a1 + nx + 1);
+          if (inner) full(j0, j1, -1, pi.x, yi, zi, -g.L[0], ysh, zsh);
+          else shell(j0, j1, -1, pi.x, yi, zi, -g.L[0], ysh, zsh);
+        }
+        const int a0 = max(u0, 0), a1 = min(u1, nx - 1);
+        if (a0 <= a1) {
+          const int j0 = __ldg(start + row + a0), j1 = __ldg(start + row + a1 + 1);
+          if (inner) full(j0, j1, same ? self : -1, pi.x, yi, zi, (R)0, ysh, zsh);
+          else shell(j0, j1, same ? self : -1, pi.x, yi, zi, (R)0, ysh, zsh);
+        }
+        if (u1 >= nx) {
+          const int b0 = max(u0, nx);
+          const int j0 = __ldg(start + row + b0 - nx), j1 = __ldg(start + row + u1 - nx + 1);
+          if (inner) full(j0, j1, -1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh);
+          else shell(j0, j1, -1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh);
+        }
+      };
+      emit(ulo, ilo - 1, false);
+      emit(ilo, ihi, true);
+      emit(ihi + 1, uhi, false);
+    }
+  }
+}
+
 // Radius of the adjoint walk of particle k: the largest cutoff in the 27
 // blocks around it (every j whose own cutoff reaches k lies in one of them),
 // at least rc_k; rc_max without the block table.
@@ -343,7 +415,8 @@ __device__ __forceinline__ void adj_range_x2(const float4* __restrict__ pos, con
     y = __ffma2_rn(y, e, y);
     y = make_float2(f0 || b0 ? y.x : 0.f, f1 || b1 ? y.y : 0.f);
     const bool t0 = p0.w >= 1.f, t1 = p1.w >= 1.f;
-    const float2 sg = make_float2(k.sg[t0], k.sg[t1]), e24 = make_float2(k.e24[t0], k.e24[t1]);
+    const float2 sg = make_float2(t0 ? k.sg[1] : k.sg[0], t1 ? k.sg[1] : k.sg[0]);
+    const float2 e24 = make_float2(t0 ? k.e24[1] : k.e24[0], t1 ? k.e24[1] : k.e24[0]);
     const float2 s2 = __fmul2_rn(sg, y);
     const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2), s12 = __fmul2_rn(s6, s6);
     const float2 ey = __fmul2_rn(e24, y);
@@ -365,7 +438,8 @@ __device__ __forceinline__ void adj_range_x2(const float4* __restrict__ pos, con
     const float2 rfa = __fmul2_rn(__fmul2_rn(y, make_float2(-dak.x, -dak.y)), make_float2(24.f, 24.f));  // 24 y (r.A_k)
     const float2 ue = __fadd2_rn(s12, make_float2(-s6.x, -s6.y));                                      // s12 - s6
     const float2 us = __ffma2_rn(make_float2(12.f, 12.f), s12, __fmul2_rn(make_float2(-6.f, -6.f), s6));
-    const float2 cu = make_float2(k.cu[t0], k.cu[t1]), cdd = make_float2(k.cd[t0], k.cd[t1]);
+    const float2 cu = make_float2(t0 ? k.cu[1] : k.cu[0], t1 ? k.cu[1] : k.cu[0]);
+    const float2 cdd = make_float2(t0 ? k.cd[1] : k.cd[0], t1 ? k.cd[1] : k.cd[0]);
     const float2 hd = make_float2(hd2, hd2);
     const float2 te = __fmul2_rn(fw, __ffma2_rn(rfa, __ffma2_rn(two, s12, make_float2(-s6.x, -s6.y)),
                                                 __fmul2_rn(hd, __fadd2_rn(ue, make_float2(-cu.x, -cu.y)))));
@@ -376,6 +450,48 @@ __device__ __forceinline__ void adj_range_x2(const float4* __restrict__ pos, con
     c.de[1] = __fadd2_rn(c.de[1], make_float2(t0 ? te.x : 0.f, t1 ? te.y : 0.f));
     c.ds[0] = __fadd2_rn(c.ds[0], make_float2(t0 ? 0.f : ts.x, t1 ? 0.f : ts.y));
     c.ds[1] = __fadd2_rn(c.ds[1], make_float2(t0 ? ts.x : 0.f, t1 ? ts.y : 0.f));
+  }
+}
+
+// Shell candidates of the packed adjoint: r >= rc_k up to cell rounding, so
+// the forward test fails for nearly all of them and the reverse test
+// (r < rc_j) rarely passes; each candidate costs a distance test, and the
+// few pairs that pass either test take the scalar terms of adj_range.
+__device__ __forceinline__ void adj_shell(const float4* __restrict__ pos, const float* __restrict__ rc,
+                                          const float4* __restrict__ A, int lo, int hi, int self, float xi, float yi,
+                                          float zi, float shx, float shy, float shz, float rck2, float rc_max,
+                                          const float4& ak, float half_dlde, const AdjRow& k, AdjAcc2& c) {
+  for (int j = lo; j < hi; ++j) {
+    const float4 pj = __ldg(pos + j);
+    const float dx = (pj.x + shx) - xi, dy = (pj.y + shy) - yi, dz = (pj.z + shz) - zi;  // d = r_j - r_k
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float rcj = clamp_cutoff<float>(__ldg(rc + j), rc_max);
+    const bool fwd = r2 < rck2 && j != self, rev = r2 < rcj * rcj && j != self;
+    if (!(fwd || rev)) continue;
+    const float4 aj = __ldg(A + j);
+    const bool t = pj.w >= 1.f;
+    const float y = recip(r2);
+    const float s2 = (t ? k.sg[1] : k.sg[0]) * y, s6 = s2 * s2 * s2, s12 = s6 * s6;
+    const float ey = (t ? k.e24[1] : k.e24[0]) * y;
+    const float g = ey * fmaf(2.f, s12, -s6), gp = ey * y * fmaf(-28.f, s12, 8.f * s6);
+    const float dak = fmaf(dx, ak.x, fmaf(dy, ak.y, dz * ak.z)), daj = fmaf(dx, aj.x, fmaf(dy, aj.y, dz * aj.z));
+    const float fw = fwd ? 1.f : 0.f, rv = rev ? 1.f : 0.f;
+    const float cd = gp * (fw * dak - rv * daj) + (fw + rv) * half_dlde * g;
+    c.gx.x += cd * dx + fw * g * ak.x - rv * g * aj.x;
+    c.gy.x += cd * dy + fw * g * ak.y - rv * g * aj.y;
+    c.gz.x += cd * dz + fw * g * ak.z - rv * g * aj.z;
+    if (fwd) {
+      const float rfa = 24.f * y * -dak, hd2 = 4.f * half_dlde, us = 12.f * s12 - 6.f * s6;
+      const float te = rfa * fmaf(2.f, s12, -s6) + hd2 * ((s12 - s6) - (t ? k.cu[1] : k.cu[0]));
+      const float ts = rfa * (24.f * s12 - 6.f * s6) + hd2 * (us - (t ? k.cd[1] : k.cd[0]));
+      if (t) {
+        c.de[1].x += te;
+        c.ds[1].x += ts;
+      } else {
+        c.de[0].x += te;
+        c.ds[0].x += ts;
+      }
+    }
   }
 }
 
@@ -397,7 +513,6 @@ __global__ void __launch_bounds__(kAdjX2Block) k_adjoint_x2(int64_t n, const flo
     const float4 ak = __ldg(A + i);
     const float rck = clamp_cutoff<float>(__ldg(rc + i), a.rc_max), rck2 = rck * rck;
     const float reach = reverse_reach<float>(pi, rck, a.rc_max, bg, bmax);
-    const float reach2s = reach * reach * 1.000004f;
     tk = type_of(pi.w, nt);
     AdjRow k;
 #pragma unroll
@@ -412,15 +527,19 @@ __global__ void __launch_bounds__(kAdjX2Block) k_adjoint_x2(int64_t n, const flo
         k.cd[t] = 12.f * c12 - 6.f * c6;
       }
     }
-    adj_walk<float>(start, a.g, pi, reach2s, reach, (int)i,
-                    [&](int lo, int hi, int self, float xi, float yi, float zi, float shx, float shy, float shz) {
-                      if (shx == 0.f && shy == 0.f && shz == 0.f)
-                        adj_range_x2<false>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak,
-                                            half_dlde, k, c);
-                      else
-                        adj_range_x2<true>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak,
-                                           half_dlde, k, c);
-                    });
+    adj_walk2<float>(
+        start, a.g, pi, rck, reach, (int)i,
+        [&](int lo, int hi, int self, float xi, float yi, float zi, float shx, float shy, float shz) {
+          if (shx == 0.f && shy == 0.f && shz == 0.f)
+            adj_range_x2<false>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak, half_dlde,
+                                k, c);
+          else
+            adj_range_x2<true>(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak, half_dlde, k,
+                               c);
+        },
+        [&](int lo, int hi, int self, float xi, float yi, float zi, float shx, float shy, float shz) {
+          adj_shell(pos, rc, A, lo, hi, self, xi, yi, zi, shx, shy, shz, rck2, a.rc_max, ak, half_dlde, k, c);
+        });
     G[i] = make_float4(c.gx.x + c.gx.y, c.gy.x + c.gy.y, c.gz.x + c.gz.y, 0.f);
   }
   if (part) {
