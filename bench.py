@@ -330,6 +330,27 @@ def run_batch(args, D, dev):
     pairs = float(st.thermo.view(-1, 4)[:, 3].sum().item())
     acc = D.ACC_NAMES[D.dcm_batch_accumulation(b)]
     b.close()
+    # stage split of both plans (direct stepping with the stage clocks; the
+    # timed run above is the graph replay, where no clock runs)
+    split = {}
+    for plan, size in (("persistent", best[3] if best[2] == "persistent" else 32),
+                       ("stages", best[3] if best[2] == "stages" else 256)):
+        bp, sp = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_MIXED, K_RECOMPUTE, best[0], best[1])
+        autotune.apply_plan(bp, plan, size)
+        D.dcm_batch_step_init(bp, sp)
+        D.dcm_batch_step(bp, sp, DT, K_RECOMPUTE)
+        D.dcm_batch_set_timing(bp, 8192)
+        D.dcm_batch_stage_times(bp)
+        D.dcm_batch_launch_count(bp, reset=True)
+        e0.record()
+        D.dcm_batch_step(bp, sp, DT, 2 * K_RECOMPUTE)
+        e1.record()
+        e1.synchronize()
+        st_ms = D.dcm_batch_stage_times(bp)
+        split[f"{plan}={size}"] = {"ms_per_timestep": e0.elapsed_time(e1) / (2 * K_RECOMPUTE),
+                                   "launches_per_timestep": D.dcm_batch_launch_count(bp) / (2 * K_RECOMPUTE),
+                                   "stage_ms_per_timestep": {k: v[0] / (2 * K_RECOMPUTE) for k, v in st_ms.items()}}
+        bp.close()
     # the plain FP64 form on the same replicas: per-stage launches, no graph
     b64, s64 = autotune.make_batch(boxes, counts, pos, vel, D.DCM_PREC_FP64, K_RECOMPUTE, 1.5, 0.0)
     D.dcm_batch_set_persistent(b64, False)
@@ -356,6 +377,7 @@ def run_batch(args, D, dev):
            "plain_fp64_form": {"value": value64, "unit": UNIT, "timesteps": n64, "ms_per_timestep": ms64 / n64,
                                "plan": "stages", "cuda_graph": False, "device_status": status64},
            "speedup_over_plain_fp64": value / value64,
+           "plans_direct_stepping": split,
            "device_status": status}
     return out
 

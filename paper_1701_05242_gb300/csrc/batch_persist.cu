@@ -247,12 +247,21 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
       int off = 0;
       for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) off += a.scan_blk[k];
       int run = block_sum_int(off);
-      for (int64_t c0 = lo; c0 < hi; c0 += blockDim.x) {
-        const int64_t c = c0 + threadIdx.x;
-        const int v = c < hi ? a.count[c] : 0;
+      for (int64_t c0 = lo; c0 < hi; c0 += 4 * blockDim.x) {  // four cells per thread
+        const int64_t c = c0 + 4 * threadIdx.x;
+        int v[4], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v[q] = c + q < hi ? a.count[c + q] : 0;
+          sum += v[q];
+        }
         int tot;
-        const int ex = block_scan_excl(v, &tot);
-        if (c < hi) a.start[c] = run + ex;
+        int ex = block_scan_excl(sum, &tot) + run;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (c + q < hi) a.start[c + q] = ex;
+          ex += v[q];
+        }
         run += tot;
       }
       if (hi == a.ncell && threadIdx.x == 0) a.start[a.ncell] = run;
