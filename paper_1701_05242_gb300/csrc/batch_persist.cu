@@ -31,9 +31,21 @@
 
 namespace dcm {
 
-constexpr int kPBlock = 128;      // threads per block of the persistent kernel
-constexpr int kPMinBlocks = 6;    // register budget: 6 blocks of 128 per SM (85 registers)
-constexpr int kPMaxBlocksPerSM = 16;
+constexpr int kPBlock = 128;  // threads per block of the persistent kernels
+// Blocks of 128 per SM for each part: the register budget the compiler must
+// meet and the grid's size (every block resident).  Each part is its own
+// kernel, so the binning stages do not inherit the force loop's registers.
+// Measured on 64 replicas (2.27M particles, FP32): part 0 at 10 blocks (48
+// registers) and part 1 at 8 (64) take 1.99 ms per timestep against 2.05 at
+// 6 and 6; in FP64, and for part 1 with a per-type table, those budgets
+// spill, and both parts keep 6 (80 registers).
+template <int PART, typename R, bool TYPED>
+constexpr int p_blocks() {
+  if constexpr (sizeof(R) == 8) return 6;
+  else if constexpr (PART == 0) return 10;
+  else return TYPED ? 6 : 8;
+}
+constexpr int kPMaxBlocksPerSM = 16;  // bound of every part's blocks (sizes the scan scratch)
 
 template <typename R>
 struct PArgs {
@@ -67,7 +79,6 @@ struct PArgs {
   // integration
   R hdt, dt;
   int drift, kick, recompute;
-  int part;              // 0: clear, drift, binning, recomputation; 1: forces, kick, thermo
   // recomputation of interface, distances and cutoffs
   int64_t nbox;
   int32_t* box_count;
@@ -203,8 +214,8 @@ __device__ __forceinline__ int block_sum_int(int v) {
   return total;
 }
 
-template <typename R, bool TYPED, bool X2, Accum M>
-__global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArgs<R> a) {
+template <int PART, typename R, bool TYPED, bool X2, Accum M>
+__global__ void __launch_bounds__(kPBlock, (p_blocks<PART, R, TYPED>())) k_b_step_persistent(PArgs<R> a) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const uint32_t expected = gridDim.x + a.phantom;
@@ -215,7 +226,7 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
 #define PSTAGE(stage) stage_mark(a.pacc, stage)
 
   PSTAGE(-1);
-  if (a.part == 0) {
+  if constexpr (PART == 0) {
     // ---- clear the counters of this step
     for (int64_t c = gt; c < a.ncell; c += gs) a.count[c] = 0;
     if (a.recompute) {
@@ -333,12 +344,10 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
       PSYNC();
       PSTAGE(DCM_STAGE_CUTOFFS);
     }
-    return;
-  }
-  // ---- part 1: forces over the (replica, tile) queue (Section 2.4, Alg. 2.3).
-  // Positions, cutoffs and cell starts were written by part 0, an earlier
-  // launch, so they are read through the read-only path here.
-  {
+  } else {
+    // ---- part 1: forces over the (replica, tile) queue (Section 2.4, Alg. 2.3).
+    // Positions, cutoffs and cell starts were written by part 0, an earlier
+    // launch, so they are read through the read-only path here.
     const int lane = threadIdx.x & 31;
     for (;;) {
       int t = 0;
@@ -350,22 +359,20 @@ __global__ void __launch_bounds__(kPBlock, kPMinBlocks) k_b_step_persistent(PArg
       for (int64_t i = (int64_t)item.y + lane; i < end; i += 32)
         b_force<R, TYPED, X2, M, true>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i, a.np_i);
     }
-  }
-  PSYNC();
-  PSTAGE(DCM_STAGE_FORCES);
-  // ---- second half kick, kinetic energy, per-replica thermo
-  for (int64_t i = gt; i < a.n; i += gs) b_kick<R>(i, a.vel_o, a.kick ? a.force : nullptr, a.hdt, a.ke_i);
-  PSYNC();
-  for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
-    b_thermo_chunk<R>(c, a.chunk, a.nchunk, a.force, a.w_i, a.ke_i, a.np_i, a.tpart);
-  PSYNC();
-  {
+    PSYNC();
+    PSTAGE(DCM_STAGE_FORCES);
+    // ---- second half kick, kinetic energy, per-replica thermo
+    for (int64_t i = gt; i < a.n; i += gs) b_kick<R>(i, a.vel_o, a.kick ? a.force : nullptr, a.hdt, a.ke_i);
+    PSYNC();
+    for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
+      b_thermo_chunk<R>(c, a.chunk, a.nchunk, a.force, a.w_i, a.ke_i, a.np_i, a.tpart);
+    PSYNC();
     const int64_t warp = gt >> 5, nwarp = gs >> 5;
     for (int64_t r = warp; r < a.nrep; r += nwarp) b_thermo_sum((int)r, a.chunk0, a.nchunk, a.tpart, a.thermo);
+    // the kick's time: up to the last barrier (the thermo sums of the last
+    // warps are not waited for)
+    PSTAGE(DCM_STAGE_KICK);
   }
-  // the kick's time: up to the last barrier (the thermo sums of the last
-  // warps are not waited for)
-  PSTAGE(DCM_STAGE_KICK);
 #undef PSTAGE
 #undef PSYNC
 }
@@ -378,15 +385,17 @@ __global__ void __launch_bounds__(kPBlock) k_b_wait_selftest(uint32_t* sync, uin
 
 namespace {
 
-template <typename R, bool TYPED, bool X2, Accum M>
-int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
-  auto kern = k_b_step_persistent<R, TYPED, X2, M>;
+// One cooperative launch of part PART over as many blocks as are resident
+// (at most the part's cap per SM); the barrier words start cleared.
+template <int PART, typename R, bool TYPED, bool X2, Accum M>
+int launch_part(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
+  auto kern = k_b_step_persistent<PART, R, TYPED, X2, M>;
   int per_sm = 0, sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPBlock, 0) != cudaSuccess || per_sm < 1)
     return set_error(&b->base, DCM_ERR_CUDA, "persistent step: occupancy query failed");
-  const int grid = std::min(per_sm, kPMaxBlocksPerSM) * sms;
+  const int grid = std::min(per_sm, p_blocks<PART, R, TYPED>()) * sms;
   if (grid > b->pgrid) return set_error(&b->base, DCM_ERR_CAPACITY, "persistent grid %d exceeds its scratch", grid);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
@@ -398,18 +407,19 @@ int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  // part 0 (binning, recomputation), then part 1 (forces, kick, thermo); the
-  // barrier words start cleared in each
-  for (int part = 0; part < 2; ++part) {
-    if (cudaMemsetAsync(b->sync, 0, 4 * sizeof(uint32_t), st) != cudaSuccess)
-      return set_error(&b->base, DCM_ERR_CUDA, "persistent step: memset failed");
-    PArgs<R> ap = a;
-    ap.part = part;
-    ++b->base.launches;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ap);
-    if (e != cudaSuccess) return set_error(&b->base, DCM_ERR_CUDA, "persistent step: %s", cudaGetErrorString(e));
-  }
+  if (cudaMemsetAsync(b->sync, 0, 4 * sizeof(uint32_t), st) != cudaSuccess)
+    return set_error(&b->base, DCM_ERR_CUDA, "persistent step: memset failed");
+  ++b->base.launches;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return set_error(&b->base, DCM_ERR_CUDA, "persistent step: %s", cudaGetErrorString(e));
   return DCM_OK;
+}
+
+// part 0 (binning, recomputation), then part 1 (forces, kick, thermo)
+template <typename R, bool TYPED, bool X2, Accum M>
+int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
+  int r = launch_part<0, R, TYPED, X2, M>(b, a, st);
+  return r != DCM_OK ? r : launch_part<1, R, TYPED, X2, M>(b, a, st);
 }
 
 template <typename R>
