@@ -40,6 +40,8 @@ REST_BYTES = 197            # HBM bytes per particle and timestep of every stage
                             # interface/distances/cutoffs 8 (amortised over the cadence)
 LIST_SKIN = 0.5             # Verlet-list skin of the lists form (the fastest measured on the 16M slab)
 FLOP_PER_PAIR = 18          # FP32-pipe instructions of the pair arithmetic per accepted pair
+FLOP_PER_PAIR_FORCES = 15   # ... without the energy (2) and virial (1) terms: the timesteps of a
+                            # dcm_step call before its last, whose energy and virial nothing reads
 FP32_LANES_PER_SM = 128
 ACC_DESCR = {"fp32": "plain FP32 running sums",
              "plane_kahan": "FP32 per z-plane of the stencil, Kahan-compensated across planes",
@@ -510,7 +512,10 @@ def run_gb300(args):
     fmax = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tinstr = sms * FP32_LANES_PER_SM * fmax * 1e6 / 1e12
     f_avg_s = (f_ms / max(f_cnt, 1)) / 1000.0
-    achieved = pairs * FLOP_PER_PAIR / f_avg_s / 1e12 if f_avg_s > 0 else None
+    # one launch per dcm_step call (its last timestep) sums energy and virial
+    n_ew = min(args.steps, f_cnt)
+    instr_pp = (FLOP_PER_PAIR * n_ew + FLOP_PER_PAIR_FORCES * (f_cnt - n_ew)) / max(f_cnt, 1)
+    achieved = pairs * instr_pp / f_avg_s / 1e12 if f_avg_s > 0 else None
     fkern = "k_forces_list" if args.skin > 0 else D.FORCE_KERNEL_NAMES[D.dcm_force_kernel(ctx)]
     acc_name = D.ACC_NAMES[D.dcm_accumulation(ctx)]
     cells = (args.cell_edge, args.cell_edge_x if args.cell_edge_x > 0 else args.cell_edge)
@@ -518,17 +523,20 @@ def run_gb300(args):
             "unit": "T FP32-instr/s", "frac": (achieved / peak_tinstr) if achieved else None,
             "traffic": recorded_traffic(args.workload, cells, acc_name),
             "avg_launch_ms": f_ms / max(f_cnt, 1),
-            "pairs_per_launch": pairs, "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
+            "pairs_per_launch": pairs, "instr_per_pair": instr_pp,
+            "instr_basis": f"{FLOP_PER_PAIR} per pair in the {n_ew} launches that sum energy and virial, "
+                           f"{FLOP_PER_PAIR_FORCES} in the other {f_cnt - n_ew}",
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {fmax:g} MHz (max clock)"}
     stage_ms = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
     # step roofline: the force kernel at the FP32-pipe peak plus every other
     # stage at the measured HBM bandwidth (REST_BYTES per particle per timestep)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    f_ideal = pairs * FLOP_PER_PAIR / (peak_tinstr * 1e12) * 1e3
+    f_ideal = pairs * instr_pp / (peak_tinstr * 1e12) * 1e3
     r_ideal = n * REST_BYTES / (hbm * 1e9) * 1e3
     t_meas = ms / max(args.steps * K_RECOMPUTE, 1)
     step_roof = {"force_ideal_ms": f_ideal, "rest_ideal_ms": r_ideal, "ideal_ms_per_timestep": f_ideal + r_ideal,
                  "measured_ms_per_timestep": t_meas, "frac": (f_ideal + r_ideal) / t_meas if t_meas > 0 else None,
-                 "basis": f"pairs x {FLOP_PER_PAIR} FP32-pipe instr at the peak above + {REST_BYTES} B/particle "
+                 "basis": f"pairs x {instr_pp:.2f} FP32-pipe instr at the peak above + {REST_BYTES} B/particle "
                           f"at {hbm:g} GB/s (measured copy bandwidth)"}
 
     # ---------------- the force launch in every per-particle accumulation form,

@@ -67,7 +67,7 @@ enum dcm_status_code {
   DCM_ERR_NOT_CONVERGED = 4, /* fast sweeping did not converge within iter_max */
   DCM_ERR_CAPACITY = 5,      /* n > n_max, or a density value range beyond the histogram */
   DCM_ERR_NOMEM = 6,         /* scratch allocation failed in dcm_create */
-  DCM_ERR_TIMEOUT = 7        /* a device-side wait ran past its time budget (batched persistent step) */
+  DCM_ERR_TIMEOUT = 7        /* a device-side wait ran past its budget (persistent batched step, cell-count scan) */
 };
 
 /* Cell-list force kernels (both walk the same culled cell rows and accept the
@@ -230,6 +230,14 @@ const char* dcm_last_error(const dcm_ctx* ctx);
  * (DCM_ERR_NOT_CONVERGED, DCM_ERR_CAPACITY). */
 int dcm_status(dcm_ctx* ctx, dcm_stream_t stream);
 
+/* Self-test of the failure path of the cell-count scan (the single-pass scan
+ * with decoupled look-back that every binning runs): scans two tiles with the
+ * first tile's block left out, so the second tile's bounded wait for its
+ * predecessor must run out (after about a second) and its block must return.
+ * Synchronises `stream` and returns the device status it read and cleared:
+ * DCM_ERR_TIMEOUT when the wait ran out as it must. */
+int dcm_scan_wait_selftest(dcm_ctx* ctx, dcm_stream_t stream);
+
 /* ---- the hot path ------------------------------------------------------ */
 
 /* Binning, Sections 2.1 and 2.3.  Cell of particle i: cx = floor(x_i / lx),
@@ -335,8 +343,12 @@ int dcm_step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, dcm_stream_t stream);
  *   v += dt/2 F;  x += dt v (wrapped);  bin;
  *   if t % K == 0: box counts, interface, distances, cutoffs;
  *   forces;  v += dt/2 F;  thermo = {E, W, KE, pairs}.
- * Masses are 1.  The distance sweeps run a fixed budget of iterations with a
- * device-side convergence flag; non-convergence is reported by dcm_status().
+ * Masses are 1.  thermo and the per-particle energies (w of st->force) are
+ * those of the call's last timestep; on the cell lists in the mixed form the
+ * timesteps before it sum forces only (energy and virial are not evaluated
+ * where nothing reads them).  The distance sweeps run a fixed budget of
+ * iterations with a device-side convergence flag; non-convergence is
+ * reported by dcm_status().
  * With params.skin == 0 the call never waits on the host.  With skin > 0
  * (Verlet lists) each step reads the largest displacement back to the host
  * to decide whether to rebin and rebuild the lists (so it synchronises the

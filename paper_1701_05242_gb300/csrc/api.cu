@@ -265,7 +265,7 @@ struct ScratchPlan {
   double skin;
   int32_t min_component, segmentation, ms_outer;
   int64_t total() const {
-    return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 4 * scan_cap + 3 * 4 * nbox + 2 * nbox +
+    return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 8 * (scan_cap + 1) + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
            8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
            (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2) + 4 * nblk +
@@ -312,7 +312,7 @@ extern "C" const char* dcm_version(void) { return "dcm-gb300 0.1 (sm_103a)"; }
 extern "C" void dcm_destroy(dcm_ctx* ctx) {
   if (!ctx) return;
   void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
-                 ctx->scan_part, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
+                 ctx->scan_state, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
                  ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
                  ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0, ctx->dq[0], ctx->dq[1], ctx->dqlen,
@@ -363,7 +363,7 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   alloc((void**)&ctx->perm, 4 * nm);
   alloc((void**)&ctx->cell_start, 4 * (s.ncell + 1));
   alloc((void**)&ctx->cell_count, 4 * s.ncell);
-  alloc((void**)&ctx->scan_part, 4 * s.scan_cap);
+  alloc((void**)&ctx->scan_state, 8 * (s.scan_cap + 1));
   alloc((void**)&ctx->box_count, 4 * s.nbox);
   alloc((void**)&ctx->g, 4 * s.nbox);
   alloc((void**)&ctx->g_tmp, 4 * s.nbox);
@@ -438,6 +438,13 @@ extern "C" int dcm_status(dcm_ctx* ctx, dcm_stream_t stream) {
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), st));
   if (code) set_error(ctx, code, "device status %d", code);
   return code;
+}
+
+extern "C" int dcm_scan_wait_selftest(dcm_ctx* ctx, dcm_stream_t stream) {
+  if (!ctx) return DCM_ERR_INVALID_ARG;
+  int r = scan_wait_selftest(ctx, (cudaStream_t)stream);
+  if (r) return r;
+  return dcm_status(ctx, stream);
 }
 
 // ---------------------------------------------------------------------------

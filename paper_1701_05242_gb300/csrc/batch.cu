@@ -380,7 +380,7 @@ extern "C" void dcm_batch_destroy(dcm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   dcm_ctx* c = &b->base;
-  void* dev[] = {c->status, c->slot,  c->cell,  c->perm,   c->cell_start, c->cell_count, c->scan_part,
+  void* dev[] = {c->status, c->slot,  c->cell,  c->perm,   c->cell_start, c->cell_count, c->scan_state,
                  c->box_count, c->g,   c->g_tmp, c->s,      c->iface,      c->D[0],       c->D[1],
                  c->flags,  c->red,   c->red_tmp, c->totals, b->geom,       b->rep_of_particle, b->rep_of_box,
                  b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart,
@@ -489,7 +489,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   alloc((void**)&c->perm, 4 * nm);
   alloc((void**)&c->cell_start, 4 * (nctot + 1));
   alloc((void**)&c->cell_count, 4 * nctot);
-  alloc((void**)&c->scan_part, 4 * c->scan_cap);
+  alloc((void**)&c->scan_state, 8 * (c->scan_cap + 1));
   alloc((void**)&c->box_count, 4 * nbtot);
   alloc((void**)&c->g, 4 * nbtot);
   alloc((void**)&c->g_tmp, 4 * nbtot);

@@ -54,103 +54,93 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total) {
   return base + inc - v;
 }
 
-// Phase 1: exclusive scan inside each tile; tile sums to part[].
-__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                                                           int64_t n, int32_t* __restrict__ part) {
-  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  int v[kScanItems];
-  int sum = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    v[k] = (base + k < n) ? in[base + k] : 0;
-    sum += v[k];
-  }
-  int total;
-  int run = block_excl_scan(sum, &total);
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < n) out[base + k] = run;
-    run += v[k];
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = total;
+// Single-pass exclusive scan with decoupled look-back (Merrill and
+// Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back",
+// 2016).  Each block takes the next tile of kScanTile items by a ticket (so
+// every tile it waits for belongs to a block that is already running),
+// scans it, publishes the tile's sum, and then its first warp walks back
+// over the preceding tiles' words, 32 at a time, adding their sums until it
+// meets a tile that has published its inclusive prefix.  A word packs its
+// kind (bits 62-63: 0 not yet published, 1 the tile's sum, 2 the inclusive
+// prefix) and its value (bits 0-31) so that one 64-bit store publishes both.
+// Every wait is bounded by a poll count; a block that runs out records
+// DCM_ERR_TIMEOUT in the device status and carries on with prefix 0 (the
+// caller reads the status).  state[0 .. ntiles] must be zero at launch
+// (state[ntiles] is the ticket counter).
+constexpr unsigned long long kScanSum = 1ull << 62, kScanPrefix = 2ull << 62;
+constexpr int64_t kScanMaxPolls = 1 << 20;  // about a second of polls
+
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
 
-// Phase 1 with one 16-byte load and store per thread (in and out 16-byte
-// aligned, kScanItems = 4).
-__global__ void __launch_bounds__(kScanBlock) k_scan_tiles4(const int32_t* __restrict__ in,
-                                                            int32_t* __restrict__ out, int64_t n,
-                                                            int32_t* __restrict__ part) {
-  static_assert(kScanItems == 4, "one int4 per thread");
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * 4;
+__global__ void __launch_bounds__(kScanBlock) k_scan_lookback(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                                              int64_t n, unsigned long long* state, int64_t ntiles,
+                                                              int32_t* status) {
+  __shared__ int64_t tile_sh;
+  __shared__ int prefix_sh;
+  if (threadIdx.x == 0) tile_sh = (int64_t)atomicAdd(state + ntiles, 1ull);
+  __syncthreads();
+  const int64_t t = tile_sh;
+  const int64_t base = t * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  static_assert(kScanItems == 4, "four items per thread");
+  const bool vec = ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0;
   int4 v = make_int4(0, 0, 0, 0);
-  if (base + 4 <= n) {
+  if (vec && base + 4 <= n) {
     v = *reinterpret_cast<const int4*>(in + base);
   } else if (base < n) {
     v.x = in[base];
     v.y = base + 1 < n ? in[base + 1] : 0;
     v.z = base + 2 < n ? in[base + 2] : 0;
+    v.w = base + 3 < n ? in[base + 3] : 0;
   }
   int total;
   const int run = block_excl_scan(v.x + v.y + v.z + v.w, &total);
-  const int4 o = make_int4(run, run + v.x, run + v.x + v.y, run + v.x + v.y + v.z);
-  if (base + 4 <= n) {
+  if (threadIdx.x < 32) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
+    int prefix = 0;
+    if (t == 0) {
+      if (lane == 0) atomicExch(state, kScanPrefix | (unsigned)total);
+    } else {
+      if (lane == 0) atomicExch(state + t, kScanSum | (unsigned)total);
+      int64_t look = t - 1;
+      int64_t polls = 0;
+      for (;;) {
+        const int64_t k = look - lane;
+        const unsigned long long wv = k >= 0 ? ld_word(state + k) : kScanPrefix;
+        if (__any_sync(full, (wv >> 62) == 0)) {
+          if (++polls > kScanMaxPolls) {
+            if (lane == 0) raise_status(status, DCM_ERR_TIMEOUT);
+            prefix = 0;
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        // the nearest inclusive prefix in the window ends the walk
+        const unsigned pre = __ballot_sync(full, (wv >> 62) == 2);
+        const int stop = pre ? __ffs(pre) - 1 : 31;
+        prefix += __reduce_add_sync(full, lane <= stop ? (unsigned)(wv & 0xffffffffull) : 0u);
+        if (pre) break;
+        look -= 32;
+      }
+      if (lane == 0) atomicExch(state + t, kScanPrefix | (unsigned)(prefix + total));
+    }
+    if (lane == 0) prefix_sh = prefix;
+  }
+  __syncthreads();
+  const int ex = prefix_sh + run;
+  const int4 o = make_int4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+  if (vec && base + 4 <= n) {
     *reinterpret_cast<int4*>(out + base) = o;
   } else if (base < n) {
     out[base] = o.x;
     if (base + 1 < n) out[base + 1] = o.y;
     if (base + 2 < n) out[base + 2] = o.z;
+    if (base + 3 < n) out[base + 3] = o.w;
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = total;
-}
-
-// Phase 2: one block scans the tile sums in chunks (exclusive, in place);
-// the grand total goes to out_total.
-__global__ void __launch_bounds__(kScanBlock) k_scan_parts(int32_t* part, int64_t nparts, int32_t* out_total) {
-  int carry = 0;
-  for (int64_t c0 = 0; c0 < nparts; c0 += kScanTile) {
-    int64_t base = c0 + (int64_t)threadIdx.x * kScanItems;
-    int v[kScanItems];
-    int sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      v[k] = (base + k < nparts) ? part[base + k] : 0;
-      sum += v[k];
-    }
-    int total;
-    int run = block_excl_scan(sum, &total) + carry;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      if (base + k < nparts) part[base + k] = run;
-      run += v[k];
-    }
-    carry += total;
-  }
-  if (threadIdx.x == 0) *out_total = carry;
-}
-
-// Phase 3: add the tile offsets.
-__global__ void k_scan_add(int32_t* __restrict__ out, int64_t n, const int32_t* __restrict__ part) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  out[i] += part[i / kScanTile];
-}
-
-// The same, four items per thread with 16-byte accesses (out 16-byte
-// aligned; a tile holds a multiple of four items, so the four share a tile).
-__global__ void k_scan_add4(int32_t* __restrict__ out, int64_t n, const int32_t* __restrict__ part) {
-  const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  if (i >= n) return;
-  const int32_t a = part[i / kScanTile];
-  if (i + 4 <= n) {
-    int4 v = *reinterpret_cast<const int4*>(out + i);
-    v.x += a;
-    v.y += a;
-    v.z += a;
-    v.w += a;
-    *reinterpret_cast<int4*>(out + i) = v;
-  } else {
-    for (int64_t k = i; k < n; ++k) out[k] += a;
-  }
+  if (t == ntiles - 1 && threadIdx.x == 0) out[n] = prefix_sh + total;
 }
 
 int exclusive_scan(dcm_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
@@ -160,17 +150,37 @@ int exclusive_scan(dcm_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, cud
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, sizeof(int32_t), st));
     return DCM_OK;
   }
-  if ((((uintptr_t)in | (uintptr_t)out) & 15) == 0)
-    DCM_LAUNCH(ctx, k_scan_tiles4, (unsigned)tiles, kScanBlock, 0, st, in, out, n, ctx->scan_part);
-  else
-    DCM_LAUNCH(ctx, k_scan_tiles, (unsigned)tiles, kScanBlock, 0, st, in, out, n, ctx->scan_part);
-  DCM_LAUNCH(ctx, k_scan_parts, 1, kScanBlock, 0, st, ctx->scan_part, tiles, out + n);
-  static_assert(kScanTile % 4 == 0, "four-item adds stay inside a tile");
-  if (((uintptr_t)out & 15) == 0)
-    DCM_LAUNCH(ctx, k_scan_add4, (unsigned)(((n + 3) / 4 + 255) / 256), 256, 0, st, out, n, ctx->scan_part);
-  else
-    DCM_LAUNCH(ctx, k_scan_add, (unsigned)((n + 255) / 256), 256, 0, st, out, n, ctx->scan_part);
+  DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->scan_state, 0, sizeof(unsigned long long) * (size_t)(tiles + 1), st));
+  DCM_LAUNCH(ctx, k_scan_lookback, (unsigned)tiles, kScanBlock, 0, st, in, out, n, ctx->scan_state, tiles, ctx->status);
   return check_launch(ctx, "exclusive_scan");
+}
+
+// The scan's failure path: two tiles of zeros with the first tile's block
+// left out (the ticket counter starts at 1), so the one block launched takes
+// tile 1 and its look-back waits for a word that is never published.
+int scan_wait_selftest(dcm_ctx* ctx, cudaStream_t st) {
+  int32_t* buf = nullptr;
+  unsigned long long* state = nullptr;
+  const int64_t n = 2 * (int64_t)kScanTile;
+  if (cudaMalloc((void**)&buf, sizeof(int32_t) * (size_t)(2 * n + 1)) != cudaSuccess)
+    return set_error(ctx, DCM_ERR_NOMEM, "scan self-test buffer");
+  if (cudaMalloc((void**)&state, sizeof(unsigned long long) * 3) != cudaSuccess) {
+    cudaFree(buf);
+    return set_error(ctx, DCM_ERR_NOMEM, "scan self-test state");
+  }
+  int r = DCM_OK;
+  if (cudaMemsetAsync(buf, 0, sizeof(int32_t) * (size_t)(2 * n + 1), st) != cudaSuccess ||
+      cudaMemsetAsync(state, 0, sizeof(unsigned long long) * 3, st) != cudaSuccess ||
+      cudaMemsetAsync(state + 2, 1, 1, st) != cudaSuccess)  // ticket counter = 1 (little-endian low byte)
+    r = set_error(ctx, DCM_ERR_CUDA, "scan self-test set-up");
+  if (r == DCM_OK) {
+    k_scan_lookback<<<1, kScanBlock, 0, st>>>(buf, buf + n, n, state, 2, ctx->status);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      r = set_error(ctx, DCM_ERR_CUDA, "scan self-test launch");
+  }
+  cudaFree(buf);
+  cudaFree(state);
+  return r;
 }
 
 __global__ void k_scatter(int64_t n, const int32_t* __restrict__ cell, const int32_t* __restrict__ slot,

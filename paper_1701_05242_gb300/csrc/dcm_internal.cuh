@@ -97,7 +97,7 @@ struct dcm_ctx {
   int32_t* perm;            // n_max
   int32_t* cell_start;      // ncell + 1
   int32_t* cell_count;      // ncell
-  int32_t* scan_part;       // scan block partials
+  unsigned long long* scan_state;  // [scan_cap + 1]: look-back words of the scan tiles, ticket
   int32_t* box_count;       // nbox
   int32_t* g;               // nbox
   int32_t* g_tmp;           // nbox
@@ -166,6 +166,7 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 int set_error(dcm_ctx* ctx, int code, const char* fmt, ...);
 
 // Cell-list force kernel and per-particle accumulation form of a context.
+int scan_wait_selftest(dcm_ctx* ctx, cudaStream_t st);  // the look-back scan's bounded wait
 int force_kernel_choice(const dcm_params& p);  // DCM_FORCE_* with AUTO resolved
 int resolve_force_kernel(const dcm_ctx* ctx);  // ... and each kernel's limits applied
 int resolve_accumulation(const dcm_ctx* ctx);  // DCM_ACC_* that the force launches run
@@ -224,10 +225,13 @@ template <typename R>
 int assign_cutoffs(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* D, R* rc,
                    cudaStream_t st);
 
-// forces.cu
+// forces.cu.  energies = false (and no totals): the packed kernel sums the
+// forces only (the force's w, the per-particle energy, is then zero), for
+// the timesteps of dcm_step whose energy and virial nothing reads.
 template <typename R>
 int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc,
-              const int32_t* cell_start, typename RT<R>::R4* force, double* totals, cudaStream_t st);
+              const int32_t* cell_start, typename RT<R>::R4* force, double* totals, cudaStream_t st,
+              bool energies = true);
 
 // adjoint.cu
 template <typename R>

@@ -71,7 +71,7 @@ constexpr int kX2Block = 64;
 template <Accum M>
 constexpr int x2_min_blocks() { return (M == Accum::kPlain || plane_form(M)) ? 16 : 12; }
 
-template <bool TYPED, Accum M>
+template <bool TYPED, Accum M, bool EW>
 __global__ void __launch_bounds__(kX2Block, x2_min_blocks<M>()) k_forces_x2(int64_t n, const float4* __restrict__ pos,
                                                                           const float* __restrict__ rc,
                                                                           const int32_t* __restrict__ start,
@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(kX2Block, x2_min_blocks<M>()) k_forces_x2(int6
   double e_out = 0, w_out = 0;
   int np = 0;
   if (i < n)
-    force[i] = force_one<float, TYPED, true, M>(pos, start, a.g, a, (int)i, __ldg(pos + i), rc[i], e_out, w_out, np);
+    force[i] = force_one<float, TYPED, true, M, true, EW>(pos, start, a.g, a, (int)i, __ldg(pos + i), rc[i], e_out, w_out,
+                                                         np);
   if (part) warp_partials3(e_out, w_out, np, part, nwarp);
 }
 
@@ -113,13 +114,21 @@ int resolve_accumulation(const dcm_ctx* ctx) {
 namespace {
 
 template <Accum M>
-void launch_x2(dcm_ctx* ctx, bool typed, int64_t n, const float4* pos, const float* rc, const int32_t* cell_start,
-               const ForceArgs<float>& a, float4* force, double* part, int64_t nwarp, cudaStream_t st) {
+void launch_x2(dcm_ctx* ctx, bool typed, bool ew, int64_t n, const float4* pos, const float* rc,
+               const int32_t* cell_start, const ForceArgs<float>& a, float4* force, double* part, int64_t nwarp,
+               cudaStream_t st) {
   const unsigned nblk = (unsigned)((n + kX2Block - 1) / kX2Block);
-  if (typed)
-    DCM_LAUNCH(ctx, (k_forces_x2<true, M>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part, nwarp);
+  if (typed && ew)
+    DCM_LAUNCH(ctx, (k_forces_x2<true, M, true>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part, nwarp);
+  else if (typed)
+    DCM_LAUNCH(ctx, (k_forces_x2<true, M, false>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
+               nwarp);
+  else if (ew)
+    DCM_LAUNCH(ctx, (k_forces_x2<false, M, true>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
+               nwarp);
   else
-    DCM_LAUNCH(ctx, (k_forces_x2<false, M>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part, nwarp);
+    DCM_LAUNCH(ctx, (k_forces_x2<false, M, false>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
+               nwarp);
 }
 
 template <typename R, Accum M>
@@ -138,7 +147,7 @@ void launch_scalar(dcm_ctx* ctx, bool typed, int64_t n, const typename RT<R>::R4
 
 template <typename R>
 int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, const int32_t* cell_start,
-              typename RT<R>::R4* force, double* totals, cudaStream_t st) {
+              typename RT<R>::R4* force, double* totals, cudaStream_t st, bool energies) {
   if (n <= 0) {
     if (totals) DCM_CUDA_TRY(ctx, cudaMemsetAsync(totals, 0, 3 * sizeof(double), st));
     return DCM_OK;
@@ -166,7 +175,8 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
     const int m = resolve_accumulation(ctx);
     if (kind == DCM_FORCE_PACKED)
       with_accum<true>(m, [&](auto tag) {
-        launch_x2<decltype(tag)::value>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st);
+        launch_x2<decltype(tag)::value>(ctx, typed, energies || totals, n, pos, rc, cell_start, a, force, part, nwarp,
+                                        st);
         return 0;
       });
     else
@@ -185,8 +195,8 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
 }
 
 template int lj_forces<float>(dcm_ctx*, int64_t, const float4*, const float*, const int32_t*, float4*, double*,
-                              cudaStream_t);
+                              cudaStream_t, bool);
 template int lj_forces<double>(dcm_ctx*, int64_t, const dvec4*, const double*, const int32_t*, dvec4*, double*,
-                               cudaStream_t);
+                               cudaStream_t, bool);
 
 }  // namespace dcm

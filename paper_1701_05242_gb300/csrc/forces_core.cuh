@@ -250,8 +250,9 @@ __device__ __forceinline__ void kahan_add2(float2& s, float2& k, float2 x) {
   s = u;
 }
 
-// Fold the partials into the sums of a row or plane form and clear them.
-template <Accum M, typename R, bool X2>
+// Fold the partials into the sums of a row or plane form and clear them
+// (without EW only the force components: energy and virial are not summed).
+template <Accum M, typename R, bool X2, bool EW = true>
 __device__ __forceinline__ void flush_partials(Acc<R>& c, Acc2& c2, Sums<M>& S) {
   if constexpr (row_form(M) || plane_form(M)) {
     float v[5];
@@ -271,7 +272,7 @@ __device__ __forceinline__ void flush_partials(Acc<R>& c, Acc2& c2, Sums<M>& S) 
       c.fx = c.fy = c.fz = c.en = c.vir = (R)0;
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < (EW ? 5 : 3); ++q) {
       if constexpr (f64_form(M))
         S.v[q] += (double)v[q];
       else
@@ -283,34 +284,41 @@ __device__ __forceinline__ void flush_partials(Acc<R>& c, Acc2& c2, Sums<M>& S) 
 
 // Add the packed terms of one step (force components, U/4 or U, r.F) into
 // the partials or the sums of form M.
-template <Accum M>
+template <Accum M, bool EW = true>
 __device__ __forceinline__ void add_terms2(Acc2& c, Sums<M>& S, float2 q, float2 dx, float2 dy, float2 dz,
                                            float2 en, float2 pv) {
   if constexpr (M == Accum::kPairKahan) {
     kahan_add2(c.fx, S.k[0], __fmul2_rn(q, dx));
     kahan_add2(c.fy, S.k[1], __fmul2_rn(q, dy));
     kahan_add2(c.fz, S.k[2], __fmul2_rn(q, dz));
-    kahan_add2(c.en, S.k[3], en);
-    kahan_add2(c.vir, S.k[4], pv);
+    if constexpr (EW) {
+      kahan_add2(c.en, S.k[3], en);
+      kahan_add2(c.vir, S.k[4], pv);
+    }
   } else if constexpr (M == Accum::kPairF64) {
     const float2 t0 = __fmul2_rn(q, dx), t1 = __fmul2_rn(q, dy), t2 = __fmul2_rn(q, dz);
     S.v[0] += (double)t0.x + (double)t0.y;
     S.v[1] += (double)t1.x + (double)t1.y;
     S.v[2] += (double)t2.x + (double)t2.y;
-    S.v[3] += (double)en.x + (double)en.y;
-    S.v[4] += (double)pv.x + (double)pv.y;
+    if constexpr (EW) {
+      S.v[3] += (double)en.x + (double)en.y;
+      S.v[4] += (double)pv.x + (double)pv.y;
+    }
   } else {
     c.fx = __ffma2_rn(q, dx, c.fx);
     c.fy = __ffma2_rn(q, dy, c.fy);
     c.fz = __ffma2_rn(q, dz, c.fz);
-    c.en = __fadd2_rn(c.en, en);
-    c.vir = __fadd2_rn(c.vir, pv);
+    if constexpr (EW) {
+      c.en = __fadd2_rn(c.en, en);
+      c.vir = __fadd2_rn(c.vir, pv);
+    }
   }
 }
 
 // One packed step on the differences d = r_j - r_i of two candidates (m0,
-// m1: whether each slot holds a real candidate).
-template <Accum M>
+// m1: whether each slot holds a real candidate).  Without EW the step sums
+// the force only (no energy, virial or pair count).
+template <Accum M, bool EW = true>
 __device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, Acc2& c,
                                           Sums<M>& S) {
   const float2 two = make_float2(2.f, 2.f), m1f = make_float2(-1.f, -1.f);
@@ -331,16 +339,18 @@ __device__ __forceinline__ void pair_x2_d(float2 dx, float2 dy, float2 dz, bool 
     c.fx = __ffma2_rn(q, dx, c.fx);
     c.fy = __ffma2_rn(q, dy, c.fy);
     c.fz = __ffma2_rn(q, dz, c.fz);
-    c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1f), c.en);
-    c.vir = __fadd2_rn(c.vir, pv);
+    if constexpr (EW) {
+      c.en = __ffma2_rn(s6, __fadd2_rn(s6, m1f), c.en);
+      c.vir = __fadd2_rn(c.vir, pv);
+    }
   } else {
-    add_terms2<M>(c, S, q, dx, dy, dz, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), pv);
+    add_terms2<M, EW>(c, S, q, dx, dy, dz, EW ? __fmul2_rn(s6, __fadd2_rn(s6, m1f)) : s6, pv);
   }
-  c.np += (int)a0 + (int)a1;
+  if constexpr (EW) c.np += (int)a0 + (int)a1;
 }
 
 // One packed step: candidates p0 and p1 against particle i.
-template <bool SJ, Accum M>
+template <bool SJ, Accum M, bool EW = true>
 __device__ __forceinline__ void pair_x2(const float4& p0, const float4& p1, bool m0, bool m1, float xi, float yi,
                                         float zi, float shx, float shy, float shz, float rc2, Acc2& c,
                                         Sums<M>& S) {
@@ -354,13 +364,13 @@ __device__ __forceinline__ void pair_x2(const float4& p0, const float4& p1, bool
     dy = make_float2(p0.y - yi, p1.y - yi);
     dz = make_float2(p0.z - zi, p1.z - zi);
   }
-  pair_x2_d<M>(dx, dy, dz, m0, m1, rc2, c, S);
+  pair_x2_d<M, EW>(dx, dy, dz, m0, m1, rc2, c, S);
 }
 
 // The packed step for up to two types: the constants of the pair type of
 // each slot (sigma^2, 24 eps, 4 eps and the energy shift) are picked from the
 // two of particle i's row by the slot's type; m0, m1 as in pair_x2_d.
-template <Accum M>
+template <Accum M, bool EW = true>
 __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool m0, bool m1, float rc2, float2 sg,
                                            float2 e24, float2 e4, float2 us, Acc2& c, Sums<M>& S) {
   const float2 two = make_float2(2.f, 2.f), m1f = make_float2(-1.f, -1.f);
@@ -378,17 +388,20 @@ __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool
   const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
   const float2 pv = __fmul2_rn(e24, __fmul2_rn(s6, __ffma2_rn(s6, two, m1f)));  // r . F_ij
   const float2 q = __fmul2_rn(pv, y);
-  const float2 u = __ffma2_rn(e4, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), make_float2(-us.x, -us.y));
+  const float2 u =
+      EW ? __ffma2_rn(e4, __fmul2_rn(s6, __fadd2_rn(s6, m1f)), make_float2(-us.x, -us.y)) : make_float2(0.f, 0.f);
   if constexpr (plain_loop(M)) {
     c.fx = __ffma2_rn(q, dx, c.fx);
     c.fy = __ffma2_rn(q, dy, c.fy);
     c.fz = __ffma2_rn(q, dz, c.fz);
-    c.en = __fadd2_rn(c.en, u);
-    c.vir = __fadd2_rn(c.vir, pv);
+    if constexpr (EW) {
+      c.en = __fadd2_rn(c.en, u);
+      c.vir = __fadd2_rn(c.vir, pv);
+    }
   } else {
-    add_terms2<M>(c, S, q, dx, dy, dz, u, pv);
+    add_terms2<M, EW>(c, S, q, dx, dy, dz, u, pv);
   }
-  c.np += (int)a0 + (int)a1;
+  if constexpr (EW) c.np += (int)a0 + (int)a1;
 }
 
 // Typed form of pair_range_x2 for one or two types.  k8 holds particle i's
@@ -396,7 +409,7 @@ __device__ __forceinline__ void pair_x2_dt(float2 dx, float2 dy, float2 dz, bool
 // 4 eps of the pair type (type of i, t); a candidate's type is 1 if its w is
 // at least 1 (type_of clamped to two types), and with one type both columns
 // are equal.
-template <bool SJ, Accum M, bool NC = true>
+template <bool SJ, Accum M, bool NC = true, bool EW = true>
 __device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                                float zi, float shx, float shy, float shz, float rc2,
                                                const float* k8, Acc2& c, Sums<M>& S) {
@@ -415,13 +428,13 @@ __device__ __forceinline__ void pair_range_x2t(const float4* __restrict__ pos, i
       dz = make_float2(p0.z - zi, p1.z - zi);
     }
     const bool t0 = p0.w >= 1.f, t1 = p1.w >= 1.f;
-    pair_x2_dt<M>(dx, dy, dz, true, has1, rc2, make_float2(t0 ? k8[3] : k8[2], t1 ? k8[3] : k8[2]),
+    pair_x2_dt<M, EW>(dx, dy, dz, true, has1, rc2, make_float2(t0 ? k8[3] : k8[2], t1 ? k8[3] : k8[2]),
                make_float2(t0 ? k8[5] : k8[4], t1 ? k8[5] : k8[4]), make_float2(t0 ? k8[7] : k8[6], t1 ? k8[7] : k8[6]),
                make_float2(t0 ? k8[1] : k8[0], t1 ? k8[1] : k8[0]), c, S);
   }
 }
 
-template <bool SJ, Accum M, bool NC = true>
+template <bool SJ, Accum M, bool NC = true, bool EW = true>
 __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, int lo, int hi, float xi, float yi,
                                               float zi, float shx, float shy, float shz, float rc2, Acc2& c,
                                               Sums<M>& S) {
@@ -429,25 +442,25 @@ __device__ __forceinline__ void pair_range_x2(const float4* __restrict__ pos, in
     const bool has1 = j + 1 < hi;
     const int j1 = has1 ? j + 1 : j;
     const float4 p0 = ld_pos<NC>(pos + j), p1 = ld_pos<NC>(pos + j1);
-    pair_x2<SJ, M>(p0, p1, true, has1, xi, yi, zi, shx, shy, shz, rc2, c, S);
+    pair_x2<SJ, M, EW>(p0, p1, true, has1, xi, yi, zi, shx, shy, shz, rc2, c, S);
   }
 }
 
 // Segment dispatch: the packed loop for FP32 (one type, or up to two types
 // with the row constants in ushift[0 .. 7]), the scalar loop otherwise; the
 // row forms of accumulation take the segment's partials over at its end.
-template <typename R, bool SJ, bool TYPED, bool X2, Accum M, bool NC = true>
+template <typename R, bool SJ, bool TYPED, bool X2, Accum M, bool NC = true, bool EW = true>
 __device__ __forceinline__ void segment(const typename RT<R>::R4* __restrict__ pos, int lo, int hi, R xi, R yi, R zi,
                                         R shx, R shy, R shz, R rc2, int ti, const ForceArgs<R>& a, const R* ushift,
                                         Acc<R>& c, Acc2& c2, Sums<M>& S) {
   if constexpr (X2 && TYPED) {
-    pair_range_x2t<SJ, M, NC>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2, S);
+    pair_range_x2t<SJ, M, NC, EW>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ushift, c2, S);
   } else if constexpr (X2) {
-    pair_range_x2<SJ, M, NC>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2, S);
+    pair_range_x2<SJ, M, NC, EW>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, c2, S);
   } else {
     pair_range<R, SJ, TYPED, NC>(pos, lo, hi, xi, yi, zi, shx, shy, shz, rc2, ti, a, ushift, c);
   }
-  if constexpr (row_form(M)) flush_partials<M, R, X2>(c, c2, S);
+  if constexpr (row_form(M)) flush_partials<M, R, X2, EW>(c, c2, S);
 }
 
 // Which segments of the row walk are evaluated: all of them, or only those
@@ -458,7 +471,7 @@ enum class Walk { kAll, kImagesOnly };
 // The culled cell-row walk of particle `self` (position pi, clamped cutoff
 // rci) over the cell grid g whose cell starts are start[0 .. ncell] (positions
 // pos sorted by cell), accumulating into c (scalar loop) or c2 (packed).
-template <typename R, bool TYPED, bool X2, Accum M, bool NC = true, Walk MODE = Walk::kAll>
+template <typename R, bool TYPED, bool X2, Accum M, bool NC = true, Walk MODE = Walk::kAll, bool EW = true>
 __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__ pos,
                                           const int32_t* __restrict__ start, const Grid<R>& g,
                                           const ForceArgs<R>& a, int self, const typename RT<R>::R4& pi, R rci,
@@ -499,7 +512,7 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       if (ulo < 0) {
         int a1 = min(uhi, -1);
         int j0 = ld_start<NC>(start + row + ulo + nx), j1 = ld_start<NC>(start + row + a1 + nx + 1);
-        segment<R, true, TYPED, X2, M, NC>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2, S);
+        segment<R, true, TYPED, X2, M, NC, EW>(pos, j0, j1, pi.x, yi, zi, -g.L[0], ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
       // segment 0 <= u < nx: no x shift; the particle itself is skipped
       const bool img_row = uy < 0 || uy >= ny || uz < 0 || uz >= nz;
@@ -508,13 +521,13 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
         if (a0 <= a1) {
           int j0 = ld_start<NC>(start + row + a0), j1 = ld_start<NC>(start + row + a1 + 1);
           if (!kImg && uy == cy && uz == cz) {  // the particle's own row: cut it out
-            segment<R, false, TYPED, X2, M, NC>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
-            segment<R, false, TYPED, X2, M, NC>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
+            segment<R, false, TYPED, X2, M, NC, EW>(pos, j0, min(j1, self), pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
+            segment<R, false, TYPED, X2, M, NC, EW>(pos, max(j0, self + 1), j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c,
                                          c2, S);
           } else if (ysh == (R)0 && zsh == (R)0) {
-            segment<R, false, TYPED, X2, M, NC>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
+            segment<R, false, TYPED, X2, M, NC, EW>(pos, j0, j1, pi.x, yi, zi, 0, 0, 0, rc2, ti, a, ushift, c, c2, S);
           } else {
-            segment<R, true, TYPED, X2, M, NC>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
+            segment<R, true, TYPED, X2, M, NC, EW>(pos, j0, j1, pi.x, yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
           }
         }
       }
@@ -522,10 +535,10 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       if (uhi >= nx) {
         int a0 = max(ulo, nx);
         int j0 = ld_start<NC>(start + row + a0 - nx), j1 = ld_start<NC>(start + row + uhi - nx + 1);
-        segment<R, true, TYPED, X2, M, NC>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
+        segment<R, true, TYPED, X2, M, NC, EW>(pos, j0, j1, pi.x - g.L[0], yi, zi, (R)0, ysh, zsh, rc2, ti, a, ushift, c, c2, S);
       }
     }
-    if constexpr (plane_form(M)) flush_partials<M, R, X2>(c, c2, S);
+    if constexpr (plane_form(M)) flush_partials<M, R, X2, EW>(c, c2, S);
   }
 }
 
@@ -544,7 +557,9 @@ __device__ __forceinline__ R clamp_cutoff(R rc_in, R rc_max) {
 // pos, sorted by cell), with the per-particle sums of accumulation form M.
 // Returns the force and writes e_i, w_i (in FP64: the totals are reduced
 // from them in FP64) and the accepted-pair count.
-template <typename R, bool TYPED, bool X2 = false, Accum M = Accum::kPlain, bool NC = true>
+// Without EW (the packed loop only) the energy, the virial and the pair
+// count are not summed: e_out, w_out, np_out and the force's w are zero.
+template <typename R, bool TYPED, bool X2 = false, Accum M = Accum::kPlain, bool NC = true, bool EW = true>
 __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4* __restrict__ pos,
                                                         const int32_t* __restrict__ start, const Grid<R>& g,
                                                         const ForceArgs<R>& a, int self,
@@ -578,7 +593,8 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
       ushift[6 + t] = a.eps4[tp];
     }
   }
-  walk_rows<R, TYPED, X2, M, NC>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2, S);
+  static_assert(EW || X2, "the scalar loop always sums energy and virial");
+  walk_rows<R, TYPED, X2, M, NC, Walk::kAll, EW>(pos, start, g, a, self, pi, rci, ti, ushift, c, c2, S);
   // The five sums (fx, fy, fz, en, vir) of the form, in FP64 where the form
   // keeps them so; the packed loop sums the sign-flipped differences r_j - r_i.
   using V = std::conditional_t<f64_form(M), double, R>;
@@ -621,6 +637,12 @@ __device__ __forceinline__ typename RT<R>::R4 force_one(const typename RT<R>::R4
     out.z = (R)((V)24 * sgn * v[2]);
     e_out = (double)((V)2 * v[3] - (V)0.5 * (V)np * (V)ushift[0]);
     w_out = (double)((V)12 * v[4]);
+  }
+  if constexpr (!EW) {
+    e_out = w_out = 0.0;
+    np_out = 0;
+    out.w = (R)0;
+    return out;
   }
   out.w = (R)e_out;
   np_out = np;

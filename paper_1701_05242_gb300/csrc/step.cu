@@ -253,8 +253,9 @@ int step_run(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int nsteps, cuda
     st->t += 1;
     if (st->t % K == 0)
       if ((r = recompute_cutoffs<R>(ctx, n, (const R4*)st->pos[o], (R*)st->rc[o], s))) return r;
+    // energy and virial only where they are reported (the call's last step)
     if ((r = lj_forces<R>(ctx, n, (const R4*)st->pos[o], (const R*)st->rc[o], ctx->cell_start, (R4*)st->force,
-                          last ? ctx->totals : nullptr, s)))
+                          last ? ctx->totals : nullptr, s, last)))
       return r;
     if (last) {
       stage_begin(ctx, DCM_STAGE_KICK, s);

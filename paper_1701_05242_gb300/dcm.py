@@ -111,6 +111,7 @@ _SIGS = {
     "dcm_batch_set_tile": (_i32, [_vp, _i32]),
     "dcm_batch_accumulation": (_i32, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "dcm_batch_barrier_selftest": (_i32, [_vp, _i32, _i64, _vp]),
+    "dcm_scan_wait_selftest": (_i32, [_vp, _vp]),
     "dcm_batch_status": (_i32, [_vp, _vp]),
     "dcm_batch_set_timing": (_i32, [_vp, _i32]),
     "dcm_batch_stage_times": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
@@ -449,6 +450,12 @@ def dcm_batch_barrier_selftest(b: Batch, phantom: int, budget_ns: int, stream=No
     """Runs the persistent grid's barrier against `phantom` missing blocks;
     returns the device status (DCM_ERR_TIMEOUT when the bounded waits ran out)."""
     return lib.dcm_batch_barrier_selftest(b.handle, int(phantom), int(budget_ns), _stream(stream))
+
+
+def dcm_scan_wait_selftest(ctx: Context, stream=None) -> int:
+    """Runs the cell-count scan with a predecessor tile that never publishes;
+    returns the device status (DCM_ERR_TIMEOUT when the bounded wait ran out)."""
+    return lib.dcm_scan_wait_selftest(ctx.handle, _stream(stream))
 
 
 def dcm_batch_graph_steps(b: Batch) -> int:

@@ -132,6 +132,39 @@ def test_bin_edges_and_empty(D):
     assert start.max() == 0 and start.shape[0] == ctx.ncell + 1
 
 
+@pytest.mark.parametrize("lx", [0.0, 0.5])
+def test_bin_many_scan_tiles(D, lx):
+    """Binning whose cell-count scan spans several look-back tiles of 4,096
+    cells with a ragged last tile (24,000 and 72,000 cells), with uniform
+    particles, a dense clump in one cell and empty regions: cells, starts and
+    order bit-exact against the oracle."""
+    box = (60.0, 45.0, 30.0)
+    rng = np.random.default_rng(11)
+    uni = rng.random((40000, 3)) * np.array(box)
+    clump = np.array([30.2, 20.1, 10.3]) + rng.random((700, 3)) * 0.2
+    half = rng.random((9000, 3)) * np.array([30.0, 45.0, 15.0])
+    pts = np.concatenate([uni, clump, half]).astype(np.float32)
+    ctx = make_ctx(D, box, len(pts), lx=lx)
+    edges = (lx if lx > 0 else 1.5, 1.5, 1.5)
+    assert ctx.ncell == int(np.prod(O.grid_dims(box, edges))) and ctx.ncell % 4096 != 0 and ctx.ncell > 4 * 4096
+    cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, pts, None, D.DCM_PREC_MIXED))
+    oc, _, ostart, operm = O.bin_particles(pts, box, edges)
+    assert np.array_equal(cell, oc) and np.array_equal(start, ostart) and np.array_equal(perm, operm)
+    assert D.dcm_status(ctx) == D.DCM_OK
+
+
+def test_scan_wait_runs_out_and_the_context_stays_usable(D, slab_1935):
+    """The scan's look-back wait for a tile that never publishes runs out
+    with DCM_ERR_TIMEOUT (no fault, no hang); the same context then bins
+    bit-exactly."""
+    ctx = make_ctx(D, slab_1935.box, slab_1935.n)
+    assert D.dcm_scan_wait_selftest(ctx) == D.DCM_ERR_TIMEOUT
+    assert D.dcm_status(ctx) == D.DCM_OK
+    cell, start, perm, _ = gpu_bin(D, ctx, pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED))
+    oc, _, ostart, operm = O.bin_particles(slab_1935.pos, slab_1935.box, 1.5)
+    assert np.array_equal(cell, oc) and np.array_equal(start, ostart) and np.array_equal(perm, operm)
+
+
 def test_capacity_error(D, slab_1935):
     ctx = make_ctx(D, slab_1935.box, 100)
     pos4 = pos4_of(D, slab_1935.pos, None, D.DCM_PREC_MIXED)
@@ -597,13 +630,17 @@ def test_step_mixed_on_shared_inputs(D, slab_1935):
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_step_batched_call_equals_single_calls(D, slab_1935, prec):
     # one call of 12 steps (the second half kicks fused into the next steps'
-    # kick-drift, thermo of the last step only) == 12 calls of one step, bit for bit
+    # kick-drift, thermo of the last step only, and in the mixed form force-only
+    # evaluations before it) == 12 calls of one step, bit for bit, forces and
+    # per-particle energies of the last step included
     P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
     _, st1, th1 = run_gpu_steps(D, slab_1935, P, 12, K=5, per_step=True)
     _, st2, th2 = run_gpu_steps(D, slab_1935, P, 12, K=5, per_step=False)
     assert np.array_equal(th1[-1], th2[-1])
     assert torch.equal(st1.current()[0], st2.current()[0])
     assert torch.equal(st1.current()[1], st2.current()[1])
+    assert torch.equal(st1.force, st2.force)
+    assert abs(st2.force[:, 3].double().sum().item() - th2[-1][0]) <= 1e-6 * abs(th2[-1][0])
 
 
 def test_jobs_on_two_states_and_a_copy_stream(D, slab_1935):
