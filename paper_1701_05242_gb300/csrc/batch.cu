@@ -130,13 +130,13 @@ __global__ void k_b_cutoffs(int64_t n, const typename RT<R>::R4* __restrict__ po
   if (i < n) b_cutoffs<R>(i, pos, D, geom, rep, h, r_grid, rc_min, rc_max, ramp, rc);
 }
 
-template <typename R, bool TYPED, bool X2, Accum M>
+template <typename R, bool TYPED, bool X2, Accum M, bool EW = true>
 __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
                            const int32_t* __restrict__ start, ForceArgs<R> a, const RepGeom* __restrict__ geom,
                            const uint16_t* __restrict__ rep, typename RT<R>::R4* __restrict__ force,
                            R* __restrict__ w_i, int32_t* __restrict__ np_i) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b_force<R, TYPED, X2, M>(i, pos, rc, start, a, geom, rep, force, w_i, np_i);
+  if (i < n) b_force<R, TYPED, X2, M, true, EW>(i, pos, rc, start, a, geom, rep, force, w_i, np_i);
 }
 
 template <typename R>
@@ -246,7 +246,7 @@ int batch_accumulation(const dcm_batch* b) {
 }
 
 template <typename R>
-static auto b_force_kernel(bool typed, int ntypes, int acc) {
+static auto b_force_kernel(bool typed, int ntypes, int acc, bool energies) {
   using K = void (*)(int64_t, const typename RT<R>::R4*, const R*, const int32_t*, ForceArgs<R>, const RepGeom*,
                      const uint16_t*, typename RT<R>::R4*, R*, int32_t*);
   if constexpr (sizeof(R) == 8) {
@@ -255,8 +255,9 @@ static auto b_force_kernel(bool typed, int ntypes, int acc) {
     const bool x2 = !(typed && ntypes > 2);
     auto pick = [&](auto tag) -> K {
       constexpr Accum M = decltype(tag)::value;
-      if (!x2) return (K)k_b_forces<R, true, false, M>;
-      return typed ? (K)k_b_forces<R, true, true, M> : (K)k_b_forces<R, false, true, M>;
+      if (!x2) return (K)k_b_forces<R, true, false, M>;  // the scalar loop always sums energy and virial
+      if (energies) return typed ? (K)k_b_forces<R, true, true, M> : (K)k_b_forces<R, false, true, M>;
+      return typed ? (K)k_b_forces<R, true, true, M, false> : (K)k_b_forces<R, false, true, M, false>;
     };
     if (acc == DCM_ACC_FP32) return pick(AccumTag<Accum::kPlain>{});
     if (acc == DCM_ACC_PLANE_FP64) return pick(AccumTag<Accum::kPlaneF64>{});
@@ -265,8 +266,11 @@ static auto b_force_kernel(bool typed, int ntypes, int acc) {
 }
 
 template <typename R>
+// Forces, second half kick and (with energies) the per-replica thermo; without
+// energies the timestep's forces alone (a timestep whose thermo nothing reads).
 static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R* rc, typename RT<R>::R4* force,
-                           typename RT<R>::R4* vel, R half_dt, bool kick, double* thermo, cudaStream_t st) {
+                           typename RT<R>::R4* vel, R half_dt, bool kick, double* thermo, cudaStream_t st,
+                           bool energies = true) {
   dcm_ctx* ctx = &b->base;
   int64_t n = b->ntot;
   if (n > 0) {
@@ -275,19 +279,21 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     int bs = b->force_block;
     // the packed loop in FP32 for one type, and for one or two types with
     // their own eps and sigma; the scalar loop otherwise
-    auto kern = b_force_kernel<R>(lj_general(t), t.ntypes, batch_accumulation(b));
+    auto kern = b_force_kernel<R>(lj_general(t), t.ntypes, batch_accumulation(b), energies);
     stage_begin(ctx, DCM_STAGE_FORCES, st);
     DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
                b->rep_of_particle, force, (R*)b->w_i, b->np_i);
     stage_end(ctx, DCM_STAGE_FORCES, st);
     stage_begin(ctx, DCM_STAGE_KICK, st);
     DCM_LAUNCH(ctx, k_b_kick<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, vel, kick ? force : nullptr, half_dt,
-               (R*)b->ke_i);
-    if (b->nchunk > 0)
-      DCM_LAUNCH(ctx, k_b_thermo_chunks<R>, (unsigned)b->nchunk, 256, 0, st, b->chunk, b->nchunk, force,
-                 (const R*)b->w_i, (const R*)b->ke_i, b->np_i, b->tpart);
-    DCM_LAUNCH(ctx, k_b_thermo_sum, (unsigned)((b->R + 7) / 8), 256, 0, st, b->chunk0, b->R, b->nchunk, b->tpart,
-               thermo);
+               energies ? (R*)b->ke_i : nullptr);
+    if (energies) {
+      if (b->nchunk > 0)
+        DCM_LAUNCH(ctx, k_b_thermo_chunks<R>, (unsigned)b->nchunk, 256, 0, st, b->chunk, b->nchunk, force,
+                   (const R*)b->w_i, (const R*)b->ke_i, b->np_i, b->tpart);
+      DCM_LAUNCH(ctx, k_b_thermo_sum, (unsigned)((b->R + 7) / 8), 256, 0, st, b->chunk0, b->R, b->nchunk, b->tpart,
+                 thermo);
+    }
     stage_end(ctx, DCM_STAGE_KICK, st);
   }
   return check_launch(ctx, "batch forces");
@@ -324,7 +330,7 @@ template <typename R>
 static int b_init(dcm_batch* b, dcm_state* s, cudaStream_t st) {
   using R4 = typename RT<R>::R4;
   if (b->persistent) {
-    int r = b_persistent_step<R>(b, s, (R)0, (R)0, false, true, false, st);
+    int r = b_persistent_step<R>(b, s, (R)0, (R)0, false, true, false, true, st);
     if (r) return r;
     s->cur = 1 - s->cur;
     s->t = 0;
@@ -348,9 +354,12 @@ static int b_steps(dcm_batch* b, dcm_state* s, double dt, int nsteps, cudaStream
   R hdt = (R)(0.5 * dt), rdt = (R)dt;
   int K = b->p.recompute_every;
   for (int k = 0; k < nsteps; ++k) {
+    // energy, virial and thermo only on the call's last timestep (the only
+    // one whose thermo is read)
+    const bool last = k == nsteps - 1;
     if (b->persistent) {
       s->t += 1;
-      int r = b_persistent_step<R>(b, s, hdt, rdt, true, s->t % K == 0, true, st);
+      int r = b_persistent_step<R>(b, s, hdt, rdt, true, s->t % K == 0, true, last, st);
       if (r) return r;
       s->cur = 1 - s->cur;
       continue;
@@ -362,7 +371,7 @@ static int b_steps(dcm_batch* b, dcm_state* s, double dt, int nsteps, cudaStream
     if (s->t % K == 0)
       if ((r = b_recompute<R>(b, (const R4*)s->pos[o], (R*)s->rc[o], st))) return r;
     if ((r = b_forces_thermo<R>(b, (const R4*)s->pos[o], (const R*)s->rc[o], (R4*)s->force, (R4*)s->vel[o], hdt,
-                                true, s->thermo, st)))
+                                true, s->thermo, st, last)))
       return r;
     s->cur = o;
   }

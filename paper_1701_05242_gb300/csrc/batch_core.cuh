@@ -431,7 +431,9 @@ __device__ __forceinline__ void b_cutoffs(int64_t i, const typename RT<R>::R4* _
 // NC: positions and cell starts through the read-only path (the per-stage
 // kernel); the persistent kernel wrote them earlier in its launch and reads
 // them with ordinary loads.
-template <typename R, bool TYPED, bool X2, Accum M, bool NC = true>
+// Without EW (the packed loop only): the force alone, no energy, virial or
+// pair count (w_i and np_i are not written).
+template <typename R, bool TYPED, bool X2, Accum M, bool NC = true, bool EW = true>
 __device__ __forceinline__ void b_force(int64_t i, const typename RT<R>::R4* __restrict__ pos,
                                         const R* __restrict__ rc, const int32_t* __restrict__ start,
                                         const ForceArgs<R>& a, const RepGeom* __restrict__ geom,
@@ -441,9 +443,11 @@ __device__ __forceinline__ void b_force(int64_t i, const typename RT<R>::R4* __r
   Grid<R> g = rep_cells<R>(G, a.g.edge, a.g.inv_edge, a.g.edge_x, a.g.inv_edge_x);
   double e = 0, w = 0;
   int np = 0;
-  force[i] = force_one<R, TYPED, X2, M, NC>(pos, start + G.c0, g, a, (int)i, ld_pos<NC>(pos + i), rc[i], e, w, np);
-  w_i[i] = (R)w;
-  np_i[i] = np;
+  force[i] = force_one<R, TYPED, X2, M, NC, EW>(pos, start + G.c0, g, a, (int)i, ld_pos<NC>(pos + i), rc[i], e, w, np);
+  if constexpr (EW) {
+    w_i[i] = (R)w;
+    np_i[i] = np;
+  }
 }
 
 template <typename R>
@@ -458,7 +462,7 @@ __device__ __forceinline__ void b_kick(int64_t i, typename RT<R>::R4* __restrict
     v.z += half_dt * f.z;
     vel[i] = v;
   }
-  ke_i[i] = (R)0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
+  if (ke_i) ke_i[i] = (R)0.5 * (v.x * v.x + v.y * v.y + v.z * v.z);
 }
 
 // Sums (E, W, KE, pairs) of chunk c by the whole block, in FP64 and a fixed
@@ -515,7 +519,7 @@ ForceArgs<R> batch_force_args(const dcm_batch* b);
 // buffer 1 - s->cur (the caller flips cur).
 template <typename R>
 int b_persistent_step(dcm_batch* b, dcm_state* s, R hdt, R dt, bool drift, bool recompute, bool kick,
-                      cudaStream_t st);
+                      bool energies, cudaStream_t st);
 // The accumulation form of the batched force stage (DCM_ACC_FP32,
 // DCM_ACC_PLANE_FP64 or DCM_ACC_PLANE_KAHAN).
 int batch_accumulation(const dcm_batch* b);

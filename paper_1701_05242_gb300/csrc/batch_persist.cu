@@ -214,7 +214,9 @@ __device__ __forceinline__ int block_sum_int(int v) {
   return total;
 }
 
-template <int PART, typename R, bool TYPED, bool X2, Accum M>
+// EW (part 1): the forces sum energy and virial and the thermo stages run
+// (the last timestep of a call); otherwise the forces alone and the kick.
+template <int PART, typename R, bool TYPED, bool X2, Accum M, bool EW>
 __global__ void __launch_bounds__(kPBlock, (p_blocks<PART, R, TYPED>())) k_b_step_persistent(PArgs<R> a) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
@@ -357,18 +359,22 @@ __global__ void __launch_bounds__(kPBlock, (p_blocks<PART, R, TYPED>())) k_b_ste
       const int2 item = a.tiles[t];
       const int64_t end = min((int64_t)item.y + a.tile, a.geom[item.x].p1);
       for (int64_t i = (int64_t)item.y + lane; i < end; i += 32)
-        b_force<R, TYPED, X2, M, true>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i, a.np_i);
+        b_force<R, TYPED, X2, M, true, EW>(i, a.pos_o, a.rc_o, a.start, a.fa, a.geom, a.rep_p, a.force, a.w_i,
+                                           a.np_i);
     }
     PSYNC();
     PSTAGE(DCM_STAGE_FORCES);
     // ---- second half kick, kinetic energy, per-replica thermo
-    for (int64_t i = gt; i < a.n; i += gs) b_kick<R>(i, a.vel_o, a.kick ? a.force : nullptr, a.hdt, a.ke_i);
-    PSYNC();
-    for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
-      b_thermo_chunk<R>(c, a.chunk, a.nchunk, a.force, a.w_i, a.ke_i, a.np_i, a.tpart);
-    PSYNC();
-    const int64_t warp = gt >> 5, nwarp = gs >> 5;
-    for (int64_t r = warp; r < a.nrep; r += nwarp) b_thermo_sum((int)r, a.chunk0, a.nchunk, a.tpart, a.thermo);
+    for (int64_t i = gt; i < a.n; i += gs)
+      b_kick<R>(i, a.vel_o, a.kick ? a.force : nullptr, a.hdt, EW ? a.ke_i : nullptr);
+    if constexpr (EW) {
+      PSYNC();
+      for (int c = blockIdx.x; c < a.nchunk; c += gridDim.x)
+        b_thermo_chunk<R>(c, a.chunk, a.nchunk, a.force, a.w_i, a.ke_i, a.np_i, a.tpart);
+      PSYNC();
+      const int64_t warp = gt >> 5, nwarp = gs >> 5;
+      for (int64_t r = warp; r < a.nrep; r += nwarp) b_thermo_sum((int)r, a.chunk0, a.nchunk, a.tpart, a.thermo);
+    }
     // the kick's time: up to the last barrier (the thermo sums of the last
     // warps are not waited for)
     PSTAGE(DCM_STAGE_KICK);
@@ -387,9 +393,9 @@ namespace {
 
 // One cooperative launch of part PART over as many blocks as are resident
 // (at most the part's cap per SM); the barrier words start cleared.
-template <int PART, typename R, bool TYPED, bool X2, Accum M>
+template <int PART, typename R, bool TYPED, bool X2, Accum M, bool EW>
 int launch_part(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
-  auto kern = k_b_step_persistent<PART, R, TYPED, X2, M>;
+  auto kern = k_b_step_persistent<PART, R, TYPED, X2, M, EW>;
   int per_sm = 0, sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -415,26 +421,32 @@ int launch_part(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
   return DCM_OK;
 }
 
-// part 0 (binning, recomputation), then part 1 (forces, kick, thermo)
+// part 0 (binning, recomputation), then part 1 (forces, kick, thermo); the
+// scalar loop (X2 false) always sums energy and virial
 template <typename R, bool TYPED, bool X2, Accum M>
-int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
-  int r = launch_part<0, R, TYPED, X2, M>(b, a, st);
-  return r != DCM_OK ? r : launch_part<1, R, TYPED, X2, M>(b, a, st);
+int launch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st, bool energies) {
+  int r = launch_part<0, R, TYPED, X2, M, true>(b, a, st);
+  if (r != DCM_OK) return r;
+  if constexpr (X2) {
+    if (!energies) return launch_part<1, R, TYPED, X2, M, false>(b, a, st);
+  }
+  return launch_part<1, R, TYPED, X2, M, true>(b, a, st);
 }
 
 template <typename R>
-int dispatch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st) {
+int dispatch_persistent(dcm_batch* b, const PArgs<R>& a, cudaStream_t st, bool energies) {
   const LJTable t = lj_table(b->p);
   const bool typed = lj_general(t);
   if constexpr (sizeof(R) == 8) {
-    return typed ? launch_persistent<R, true, false, Accum::kPlain>(b, a, st)
-                 : launch_persistent<R, false, false, Accum::kPlain>(b, a, st);
+    return typed ? launch_persistent<R, true, false, Accum::kPlain>(b, a, st, energies)
+                 : launch_persistent<R, false, false, Accum::kPlain>(b, a, st, energies);
   } else {
     const bool x2 = !(typed && t.ntypes > 2);
     auto go = [&](auto tag) {
       constexpr Accum M = decltype(tag)::value;
-      if (!x2) return launch_persistent<R, true, false, M>(b, a, st);
-      return typed ? launch_persistent<R, true, true, M>(b, a, st) : launch_persistent<R, false, true, M>(b, a, st);
+      if (!x2) return launch_persistent<R, true, false, M>(b, a, st, energies);
+      return typed ? launch_persistent<R, true, true, M>(b, a, st, energies)
+                   : launch_persistent<R, false, true, M>(b, a, st, energies);
     };
     const int acc = batch_accumulation(b);
     if (acc == DCM_ACC_FP32) return go(AccumTag<Accum::kPlain>{});
@@ -488,7 +500,7 @@ int b_persistent_set_tile(dcm_batch* b, int tile) {
 
 template <typename R>
 int b_persistent_step(dcm_batch* b, dcm_state* s, R hdt, R dt, bool drift, bool recompute, bool kick,
-                      cudaStream_t st) {
+                      bool energies, cudaStream_t st) {
   using R4 = typename RT<R>::R4;
   dcm_ctx* ctx = &b->base;
   const dcm_params& p = b->p;
@@ -566,12 +578,12 @@ int b_persistent_step(dcm_batch* b, dcm_state* s, R hdt, R dt, bool drift, bool 
   a.phantom = 0;
   a.pacc = b->base.timing ? b->pacc : nullptr;
   if (b->ntot == 0) return DCM_OK;
-  int r = dispatch_persistent<R>(b, a, st);
+  int r = dispatch_persistent<R>(b, a, st, energies);
   return r ? r : check_launch(ctx, "persistent step");
 }
 
-template int b_persistent_step<float>(dcm_batch*, dcm_state*, float, float, bool, bool, bool, cudaStream_t);
-template int b_persistent_step<double>(dcm_batch*, dcm_state*, double, double, bool, bool, bool, cudaStream_t);
+template int b_persistent_step<float>(dcm_batch*, dcm_state*, float, float, bool, bool, bool, bool, cudaStream_t);
+template int b_persistent_step<double>(dcm_batch*, dcm_state*, double, double, bool, bool, bool, bool, cudaStream_t);
 
 int b_persistent_wait_selftest(dcm_batch* b, int32_t phantom, int64_t budget_ns, cudaStream_t st) {
   int r = b_persistent_setup(b);
