@@ -692,10 +692,14 @@ def run_gb300(args):
             ul, tl = aggregate(dist, float(n) * kl * K_RECOMPUTE, msl / 1000.0)
             lf_ms, lf_cnt = lst["forces"]
             lf_avg = lf_ms / max(lf_cnt, 1)
+            # the list kernels sum energy and virial on every timestep
+            l_ew = lf_cnt
+            l_ipp = (FLOP_PER_PAIR * l_ew + FLOP_PER_PAIR_FORCES * (lf_cnt - l_ew)) / max(lf_cnt, 1)
             rec = {"value": ul / tl, "unit": UNIT, "steps": kl, "ms_per_step": msl / kl, "skin": LIST_SKIN,
                    "force_kernel": "k_forces_list_n3" if newton3 else "k_forces_list_x2",
                    "force_avg_launch_ms": lf_avg,
-                   "force_frac_fp32": pl * FLOP_PER_PAIR / (lf_avg / 1000.0) / 1e12 / peak_tinstr if lf_avg > 0 else None,
+                   "force_frac_fp32": pl * l_ipp / (lf_avg / 1000.0) / 1e12 / peak_tinstr if lf_avg > 0 else None,
+                   "instr_per_pair": l_ipp,
                    "list_builds": int(lst["lists"][1]), "build_avg_ms": lst["lists"][0] / max(lst["lists"][1], 1),
                    "stage_ms_per_step": {k: v[0] / kl for k, v in lst.items()}, "pairs_last": pl,
                    "note": ("half lists kept by the larger-cutoff particle, each pair evaluated once and scattered "

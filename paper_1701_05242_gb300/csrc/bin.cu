@@ -83,19 +83,27 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_lookback(const int32_t* __r
   __syncthreads();
   const int64_t t = tile_sh;
   const int64_t base = t * kScanTile + (int64_t)threadIdx.x * kScanItems;
-  static_assert(kScanItems == 4, "four items per thread");
+  static_assert(kScanItems % 4 == 0, "whole 16-byte groups per thread");
+  constexpr int kQ = kScanItems / 4;
   const bool vec = ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0;
-  int4 v = make_int4(0, 0, 0, 0);
-  if (vec && base + 4 <= n) {
-    v = *reinterpret_cast<const int4*>(in + base);
-  } else if (base < n) {
-    v.x = in[base];
-    v.y = base + 1 < n ? in[base + 1] : 0;
-    v.z = base + 2 < n ? in[base + 2] : 0;
-    v.w = base + 3 < n ? in[base + 3] : 0;
+  int4 v[kQ];
+  int sum = 0;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int64_t b = base + 4 * q;
+    v[q] = make_int4(0, 0, 0, 0);
+    if (vec && b + 4 <= n) {
+      v[q] = *reinterpret_cast<const int4*>(in + b);
+    } else if (b < n) {
+      v[q].x = in[b];
+      v[q].y = b + 1 < n ? in[b + 1] : 0;
+      v[q].z = b + 2 < n ? in[b + 2] : 0;
+      v[q].w = b + 3 < n ? in[b + 3] : 0;
+    }
+    sum += v[q].x + v[q].y + v[q].z + v[q].w;
   }
   int total;
-  const int run = block_excl_scan(v.x + v.y + v.z + v.w, &total);
+  const int run = block_excl_scan(sum, &total);
   if (threadIdx.x < 32) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x;
@@ -130,15 +138,20 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_lookback(const int32_t* __r
     if (lane == 0) prefix_sh = prefix;
   }
   __syncthreads();
-  const int ex = prefix_sh + run;
-  const int4 o = make_int4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
-  if (vec && base + 4 <= n) {
-    *reinterpret_cast<int4*>(out + base) = o;
-  } else if (base < n) {
-    out[base] = o.x;
-    if (base + 1 < n) out[base + 1] = o.y;
-    if (base + 2 < n) out[base + 2] = o.z;
-    if (base + 3 < n) out[base + 3] = o.w;
+  int ex = prefix_sh + run;
+#pragma unroll
+  for (int q = 0; q < kQ; ++q) {
+    const int64_t b = base + 4 * q;
+    const int4 o = make_int4(ex, ex + v[q].x, ex + v[q].x + v[q].y, ex + v[q].x + v[q].y + v[q].z);
+    if (vec && b + 4 <= n) {
+      *reinterpret_cast<int4*>(out + b) = o;
+    } else if (b < n) {
+      out[b] = o.x;
+      if (b + 1 < n) out[b + 1] = o.y;
+      if (b + 2 < n) out[b + 2] = o.z;
+      if (b + 3 < n) out[b + 3] = o.w;
+    }
+    ex = o.w + v[q].w;
   }
   if (t == ntiles - 1 && threadIdx.x == 0) out[n] = prefix_sh + total;
 }

@@ -159,8 +159,8 @@ struct dcm_ctx {
 namespace dcm {
 
 constexpr int kHistCap = 1 << 20;
-constexpr int kScanBlock = 1024;       // threads of the scan kernels
-constexpr int kScanItems = 4;          // items per thread
+constexpr int kScanBlock = 512;        // threads of the scan kernel (two blocks per SM at its registers)
+constexpr int kScanItems = 16;         // items per thread (four 16-byte loads)
 constexpr int kScanTile = kScanBlock * kScanItems;
 
 int set_error(dcm_ctx* ctx, int code, const char* fmt, ...);
@@ -241,9 +241,11 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
 // verlet.cu
 template <typename R>
 int list_build(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, cudaStream_t st);
+// energies: whether the caller reads energy and virial (the list kernels sum
+// them in any case).
 template <typename R>
 int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* rc, typename RT<R>::R4* force,
-                double* totals, cudaStream_t st);
+                double* totals, cudaStream_t st, bool energies = true);
 template <typename R>
 int list_kick_drift(dcm_ctx* ctx, dcm_state* s, int64_t n, R hdt, R dt, int kicks, bool* rebuild, cudaStream_t st);
 template <typename R>

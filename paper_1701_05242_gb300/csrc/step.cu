@@ -214,7 +214,7 @@ static int step_run_lists(dcm_ctx* ctx, dcm_state* st, int64_t n, double dt, int
     }
     int c = st->cur;
     if ((r = list_forces<R>(ctx, n, (const R4*)st->pos[c], (const R*)st->rc[c], (R4*)st->force,
-                            last ? ctx->totals : nullptr, s)))
+                            last ? ctx->totals : nullptr, s, last)))
       return r;
     if (last) {
       stage_begin(ctx, DCM_STAGE_KICK, s);

@@ -134,7 +134,7 @@ def test_bin_edges_and_empty(D):
 
 @pytest.mark.parametrize("lx", [0.0, 0.5])
 def test_bin_many_scan_tiles(D, lx):
-    """Binning whose cell-count scan spans several look-back tiles of 4,096
+    """Binning whose cell-count scan spans several look-back tiles of 8,192
     cells with a ragged last tile (24,000 and 72,000 cells), with uniform
     particles, a dense clump in one cell and empty regions: cells, starts and
     order bit-exact against the oracle."""
@@ -146,7 +146,7 @@ def test_bin_many_scan_tiles(D, lx):
     pts = np.concatenate([uni, clump, half]).astype(np.float32)
     ctx = make_ctx(D, box, len(pts), lx=lx)
     edges = (lx if lx > 0 else 1.5, 1.5, 1.5)
-    assert ctx.ncell == int(np.prod(O.grid_dims(box, edges))) and ctx.ncell % 4096 != 0 and ctx.ncell > 4 * 4096
+    assert ctx.ncell == int(np.prod(O.grid_dims(box, edges))) and ctx.ncell % 8192 != 0 and ctx.ncell > 2 * 8192
     cell, start, perm, ps = gpu_bin(D, ctx, pos4_of(D, pts, None, D.DCM_PREC_MIXED))
     oc, _, ostart, operm = O.bin_particles(pts, box, edges)
     assert np.array_equal(cell, oc) and np.array_equal(start, ostart) and np.array_equal(perm, operm)
