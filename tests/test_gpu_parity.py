@@ -132,17 +132,18 @@ def test_bin_edges_and_empty(D):
     assert start.max() == 0 and start.shape[0] == ctx.ncell + 1
 
 
-@pytest.mark.parametrize("lx", [0.0, 0.5])
-def test_bin_many_scan_tiles(D, lx):
+@pytest.mark.parametrize("box,lx", [((60.0, 45.0, 30.0), 0.0), ((60.0, 45.0, 30.0), 0.5), ((61.5, 45.0, 31.5), 0.0)])
+def test_bin_many_scan_tiles(D, box, lx):
     """Binning whose cell-count scan spans several look-back tiles of 8,192
-    cells with a ragged last tile (24,000 and 72,000 cells), with uniform
-    particles, a dense clump in one cell and empty regions: cells, starts and
-    order bit-exact against the oracle."""
-    box = (60.0, 45.0, 30.0)
+    cells with a ragged last tile (24,000, 72,000 and 25,830 cells, the last
+    not a multiple of a thread's 16 cells nor of 4), with uniform particles,
+    a dense clump in one cell and empty regions: cells, starts and order
+    bit-exact against the oracle."""
     rng = np.random.default_rng(11)
     uni = rng.random((40000, 3)) * np.array(box)
     clump = np.array([30.2, 20.1, 10.3]) + rng.random((700, 3)) * 0.2
     half = rng.random((9000, 3)) * np.array([30.0, 45.0, 15.0])
+    uni = np.minimum(uni, np.nextafter(np.array(box, np.float32), np.float32(0)))
     pts = np.concatenate([uni, clump, half]).astype(np.float32)
     ctx = make_ctx(D, box, len(pts), lx=lx)
     edges = (lx if lx > 0 else 1.5, 1.5, 1.5)
