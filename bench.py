@@ -261,7 +261,8 @@ def gpu_config(args, slab, world=1):
     return {"workload": args.workload, "particles_per_gpu": slab.n, "box": list(slab.box),
             "rc_min": 3.0, "rc_max": 6.0, "h": 1.5, "l": args.cell_edge,
             "lx": args.cell_edge_x if args.cell_edge_x > 0 else args.cell_edge, "skin": args.skin, "dt": DT,
-            "recompute_every": K_RECOMPUTE, "l2": f"inputs larger than L2 (positions {16 * slab.n / 1e6:.0f} MB)",
+            "recompute_every": K_RECOMPUTE, "thermo_every": K_RECOMPUTE,
+            "l2": f"inputs larger than L2 (positions {16 * slab.n / 1e6:.0f} MB)",
             "parallelism": f"replicas x{world}"}
 
 
@@ -503,6 +504,21 @@ def run_gb300(args):
     units = float(n) * args.steps * K_RECOMPUTE
     tot_units, secs = aggregate(dist, units, ms / 1000.0)
     value = tot_units / secs
+
+    # the same path with energy, virial and thermo on every timestep (one
+    # dcm_step call per timestep), for comparison with the headline's
+    # thermo once per call of K timesteps
+    kt = 2 * K_RECOMPUTE
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for _ in range(kt):
+        D.dcm_step(ctx, st, DT, 1)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ue1, te1 = aggregate(dist, float(n) * kt, t0.elapsed_time(t1) / 1000.0)
+    every_ts = {"value": ue1 / te1, "unit": UNIT, "timesteps": kt,
+                "note": "one dcm_step call per timestep: energy, virial and thermo every timestep"}
 
     # roofline of the dominant kernel (forces): FP32-pipe instructions
     f_ms, f_cnt = stages["forces"]
@@ -750,7 +766,7 @@ def run_gb300(args):
                "precision": f"fp32 pair math, per-particle sums {acc_name} "
                             f"({ACC_DESCR.get(acc_name, acc_name)}), fp64 totals",
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "stage_ms_per_step": stage_ms, "step_roofline": step_roof,
+               "stage_ms_per_step": stage_ms, "step_roofline": step_roof, "thermo_every_timestep": every_ts,
                "accumulation_forms": acc_forms, "fp64_form": fp64, "lists_form": lists, "lists_newton3_form": lists_n3, "batched_form": batch,
                "adjoint_form": adjoint, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
