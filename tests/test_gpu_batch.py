@@ -215,6 +215,27 @@ def test_persistent_plan_equals_per_stage_plan(D, replicas, prec, lx):
     assert ls > 10 * nsteps
 
 
+@pytest.mark.parametrize("persistent", [True, False])
+def test_batch_call_of_several_steps_equals_single_steps(D, replicas, persistent):
+    """One call of several timesteps (forces only before its last timestep:
+    no energy, virial or thermo stages) leaves the state, the forces with
+    their per-particle energies, and the per-replica thermo bit-identical to
+    the same timesteps taken one call each (energy and thermo every time)."""
+    P = D.DCM_PREC_MIXED
+    nsteps = K + 2
+    a, tha, _, _ = _run_plan(D, replicas, P, persistent, nsteps)
+    b, st = batch_state(D, replicas, P)
+    D.dcm_batch_set_persistent(b, persistent)
+    D.dcm_batch_step_init(b, st)
+    for _ in range(nsteps):
+        D.dcm_batch_step(b, st, DT, 1)
+    assert D.dcm_batch_status(b) == D.DCM_OK
+    pos, vel, rc, ids = st.current()
+    for x, y in zip(a, [t.cpu().numpy() for t in (pos, vel, rc, ids, st.force)]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(tha, st.thermo.cpu().numpy().reshape(-1, 4))
+
+
 def test_persistent_plan_two_types_and_accumulation_forms(D):
     """Two types on the packed typed loop, each batched accumulation form."""
     reps = []
