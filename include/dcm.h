@@ -389,7 +389,9 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
  * validated as a single system (dcm_validate_params).  The state arrays of
  * dcm_state are the concatenation of the replicas: replica r owns slots
  * [offset[r], offset[r+1]) (dcm_batch_offsets) and its particles stay there;
- * thermo is double[4 R] = {E, W, KE, pairs} per replica.  By default a whole
+ * thermo is double[4 R] = {E, W, KE, pairs} per replica, of the last
+ * timestep of a dcm_batch_step call (the timesteps before it evaluate forces
+ * only and run no thermo stage).  By default a whole
  * timestep of all replicas is two persistent cooperative launches (the
  * persistent plan): binning and recomputation, then forces, kick and thermo;
  * the stages inside each are separated by grid-wide barriers, and the force
