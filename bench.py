@@ -74,6 +74,7 @@ def parse_args(argv=None):
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-lists", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--skip-interface", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=500)
     return ap.parse_args(argv)
 
@@ -382,6 +383,69 @@ def run_batch(args, D, dev):
            "speedup_over_plain_fp64": value / value64,
            "plans_direct_stepping": split,
            "device_status": status}
+    return out
+
+
+def run_interface_forms(args, D, dev, slab, ps):
+    """The interface stage's forms on the benchmark's box grid (16.4M density
+    boxes of 1.5 at 16M), from the box counts of the sorted positions ps:
+    the default 2-means threshold of the smoothed counts, the regularised
+    two-phase segmentation with its length term (Section 2.1; nu = 4, 200
+    inner and 4 outer iterations), and the default with the bubble filter
+    (components under 20 boxes removed); then the whole timestep on the
+    curved (cylindrical) interface workload.  CUDA events on the launching
+    stream, three repetitions each after one untimed."""
+    import torch
+    from paper_1701_05242_gb300 import synth
+    stream = torch.cuda.current_stream(dev)
+    n = ps.shape[0]
+    i32 = dict(dtype=torch.int32, device=dev)
+    out = {"boxes": None}
+    ref_s = None
+    for name, kw in (("two_means", {}), ("regularised", dict(segmentation=1, ms_nu=4.0, ms_inner=200, ms_outer=4)),
+                     ("bubble_filter", dict(min_component=20))):
+        p = D.make_params(slab.box, n_max=n, l=args.cell_edge, lx=args.cell_edge_x, **kw)
+        c = D.Context(p)
+        bc = torch.empty(c.nbox, **i32)
+        s = torch.empty(c.nbox, dtype=torch.uint8, device=dev)
+        iface = torch.empty_like(s)
+        thr = torch.empty(1, **i32)
+        D.dcm_box_counts(c, n, ps, bc)
+        D.dcm_detect_interface(c, bc, s, iface, thr)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(3):
+            D.dcm_detect_interface(c, bc, s, iface, thr)
+        ev1.record(stream)
+        ev1.synchronize()
+        rec = {"ms": ev0.elapsed_time(ev1) / 3, "interface_boxes": int(iface.sum().item()),
+               "device_status": D.dcm_status(c)}
+        if ref_s is None:
+            ref_s = s.clone()
+            out["boxes"] = int(c.nbox)
+        else:
+            rec["boxes_changed"] = int((s != ref_s).sum().item())
+        out[name] = rec
+        c.close()
+        del bc, s, iface
+    torch.cuda.empty_cache()
+    cyl = synth.make_slab(synth.named("cylinder_299k"))
+    p = D.make_params(cyl.box, n_max=cyl.n, recompute_every=K_RECOMPUTE, l=args.cell_edge, lx=args.cell_edge_x)
+    c = D.Context(p)
+    stc = D.State(c, D.to_real4(torch.from_numpy(cyl.pos), None, torch.float32, dev),
+                  D.to_real4(torch.from_numpy(cyl.vel), None, torch.float32, dev))
+    D.dcm_step_init(c, stc)
+    D.dcm_step(c, stc, DT, K_RECOMPUTE)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(5):
+        D.dcm_step(c, stc, DT, K_RECOMPUTE)
+    ev1.record(stream)
+    ev1.synchronize()
+    msc = ev0.elapsed_time(ev1)
+    out["cylinder_299k"] = {"value": cyl.n * 5 * K_RECOMPUTE / (msc / 1000.0), "unit": UNIT, "particles": cyl.n,
+                            "timesteps": 5 * K_RECOMPUTE, "device_status": D.dcm_status(c)}
+    c.close()
     return out
 
 
@@ -732,6 +796,14 @@ def run_gb300(args):
             torch.cuda.empty_cache()
         ctx, st = new_state(D.DCM_PREC_MIXED)
 
+    # ---------------- interface forms (f1, f2) on the same box grid
+    interface = None
+    if not args.skip_interface and rank == 0:
+        ps_i, _, _, _ = st.current()
+        interface = run_interface_forms(args, D, dev, slab, ps_i)
+        del ps_i
+        torch.cuda.empty_cache()
+
     # ---------------- batched form: 64 replicas, autotuned, graph-captured
     batch = adjoint = None
     if not args.skip_batch or not args.skip_adjoint:
@@ -768,7 +840,7 @@ def run_gb300(args):
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "stage_ms_per_step": stage_ms, "step_roofline": step_roof, "thermo_every_timestep": every_ts,
                "accumulation_forms": acc_forms, "fp64_form": fp64, "lists_form": lists, "lists_newton3_form": lists_n3, "batched_form": batch,
-               "adjoint_form": adjoint, "device_status": status,
+               "adjoint_form": adjoint, "interface_forms": interface, "device_status": status,
                "thermo_last": {"E": float(thermo[0]), "W": float(thermo[1]), "KE": float(thermo[2]),
                                "pairs": pairs}}
         print(json.dumps(out), flush=True)

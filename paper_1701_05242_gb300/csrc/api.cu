@@ -265,7 +265,7 @@ struct ScratchPlan {
   double skin;
   int32_t min_component, segmentation, ms_outer;
   int64_t total() const {
-    return 4 * 4 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 8 * (scan_cap + 1) + 3 * 4 * nbox + 2 * nbox +
+    return 4 * 4 + 16 + 3 * 4 * n_max + 4 * (ncell + 1) + 4 * ncell + 8 * (scan_cap + 1) + 3 * 4 * nbox + 2 * nbox +
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
            8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
            (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2) + 4 * nblk +
@@ -311,7 +311,7 @@ extern "C" const char* dcm_version(void) { return "dcm-gb300 0.1 (sm_103a)"; }
 // ---------------------------------------------------------------------------
 extern "C" void dcm_destroy(dcm_ctx* ctx) {
   if (!ctx) return;
-  void* dev[] = {ctx->status, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
+  void* dev[] = {ctx->status, ctx->coop_sync, ctx->slot,  ctx->cell,  ctx->perm,  ctx->cell_start, ctx->cell_count,
                  ctx->scan_state, ctx->box_count, ctx->g, ctx->g_tmp, ctx->s, ctx->iface,
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
                  ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
@@ -358,6 +358,7 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
     if (cudaMalloc(ptr, (size_t)(bytes > 0 ? bytes : 16)) != cudaSuccess) ok = false;
   };
   alloc((void**)&ctx->status, 16);
+  alloc((void**)&ctx->coop_sync, 16);
   alloc((void**)&ctx->slot, 4 * nm);
   alloc((void**)&ctx->cell, 4 * nm);
   alloc((void**)&ctx->perm, 4 * nm);

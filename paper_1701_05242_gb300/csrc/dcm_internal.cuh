@@ -92,6 +92,7 @@ struct dcm_ctx {
   char err[512];
   // device scratch
   int32_t* status;          // [4]: first device-side error code, ...
+  uint32_t* coop_sync;      // [4]: grid-barrier words of the cooperative distance sweeps
   int32_t* slot;            // n_max: rank of a particle inside its cell (atomics)
   int32_t* cell;            // n_max: cell of each particle (step)
   int32_t* perm;            // n_max

@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "dcm_internal.cuh"
+#include "grid_sync.cuh"
 
 namespace dcm {
 
@@ -77,18 +78,27 @@ __device__ __forceinline__ void dist_push(int64_t b, int x, int y, int z, int nx
   }
 }
 
+// Loads of the iterates: COH through L2 (__ldcg), for the cooperative sweep
+// kernel, whose blocks read what other blocks wrote earlier in the same
+// launch (behind a grid barrier); ordinary loads otherwise.
+template <typename R, bool COH>
+__device__ __forceinline__ R dld(const R* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
 // Update of one box from the previous iterate; true if it changed.
-template <typename R>
-__device__ __forceinline__ bool dist_update(const R* __restrict__ Din, R* __restrict__ Dout, int64_t b, int x, int y,
-                                            int z, int nx, int ny, int nz, R h, R r_grid) {
-  R cur = Din[b];
+template <typename R, bool COH = false>
+__device__ __forceinline__ bool dist_update(const R* Din, R* Dout, int64_t b, int x, int y, int z, int nx, int ny,
+                                            int nz, R h, R r_grid) {
+  R cur = dld<R, COH>(Din + b);
   int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
   int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
   int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
-  R a0 = fmin(Din[row + xm], Din[row + xp]);
-  R a1 = fmin(Din[x + nx * (ym + (int64_t)ny * z)], Din[x + nx * (yp + (int64_t)ny * z)]);
-  R a2 = fmin(Din[x + nx * (y + (int64_t)ny * zm)], Din[x + nx * (y + (int64_t)ny * zp)]);
+  R a0 = fmin(dld<R, COH>(Din + row + xm), dld<R, COH>(Din + row + xp));
+  R a1 = fmin(dld<R, COH>(Din + x + nx * (ym + (int64_t)ny * z)), dld<R, COH>(Din + x + nx * (yp + (int64_t)ny * z)));
+  R a2 = fmin(dld<R, COH>(Din + x + nx * (y + (int64_t)ny * zm)), dld<R, COH>(Din + x + nx * (y + (int64_t)ny * zp)));
   R d = godunov3<R>(a0, a1, a2, h);
   bool ch = d < cur && d <= r_grid;
   Dout[b] = ch ? d : cur;
@@ -136,6 +146,61 @@ __global__ void k_dist_sweep_queue(const R* __restrict__ Din, R* __restrict__ Do
     }
   }
   if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
+}
+
+// All sweeps in one cooperative launch (every block resident): sweep 0 over
+// the whole grid, then the queue sweeps, a bounded grid barrier after each,
+// until a sweep changes nothing or `budget` sweeps have run.  The same
+// iterates as one launch per sweep (bit for bit); the loop needs no host
+// check and launches nothing per sweep.  A barrier wait that runs past
+// budget_ns records DCM_ERR_TIMEOUT and ends the launch.
+template <typename R>
+__global__ void __launch_bounds__(256) k_dist_coop(R* D0, R* D1, int nx, int ny, int nz, R h, R r_grid,
+                                                   const uint8_t* __restrict__ fixed0, int32_t* stamp, int32_t* q0,
+                                                   int32_t* q1, int32_t* qlen, int32_t* flags, int budget,
+                                                   uint32_t* sync, int64_t budget_ns, int32_t* status) {
+  const unsigned full = 0xffffffffu;
+  const uint32_t expected = gridDim.x;
+  const int64_t nxy = (int64_t)nx * ny;
+  {
+    const int chunks = (nx + blockDim.x - 1) / blockDim.x;
+    const int64_t items = (int64_t)ny * nz * chunks;
+    bool changed = false;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+      const int yz = (int)(w / chunks);
+      const int x = (int)(w - (int64_t)yz * chunks) * blockDim.x + threadIdx.x;
+      if (x >= nx) continue;
+      const int y = yz % ny, z = yz / ny;
+      const int64_t b = x + (int64_t)nx * yz;
+      if (fixed0[b]) continue;
+      if (dist_update<R, true>(D0, D1, b, x, y, z, nx, ny, nz, h, r_grid)) {
+        changed = true;
+        dist_push(b, x, y, z, nx, ny, nz, fixed0, stamp, q1, qlen, 0);
+      }
+    }
+    if (__any_sync(full, changed) && (threadIdx.x & 31) == 0) flags[0] = 1;
+  }
+  if (!grid_sync(sync, expected, budget_ns, status)) return;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+  for (int it = 1; it < budget; ++it) {
+    if (((volatile int32_t*)flags)[it - 1] == 0) break;  // the previous sweep changed nothing
+    const R* Din = (it & 1) ? D1 : D0;
+    R* Dout = (it & 1) ? D0 : D1;
+    const int32_t* qin = (it & 1) ? q1 : q0;
+    int32_t* qout = (it & 1) ? q0 : q1;
+    const int32_t n = ((volatile int32_t*)qlen)[it];
+    bool changed = false;
+    for (int64_t k = gt; k < n; k += gs) {
+      const int64_t b = __ldcg(qin + k);
+      const int x = (int)(b % nx), y = (int)((b / nx) % ny), z = (int)(b / nxy);
+      if (dist_update<R, true>(Din, Dout, b, x, y, z, nx, ny, nz, h, r_grid)) {
+        changed = true;
+        dist_push(b, x, y, z, nx, ny, nz, fixed0, stamp, qout, qlen, it);
+      }
+    }
+    if (__any_sync(full, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
+    if (!grid_sync(sync, expected, budget_ns, status)) return;
+  }
 }
 
 // iters = 1 + index of the first sweep that changed nothing (or -1), and a
@@ -196,14 +261,33 @@ int distance_sweeps(dcm_ctx* ctx, const uint8_t* s, const uint8_t* iface, R* D, 
       return set_error(ctx, DCM_ERR_NOT_CONVERGED, "fast sweeping did not converge in %d sweeps", iter_max);
     }
   } else {
-    // fixed even budget (result ends in buf[0] = D).  Along a front the
-    // Godunov update can add arbitrarily little per box, so the sweep count is
-    // not bounded by r_grid / h; 8 r_grid / h + 8 leaves a wide margin over
-    // what wavy slab interfaces need (about 5 r_grid / h), and sweeps after
-    // convergence exit at once.
-    int budget = (int)std::ceil(8.0 * ctx->p.r_grid / ctx->p.h) + 8;
-    budget = std::min(budget + (budget & 1), iter_max + (iter_max & 1));
-    for (; done < budget; ++done) sweep(done);
+    // every sweep in one cooperative launch, until one changes nothing or
+    // the even budget iter_max (rounded up) runs out (the last iterate then
+    // in buf[0] = D); no host check
+    const int budget = iter_max + (iter_max & 1);
+    auto kern = k_dist_coop<R>;
+    int per_sm = 0, sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+      return set_error(ctx, DCM_ERR_CUDA, "distance sweeps: occupancy query failed");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(std::min(per_sm, 4) * sms));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->coop_sync, 0, 4 * sizeof(uint32_t), st));
+    ++ctx->launches;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, buf[0], buf[1], nx, ny, nz, h, rg, (const uint8_t*)ctx->dfixed,
+                                       ctx->dstamp, q[0], q[1], ctx->dqlen, ctx->flags, budget, ctx->coop_sync,
+                                       (int64_t)2000000000, ctx->status);
+    if (e != cudaSuccess) return set_error(ctx, DCM_ERR_CUDA, "distance sweeps: %s", cudaGetErrorString(e));
+    done = budget;
     DCM_LAUNCH(ctx, k_dist_finish, 1, 1, 0, st, ctx->flags, done, iters, ctx->status);
   }
   return check_launch(ctx, "distance_sweeps");

@@ -1059,6 +1059,34 @@ def test_cylinder_299k_step_on_shared_inputs(D):
     assert abs(th[0] - ref.E) <= EW_TOL * abs(ref.E)
     assert abs(th[1] - ref.W) <= EW_TOL * abs(ref.W)
     assert abs(int(th[3]) - ref.npairs) <= near_cutoff_pairs(pos, rcn, slab.box)
+    # the curved front takes more sweeps than a slab (the oracle's Jacobi:
+    # 75 on this grid); the step's sweeps run to convergence
+    assert D.dcm_status(ctx) == D.DCM_OK
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_step_sweeps_equal_the_host_checked_distance(D, prec):
+    """The cutoffs of dcm_step_init (all distance sweeps in one cooperative
+    launch, no host check) equal, bit for bit, those of the stage calls with
+    dcm_distance (one launch per sweep, host convergence check) on the same
+    sorted positions; the cylinder's curved front needs about 75 sweeps."""
+    P = D.DCM_PREC_MIXED if prec == "mixed" else D.DCM_PREC_FP64
+    real = real_of(D, P)
+    slab = synth.make_slab(synth.named("cylinder_299k"))
+    ctx = make_ctx(D, slab.box, slab.n, P, recompute_every=10)
+    st = D.State(ctx, pos4_of(D, slab.pos, None, P), D.to_real4(torch.from_numpy(slab.vel), None, real))
+    D.dcm_step_init(ctx, st)
+    assert D.dcm_status(ctx) == D.DCM_OK
+    pos, _, rc, _ = st.current()
+    _, _, _, s, iface = gpu_detect(D, ctx, pos)
+    Dg = torch.empty(ctx.nbox, dtype=real, device="cuda")
+    iters = torch.zeros(1, dtype=torch.int32, device="cuda")
+    D.dcm_distance(ctx, s, iface, Dg, iters)
+    assert int(iters.item()) > 40
+    rc2 = torch.empty_like(rc)
+    D.dcm_cutoffs(ctx, slab.n, pos, Dg, rc2)
+    torch.cuda.synchronize()
+    assert torch.equal(rc, rc2)
 
 
 # ------------------------------------------------------------------ edge cases
