@@ -11,9 +11,11 @@
 // previous sweep and their six neighbours — which are exactly the boxes
 // whose update can differ from the previous sweep's, so the iterates are
 // those of full Jacobi sweeps while the work follows the moving front (the
-// paper's queue Q).  A sweep whose queue is empty exits at once, so a fixed
-// budget of launches costs little once converged; the MPI_Allreduce of the
-// paper's version becomes the queue length in device memory.
+// paper's queue Q); the MPI_Allreduce of the paper's version becomes the
+// queue length in device memory.  dcm_distance launches one kernel per sweep
+// and checks convergence on the host every eight sweeps; the timestep runs
+// every sweep in one cooperative launch with a grid barrier between sweeps
+// (no host wait), until a sweep changes nothing or iter_max sweeps have run.
 #include <algorithm>
 
 #include "dcm_internal.cuh"
