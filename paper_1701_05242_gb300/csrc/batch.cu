@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "batch_core.cuh"
+#include "grid_sync.cuh"
 
 namespace dcm {
 
@@ -101,15 +102,27 @@ __global__ void k_b_dist_init(const uint8_t* __restrict__ s, const uint8_t* __re
   if (b < nbox) b_dist_init<R>(b, s, iface, D0, D1);
 }
 
+// All Jacobi sweeps of every replica in one cooperative launch (every block
+// resident): a bounded grid barrier after each sweep, until a sweep changes
+// nothing or `budget` sweeps have run (the same iterates as one launch per
+// sweep).  A barrier wait past budget_ns records DCM_ERR_TIMEOUT.
 template <typename R>
-__global__ void k_b_dist_sweep(const R* __restrict__ Din, R* __restrict__ Dout, int64_t nbox,
-                               const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep, R h, R r_grid,
-                               int32_t* __restrict__ flags, int it) {
-  if (it > 0 && flags[it - 1] == 0) return;
-  bool changed = false;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += (int64_t)gridDim.x * blockDim.x)
-    changed |= b_dist_update<R>(b, Din, Dout, geom, rep, h, r_grid);
-  if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
+__global__ void __launch_bounds__(256) k_b_dist_coop(R* D0, R* D1, int64_t nbox, const RepGeom* __restrict__ geom,
+                                                     const uint16_t* __restrict__ rep, R h, R r_grid, int32_t* flags,
+                                                     int budget, uint32_t* sync, int64_t budget_ns, int32_t* status) {
+  const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+  for (int it = 0; it < budget; ++it) {
+    if (it > 0 && ((volatile int32_t*)flags)[it - 1] == 0) break;  // the previous sweep changed nothing
+    const R* Din = (it & 1) ? D1 : D0;
+    R* Dout = (it & 1) ? D0 : D1;
+    bool changed = false;
+    for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < nbox; k0 += gs) {
+      const int64_t k = k0 + threadIdx.x;
+      if (k < nbox) changed |= b_dist_update<R, true>(k, Din, Dout, geom, rep, h, r_grid);
+    }
+    if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) flags[it] = 1;
+    if (!grid_sync(sync, gridDim.x, budget_ns, status)) return;
+  }
 }
 
 __global__ void k_b_dist_finish(const int32_t* flags, int sweeps, int32_t* status) {
@@ -197,13 +210,35 @@ static int b_recompute(dcm_batch* b, const typename RT<R>::R4* pos, R* rc, cudaS
   R* D1 = (R*)ctx->D[1];
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(int32_t) * (size_t)(p.iter_max + 2), st));
   DCM_LAUNCH(ctx, k_b_dist_init<R>, gb, 256, 0, st, ctx->s, ctx->iface, nb, D0, D1);
-  int budget = (int)std::ceil(8.0 * p.r_grid / p.h) + 8;
-  budget = std::min(budget + (budget & 1), p.iter_max + (p.iter_max & 1));
-  unsigned gs = (unsigned)std::min<int64_t>((nb + 255) / 256, 152 * 8);
-  R* buf[2] = {D0, D1};
-  for (int it = 0; it < budget; ++it)
-    DCM_LAUNCH(ctx, k_b_dist_sweep<R>, gs, 256, 0, st, buf[it & 1], buf[(it + 1) & 1], nb, b->geom, b->rep_of_box,
-               (R)p.h, (R)p.r_grid, ctx->flags, it);
+  // every sweep in one cooperative launch, until one changes nothing or the
+  // even budget iter_max (rounded up) runs out
+  const int budget = p.iter_max + (p.iter_max & 1);
+  {
+    auto kern = k_b_dist_coop<R>;
+    int per_sm = 0, sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess || per_sm < 1)
+      return set_error(ctx, DCM_ERR_CUDA, "batch distance sweeps: occupancy query failed");
+    const unsigned grid =
+        (unsigned)std::min<int64_t>((int64_t)std::min(per_sm, 4) * sms, std::max<int64_t>((nb + 255) / 256, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->coop_sync, 0, 4 * sizeof(uint32_t), st));
+    ++ctx->launches;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, D0, D1, nb, (const RepGeom*)b->geom, (const uint16_t*)b->rep_of_box,
+                                       (R)p.h, (R)p.r_grid, ctx->flags, budget, ctx->coop_sync, (int64_t)2000000000,
+                                       ctx->status);
+    if (e != cudaSuccess) return set_error(ctx, DCM_ERR_CUDA, "batch distance sweeps: %s", cudaGetErrorString(e));
+  }
   DCM_LAUNCH(ctx, k_b_dist_finish, 1, 1, 0, st, ctx->flags, budget, ctx->status);
   stage_end(ctx, DCM_STAGE_DISTANCE, st);
   stage_begin(ctx, DCM_STAGE_CUTOFFS, st);
@@ -389,7 +424,7 @@ extern "C" void dcm_batch_destroy(dcm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   dcm_ctx* c = &b->base;
-  void* dev[] = {c->status, c->slot,  c->cell,  c->perm,   c->cell_start, c->cell_count, c->scan_state,
+  void* dev[] = {c->status, c->coop_sync, c->slot,  c->cell,  c->perm,   c->cell_start, c->cell_count, c->scan_state,
                  c->box_count, c->g,   c->g_tmp, c->s,      c->iface,      c->D[0],       c->D[1],
                  c->flags,  c->red,   c->red_tmp, c->totals, b->geom,       b->rep_of_particle, b->rep_of_box,
                  b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart,
@@ -493,6 +528,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
     if (ok && cudaMalloc(ptr, (size_t)(bytes > 0 ? bytes : 16)) != cudaSuccess) ok = false;
   };
   alloc((void**)&c->status, 16);
+  alloc((void**)&c->coop_sync, 16);
   alloc((void**)&c->slot, 4 * nm);
   alloc((void**)&c->cell, 4 * nm);
   alloc((void**)&c->perm, 4 * nm);

@@ -351,11 +351,18 @@ __device__ __forceinline__ R b_godunov3(R a0, R a1, R a2, R h) {
 }
 
 // Jacobi update of box b from Din into Dout; true if its value changed.
-template <typename R>
-__device__ __forceinline__ bool b_dist_update(int64_t b, const R* __restrict__ Din, R* __restrict__ Dout,
-                                              const RepGeom* __restrict__ geom, const uint16_t* __restrict__ rep, R h,
-                                              R r_grid) {
-  R cur = Din[b];
+// COH: the iterates read through L2 (__ldcg), for kernels whose blocks read
+// what other blocks wrote earlier in the same launch (behind a grid barrier).
+template <typename R, bool COH>
+__device__ __forceinline__ R b_dld(const R* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
+template <typename R, bool COH = false>
+__device__ __forceinline__ bool b_dist_update(int64_t b, const R* Din, R* Dout, const RepGeom* __restrict__ geom,
+                                              const uint16_t* __restrict__ rep, R h, R r_grid) {
+  R cur = b_dld<R, COH>(Din + b);
   if (cur == (R)0) return false;
   const RepGeom& G = geom[rep[b]];
   int64_t lb = b - G.b0;
@@ -366,9 +373,9 @@ __device__ __forceinline__ bool b_dist_update(int64_t b, const R* __restrict__ D
   int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
   int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
   int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
-  R a0 = fmin(D[row + xm], D[row + xp]);
-  R a1 = fmin(D[x + nx * (ym + (int64_t)ny * z)], D[x + nx * (yp + (int64_t)ny * z)]);
-  R a2 = fmin(D[x + nx * (y + (int64_t)ny * zm)], D[x + nx * (y + (int64_t)ny * zp)]);
+  R a0 = fmin(b_dld<R, COH>(D + row + xm), b_dld<R, COH>(D + row + xp));
+  R a1 = fmin(b_dld<R, COH>(D + x + nx * (ym + (int64_t)ny * z)), b_dld<R, COH>(D + x + nx * (yp + (int64_t)ny * z)));
+  R a2 = fmin(b_dld<R, COH>(D + x + nx * (y + (int64_t)ny * zm)), b_dld<R, COH>(D + x + nx * (y + (int64_t)ny * zp)));
   R d = b_godunov3<R>(a0, a1, a2, h);
   R out = cur;
   bool changed = false;

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kPBlock, (p_blocks<PART, R, TYPED>())) k_b_ste
         bool changed = false;
         for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < a.nbox; k0 += gs) {
           const int64_t k = k0 + threadIdx.x;
-          if (k < a.nbox) changed |= b_dist_update<R>(k, Din, Dout, a.geom, a.rep_b, a.h, a.r_grid);
+          if (k < a.nbox) changed |= b_dist_update<R, true>(k, Din, Dout, a.geom, a.rep_b, a.h, a.r_grid);
         }
         if (__any_sync(0xffffffffu, changed) && (threadIdx.x & 31) == 0) a.flags[it] = 1;
         PSYNC();
@@ -503,8 +503,7 @@ int b_persistent_step(dcm_batch* b, dcm_state* s, R hdt, R dt, bool drift, bool 
   a.w = p.smooth_w;
   a.fixed_thr = p.threshold;
   a.own_boxes = (p.h != p.l || p.lx != p.l) ? 1 : 0;
-  int sweeps = (int)std::ceil(8.0 * p.r_grid / p.h) + 8;
-  a.sweeps = std::min(sweeps + (sweeps & 1), p.iter_max + (p.iter_max & 1));
+  a.sweeps = p.iter_max + (p.iter_max & 1);  // the sweep loop leaves once a sweep changes nothing
   a.h = (R)p.h;
   a.ih = (R)(1.0 / p.h);
   a.r_grid = (R)p.r_grid;

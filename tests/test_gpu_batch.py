@@ -212,7 +212,7 @@ def test_persistent_plan_equals_per_stage_plan(D, replicas, prec, lx):
         assert np.array_equal(x, y)
     assert np.allclose(tha, ths, rtol=1e-12, atol=1e-9)
     assert la == 2 * nsteps
-    assert ls > 10 * nsteps
+    assert ls > 5 * nsteps
 
 
 @pytest.mark.parametrize("persistent", [True, False])
