@@ -145,6 +145,7 @@ def test_batch_fp64_tracks_oracle(D, replicas, lx):
     b, st = batch_state(D, replicas, D.DCM_PREC_FP64, lx)
     D.dcm_batch_step_init(b, st)
     D.dcm_batch_step(b, st, DT, 3)
+    assert D.dcm_batch_status(b) == D.DCM_OK
     th = st.thermo.cpu().numpy().reshape(-1, 4)
     for r, slab in enumerate(replicas):
         p = O.Params(box=slab.box, recompute_every=K)
@@ -168,6 +169,7 @@ def test_batch_thermo_over_several_chunks(D):
     b, st = batch_state(D, reps, D.DCM_PREC_FP64)
     D.dcm_batch_step_init(b, st)
     D.dcm_batch_step(b, st, DT, 3)
+    assert D.dcm_batch_status(b) == D.DCM_OK
     th = st.thermo.cpu().numpy().reshape(-1, 4)
     for r, slab in enumerate(reps):
         _, th1 = single_run(D, slab, D.DCM_PREC_FP64, 3)

@@ -751,6 +751,7 @@ def test_step_verlet_lists_mixed_close_to_cells(D, slab_1935):
     D.dcm_step_init(ctx, st)
     for _ in range(12):
         D.dcm_step(ctx, st, 0.005, 1)
+    assert D.dcm_status(ctx) == D.DCM_OK
     th_c = st.thermo.cpu().numpy()
     assert th_l[-1, 0] == pytest.approx(th_c[0], rel=1e-4)
     assert th_l[-1, 2] == pytest.approx(th_c[2], rel=1e-4)
@@ -793,6 +794,7 @@ def test_step_lists_batched_call_equals_single_calls(D, slab_1935, prec):
                   D.to_real4(torch.from_numpy(slab_1935.vel), None, real_of(D, P)))
     D.dcm_step_init(ctx2, st2)
     D.dcm_step(ctx2, st2, 0.005, 12)
+    assert D.dcm_status(ctx2) == D.DCM_OK
     assert np.array_equal(th1[-1], st2.thermo.cpu().numpy())
     assert torch.equal(st1.current()[0], st2.current()[0]) and torch.equal(st1.current()[1], st2.current()[1])
 
@@ -1297,6 +1299,7 @@ def test_degenerate_pipelines(D, slab_1935, case):
     ctx = make_ctx(D, box, n, D.DCM_PREC_FP64, **kw)
     st = D.State(ctx, pos4_of(D, pos, None, D.DCM_PREC_FP64), D.to_real4(torch.from_numpy(vel), None, torch.float64))
     D.dcm_step_init(ctx, st)
+    assert D.dcm_status(ctx) == D.DCM_OK
     p_, v_, rc, ids = st.current()
     p_ = p_.cpu().numpy()[:, :3]
     rcn = rc.cpu().numpy()
