@@ -672,7 +672,7 @@ def run_gb300(args):
         ms64 = e0.elapsed_time(e1)
         u64, t64 = aggregate(dist, float(n) * k64 * K_RECOMPUTE, ms64 / 1000.0)
         fp64 = {"value": u64 / t64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                "speedup_mixed_over_fp64": value / (u64 / t64)}
+                "speedup_mixed_over_fp64": value / (u64 / t64), "device_status": D.dcm_status(c64)}
         del s64
         c64.close()
         torch.cuda.empty_cache()
@@ -782,6 +782,7 @@ def run_gb300(args):
                    "instr_per_pair": l_ipp,
                    "list_builds": int(lst["lists"][1]), "build_avg_ms": lst["lists"][0] / max(lst["lists"][1], 1),
                    "stage_ms_per_step": {k: v[0] / kl for k, v in lst.items()}, "pairs_last": pl,
+                   "device_status": D.dcm_status(cl),
                    "note": ("half lists kept by the larger-cutoff particle, each pair evaluated once and scattered "
                             "(atomics) to the other particle where its cutoff reaches" if newton3 else
                             "neighbour lists of radius rc_i + skin") +
