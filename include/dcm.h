@@ -67,7 +67,7 @@ enum dcm_status_code {
   DCM_ERR_NOT_CONVERGED = 4, /* fast sweeping did not converge within iter_max */
   DCM_ERR_CAPACITY = 5,      /* n > n_max, or a density value range beyond the histogram */
   DCM_ERR_NOMEM = 6,         /* scratch allocation failed in dcm_create */
-  DCM_ERR_TIMEOUT = 7        /* a device-side wait ran past its budget (persistent batched step, cell-count scan) */
+  DCM_ERR_TIMEOUT = 7        /* a device-side wait ran past its budget (a grid barrier, the cell-count scan) */
 };
 
 /* Cell-list force kernels (both walk the same culled cell rows and accept the
@@ -346,9 +346,10 @@ int dcm_step_init(dcm_ctx* ctx, dcm_state* st, int64_t n, dcm_stream_t stream);
  * Masses are 1.  thermo and the per-particle energies (w of st->force) are
  * those of the call's last timestep; on the cell lists in the mixed form the
  * timesteps before it sum forces only (energy and virial are not evaluated
- * where nothing reads them).  The distance sweeps run a fixed budget of
- * iterations with a device-side convergence flag; non-convergence is
- * reported by dcm_status().
+ * where nothing reads them).  The distance sweeps run in one cooperative
+ * launch (bounded grid barriers between sweeps) until a sweep changes
+ * nothing, at most params.iter_max sweeps; non-convergence, or a barrier wait
+ * that ran out (DCM_ERR_TIMEOUT), is reported by dcm_status().
  * With params.skin == 0 the call never waits on the host.  With skin > 0
  * (Verlet lists) each step reads the largest displacement back to the host
  * to decide whether to rebin and rebuild the lists (so it synchronises the
@@ -415,8 +416,8 @@ int dcm_batch_offsets(const dcm_batch* b, int64_t* offsets);
 int dcm_batch_set_force_block(dcm_batch* b, int32_t threads);
 
 /* As dcm_step_init / dcm_step for all replicas at once (asynchronous; the
- * distance sweeps run a fixed budget and report non-convergence through
- * dcm_batch_status).  In the persistent plan a barrier wait that runs past
+ * distance sweeps run until a sweep changes nothing, at most
+ * params.iter_max, and report non-convergence through dcm_batch_status).  In the persistent plan a barrier wait that runs past
  * the wait budget (dcm_batch_set_wait_budget) ends the launch and records
  * DCM_ERR_TIMEOUT in the batch's device status; the step's results are then
  * undefined. */

@@ -9,8 +9,9 @@
 //     replicas (this file).
 // The whole K-step recomputation period can be captured once in a CUDA graph
 // and replayed (dcm_batch_capture / dcm_batch_replay): every size is fixed,
-// the distance sweeps run a fixed budget with device-side early exit, and no
-// call inside a step waits on the host.
+// the distance sweeps run inside one cooperative launch until a sweep
+// changes nothing (at most iter_max), and no call inside a step waits on the
+// host.
 #include <algorithm>
 #include <climits>
 #include <cstdarg>
