@@ -507,7 +507,8 @@ __device__ __forceinline__ void walk_rows(const typename RT<R>::R4* __restrict__
       // segments come out empty and every index stays in range
       ulo = min(max(ulo, cx - Hx), cx + Hx + 1);
       uhi = max(min(uhi, cx + Hx), cx - Hx - 1);
-      const int64_t row = (int64_t)nx * (wy + (int64_t)ny * wz);
+      // 32-bit: parameter validation keeps the cell count below 2^31 - 1
+      const int row = nx * (wy + ny * wz);
       // segment u < 0: image -L (shift j)
       if (ulo < 0) {
         int a1 = min(uhi, -1);
