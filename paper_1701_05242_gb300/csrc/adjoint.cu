@@ -33,6 +33,7 @@
 #include <algorithm>
 
 #include "forces_core.cuh"
+#include "tile_order.cuh"
 
 namespace dcm {
 
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(adj_block<R>()) k_adjoint(int64_t n, const typ
                                                             double* __restrict__ part, int64_t nwarp, BlockGrid bg,
                                                             const int32_t* __restrict__ bmax,
                                                             const int32_t* __restrict__ order) {
-  const int64_t i = (int64_t)__ldg(order + blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)(order ? __ldg(order + blockIdx.x) : (int32_t)blockIdx.x) * blockDim.x + threadIdx.x;
   const int np = a.ntypes * a.ntypes;
   AdjAcc<R> c;
   for (int p = 0; p < 16; ++p) c.de[p] = c.ds[p] = (R)0;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kAdjX2Block) k_adjoint_x2(int64_t n, const flo
                                                             int64_t nwarp, BlockGrid bg,
                                                             const int32_t* __restrict__ bmax,
                                                             const int32_t* __restrict__ order) {
-  const int64_t i = (int64_t)__ldg(order + blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)(order ? __ldg(order + blockIdx.x) : (int32_t)blockIdx.x) * blockDim.x + threadIdx.x;
   const int nt = a.ntypes;
   AdjAcc2 c;
   int tk = 0;
@@ -563,49 +564,19 @@ __global__ void __launch_bounds__(kAdjX2Block) k_adjoint_x2(int64_t n, const flo
   }
 }
 
-// Launch order of the adjoint's tiles (a tile: the TB particles of one block).
-// A tile costs about as much as its widest walk, the largest reverse reach
-// among its particles, and the costly tiles form bands near the interfaces,
-// one of them close to the end of the cell order.  Blocks start roughly in
-// launch order, so the tiles are launched by decreasing largest reach (a
-// counting sort over kAdjTileBins bins of reach / rc_max): the costly tiles
-// start in the first wave and the launch ends on cheap ones.  A tile keeps its
-// particles and its partial-sum slots wherever it runs, so the results do not
-// depend on the order (ties within a bin are placed by atomics).
-template <typename R, int TB>
-__global__ void __launch_bounds__(TB) k_adj_tile_key(int64_t n, const typename RT<R>::R4* __restrict__ pos,
-                                                     const R* __restrict__ rc, R rc_max, BlockGrid bg,
-                                                     const int32_t* __restrict__ bmax, int32_t* __restrict__ key,
-                                                     int32_t* __restrict__ hist) {
-  const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+// Cost key of the adjoint's tiles (tile_order.cuh): the largest reverse reach
+// among a tile's particles, the radius of its widest walk.
+template <typename R>
+__global__ void k_adj_tile_key(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
+                               R rc_max, BlockGrid bg, const int32_t* __restrict__ bmax, int32_t* __restrict__ key,
+                               int32_t* __restrict__ cnt, int64_t nchunk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float r = 0.f;
   if (i < n) {
     const auto p = ldg4(pos + i);
     r = (float)reverse_reach<R>(p, clamp_cutoff<R>(rc[i], rc_max), rc_max, bg, bmax);
   }
-  for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-  __shared__ float wmax[TB / 32];
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = r;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float m = wmax[0];
-    for (int w = 1; w < TB / 32; ++w) m = fmaxf(m, wmax[w]);
-    int b = (int)(m / (float)rc_max * (float)kAdjTileBins);
-    b = b < 0 ? 0 : (b > kAdjTileBins - 1 ? kAdjTileBins - 1 : b);
-    const int k = kAdjTileBins - 1 - b;  // widest first
-    key[blockIdx.x] = k;
-    atomicAdd(hist + k, 1);
-  }
-}
-
-__global__ void k_adj_tile_place(int64_t ntile, const int32_t* __restrict__ key, const int32_t* __restrict__ hist,
-                                 int32_t* __restrict__ cursor, int32_t* __restrict__ order) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntile) return;
-  const int k = key[t];
-  int base = 0;
-  for (int b = 0; b < k; ++b) base += __ldg(hist + b);
-  order[base + atomicAdd(cursor + k, 1)] = (int32_t)t;
+  tile_key_of_block(r, (float)rc_max, key, cnt, nchunk);
 }
 
 // Per-type gradients from per-type-pair sums: eps_ab = sqrt(eps_a eps_b),
@@ -660,36 +631,32 @@ int lj_adjoint(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* 
   }
   DCM_CUDA_TRY(ctx, cudaMemsetAsync(ctx->blk_max, 0, sizeof(int32_t) * ctx->nblk, st));
   DCM_LAUNCH(ctx, k_block_max<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, pos, rc, a.rc_max, bg, ctx->blk_max);
-  // tile order: [order: ntile][key: ntile][bin counts][bin cursors]
+  // the packed loop (FP32, one or two types), else the scalar loop
   const bool x2 = sizeof(R) == 4 && nt <= 2;
   const int tb = x2 ? kAdjX2Block : kBlock;
-  const int64_t ntile = (n + tb - 1) / tb;
-  int32_t* order = ctx->adj_tiles;
-  int32_t* key = order + ntile;
-  int32_t* hist = key + ntile;
-  DCM_CUDA_TRY(ctx, cudaMemsetAsync(hist, 0, sizeof(int32_t) * 2 * kAdjTileBins, st));
-  if (tb == 64)
-    DCM_LAUNCH(ctx, (k_adj_tile_key<R, 64>), (unsigned)ntile, 64, 0, st, n, pos, rc, a.rc_max, bg,
-               (const int32_t*)ctx->blk_max, key, hist);
-  else
-    DCM_LAUNCH(ctx, (k_adj_tile_key<R, 32>), (unsigned)ntile, 32, 0, st, n, pos, rc, a.rc_max, bg,
-               (const int32_t*)ctx->blk_max, key, hist);
-  DCM_LAUNCH(ctx, k_adj_tile_place, (unsigned)((ntile + 255) / 256), 256, 0, st, ntile, key, hist,
-             hist + kAdjTileBins, order);
-  bool packed = false;
-  if constexpr (sizeof(R) == 4) {
-    if (nt <= 2) {  // the packed loop (FP32, one or two types)
-      const int64_t nb2 = (n + kAdjX2Block - 1) / kAdjX2Block;
-      static_assert(kAdjX2Block == adj_block<float>(), "the partials layout assumes equal blocks");
-      DCM_LAUNCH(ctx, k_adjoint_x2, (unsigned)nb2, kAdjX2Block, 0, st, n, pos, rc, cell_start, a, A,
-                 (float)(0.5 * dlde), G, part, nwarp, bg, (const int32_t*)ctx->blk_max, (const int32_t*)order);
-      packed = true;
-    }
+  const void* kern = x2 ? (const void*)k_adjoint_x2
+                        : (lj_general(t) ? (const void*)k_adjoint<R, true> : (const void*)k_adjoint<R, false>);
+  static_assert(kAdjX2Block == adj_block<float>(), "the partials layout assumes equal blocks");
+  // launch order of the tiles, the widest walks first, where that pays
+  const TileOrder to = tile_order_layout(ctx->tile_scratch, (n + tb - 1) / tb);
+  const int32_t* order = nullptr;
+  if (tile_order_pays(kern, tb, to.ntile)) {
+    int r0 = tile_order_begin(ctx, to, st);
+    if (r0) return r0;
+    DCM_LAUNCH(ctx, k_adj_tile_key<R>, (unsigned)to.ntile, tb, 0, st, n, pos, rc, a.rc_max, bg,
+               (const int32_t*)ctx->blk_max, to.key, to.cnt, to.nchunk);
+    if ((r0 = tile_order_finish(ctx, to, st))) return r0;
+    order = to.order;
   }
-  if (!packed) {
-    auto kern = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
-    DCM_LAUNCH(ctx, kern, (unsigned)nblk, kBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
-               nwarp, bg, (const int32_t*)ctx->blk_max, (const int32_t*)order);
+  if constexpr (sizeof(R) == 4) {
+    if (x2)
+      DCM_LAUNCH(ctx, k_adjoint_x2, (unsigned)to.ntile, kAdjX2Block, 0, st, n, pos, rc, cell_start, a, A,
+                 (float)(0.5 * dlde), G, part, nwarp, bg, (const int32_t*)ctx->blk_max, order);
+  }
+  if (!x2) {
+    auto k = lj_general(t) ? k_adjoint<R, true> : k_adjoint<R, false>;
+    DCM_LAUNCH(ctx, k, (unsigned)to.ntile, kBlock, 0, st, n, pos, rc, cell_start, a, A, (R)(0.5 * dlde), G, part,
+               nwarp, bg, (const int32_t*)ctx->blk_max, order);
   }
   int r = check_launch(ctx, "lj_adjoint");
   if (r || !want) return r;

@@ -269,7 +269,7 @@ struct ScratchPlan {
            2 * rsize * nbox + 4 * flags + 4 * (int64_t)kHistCap + 4 * 8 + 8 * 3 * red_cap + 8 * 8 + 8 * 8 * 256 +
            8 * 32 * red_cap + 8 * 48 + (skin > 0 ? 8 * n_max + 8 * (n_max / 32 + 16) + 4 * rsize * n_max + 32 : 0) +
            (min_component > 0 ? 9 * nbox + 4 * 80 : 0) + 13 * nbox + 4 * (flags + 2) + 4 * nblk +
-           4 * adj_tile_ints(n_max) +
+           4 * tile_scratch_ints(n_max) +
            (segmentation ? 6 * rsize * nbox + 32 * ms_outer + 16 + 4 * (ms_outer + 2) : 0);
   }
 };
@@ -317,7 +317,7 @@ extern "C" void dcm_destroy(dcm_ctx* ctx) {
                  ctx->D[1], ctx->flags, ctx->hist, ctx->thr, ctx->red, ctx->totals, ctx->D[0], ctx->red_tmp, ctx->adj_part, ctx->adj_pairs,
                  ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list, ctx->xbuild, ctx->dmax, ctx->lflag,
                  ctx->cc_lab, ctx->cc_cnt, ctx->cc_flags, ctx->cc_s0, ctx->dq[0], ctx->dq[1], ctx->dqlen,
-                 ctx->dstamp, ctx->dfixed, ctx->blk_max, ctx->adj_tiles, ctx->ms_u, ctx->ms_ub, ctx->ms_p, ctx->ms_w,
+                 ctx->dstamp, ctx->dfixed, ctx->blk_max, ctx->tile_scratch, ctx->ms_u, ctx->ms_ub, ctx->ms_p, ctx->ms_w,
                  ctx->ms_sums, ctx->ms_c, ctx->ms_flags};
   for (void* q : dev)
     if (q) cudaFree(q);
@@ -413,7 +413,7 @@ extern "C" int dcm_create(const dcm_params* p, dcm_ctx** out) {
   for (int d = 0; d < 3; ++d) ctx->nblk3[d] = (int)adjoint_blocks(p, d);  // as counted in the plan
   ctx->nblk = s.nblk;
   alloc((void**)&ctx->blk_max, 4 * s.nblk);
-  alloc((void**)&ctx->adj_tiles, 4 * adj_tile_ints(s.n_max));
+  alloc((void**)&ctx->tile_scratch, 4 * tile_scratch_ints(s.n_max));
   if (ok && cudaMallocHost((void**)&ctx->host_status, 16) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();

@@ -21,6 +21,7 @@
 
 #include "batch_core.cuh"
 #include "grid_sync.cuh"
+#include "tile_order.cuh"
 
 namespace dcm {
 
@@ -148,9 +149,18 @@ template <typename R, bool TYPED, bool X2, Accum M, bool EW = true>
 __global__ void k_b_forces(int64_t n, const typename RT<R>::R4* __restrict__ pos, const R* __restrict__ rc,
                            const int32_t* __restrict__ start, ForceArgs<R> a, const RepGeom* __restrict__ geom,
                            const uint16_t* __restrict__ rep, typename RT<R>::R4* __restrict__ force,
-                           R* __restrict__ w_i, int32_t* __restrict__ np_i) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                           R* __restrict__ w_i, int32_t* __restrict__ np_i, const int32_t* __restrict__ order) {
+  const int64_t i = (int64_t)(order ? __ldg(order + blockIdx.x) : (int32_t)blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) b_force<R, TYPED, X2, M, true, EW>(i, pos, rc, start, a, geom, rep, force, w_i, np_i);
+}
+
+// Cost key of the force tiles (tile_order.cuh): the largest cutoff among a
+// tile's particles.
+template <typename R>
+__global__ void k_b_tile_key(int64_t n, const R* __restrict__ rc, R rc_max, int32_t* __restrict__ key,
+                             int32_t* __restrict__ cnt, int64_t nchunk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  tile_key_of_block(i < n ? (float)clamp_cutoff<R>(rc[i], rc_max) : 0.f, (float)rc_max, key, cnt, nchunk);
 }
 
 template <typename R>
@@ -284,7 +294,7 @@ int batch_accumulation(const dcm_batch* b) {
 template <typename R>
 static auto b_force_kernel(bool typed, int ntypes, int acc, bool energies) {
   using K = void (*)(int64_t, const typename RT<R>::R4*, const R*, const int32_t*, ForceArgs<R>, const RepGeom*,
-                     const uint16_t*, typename RT<R>::R4*, R*, int32_t*);
+                     const uint16_t*, typename RT<R>::R4*, R*, int32_t*, const int32_t*);
   if constexpr (sizeof(R) == 8) {
     return typed ? (K)k_b_forces<R, true, false, Accum::kPlain> : (K)k_b_forces<R, false, false, Accum::kPlain>;
   } else {
@@ -317,8 +327,17 @@ static int b_forces_thermo(dcm_batch* b, const typename RT<R>::R4* pos, const R*
     // their own eps and sigma; the scalar loop otherwise
     auto kern = b_force_kernel<R>(lj_general(t), t.ntypes, batch_accumulation(b), energies);
     stage_begin(ctx, DCM_STAGE_FORCES, st);
-    DCM_LAUNCH(ctx, kern, (unsigned)((n + bs - 1) / bs), bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
-               b->rep_of_particle, force, (R*)b->w_i, b->np_i);
+    const TileOrder to = tile_order_layout(ctx->tile_scratch, (n + bs - 1) / bs);
+    const int32_t* order = nullptr;  // the widest tiles first, where that pays
+    if (tile_order_pays((const void*)kern, bs, to.ntile)) {
+      int r = tile_order_begin(ctx, to, st);
+      if (r) return r;
+      DCM_LAUNCH(ctx, k_b_tile_key<R>, (unsigned)to.ntile, bs, 0, st, n, rc, a.rc_max, to.key, to.cnt, to.nchunk);
+      if ((r = tile_order_finish(ctx, to, st))) return r;
+      order = to.order;
+    }
+    DCM_LAUNCH(ctx, kern, (unsigned)to.ntile, bs, 0, st, n, pos, rc, ctx->cell_start, a, b->geom,
+               b->rep_of_particle, force, (R*)b->w_i, b->np_i, order);
     stage_end(ctx, DCM_STAGE_FORCES, st);
     stage_begin(ctx, DCM_STAGE_KICK, st);
     DCM_LAUNCH(ctx, k_b_kick<R>, (unsigned)((n + 255) / 256), 256, 0, st, n, vel, kick ? force : nullptr, half_dt,
@@ -429,7 +448,7 @@ extern "C" void dcm_batch_destroy(dcm_batch* b) {
                  c->box_count, c->g,   c->g_tmp, c->s,      c->iface,      c->D[0],       c->D[1],
                  c->flags,  c->red,   c->red_tmp, c->totals, b->geom,       b->rep_of_particle, b->rep_of_box,
                  b->thr,    b->hist,  b->w_i,   b->ke_i,   b->np_i, b->chunk, b->chunk0, b->tpart,
-                 b->tiles,  b->sync,  b->scan_blk, b->pacc};
+                 b->tiles,  b->sync,  b->scan_blk, b->pacc, c->tile_scratch};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (c->host_status) cudaFreeHost(c->host_status);
@@ -547,6 +566,7 @@ extern "C" int dcm_batch_create(const dcm_params* p, int32_t R, const double* bo
   alloc((void**)&c->red, 8 * 3 * c->red_cap);
   alloc((void**)&c->red_tmp, 8 * 8 * 256);
   alloc((void**)&c->totals, 8 * 8);
+  alloc((void**)&c->tile_scratch, 4 * tile_scratch_ints(nm));
   alloc((void**)&b->geom, (int64_t)sizeof(RepGeom) * R);
   alloc((void**)&b->rep_of_particle, 2 * nm);
   alloc((void**)&b->rep_of_box, 2 * nbtot);

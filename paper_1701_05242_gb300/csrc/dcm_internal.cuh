@@ -116,7 +116,7 @@ struct dcm_ctx {
   int32_t* host_status;     // pinned host mirror
   int64_t red_cap;          // number of partial slots in red (per quantity)
   int32_t* blk_max;         // nblk: largest cutoff (float bits) per adjoint block
-  int32_t* adj_tiles;       // adj_tile_ints(n_max): the adjoint's tile order, tile keys, bin counts
+  int32_t* tile_scratch;    // tile_scratch_ints(n_max): launch order of the force and adjoint tiles
   int nblk3[3];             // adjoint blocks per dimension (edge >= 1.001 rc_max)
   int64_t nblk;
   int64_t scan_cap;
@@ -164,10 +164,16 @@ constexpr int kHistCap = 1 << 20;
 constexpr int kScanBlock = 512;        // threads of the scan kernel (two blocks per SM at its registers)
 constexpr int kScanItems = 16;         // items per thread (four 16-byte loads)
 constexpr int kScanTile = kScanBlock * kScanItems;
-// The adjoint's tile order: for each tile (a block of at least 32 particles)
-// its launch slot and its key, then two rows of bin counts.
-constexpr int kAdjTileBins = 64;
-constexpr int64_t adj_tile_ints(int64_t n_max) { return 2 * ((n_max + 31) / 32 + 1) + 2 * kAdjTileBins; }
+// Launch order of tiles (the particles of one block) by decreasing cost key
+// (tile_order.cu): a stable counting sort over kTileBins bins, chunks of
+// kTileChunk tiles.  Scratch: order[ntile], key[ntile], the bin counts of
+// every chunk [kTileBins][nchunk].
+constexpr int kTileBins = 64;
+constexpr int kTileChunk = 1024;
+constexpr int64_t tile_chunks(int64_t ntile) { return (ntile + kTileChunk - 1) / kTileChunk; }
+constexpr int64_t tile_order_ints(int64_t ntile) { return 2 * ntile + kTileBins * tile_chunks(ntile) + 1; }
+// tiles of at least 32 particles
+constexpr int64_t tile_scratch_ints(int64_t n_max) { return tile_order_ints((n_max + 31) / 32 + 1); }
 
 int set_error(dcm_ctx* ctx, int code, const char* fmt, ...);
 

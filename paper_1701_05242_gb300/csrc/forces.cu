@@ -24,20 +24,21 @@
 #include <cmath>
 
 #include "forces_core.cuh"
+#include "tile_order.cuh"
 
 namespace dcm {
 
 // Per-warp partial sums of (E, W, pairs): summed across the warp in FP64,
 // then stored as one FP64 partial per warp; no block barrier, so warps that
 // finish early do not wait.
-__device__ __forceinline__ void warp_partials3(double a, double b, int c, double* part, int64_t nslot) {
+__device__ __forceinline__ void warp_partials3(double a, double b, int c, double* part, int64_t nslot,
+                                               int64_t w) {
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
     c += __shfl_xor_sync(0xffffffffu, c, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     part[w] = a;
     part[nslot + w] = b;
     part[2 * nslot + w] = (double)c;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kForceBlock) k_forces(int64_t n, const typenam
   int np = 0;
   if (i < n)
     force[i] = force_one<R, TYPED, false, M>(pos, start, a.g, a, (int)i, ldg4(pos + i), rc[i], e_out, w_out, np);
-  if (part) warp_partials3(e_out, w_out, np, part, nwarp);
+  if (part) warp_partials3(e_out, w_out, np, part, nwarp, i >> 5);
 }
 
 // The same walk with the packed two-candidates-per-instruction pair loop
@@ -77,14 +78,15 @@ __global__ void __launch_bounds__(kX2Block, x2_min_blocks<M>()) k_forces_x2(int6
                                                                           const int32_t* __restrict__ start,
                                                                           ForceArgs<float> a,
                                                                           float4* __restrict__ force,
-                                                                          double* __restrict__ part, int64_t nwarp) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                                                          double* __restrict__ part, int64_t nwarp,
+                                                                          const int32_t* __restrict__ order) {
+  const int64_t i = (int64_t)(order ? __ldg(order + blockIdx.x) : (int32_t)blockIdx.x) * kX2Block + threadIdx.x;
   double e_out = 0, w_out = 0;
   int np = 0;
   if (i < n)
     force[i] = force_one<float, TYPED, true, M, true, EW>(pos, start, a.g, a, (int)i, __ldg(pos + i), rc[i], e_out, w_out,
                                                          np);
-  if (part) warp_partials3(e_out, w_out, np, part, nwarp);
+  if (part) warp_partials3(e_out, w_out, np, part, nwarp, i >> 5);
 }
 
 // The packed kernel serves mixed-precision runs of one or two types; the
@@ -113,22 +115,42 @@ int resolve_accumulation(const dcm_ctx* ctx) {
 
 namespace {
 
+// Cost key of the packed kernel's tiles (tile_order.cuh): the largest cutoff
+// among a tile's particles.
+__global__ void __launch_bounds__(kX2Block) k_force_tile_key(int64_t n, const float* __restrict__ rc, float rc_max,
+                                                             int32_t* __restrict__ key, int32_t* __restrict__ cnt,
+                                                             int64_t nchunk) {
+  const int64_t i = (int64_t)blockIdx.x * kX2Block + threadIdx.x;
+  tile_key_of_block(i < n ? clamp_cutoff<float>(__ldg(rc + i), rc_max) : 0.f, rc_max, key, cnt, nchunk);
+}
+
 template <Accum M>
 void launch_x2(dcm_ctx* ctx, bool typed, bool ew, int64_t n, const float4* pos, const float* rc,
                const int32_t* cell_start, const ForceArgs<float>& a, float4* force, double* part, int64_t nwarp,
                cudaStream_t st) {
   const unsigned nblk = (unsigned)((n + kX2Block - 1) / kX2Block);
+  // launch order of the tiles, the widest walks first, where the launch is
+  // short enough for that to pay
+  const int32_t* order = nullptr;
+  if (tile_order_pays((const void*)k_forces_x2<false, M, false>, kX2Block, nblk)) {
+    const TileOrder to = tile_order_layout(ctx->tile_scratch, nblk);
+    if (tile_order_begin(ctx, to, st)) return;
+    DCM_LAUNCH(ctx, k_force_tile_key, nblk, kX2Block, 0, st, n, rc, a.rc_max, to.key, to.cnt, to.nchunk);
+    if (tile_order_finish(ctx, to, st)) return;
+    order = to.order;
+  }
   if (typed && ew)
-    DCM_LAUNCH(ctx, (k_forces_x2<true, M, true>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part, nwarp);
+    DCM_LAUNCH(ctx, (k_forces_x2<true, M, true>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part, nwarp,
+               order);
   else if (typed)
     DCM_LAUNCH(ctx, (k_forces_x2<true, M, false>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
-               nwarp);
+               nwarp, order);
   else if (ew)
     DCM_LAUNCH(ctx, (k_forces_x2<false, M, true>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
-               nwarp);
+               nwarp, order);
   else
     DCM_LAUNCH(ctx, (k_forces_x2<false, M, false>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
-               nwarp);
+               nwarp, order);
 }
 
 template <typename R, Accum M>
