@@ -1,6 +1,9 @@
 // Stable counting sort of tiles by their cost bin (see tile_order.cuh).
 #include "tile_order.cuh"
 
+#include <mutex>
+#include <vector>
+
 namespace dcm {
 
 namespace {
@@ -64,12 +67,37 @@ __global__ void __launch_bounds__(kTileChunk) k_tile_place(int64_t ntile, const 
 
 }  // namespace
 
+// Resident blocks of (kernel, threads) on the current device, remembered per
+// device (the query is made once per kernel, not once per launch).
+static int64_t resident_blocks(const void* kernel, int threads) {
+  struct Entry {
+    const void* kernel;
+    int threads, dev;
+    int64_t blocks;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.kernel == kernel && e.threads == threads && e.dev == dev) return e.blocks;
+  int sms = 0, nb = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess) {
+    cudaGetLastError();  // a failed query only turns the order off; it is not a launch error
+    return 0;
+  }
+  cache.push_back(Entry{kernel, threads, dev, (int64_t)nb * sms});
+  return (int64_t)nb * sms;
+}
+
 bool tile_order_pays(const void* kernel, int threads, int64_t ntile) {
-  int dev = 0, sms = 0, nb = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess)
-    return false;
-  return nb > 0 && ntile <= (int64_t)kTileOrderWaves * nb * sms;
+  const int64_t r = resident_blocks(kernel, threads);
+  return r > 0 && ntile <= (int64_t)kTileOrderWaves * r;
 }
 
 int tile_order_begin(dcm_ctx* ctx, const TileOrder& t, cudaStream_t st) {
