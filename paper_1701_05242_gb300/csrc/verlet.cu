@@ -601,6 +601,20 @@ __global__ void k_wrap_count(int64_t n, typename RT<R>::R4* __restrict__ pos, Gr
 // contributions to j (and i's own total, since other threads add to it) are
 // added with atomics into the force array, which is cleared first; the
 // order of those additions varies from run to run.
+// Atomic add of (x, y, z, w) to a force record: one 16-byte vector atomic in
+// FP32 (sm_90 and later), four scalar ones in FP64.
+template <typename R>
+__device__ __forceinline__ void add_force4(typename RT<R>::R4* f, R x, R y, R z, R w) {
+  if constexpr (sizeof(R) == 4) {
+    atomicAdd(f, make_float4(x, y, z, w));
+  } else {
+    atomicAdd(&f->x, x);
+    atomicAdd(&f->y, y);
+    atomicAdd(&f->z, z);
+    atomicAdd(&f->w, w);
+  }
+}
+
 template <typename R, bool TYPED>
 __global__ void __launch_bounds__(128) k_forces_list_n3(int64_t n, const typename RT<R>::R4* __restrict__ pos,
                                                         const R* __restrict__ rc, const int32_t* __restrict__ nnb,
@@ -660,10 +674,7 @@ __global__ void __launch_bounds__(128) k_forces_list_n3(int64_t n, const typenam
       }
       if (acc_j) {
         const R ej = (R)0.5 * (u - ushift(tp, rcj * rcj));
-        atomicAdd(&force[j].x, -fs * dx);
-        atomicAdd(&force[j].y, -fs * dy);
-        atomicAdd(&force[j].z, -fs * dz);
-        atomicAdd(&force[j].w, ej);
+        add_force4<R>(force + j, -fs * dx, -fs * dy, -fs * dz, ej);
         E += (double)ej;
         W += 0.5 * (double)pv;
         ++np;
@@ -673,10 +684,7 @@ __global__ void __launch_bounds__(128) k_forces_list_n3(int64_t n, const typenam
     for (int k = cap - mb; k < cap; ++k) pair(__ldg(lp + (int64_t)k * 32), true);
     ei *= (R)0.5;
     E += (double)ei;
-    atomicAdd(&force[i].x, fx);
-    atomicAdd(&force[i].y, fy);
-    atomicAdd(&force[i].z, fz);
-    atomicAdd(&force[i].w, ei);
+    add_force4<R>(force + i, fx, fy, fz, ei);
   }
   if (part) {
     for (int o = 16; o > 0; o >>= 1) {
