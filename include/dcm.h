@@ -398,8 +398,10 @@ int dcm_distance_noalloc(const dcm_params* p, const uint8_t* s, const uint8_t* i
  * the stages inside each are separated by grid-wide barriers, and the force
  * stage pulls (replica, tile) work items of 32 particles from a device queue
  * (Section 2.4's dynamic tasks).  dcm_batch_set_persistent(b, 0)
- * selects the per-stage plan instead (each stage one launch over all
- * replicas).  Per-replica boxes, grids, thresholds and reductions are read
+ * selects the per-stage plan instead (each stage launched over all
+ * replicas; a force launch of at most 16 waves of blocks takes its tiles
+ * widest cutoff first, after three small launches that order them).
+ * Per-replica boxes, grids, thresholds and reductions are read
  * from a device table in both plans.  The batched form steps over
  * cell lists: p->skin must be 0, and p->min_component 0 (no bubble filter).
  * Synchronous; allocates. */
