@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kX2Block) k_force_tile_key(int64_t n, const fl
 }
 
 template <Accum M>
-void launch_x2(dcm_ctx* ctx, bool typed, bool ew, int64_t n, const float4* pos, const float* rc,
+int launch_x2(dcm_ctx* ctx, bool typed, bool ew, int64_t n, const float4* pos, const float* rc,
                const int32_t* cell_start, const ForceArgs<float>& a, float4* force, double* part, int64_t nwarp,
                cudaStream_t st) {
   const unsigned nblk = (unsigned)((n + kX2Block - 1) / kX2Block);
@@ -134,9 +134,10 @@ void launch_x2(dcm_ctx* ctx, bool typed, bool ew, int64_t n, const float4* pos, 
   const int32_t* order = nullptr;
   if (tile_order_pays((const void*)k_forces_x2<false, M, false>, kX2Block, nblk)) {
     const TileOrder to = tile_order_layout(ctx->tile_scratch, nblk);
-    if (tile_order_begin(ctx, to, st)) return;
+    int r = tile_order_begin(ctx, to, st);
+    if (r) return r;
     DCM_LAUNCH(ctx, k_force_tile_key, nblk, kX2Block, 0, st, n, rc, a.rc_max, to.key, to.cnt, to.nchunk);
-    if (tile_order_finish(ctx, to, st)) return;
+    if ((r = tile_order_finish(ctx, to, st))) return r;
     order = to.order;
   }
   if (typed && ew)
@@ -151,6 +152,7 @@ void launch_x2(dcm_ctx* ctx, bool typed, bool ew, int64_t n, const float4* pos, 
   else
     DCM_LAUNCH(ctx, (k_forces_x2<false, M, false>), nblk, kX2Block, 0, st, n, pos, rc, cell_start, a, force, part,
                nwarp, order);
+  return DCM_OK;
 }
 
 template <typename R, Accum M>
@@ -195,13 +197,13 @@ int lj_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R* r
   stage_begin(ctx, DCM_STAGE_FORCES, st);
   if constexpr (sizeof(R) == 4) {
     const int m = resolve_accumulation(ctx);
-    if (kind == DCM_FORCE_PACKED)
-      with_accum<true>(m, [&](auto tag) {
-        launch_x2<decltype(tag)::value>(ctx, typed, energies || totals, n, pos, rc, cell_start, a, force, part, nwarp,
-                                        st);
-        return 0;
+    if (kind == DCM_FORCE_PACKED) {
+      const int r = with_accum<true>(m, [&](auto tag) {
+        return launch_x2<decltype(tag)::value>(ctx, typed, energies || totals, n, pos, rc, cell_start, a, force, part,
+                                               nwarp, st);
       });
-    else
+      if (r) return r;
+    } else
       with_accum<false>(m, [&](auto tag) {
         launch_scalar<float, decltype(tag)::value>(ctx, typed, n, pos, rc, cell_start, a, force, part, nwarp, st);
         return 0;
