@@ -701,6 +701,141 @@ __global__ void __launch_bounds__(128) k_forces_list_n3(int64_t n, const typenam
   }
 }
 
+// The half-list kernel for one type with eps = sigma = 1 in FP32: two plain
+// entries per step with packed FP32x2 arithmetic for the pair terms they
+// share (with d = r_i - r_j, y = 1/r^2, s6 = y^3: r.F = 24 s6 (2 s6 - 1),
+// F_ij = (r.F) y d, U = 4 s6 (s6 - 1)), then each side masked by its own
+// cutoff: i's sums take the slots with r^2 < rc_i^2, and j's vector atomic is
+// issued for the slots with r^2 < rc_j^2.  No branch skips a slot that
+// neither cutoff reaches (its terms are masked out).  Odd and image entries
+// take the scalar step of k_forces_list_n3; per-thread energy and virial sums
+// in FP32, as in the full-list kernels.
+__global__ void __launch_bounds__(128) k_forces_list_n3_x2(int64_t n, const float4* __restrict__ pos,
+                                                           const float* __restrict__ rc,
+                                                           const int32_t* __restrict__ nnb,
+                                                           const int32_t* __restrict__ nimg,
+                                                           const int32_t* __restrict__ capw,
+                                                           const int32_t* __restrict__ offw,
+                                                           const uint32_t* __restrict__ list, ForceArgs<float> a,
+                                                           float4* __restrict__ force, double* __restrict__ part,
+                                                           int64_t nwarp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float ei = 0.f, ej = 0.f, w = 0.f;
+  int np = 0;
+  if (i < n) {
+    const float4 pi = __ldg(pos + i);
+    const float rci = clamp_cutoff<float>(__ldg(rc + i), a.rc_max), rc2 = rci * rci;
+    // U(rc) of a cutoff for the shifted energy (zero without the shift)
+    auto ushift = [&](float r2c) -> float {
+      if (!a.shift || !(r2c > 0.f)) return 0.f;
+      const float s2 = 1.f / r2c, s6 = s2 * s2 * s2;
+      return 4.f * s6 * (s6 - 1.f);
+    };
+    const float usi = ushift(rc2);
+    const uint32_t* lp = list + (int64_t)offw[i >> 5] * 32 + (threadIdx.x & 31);
+    const int m = nnb[i], cap = capw[i >> 5], mb = nimg[i];
+    float2 fx = f2(0.f, 0.f), fy = f2(0.f, 0.f), fz = f2(0.f, 0.f);
+    const float2 two = f2(2.f, 2.f), m1 = f2(-1.f, -1.f);
+    int k = 0;
+    for (; k + 1 < m; k += 2) {
+      const int j0 = (int)__ldcs(lp + (int64_t)k * 32), j1 = (int)__ldcs(lp + (int64_t)(k + 1) * 32);
+      const float4 p0 = __ldg(pos + j0), p1 = __ldg(pos + j1);
+      const float rj0 = clamp_cutoff<float>(__ldg(rc + j0), a.rc_max), rj1 = clamp_cutoff<float>(__ldg(rc + j1), a.rc_max);
+      const float2 dx = f2(pi.x - p0.x, pi.x - p1.x), dy = f2(pi.y - p0.y, pi.y - p1.y), dz = f2(pi.z - p0.z, pi.z - p1.z);
+      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float y0, y1;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(r2.x));
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y1) : "f"(r2.y));
+      float2 y = f2(y0, y1);
+      y = __ffma2_rn(y, f2(fmaf(-r2.x, y0, 1.f), fmaf(-r2.y, y1, 1.f)), y);
+      const bool ai0 = r2.x < rc2, ai1 = r2.y < rc2;
+      const bool aj0 = r2.x < rj0 * rj0, aj1 = r2.y < rj1 * rj1;
+      y = f2(ai0 || aj0 ? y.x : 0.f, ai1 || aj1 ? y.y : 0.f);
+      const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+      const float2 pv = __fmul2_rn(f2(24.f, 24.f), __fmul2_rn(s6, __ffma2_rn(s6, two, m1)));  // r . F_ij
+      const float2 fs = __fmul2_rn(pv, y);
+      const float2 u = __fmul2_rn(f2(4.f, 4.f), __fmul2_rn(s6, __fadd2_rn(s6, m1)));
+      const float2 fi = f2(ai0 ? fs.x : 0.f, ai1 ? fs.y : 0.f);
+      fx = __ffma2_rn(fi, dx, fx);
+      fy = __ffma2_rn(fi, dy, fy);
+      fz = __ffma2_rn(fi, dz, fz);
+      ei += (ai0 ? u.x - usi : 0.f) + (ai1 ? u.y - usi : 0.f);
+      w += (ai0 ? 0.5f * pv.x : 0.f) + (ai1 ? 0.5f * pv.y : 0.f);
+      np += (int)ai0 + (int)ai1;
+      if (aj0) {
+        const float e0 = 0.5f * (u.x - ushift(rj0 * rj0));
+        add_force4<float>(force + j0, -fs.x * dx.x, -fs.x * dy.x, -fs.x * dz.x, e0);
+        ej += e0;
+        w += 0.5f * pv.x;
+        ++np;
+      }
+      if (aj1) {
+        const float e1 = 0.5f * (u.y - ushift(rj1 * rj1));
+        add_force4<float>(force + j1, -fs.y * dx.y, -fs.y * dy.y, -fs.y * dz.y, e1);
+        ej += e1;
+        w += 0.5f * pv.y;
+        ++np;
+      }
+    }
+    // the odd entry and the image entries: the scalar step
+    float sfx = 0.f, sfy = 0.f, sfz = 0.f, sei = 0.f;
+    auto pair = [&](uint32_t e, bool image) {
+      const int j = (int)(e & kIdxMask);
+      const float4 pj = __ldg(pos + j);
+      float dx, dy, dz;
+      if (image)
+        image_delta<float>(e >> kIdxBits, pi, pj, a.g, dx, dy, dz);
+      else {
+        dx = pi.x - pj.x;
+        dy = pi.y - pj.y;
+        dz = pi.z - pj.z;
+      }
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float rcj = clamp_cutoff<float>(__ldg(rc + j), a.rc_max);
+      const bool acc_i = r2 < rc2, acc_j = r2 < rcj * rcj;
+      if (!acc_i && !acc_j) return;
+      const float inv = recip(r2);
+      const float s6 = inv * inv * inv;
+      const float pv = 24.f * s6 * fmaf(2.f, s6, -1.f);
+      const float fs = pv * inv;
+      const float u = 4.f * s6 * (s6 - 1.f);
+      if (acc_i) {
+        sfx = fmaf(fs, dx, sfx);
+        sfy = fmaf(fs, dy, sfy);
+        sfz = fmaf(fs, dz, sfz);
+        sei += u - usi;
+        w += 0.5f * pv;
+        ++np;
+      }
+      if (acc_j) {
+        const float e1 = 0.5f * (u - ushift(rcj * rcj));
+        add_force4<float>(force + j, -fs * dx, -fs * dy, -fs * dz, e1);
+        ej += e1;
+        w += 0.5f * pv;
+        ++np;
+      }
+    };
+    if (k < m) pair(__ldg(lp + (int64_t)k * 32), false);
+    for (int kk = cap - mb; kk < cap; ++kk) pair(__ldg(lp + (int64_t)kk * 32), true);
+    ei = 0.5f * (ei + sei);
+    add_force4<float>(force + i, (fx.x + fx.y) + sfx, (fy.x + fy.y) + sfy, (fz.x + fz.y) + sfz, ei);
+  }
+  if (part) {
+    double E = (double)ei + (double)ej, W = (double)w;
+    for (int o = 16; o > 0; o >>= 1) {
+      E += __shfl_xor_sync(0xffffffffu, E, o);
+      W += __shfl_xor_sync(0xffffffffu, W, o);
+      np += __shfl_xor_sync(0xffffffffu, np, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      const int64_t wi = i >> 5;
+      part[wi] = E;
+      part[nwarp + wi] = W;
+      part[2 * nwarp + wi] = (double)np;
+    }
+  }
+}
+
 // ---- launchers -------------------------------------------------------------------
 
 static int ensure_list_capacity(dcm_ctx* ctx, int64_t need) {
@@ -786,9 +921,19 @@ int list_forces(dcm_ctx* ctx, int64_t n, const typename RT<R>::R4* pos, const R*
   stage_begin(ctx, DCM_STAGE_FORCES, st);
   if (ctx->p.newton3) {
     DCM_CUDA_TRY(ctx, cudaMemsetAsync(force, 0, sizeof(typename RT<R>::R4) * n, st));
-    auto k3 = lj_general(t) ? k_forces_list_n3<R, true> : k_forces_list_n3<R, false>;
-    DCM_LAUNCH(ctx, k3, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->nimg, ctx->capw, ctx->offw, ctx->list,
-               a, force, part, nwarp);
+    bool packed3 = false;
+    if constexpr (sizeof(R) == 4) {
+      if (!lj_general(t)) {
+        DCM_LAUNCH(ctx, k_forces_list_n3_x2, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->nimg, ctx->capw,
+                   ctx->offw, ctx->list, a, force, part, nwarp);
+        packed3 = true;
+      }
+    }
+    if (!packed3) {
+      auto k3 = lj_general(t) ? k_forces_list_n3<R, true> : k_forces_list_n3<R, false>;
+      DCM_LAUNCH(ctx, k3, (unsigned)nblk, 128, 0, st, n, pos, rc, ctx->nnb, ctx->nimg, ctx->capw, ctx->offw,
+                 ctx->list, a, force, part, nwarp);
+    }
     stage_end(ctx, DCM_STAGE_FORCES, st);
     int r = check_launch(ctx, "list_forces");
     if (r) return r;
