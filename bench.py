@@ -776,7 +776,7 @@ def run_gb300(args):
             l_ew = lf_cnt
             l_ipp = (FLOP_PER_PAIR * l_ew + FLOP_PER_PAIR_FORCES * (lf_cnt - l_ew)) / max(lf_cnt, 1)
             rec = {"value": ul / tl, "unit": UNIT, "steps": kl, "ms_per_step": msl / kl, "skin": LIST_SKIN,
-                   "force_kernel": "k_forces_list_n3" if newton3 else "k_forces_list_x2",
+                   "force_kernel": "k_forces_list_n3_x2" if newton3 else "k_forces_list_x2",
                    "force_avg_launch_ms": lf_avg,
                    "force_frac_fp32": pl * l_ipp / (lf_avg / 1000.0) / 1e12 / peak_tinstr if lf_avg > 0 else None,
                    "instr_per_pair": l_ipp,
